@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""Benchmark of the SOR-SVD hot path on GB300 (one JSON line on stdout).
+
+A step is one whole SOR-SVD solve (Algorithm 3: Omega, q+1 power passes with
+re-orthonormalisation, CholeskyQR of both sketches, core product Q1^T A Q2,
+Jacobi SVD of the core, output assembly) on a synthetic matrix already
+resident in HBM.  Default workload: fp32 A 20000 x 10000 = U diag(1/i) V^T
+(Haar U, V of width 500) + 1e-3 N(0,1) noise, k = 100, p = 10, q = 1.
+
+``value`` is whole-job TFLOP/s with the operation count of the paper's eq.
+(C_SOR-SVD+PM) (2q+3) l C_mult + 2 l (m+n)(l+k) + 2 l^2 (m+l), C_mult = 2mn.
+``e2e`` is the same metric through the public API with the matrix in pinned
+host memory: host-to-device copy of A and device-to-host copy of U, S, V are
+inside the timed region.  Multi-GPU runs (torchrun) solve one independent
+replica per rank (the path has no exchange step): scaling is weak.
+
+``--impl reference`` times the binary64 CPU oracle on the host cores instead
+(rank 0 only), on a row-sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SOR-SVD TFLOP/s & % roofline; BF16 vs FP32 time at equal relative error"
+
+WORKLOADS = {
+    "cfg2": dict(m=20000, n=10000, k=100, p=10, q=1, dtype="f32", width=500, noise=1e-3, spectrum="poly1",
+                 desc="fp32 A 20000x10000 = U diag(1/i) V^T (Haar U, V of width 500) + 1e-3 N(0,1); "
+                      "k=100, p=10, q=1"),
+    "cfg3": dict(m=65536, n=16384, k=256, p=10, q=2, dtype="bf16", width=1024, noise=0.0, spectrum="exp64",
+                 desc="bf16 A 65536x16384 = U diag(exp(-i/64))_{i<=1024} V^T (Haar); k=256, p=10, q=2"),
+    "cfg1": dict(m=1000, n=1000, k=20, p=5, q=1, dtype="f64", width=1000, noise=0.0, spectrum="cfg1",
+                 desc="fp64 A 1000x1000, sigma_i = 1 (i<=20), 10^{-(i-20)/10}; k=20, p=5, q=1"),
+}
+
+
+def flops(m, n, k, p, q):
+    """eq. (C_SOR-SVD+PM) with C_mult = 2mn."""
+    l = k + p
+    return float((2 * q + 3) * l * 2 * m * n + 2 * l * (m + n) * (l + k) + 2 * l * l * (m + l))
+
+
+def sigma_of(w):
+    from paper_1804_00462_gb300 import inputs
+    if w["spectrum"] == "poly1":
+        return inputs.sigma_poly(w["width"])
+    if w["spectrum"] == "exp64":
+        return inputs.sigma_exp(w["width"], 64.0)
+    return inputs.sigma_cfg1(w["width"])
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return None
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        except Exception:
+            return None
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def build_input(w, seed, device):
+    import torch
+    from paper_1804_00462_gb300 import inputs
+    tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f64": torch.float32}[w["dtype"]]
+    At = inputs.spectral_torch(w["m"], w["n"], sigma_of(w), seed, device=device, noise=w["noise"], out_dtype=tdt)
+    if w["dtype"] == "f64":
+        At = At.double()
+    return At            # (n, m) contiguous = column-major A
+
+
+def traffic_from_profiles(kernel_key: str):
+    """dram bytes per launch from a committed ncu summary, if it still matches the source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    ent = d.get(kernel_key)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, ent["source"])
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except Exception:
+        return None
+    return ent["bytes_per_launch"] if h == ent.get("source_sha256_16") else None
+
+
+def run_ours(args, w, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_1804_00462_gb300 import native
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    m, n, k, p, q, dt = w["m"], w["n"], w["k"], w["p"], w["q"], w["dtype"]
+    At = build_input(w, seed=rank, device=dev)
+    A = At.T
+    od = native.out_dtype(native.dtype_code(dt))
+    U = native.colmajor_empty(m, k, od, dev)
+    S = torch.empty(k, dtype=od, device=dev)
+    V = native.colmajor_empty(n, k, od, dev)
+    ws = native.alloc_workspace(m, n, k, p, dt, 0, dev)
+    stream = torch.cuda.current_stream()
+
+    def step(seed):
+        native.run(A, k, p, q, seed=seed, dtype=dt, workspace=ws, out=(U, S, V))
+
+    for i in range(args.warmup):
+        step(i)
+    st, info = native.get_status(ws)
+    if st != 0:
+        raise RuntimeError(f"device status after warm-up: {native.status_string(st)}")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # --- timed region (kernel-only: A resident in HBM; A is 800 MB > L2, so
+    # no L2 flush is needed between steps) ---
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    lc0 = native.launch_count()
+    native.profile_begin(("pass", "core_pass"))
+    with ClockSampler(local_rank) as clk:
+        t_wall = time.perf_counter()
+        ev0.record(stream)
+        for i in range(args.steps):
+            step(1000 + i)
+        ev1.record(stream)
+        barrier()
+        t_wall = time.perf_counter() - t_wall
+    prof = native.profile_end()
+    launches = native.launch_count() - lc0
+    ms = ev0.elapsed_time(ev1) / args.steps
+    clocks = clk.summary()
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    F = flops(m, n, k, p, q)
+    value = F * world / (ms * 1e-3) / 1e12
+
+    # --- end to end through the public API: pinned host A -> device, solve, U S V -> host ---
+    esz = A.element_size()
+    hostA = torch.empty(At.shape, dtype=At.dtype, pin_memory=True)
+    hostA.copy_(At)
+    hU = torch.empty(k, m, dtype=od, pin_memory=True)
+    hS = torch.empty(k, dtype=od, pin_memory=True)
+    hV = torch.empty(k, n, dtype=od, pin_memory=True)
+    dAt = torch.empty_like(At)
+    e_steps = max(3, min(args.steps, 10))
+
+    def e2e_step(seed):
+        dAt.copy_(hostA, non_blocking=True)
+        native.run(dAt.T, k, p, q, seed=seed, dtype=dt, workspace=ws, out=(U, S, V))
+        hU.copy_(U.T, non_blocking=True)
+        hS.copy_(S, non_blocking=True)
+        hV.copy_(V.T, non_blocking=True)
+
+    e2e_step(0)
+    barrier()
+    ev0.record(stream)
+    for i in range(e_steps):
+        e2e_step(2000 + i)
+    ev1.record(stream)
+    barrier()
+    e_ms = ev0.elapsed_time(ev1) / e_steps
+    if world > 1:
+        t = torch.tensor([e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e_ms = float(t.item())
+    h2d = m * n * esz
+    d2h = (m * k + k + n * k) * torch.empty(0, dtype=od).element_size()
+
+    # --- roofline of the dominant kernel class ---
+    pk, pk_src = peaks()
+    dom = max(("pass", "core_pass"), key=lambda c: prof[c][0])
+    dom_ms, dom_n = prof[dom]
+    per_launch_ms = dom_ms / max(dom_n, 1)
+    l = k + p
+    algo_flops = 2.0 * m * n * l
+    algo_bytes = m * n * esz + (m + n) * l * (8 if dt == "f64" else 4)
+    sm_max = pk.get("sm_max_mhz", 2070.0)
+    # CUDA-core (SIMT) fp32 FMA peak: 152 SMs x 128 lanes x 2 flop x max SM clock
+    alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12 if dt != "f64" else 152 * 2 * 2 * sm_max * 1e6 / 1e12
+    achieved = algo_flops / (per_launch_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": "gemm_kernel (" + dom + ")", "achieved": achieved, "peak": alu_peak,
+                "unit": "TFLOP/s", "frac": achieved / alu_peak,
+                "peak_source": f"derived: 152 SMs x {'128 fp32' if dt != 'f64' else '2 fp64'} FMA/clk x "
+                               f"{sm_max:.0f} MHz",
+                "algorithmic_bytes_per_launch": algo_bytes,
+                "achieved_gbs": algo_bytes / (per_launch_ms * 1e-3) / 1e9,
+                "hbm_peak_gbs": pk["hbm_gbs"], "hbm_frac": algo_bytes / (per_launch_ms * 1e-3) / 1e9 / pk["hbm_gbs"],
+                "launch_ms": per_launch_ms, "launches": dom_n,
+                "traffic": traffic_from_profiles(f"{dom}:{args.workload}")}
+    out = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": dt, "data": "synthetic (seeded, built on the GPU)",
+           "config": {"workload": f"{args.workload}: {w['desc']}", "m": m, "n": n, "k": k, "p": p, "q": q,
+                      "flops_per_step": F, "l2": "inputs larger than L2 (A is %d MB)" % (m * n * esz // 2**20),
+                      "parallelism": f"replicas x{world}"},
+           "e2e": {"value": F * world / (e_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": e_ms,
+                   "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+           "gpu_launches": launches, "roofline": roofline, "clocks": clocks,
+           "kernel_ms_per_step": {c: prof[c][0] / args.steps for c in ("pass", "core_pass")},
+           "wall_s_timed": t_wall}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(w, args.cpu_rows)
+    return out
+
+
+def cpu_baseline(w, rows):
+    """The binary64 oracle timed on the host on a row-sample of the workload."""
+    import numpy as np
+    import oracle
+    from paper_1804_00462_gb300 import inputs
+    m_s = min(rows, w["m"])
+    A64, _, _, _ = inputs.noisy_poly(m_s, w["n"], min(w["width"], m_s, w["n"]), w["noise"], seed=0) \
+        if w["spectrum"] == "poly1" else inputs.spectral(m_s, w["n"], sigma_of(w)[:min(m_s, w["n"], w["width"])], 0)
+    _, exact = inputs.to_storage(A64, w["dtype"])
+    exact = np.ascontiguousarray(exact)
+    t = time.perf_counter()
+    oracle.sorsvd(exact, w["k"], w["p"], w["q"], 0, omega_dtype=w["dtype"])
+    t = time.perf_counter() - t
+    F = flops(m_s, w["n"], w["k"], w["p"], w["q"])
+    return {"value": F / t / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"one solve of the same recipe with {m_s} of {w['m']} rows "
+                      f"({m_s}x{w['n']}, k={w['k']}, p={w['p']}, q={w['q']}), numpy BLAS threads",
+            "seconds": t}
+
+
+def run_reference(args, w, rank, world):
+    """The oracle (binary64, host cores) as the reference arm."""
+    if rank != 0:
+        return None
+    import numpy as np
+    import oracle
+    from paper_1804_00462_gb300 import inputs
+    m_s = min(args.cpu_rows, w["m"])
+    A64, _, _, _ = inputs.noisy_poly(m_s, w["n"], min(w["width"], m_s, w["n"]), w["noise"], seed=0) \
+        if w["spectrum"] == "poly1" else inputs.spectral(m_s, w["n"], sigma_of(w)[:min(m_s, w["n"], w["width"])], 0)
+    _, exact = inputs.to_storage(A64, w["dtype"])
+    exact = np.ascontiguousarray(exact)
+    for i in range(args.warmup):
+        oracle.sorsvd(exact, w["k"], w["p"], w["q"], i, omega_dtype=w["dtype"])
+    t = time.perf_counter()
+    for i in range(args.steps):
+        oracle.sorsvd(exact, w["k"], w["p"], w["q"], 1000 + i, omega_dtype=w["dtype"])
+    t = (time.perf_counter() - t) / args.steps
+    F = flops(m_s, w["n"], w["k"], w["p"], w["q"])
+    v = F / t / 1e12
+    sample = (f"each step one oracle solve of the same recipe with {m_s} of {w['m']} rows "
+              f"({m_s}x{w['n']}, k={w['k']}, p={w['p']}, q={w['q']})")
+    return {"metric": METRIC, "value": v, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded, built on the host)",
+            "config": {"workload": f"{args.workload}: {w['desc']}", "m": w["m"], "n": w["n"], "k": w["k"],
+                       "p": w["p"], "q": w["q"], "sample_rows": m_s},
+            "impl": "reference",
+            "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", choices=tuple(WORKLOADS), default="cfg2")
+    ap.add_argument("--cpu-rows", type=int, default=20000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        out = run_reference(args, w, rank, world)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    out = run_ours(args, w, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

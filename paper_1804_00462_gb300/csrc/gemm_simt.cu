@@ -1,0 +1,226 @@
+// CUDA-core GEMMs for the tall-skinny products of SOR-SVD, and the small
+// elementwise helpers around them.
+//
+// The products of Algorithm 3 all have one long dimension (m or n, the rows
+// of A) and one short one (l = k + p):
+//   T1 = A T2, W = A Q2, Q = T R^{-1}, U = Q1 U~_k        (op(A) = A)
+//   T2 = A^T T1, G = T^T T, M = Q1^T W                    (op(A) = A^T)
+// The kernel below covers both with a 128 x 64 output tile, 16-deep K
+// slices staged in shared memory and 8 x 4 register blocking per thread.
+// K may be split across blockIdx.z; partial tiles are combined by
+// reduce_splits in a fixed order (no atomics, deterministic results).
+#include "internal.cuh"
+
+namespace sorsvd {
+
+int num_sms() {
+  static int cache[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (cache[dev] == 0) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    cache[dev] = v > 0 ? v : 1;
+  }
+  return cache[dev];
+}
+
+namespace {
+
+constexpr int BM = 128, BN = 64, BK = 16, TM = 8, TN = 4, NT = 256;
+
+template <typename Acc, typename T> __device__ __forceinline__ Acc ld_as(const T* p) { return to_acc<Acc, T>(*p); }
+
+template <typename TA, typename TB, typename Acc, bool TRANS>
+__global__ void __launch_bounds__(NT)
+gemm_kernel(int64_t M, int64_t N, int64_t K, const TA* __restrict__ A, int64_t lda,
+            const TB* __restrict__ B, int64_t ldb, Acc* __restrict__ C, int64_t ldc,
+            int64_t k_chunk, int64_t split_stride) {
+  __shared__ Acc As[BK][BM];
+  __shared__ Acc Bs[BK][BN];
+  const int t = threadIdx.x;
+  const int tx = t % (BN / TN), ty = t / (BN / TN);
+  const int64_t row0 = (int64_t)blockIdx.x * BM, col0 = (int64_t)blockIdx.y * BN;
+  const int64_t kbeg = (int64_t)blockIdx.z * k_chunk;
+  const int64_t kend = min(K, kbeg + k_chunk);
+  C += (int64_t)blockIdx.z * split_stride;
+
+  Acc acc[TM][TN];
+#pragma unroll
+  for (int a = 0; a < TM; ++a)
+#pragma unroll
+    for (int b = 0; b < TN; ++b) acc[a][b] = Acc(0);
+
+  for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
+#pragma unroll
+    for (int r = 0; r < (BM * BK) / NT; ++r) {
+      int idx = t + r * NT;
+      int i, kk;
+      if (TRANS) { kk = idx % BK; i = idx / BK; } else { i = idx % BM; kk = idx / BM; }
+      int64_t gi = row0 + i, gk = k0 + kk;
+      Acc v = Acc(0);
+      if (gi < M && gk < kend) v = TRANS ? ld_as<Acc>(A + gk + gi * lda) : ld_as<Acc>(A + gi + gk * lda);
+      As[kk][i] = v;
+    }
+#pragma unroll
+    for (int r = 0; r < (BN * BK) / NT; ++r) {
+      int idx = t + r * NT;
+      int kk = idx % BK, j = idx / BK;
+      int64_t gj = col0 + j, gk = k0 + kk;
+      Acc v = Acc(0);
+      if (gj < N && gk < kend) v = ld_as<Acc>(B + gk + gj * ldb);
+      Bs[kk][j] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      Acc a[TM], b[TN];
+#pragma unroll
+      for (int q = 0; q < TM; ++q) a[q] = As[kk][ty * TM + q];
+#pragma unroll
+      for (int q = 0; q < TN; ++q) b[q] = Bs[kk][tx * TN + q];
+#pragma unroll
+      for (int x = 0; x < TM; ++x)
+#pragma unroll
+        for (int y = 0; y < TN; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int y = 0; y < TN; ++y) {
+    int64_t gj = col0 + tx * TN + y;
+    if (gj >= N) continue;
+#pragma unroll
+    for (int x = 0; x < TM; ++x) {
+      int64_t gi = row0 + ty * TM + x;
+      if (gi < M) C[gi + gj * ldc] = acc[x][y];
+    }
+  }
+}
+
+template <typename TA, typename TB, typename Acc>
+cudaError_t gemm_dispatch(bool trans, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
+                          const void* B, int64_t ldb, void* C, int64_t ldc, int splits,
+                          int64_t split_stride, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (splits < 1) splits = 1;
+  int64_t k_chunk = (K + splits - 1) / splits;
+  k_chunk = ((k_chunk + BK - 1) / BK) * BK;
+  if (k_chunk < BK) k_chunk = BK;
+  dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN), (unsigned)splits);
+  if (trans)
+    gemm_kernel<TA, TB, Acc, true><<<grid, NT, 0, st>>>(M, N, K, (const TA*)A, lda, (const TB*)B, ldb,
+                                                        (Acc*)C, ldc, k_chunk, split_stride);
+  else
+    gemm_kernel<TA, TB, Acc, false><<<grid, NT, 0, st>>>(M, N, K, (const TA*)A, lda, (const TB*)B, ldb,
+                                                         (Acc*)C, ldc, k_chunk, split_stride);
+  return cudaGetLastError();
+}
+
+template <typename TP, typename TO>
+__global__ void reduce_kernel(const TP* __restrict__ parts, int splits, int64_t stride, int64_t rows,
+                              int64_t cols, int64_t ldp, TO* __restrict__ out, int64_t ldo) {
+  const int64_t total = rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t j = e / rows, i = e - j * rows;
+    double s = 0.0;
+    for (int p = 0; p < splits; ++p) s += (double)parts[p * stride + i + j * ldp];
+    out[i + j * ldo] = (TO)s;
+  }
+}
+
+template <typename TY>
+__global__ void convert_kernel(const float* __restrict__ x, int64_t ldx, int64_t rows, int64_t cols,
+                               TY* __restrict__ y, int64_t ldy, TY* __restrict__ lo) {
+  const int64_t total = rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t j = e / rows, i = e - j * rows;
+    float v = x[i + j * ldx];
+    TY h = from_f32<TY>(v);
+    y[i + j * ldy] = h;
+    if (lo) lo[i + j * ldy] = from_f32<TY>(v - to_f32<TY>(h));
+  }
+}
+
+template <typename T>
+__global__ void copy2d_kernel(const T* __restrict__ x, int64_t ldx, T* __restrict__ y, int64_t ldy,
+                              int64_t rows, int64_t cols) {
+  const int64_t total = rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t j = e / rows, i = e - j * rows;
+    y[i + j * ldy] = x[i + j * ldx];
+  }
+}
+
+inline int grid_for(int64_t total) {
+  int64_t b = (total + 255) / 256;
+  int64_t cap = (int64_t)num_sms() * 16;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_gemm(bool trans_a, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda, int a_dt,
+                        const void* B, int64_t ldb, int b_dt, void* C, int64_t ldc, bool acc_f64,
+                        int splits, int64_t split_stride, cudaStream_t st) {
+  if (acc_f64) {
+    if (a_dt == SORSVD_F64 && b_dt == SORSVD_F64)
+      return gemm_dispatch<double, double, double>(trans_a, M, N, K, A, lda, B, ldb, C, ldc, splits, split_stride, st);
+    return cudaErrorInvalidValue;
+  }
+  bool a32 = (a_dt == SORSVD_F32 || a_dt == SORSVD_TF32), b32 = (b_dt == SORSVD_F32 || b_dt == SORSVD_TF32);
+  if (a32 && b32) return gemm_dispatch<float, float, float>(trans_a, M, N, K, A, lda, B, ldb, C, ldc, splits, split_stride, st);
+  if (a_dt == SORSVD_BF16 && b_dt == SORSVD_BF16) return gemm_dispatch<bf16, bf16, float>(trans_a, M, N, K, A, lda, B, ldb, C, ldc, splits, split_stride, st);
+  if (a_dt == SORSVD_BF16 && b32) return gemm_dispatch<bf16, float, float>(trans_a, M, N, K, A, lda, B, ldb, C, ldc, splits, split_stride, st);
+  if (a_dt == SORSVD_F16 && b_dt == SORSVD_F16) return gemm_dispatch<f16, f16, float>(trans_a, M, N, K, A, lda, B, ldb, C, ldc, splits, split_stride, st);
+  if (a_dt == SORSVD_F16 && b32) return gemm_dispatch<f16, float, float>(trans_a, M, N, K, A, lda, B, ldb, C, ldc, splits, split_stride, st);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_reduce_splits(const void* parts, bool parts_f64, int splits, int64_t split_stride,
+                                 int64_t rows, int64_t cols, int64_t ld_part, void* out, bool out_f64,
+                                 int64_t ld_out, cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  int g = grid_for(rows * cols);
+  if (parts_f64 && out_f64)
+    reduce_kernel<double, double><<<g, 256, 0, st>>>((const double*)parts, splits, split_stride, rows, cols, ld_part, (double*)out, ld_out);
+  else if (parts_f64)
+    reduce_kernel<double, float><<<g, 256, 0, st>>>((const double*)parts, splits, split_stride, rows, cols, ld_part, (float*)out, ld_out);
+  else if (out_f64)
+    reduce_kernel<float, double><<<g, 256, 0, st>>>((const float*)parts, splits, split_stride, rows, cols, ld_part, (double*)out, ld_out);
+  else
+    reduce_kernel<float, float><<<g, 256, 0, st>>>((const float*)parts, splits, split_stride, rows, cols, ld_part, (float*)out, ld_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert_f32(const float* x, int64_t ldx, int64_t rows, int64_t cols, void* y, int64_t ldy,
+                               int y_dt, void* lo, cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  int g = grid_for(rows * cols);
+  if (y_dt == SORSVD_BF16)
+    convert_kernel<bf16><<<g, 256, 0, st>>>(x, ldx, rows, cols, (bf16*)y, ldy, (bf16*)lo);
+  else if (y_dt == SORSVD_F16)
+    convert_kernel<f16><<<g, 256, 0, st>>>(x, ldx, rows, cols, (f16*)y, ldy, (f16*)lo);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy2d(const void* x, int64_t ldx, void* y, int64_t ldy, int64_t rows, int64_t cols,
+                          size_t elem, cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  int g = grid_for(rows * cols);
+  if (elem == 8) copy2d_kernel<double><<<g, 256, 0, st>>>((const double*)x, ldx, (double*)y, ldy, rows, cols);
+  else if (elem == 4) copy2d_kernel<float><<<g, 256, 0, st>>>((const float*)x, ldx, (float*)y, ldy, rows, cols);
+  else if (elem == 2) copy2d_kernel<uint16_t><<<g, 256, 0, st>>>((const uint16_t*)x, ldx, (uint16_t*)y, ldy, rows, cols);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+}  // namespace sorsvd

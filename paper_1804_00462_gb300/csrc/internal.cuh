@@ -1,0 +1,112 @@
+// Internal declarations shared by the translation units of libsorsvd.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/sorsvd.h"
+
+namespace sorsvd {
+
+// ---------------------------------------------------------------------------
+// device status word (lives at the start of every workspace)
+// ---------------------------------------------------------------------------
+struct DeviceStatus {
+  int code;        // first non-OK sorsvd_status raised on the device
+  int info;        // bit 0: shifted Cholesky retry; bits 8..15: Jacobi sweeps
+  int pad[14];
+};
+
+__device__ __forceinline__ void raise_status(DeviceStatus* st, int code) {
+  atomicCAS(&st->code, 0, code);
+}
+
+// ---------------------------------------------------------------------------
+// element types
+// ---------------------------------------------------------------------------
+typedef __nv_bfloat16 bf16;
+typedef __half f16;
+
+template <typename T> __device__ __forceinline__ float to_f32(T x);
+template <> __device__ __forceinline__ float to_f32<float>(float x) { return x; }
+template <> __device__ __forceinline__ float to_f32<bf16>(bf16 x) { return __bfloat162float(x); }
+template <> __device__ __forceinline__ float to_f32<f16>(f16 x) { return __half2float(x); }
+
+template <typename Acc, typename T> __device__ __forceinline__ Acc to_acc(T x) { return (Acc)to_f32<T>(x); }
+template <> __device__ __forceinline__ double to_acc<double, double>(double x) { return x; }
+template <> __device__ __forceinline__ float to_acc<float, double>(double x) { return (float)x; }
+
+template <typename T> __device__ __forceinline__ T from_f64(double x);
+template <> __device__ __forceinline__ double from_f64<double>(double x) { return x; }
+template <> __device__ __forceinline__ float from_f64<float>(double x) { return __double2float_rn(x); }
+// two-step rounding binary64 -> fp32 -> 16-bit, both round-to-nearest-even
+template <> __device__ __forceinline__ bf16 from_f64<bf16>(double x) { return __float2bfloat16_rn(__double2float_rn(x)); }
+template <> __device__ __forceinline__ f16 from_f64<f16>(double x) { return __float2half_rn(__double2float_rn(x)); }
+
+template <typename T> __device__ __forceinline__ T from_f32(float x);
+template <> __device__ __forceinline__ float from_f32<float>(float x) { return x; }
+template <> __device__ __forceinline__ double from_f32<double>(float x) { return (double)x; }
+template <> __device__ __forceinline__ bf16 from_f32<bf16>(float x) { return __float2bfloat16_rn(x); }
+template <> __device__ __forceinline__ f16 from_f32<f16>(float x) { return __float2half_rn(x); }
+
+inline size_t dtype_size(int dt) {
+  switch (dt) {
+    case SORSVD_F64: return 8;
+    case SORSVD_F32: case SORSVD_TF32: return 4;
+    case SORSVD_BF16: case SORSVD_F16: return 2;
+    default: return 0;
+  }
+}
+inline bool dtype_is_16(int dt) { return dt == SORSVD_BF16 || dt == SORSVD_F16; }
+inline size_t acc_size(int dt) { return dt == SORSVD_F64 ? 8 : 4; }
+
+// ---------------------------------------------------------------------------
+// host-side launchers (defined next to their kernels)
+// ---------------------------------------------------------------------------
+int num_sms();
+
+// gaussian.cu
+cudaError_t launch_gaussian(void* out, int64_t rows, int64_t cols, int64_t ld, uint64_t seed,
+                            uint64_t stream_id, int dtype, cudaStream_t st);
+
+// gemm_simt.cu
+// C (M x N) = op(A) * B with A column-major.  trans_a = false: A is M x K;
+// trans_a = true: A is K x M (used as A^T).  B is K x N column-major.  When
+// `splits` > 1 the K range is cut in `splits` chunks and chunk s writes the
+// partial product to C + s * split_stride; reduce_splits combines them.
+// a_dt / b_dt: element types (sorsvd_dtype); c is fp32 for acc_f64 = false,
+// binary64 otherwise.
+cudaError_t launch_gemm(bool trans_a, int64_t M, int64_t N, int64_t K,
+                        const void* A, int64_t lda, int a_dt,
+                        const void* B, int64_t ldb, int b_dt,
+                        void* C, int64_t ldc, bool acc_f64,
+                        int splits, int64_t split_stride, cudaStream_t st);
+// out = sum_s parts[s] (fixed order, binary64 sums); parts are fp32 or f64.
+cudaError_t launch_reduce_splits(const void* parts, bool parts_f64, int splits, int64_t split_stride,
+                                 int64_t rows, int64_t cols, int64_t ld_part,
+                                 void* out, bool out_f64, int64_t ld_out, cudaStream_t st);
+// y (16-bit) = round(x) elementwise; x fp32 (rows x cols, ldx) -> y (ldy).
+// When `lo` is non-null it also receives round(x - float(y)) (hi/lo split).
+cudaError_t launch_convert_f32(const float* x, int64_t ldx, int64_t rows, int64_t cols,
+                               void* y, int64_t ldy, int y_dt, void* lo, cudaStream_t st);
+// copy with leading dimensions (same element size)
+cudaError_t launch_copy2d(const void* x, int64_t ldx, void* y, int64_t ldy,
+                          int64_t rows, int64_t cols, size_t elem, cudaStream_t st);
+
+// chol.cu: R^{-1} (upper triangular, l x l, column-major, ld = l) of the
+// Cholesky factor of G + s I, s = shift_rel * trace(G) / l.  G binary64.
+// Output in binary64 (f64 = true) or fp32.
+cudaError_t launch_chol_inv(const double* G, int l, double shift_rel, void* Rinv, bool f64,
+                            DeviceStatus* status, cudaStream_t st);
+
+// jacobi.cu: SVD of the l x l matrix M (binary64 input) by one-sided Jacobi
+// in binary64 (f64) or fp32.  Writes sigma (descending) to S (k entries,
+// S_f64 selects its type), U~ and V~ (l x l, ld = l, same precision as the
+// sweep) with the sign convention of the oracle.  Work buffer: 2 l^2 words.
+cudaError_t launch_jacobi(const double* M, int l, int k, bool f64, void* Ut, void* Vt,
+                          void* S, bool S_f64, void* work, DeviceStatus* status, cudaStream_t st);
+
+}  // namespace sorsvd

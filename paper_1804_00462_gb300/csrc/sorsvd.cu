@@ -1,0 +1,324 @@
+// Host driver of the C ABI: argument checks, workspace layout, and the
+// sequence of kernels that realises Algorithm 3 (SOR-SVD with power method):
+//
+//   Omega -> T2op                                 (sorsvd_gaussian)
+//   for i = 1 .. q+1:                             (power loop)
+//     [i > 1] T2 <- orth(T2)   shifted CholeskyQR, one pass: keeps range(T2)
+//                              (Lemma 1: QR projectors are invariant under
+//                              right multiplication by a nonsingular matrix)
+//     T1 = A T2op ; T2 = A^T T1op                 (eqs. T1, AT1)
+//   Q1 = orth3(T1), Q2 = orth3(T2)                (QR step: shifted CholeskyQR3)
+//   M = Q1^T (A Q2)                               (eq. M)
+//   M = U~ S~ V~^T (one-sided Jacobi), keep k     (truncated SVD)
+//   U = Q1 U~_k, V = Q2 V~_k                      (output assembly)
+//
+// "op" buffers hold the operand that multiplies A: the 16-bit rounding of the
+// fp32 sketch for BF16/F16, the sketch itself otherwise.
+#include "internal.cuh"
+#include "profile.cuh"
+
+#include <algorithm>
+
+namespace sorsvd {
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+// relative shift of the first CholeskyQR pass (unit-diagonal Gram)
+inline double first_shift(int dt) { return dt == SORSVD_F64 ? 1e-13 : 1e-5; }
+
+// K splits of a product with an M x N output and reduction length K
+int splits_for(int64_t M, int64_t N, int64_t K, int cap) {
+  int64_t tiles = ((M + 127) / 128) * ((N + 63) / 64);
+  int64_t want = 2 * (int64_t)num_sms();
+  int64_t s = (want + tiles - 1) / tiles;
+  int64_t by_k = (K + 255) / 256;
+  s = std::min<int64_t>(s, by_k);
+  s = std::min<int64_t>(s, cap);
+  return (int)std::max<int64_t>(s, 1);
+}
+constexpr int kCapBig = 16, kCapSmall = 256;
+
+struct Layout {
+  size_t status, t2op, t2, t1, t1op, q2op, tmp, parts, G, Rinv, M, Ut, Vt, jwork, total;
+};
+
+Layout make_layout(int64_t m, int64_t n, int l, int dt) {
+  Layout L{};
+  const size_t acc = acc_size(dt), op = dtype_size(dt);
+  const bool h16 = dtype_is_16(dt);
+  const int64_t mx = std::max(m, n);
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
+  L.status = take(sizeof(DeviceStatus));
+  L.t2op = h16 ? take((size_t)n * l * op) : 0;
+  L.t2 = take((size_t)n * l * acc);
+  if (!h16) L.t2op = L.t2;
+  L.t1 = take((size_t)m * l * acc);
+  L.t1op = h16 ? take((size_t)m * l * op) : L.t1;
+  L.q2op = h16 ? take((size_t)2 * n * l * op) : 0;
+  L.tmp = take((size_t)mx * l * acc);
+  // split-K partials: the largest of the big passes and the l x l products
+  // (every gemm() call of the pipeline is listed; an l x l product always
+  // goes through the buffer because its binary64 result is a reduction)
+  size_t pb = 0;
+  auto need = [&](int64_t M, int64_t N, int64_t K, int cap, bool always) {
+    int s = splits_for(M, N, K, cap);
+    if (s > 1 || always) pb = std::max(pb, (size_t)s * M * N * acc);
+  };
+  need(m, l, n, kCapBig, false);     // T1 = A T2, W = A Q2
+  need(n, l, m, kCapBig, false);     // T2 = A^T T1
+  need(l, l, m, kCapSmall, true);    // Gram of T1, M = Q1^T W
+  need(l, l, n, kCapSmall, true);    // Gram of T2
+  need(m, l, l, kCapBig, false);     // T1 R^{-1}
+  need(n, l, l, kCapBig, false);     // T2 R^{-1}
+  for (int k = 1; k <= l; ++k) {     // U = Q1 U~_k, V = Q2 V~_k (k unknown here)
+    need(m, k, l, kCapBig, false);
+    need(n, k, l, kCapBig, false);
+  }
+  L.parts = take(pb);
+  L.G = take((size_t)l * l * 8);
+  L.Rinv = take((size_t)l * l * acc);
+  L.M = take((size_t)l * l * 8);
+  L.Ut = take((size_t)l * l * acc);
+  L.Vt = take((size_t)l * l * acc);
+  L.jwork = take((size_t)2 * l * l * acc);
+  L.total = off;
+  return L;
+}
+
+struct Ctx {
+  char* ws;
+  Layout L;
+  int dt;
+  bool f64;
+  cudaStream_t st;
+  DeviceStatus* status() const { return reinterpret_cast<DeviceStatus*>(ws + L.status); }
+  void* at(size_t o) const { return ws + o; }
+};
+
+#define CK(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) return SORSVD_ERR_CUDA; } while (0)
+
+// C (M x N, ldc) = op(A) B, with split-K through the partial buffer when useful.
+int gemm(const Ctx& c, int kcls, bool trans, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
+         int adt, const void* B, int64_t ldb, int bdt, void* C, int64_t ldc, bool c_f64, int cap) {
+  const bool accf = c.f64;
+  int s = splits_for(M, N, K, cap);
+  if (s == 1 && (c_f64 == accf)) {
+    ProfScope ps(kcls, c.st);
+    CK(launch_gemm(trans, M, N, K, A, lda, adt, B, ldb, bdt, C, ldc, accf, 1, 0, c.st));
+    return SORSVD_OK;
+  }
+  int64_t stride = M * N;
+  {
+    ProfScope ps(kcls, c.st);
+    CK(launch_gemm(trans, M, N, K, A, lda, adt, B, ldb, bdt, c.at(c.L.parts), M, accf, s, stride, c.st));
+  }
+  ProfScope ps(K_REDUCE, c.st);
+  CK(launch_reduce_splits(c.at(c.L.parts), accf, s, stride, M, N, M, C, c_f64, ldc, c.st));
+  return SORSVD_OK;
+}
+
+// a single launch of class `kcls`
+#define LAUNCH(kcls, expr) do { ProfScope ps_(kcls, c.st); CK(expr); } while (0)
+
+// T (rows x l, ld = rows, accumulator type) <- T R^{-1}, repeated `passes`
+// times (CholeskyQR); the first pass is shifted by shift0.
+int orth(const Ctx& c, void* T, int64_t rows, int l, int passes, double shift0) {
+  const int adt = c.f64 ? SORSVD_F64 : SORSVD_F32;
+  for (int p = 0; p < passes; ++p) {
+    int r = gemm(c, K_SMALL_GEMM, true, l, l, rows, T, rows, adt, T, rows, adt, c.at(c.L.G), l, true, kCapSmall);
+    if (r) return r;
+    LAUNCH(K_CHOL, launch_chol_inv((const double*)c.at(c.L.G), l, p == 0 ? shift0 : 0.0, c.at(c.L.Rinv), c.f64,
+                                   c.status(), c.st));
+    r = gemm(c, K_SMALL_GEMM, false, rows, l, l, T, rows, adt, c.at(c.L.Rinv), l, adt, c.at(c.L.tmp), rows, c.f64,
+             kCapBig);
+    if (r) return r;
+    LAUNCH(K_MISC, launch_copy2d(c.at(c.L.tmp), rows, T, rows, rows, l, acc_size(c.dt), c.st));
+  }
+  return SORSVD_OK;
+}
+
+// T1 = A X (X given as the operand buffer xop, type of the passes), then
+// T2 = A^T T1 (rounded to 16 bits first for BF16/F16).
+int power_pass_impl(const Ctx& c, const void* A, int64_t m, int64_t n, int64_t lda, const void* xop,
+                    int64_t ldx, int l, void* T1, int64_t ldt1, void* T2, int64_t ldt2) {
+  const int dt = c.dt, adt = c.f64 ? SORSVD_F64 : SORSVD_F32;
+  int r = gemm(c, K_PASS, false, m, l, n, A, lda, dt, xop, ldx, dt, T1, ldt1, c.f64, kCapBig);
+  if (r) return r;
+  const void* t1op = T1;
+  int64_t ldop = ldt1;
+  int opdt = adt;
+  if (dtype_is_16(dt)) {
+    LAUNCH(K_MISC, launch_convert_f32((const float*)T1, ldt1, m, l, c.at(c.L.t1op), m, dt, nullptr, c.st));
+    t1op = c.at(c.L.t1op);
+    ldop = m;
+    opdt = dt;
+  }
+  return gemm(c, K_PASS, true, n, l, m, A, lda, dt, t1op, ldop, opdt, T2, ldt2, c.f64, kCapBig);
+}
+
+// M (l x l, f64, ldm) = Q1^T (A Q2)
+int core_impl(const Ctx& c, const void* A, int64_t m, int64_t n, int64_t lda, unsigned flags,
+              const void* Q1, int64_t ldq1, const void* Q2, int64_t ldq2, int l, double* M, int64_t ldm) {
+  const int dt = c.dt, adt = c.f64 ? SORSVD_F64 : SORSVD_F32;
+  const void* q2 = Q2;
+  int64_t ldq = ldq2;
+  int qdt = adt;
+  if (dtype_is_16(dt) && !(flags & SORSVD_FLAG_REFINE)) {
+    LAUNCH(K_MISC, launch_convert_f32((const float*)Q2, ldq2, n, l, c.at(c.L.q2op), n, dt, nullptr, c.st));
+    q2 = c.at(c.L.q2op);
+    ldq = n;
+    qdt = dt;
+  }
+  // With REFINE the CUDA-core path multiplies by the fp32 Q2 directly, which
+  // is at least as accurate as the hi+lo pair of the tensor-core path.
+  int r = gemm(c, K_CORE, false, m, l, n, A, lda, dt, q2, ldq, qdt, c.at(c.L.tmp), m, c.f64, kCapBig);
+  if (r) return r;
+  return gemm(c, K_SMALL_GEMM, true, l, l, m, Q1, ldq1, adt, c.at(c.L.tmp), m, adt, M, ldm, true, kCapSmall);
+}
+
+int check_dtype(int dt) { return (dt >= SORSVD_F64 && dt <= SORSVD_F16) ? SORSVD_OK : SORSVD_ERR_DTYPE; }
+
+int check_ws(void* ws, size_t ws_bytes, const Layout& L) {
+  if (!ws) return SORSVD_ERR_WORKSPACE;
+  if (((uintptr_t)ws) % kAlign) return SORSVD_ERR_WORKSPACE;
+  if (ws_bytes < L.total) return SORSVD_ERR_WORKSPACE;
+  return SORSVD_OK;
+}
+
+int max_l(int dt) { return dt == SORSVD_F64 ? SORSVD_MAX_L_F64 : SORSVD_MAX_L; }
+
+}  // namespace
+}  // namespace sorsvd
+
+using namespace sorsvd;
+
+extern "C" {
+
+size_t sorsvd_workspace_size(int64_t m, int64_t n, int k, int p, int dtype, unsigned flags) {
+  (void)flags;
+  if (check_dtype(dtype) || m < 1 || n < 1 || k < 1 || p < 0) return 0;
+  int l = k + p;
+  if (l > std::min(m, n) || l > max_l(dtype)) return 0;
+  return make_layout(m, n, l, dtype).total;
+}
+
+const char* sorsvd_status_string(int s) {
+  switch (s) {
+    case SORSVD_OK: return "ok";
+    case SORSVD_ERR_ARG: return "invalid argument";
+    case SORSVD_ERR_DTYPE: return "unknown dtype";
+    case SORSVD_ERR_CUDA: return "CUDA runtime error";
+    case SORSVD_ERR_NOT_CONVERGED: return "Jacobi SVD did not converge";
+    case SORSVD_ERR_BREAKDOWN: return "Cholesky breakdown after shifted retries";
+    case SORSVD_ERR_TIMEOUT: return "bounded wait timed out";
+    case SORSVD_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case SORSVD_ERR_UNSUPPORTED: return "size beyond a documented limit";
+    default: return "unknown status";
+  }
+}
+
+int sorsvd_get_status(const void* workspace, int* device_status, int* info, void* stream) {
+  if (!workspace) return SORSVD_ERR_WORKSPACE;
+  DeviceStatus h{};
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(&h, workspace, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess) return SORSVD_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return SORSVD_ERR_CUDA;
+  if (device_status) *device_status = h.code;
+  if (info) *info = h.info;
+  return SORSVD_OK;
+}
+
+int sorsvd_gaussian(void* out, int64_t rows, int64_t cols, int64_t ld, uint64_t seed, uint64_t stream_id,
+                    int dtype, void* stream) {
+  if (check_dtype(dtype)) return SORSVD_ERR_DTYPE;
+  if (!out || rows < 0 || cols < 0 || ld < rows || ld < 1) return SORSVD_ERR_ARG;
+  ProfScope ps(K_GAUSSIAN, (cudaStream_t)stream);
+  if (launch_gaussian(out, rows, cols, ld, seed, stream_id, dtype, (cudaStream_t)stream) != cudaSuccess)
+    return SORSVD_ERR_CUDA;
+  return SORSVD_OK;
+}
+
+int sorsvd_power_pass(const void* A, int64_t m, int64_t n, int64_t lda, int dtype, const void* X, int64_t ldx,
+                      int l, void* T1, int64_t ldt1, void* T2, int64_t ldt2, void* workspace, size_t ws_bytes,
+                      void* stream) {
+  if (check_dtype(dtype)) return SORSVD_ERR_DTYPE;
+  if (!A || !X || !T1 || !T2 || m < 1 || n < 1 || l < 1 || lda < m || ldx < n || ldt1 < m || ldt2 < n)
+    return SORSVD_ERR_ARG;
+  if (l > std::min(m, n) || l > max_l(dtype)) return SORSVD_ERR_UNSUPPORTED;
+  Layout L = make_layout(m, n, l, dtype);
+  if (int r = check_ws(workspace, ws_bytes, L)) return r;
+  Ctx c{(char*)workspace, L, dtype, dtype == SORSVD_F64, (cudaStream_t)stream};
+  const void* xop = X;
+  int64_t ldop = ldx;
+  if (dtype_is_16(dtype)) {
+    LAUNCH(K_MISC, launch_convert_f32((const float*)X, ldx, n, l, c.at(L.t2op), n, dtype, nullptr, c.st));
+    xop = c.at(L.t2op);
+    ldop = n;
+  }
+  return power_pass_impl(c, A, m, n, lda, xop, ldop, l, T1, ldt1, T2, ldt2);
+}
+
+int sorsvd_core(const void* A, int64_t m, int64_t n, int64_t lda, int dtype, unsigned flags, const void* Q1,
+                int64_t ldq1, const void* Q2, int64_t ldq2, int l, double* M, int64_t ldm, void* workspace,
+                size_t ws_bytes, void* stream) {
+  if (check_dtype(dtype)) return SORSVD_ERR_DTYPE;
+  if (!A || !Q1 || !Q2 || !M || m < 1 || n < 1 || l < 1 || lda < m || ldq1 < m || ldq2 < n || ldm < l)
+    return SORSVD_ERR_ARG;
+  if (flags & ~(SORSVD_FLAG_LITERAL_POWER | SORSVD_FLAG_REFINE)) return SORSVD_ERR_ARG;
+  if (l > std::min(m, n) || l > max_l(dtype)) return SORSVD_ERR_UNSUPPORTED;
+  Layout L = make_layout(m, n, l, dtype);
+  if (int r = check_ws(workspace, ws_bytes, L)) return r;
+  Ctx c{(char*)workspace, L, dtype, dtype == SORSVD_F64, (cudaStream_t)stream};
+  return core_impl(c, A, m, n, lda, flags, Q1, ldq1, Q2, ldq2, l, M, ldm);
+}
+
+int sorsvd_run(const void* A, int64_t m, int64_t n, int64_t lda, int k, int p, int q, uint64_t seed, int dtype,
+               unsigned flags, void* U, int64_t ldu, void* S, void* V, int64_t ldv, void* workspace,
+               size_t ws_bytes, void* stream) {
+  if (check_dtype(dtype)) return SORSVD_ERR_DTYPE;
+  if (!A || !U || !S || !V) return SORSVD_ERR_ARG;
+  if (m < 1 || n < 1 || k < 1 || p < 0 || q < 0 || q > 1000 || lda < m || ldu < m || ldv < n)
+    return SORSVD_ERR_ARG;
+  if (flags & ~(SORSVD_FLAG_LITERAL_POWER | SORSVD_FLAG_REFINE)) return SORSVD_ERR_ARG;
+  const int l = k + p;
+  if (l > std::min(m, n)) return SORSVD_ERR_ARG;
+  if (l > max_l(dtype)) return SORSVD_ERR_UNSUPPORTED;
+  Layout L = make_layout(m, n, l, dtype);
+  if (int r = check_ws(workspace, ws_bytes, L)) return r;
+  Ctx c{(char*)workspace, L, dtype, dtype == SORSVD_F64, (cudaStream_t)stream};
+  const int adt = c.f64 ? SORSVD_F64 : SORSVD_F32;
+  const bool h16 = dtype_is_16(dtype);
+  int r;
+
+  CK(cudaMemsetAsync(c.status(), 0, sizeof(DeviceStatus), c.st));
+  LAUNCH(K_GAUSSIAN, launch_gaussian(c.at(L.t2op), n, l, n, seed, 0, dtype, c.st));
+  for (int i = 1; i <= q + 1; ++i) {
+    if (i > 1) {
+      if (!(flags & SORSVD_FLAG_LITERAL_POWER)) {
+        r = orth(c, c.at(L.t2), n, l, 1, first_shift(dtype));
+        if (r) return r;
+      }
+      if (h16) LAUNCH(K_MISC, launch_convert_f32((const float*)c.at(L.t2), n, n, l, c.at(L.t2op), n, dtype, nullptr, c.st));
+    }
+    r = power_pass_impl(c, A, m, n, lda, c.at(L.t2op), n, l, c.at(L.t1), m, c.at(L.t2), n);
+    if (r) return r;
+  }
+  r = orth(c, c.at(L.t1), m, l, 3, first_shift(dtype));
+  if (r) return r;
+  r = orth(c, c.at(L.t2), n, l, 3, first_shift(dtype));
+  if (r) return r;
+  r = core_impl(c, A, m, n, lda, flags, c.at(L.t1), m, c.at(L.t2), n, l, (double*)c.at(L.M), l);
+  if (r) return r;
+  LAUNCH(K_JACOBI, launch_jacobi((const double*)c.at(L.M), l, k, c.f64, c.at(L.Ut), c.at(L.Vt), S, c.f64,
+                                  c.at(L.jwork), c.status(), c.st));
+  r = gemm(c, K_SMALL_GEMM, false, m, k, l, c.at(L.t1), m, adt, c.at(L.Ut), l, adt, U, ldu, c.f64, kCapBig);
+  if (r) return r;
+  r = gemm(c, K_SMALL_GEMM, false, n, k, l, c.at(L.t2), n, adt, c.at(L.Vt), l, adt, V, ldv, c.f64, kCapBig);
+  if (r) return r;
+  return SORSVD_OK;
+}
+
+}  // extern "C"

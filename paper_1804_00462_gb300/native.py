@@ -1,0 +1,236 @@
+"""Python binding of libsorsvd (C ABI in include/sorsvd.h).
+
+Argument marshalling only: every step of SOR-SVD runs in the library's CUDA
+kernels.  Tensors are torch CUDA tensors (device memory and streams come
+from PyTorch).  There is no CPU fallback: if the shared library is missing
+the import fails with an explanation.
+
+Matrix layout: the C ABI is column-major.  A torch tensor ``A`` of shape
+(m, n) is passed as-is when it is column-major (``A.stride() == (1, lda)``,
+e.g. ``At.T`` of a contiguous (n, m) tensor).  A row-major (C-contiguous)
+tensor is the column-major storage of A^T; ``run`` then factors A^T and
+swaps U and V, which is the same decomposition of A.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+from ._build import LIB
+
+F64, F32, TF32, BF16, F16 = 0, 1, 2, 3, 4
+FLAG_LITERAL_POWER = 0x1
+FLAG_REFINE = 0x2
+MAX_L, MAX_L_F64 = 320, 224
+
+_TORCH_OF = {F64: torch.float64, F32: torch.float32, TF32: torch.float32, BF16: torch.bfloat16,
+             F16: torch.float16}
+_DT_NAMES = {"f64": F64, "f32": F32, "tf32": TF32, "bf16": BF16, "f16": F16}
+
+if not os.path.exists(LIB):
+    raise ImportError(f"libsorsvd.so is not built ({LIB}); run "
+                      "`python -c 'import __graft_entry__ as g; g.build()'` first")
+_lib = C.CDLL(LIB)
+
+_i64, _int, _u64, _uint, _vp, _sz = C.c_int64, C.c_int, C.c_uint64, C.c_uint, C.c_void_p, C.c_size_t
+_lib.sorsvd_workspace_size.argtypes = [_i64, _i64, _int, _int, _int, _uint]
+_lib.sorsvd_workspace_size.restype = _sz
+_lib.sorsvd_run.argtypes = [_vp, _i64, _i64, _i64, _int, _int, _int, _u64, _int, _uint,
+                            _vp, _i64, _vp, _vp, _i64, _vp, _sz, _vp]
+_lib.sorsvd_run.restype = _int
+_lib.sorsvd_get_status.argtypes = [_vp, C.POINTER(_int), C.POINTER(_int), _vp]
+_lib.sorsvd_get_status.restype = _int
+_lib.sorsvd_status_string.argtypes = [_int]
+_lib.sorsvd_status_string.restype = C.c_char_p
+_lib.sorsvd_gaussian.argtypes = [_vp, _i64, _i64, _i64, _u64, _u64, _int, _vp]
+_lib.sorsvd_gaussian.restype = _int
+_lib.sorsvd_power_pass.argtypes = [_vp, _i64, _i64, _i64, _int, _vp, _i64, _int, _vp, _i64, _vp, _i64,
+                                   _vp, _sz, _vp]
+_lib.sorsvd_power_pass.restype = _int
+_lib.sorsvd_core.argtypes = [_vp, _i64, _i64, _i64, _int, _uint, _vp, _i64, _vp, _i64, _int, _vp, _i64,
+                             _vp, _sz, _vp]
+_lib.sorsvd_core.restype = _int
+
+lib = _lib
+
+
+class SorsvdError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {status_string(code)} (status {code})")
+
+
+def status_string(code: int) -> str:
+    return _lib.sorsvd_status_string(int(code)).decode()
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise SorsvdError(code, where)
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def dtype_code(dtype) -> int:
+    if isinstance(dtype, int):
+        return dtype
+    if isinstance(dtype, str):
+        return _DT_NAMES[dtype]
+    for code, td in ((F64, torch.float64), (F32, torch.float32), (BF16, torch.bfloat16), (F16, torch.float16)):
+        if dtype == td:
+            return code
+    raise ValueError(f"unsupported dtype {dtype}")
+
+
+def out_dtype(code: int):
+    return torch.float64 if code == F64 else torch.float32
+
+
+def workspace_size(m: int, n: int, k: int, p: int, dtype, flags: int = 0) -> int:
+    return int(_lib.sorsvd_workspace_size(m, n, k, p, dtype_code(dtype), flags))
+
+
+def alloc_workspace(m: int, n: int, k: int, p: int, dtype, flags: int = 0, device=None) -> torch.Tensor:
+    nb = workspace_size(m, n, k, p, dtype, flags)
+    if nb == 0:
+        raise SorsvdError(1, "sorsvd_workspace_size")
+    return torch.empty(nb, dtype=torch.uint8, device=device or "cuda")
+
+
+def _colmajor(A: torch.Tensor):
+    """(ptr, rows, cols, ld, transposed) of a 2-D CUDA tensor."""
+    if A.dim() != 2 or not A.is_cuda:
+        raise ValueError("expected a 2-D CUDA tensor")
+    r, c = A.shape
+    s0, s1 = A.stride()
+    if s0 == 1 and (s1 >= max(r, 1) or c == 1):
+        return A.data_ptr(), r, c, max(s1, r), False
+    if s1 == 1 and (s0 >= max(c, 1) or r == 1):
+        return A.data_ptr(), c, r, max(s0, c), True
+    raise ValueError("A must be column-major or row-major with unit inner stride")
+
+
+def colmajor_empty(rows: int, cols: int, dtype, device) -> torch.Tensor:
+    return torch.empty(cols, rows, dtype=dtype, device=device).T
+
+
+def run(A: torch.Tensor, k: int, p: int, q: int, seed: int = 0, dtype=None, flags: int = 0,
+        workspace: torch.Tensor | None = None, stream=None, out=None, check: bool = False):
+    """Rank-k SOR-SVD of A (Algorithm 3).  Returns (U m x k, S k, V n x k)."""
+    ptr, m, n, lda, trans = _colmajor(A)
+    code = dtype_code(dtype if dtype is not None else A.dtype)
+    if _TORCH_OF[code] != A.dtype:
+        raise ValueError(f"dtype code {code} does not match tensor dtype {A.dtype}")
+    od = out_dtype(code)
+    if out is None:
+        U = colmajor_empty(m, k, od, A.device)
+        S = torch.empty(k, dtype=od, device=A.device)
+        V = colmajor_empty(n, k, od, A.device)
+    else:
+        U, S, V = out
+        if trans:
+            U, V = V, U
+    if workspace is None:
+        workspace = alloc_workspace(m, n, k, p, code, flags, A.device)
+    _check(_lib.sorsvd_run(ptr, m, n, lda, k, p, q, seed & 0xFFFFFFFFFFFFFFFF, code, flags,
+                           U.data_ptr(), U.stride(1), S.data_ptr(), V.data_ptr(), V.stride(1),
+                           workspace.data_ptr(), workspace.numel(), _stream(stream)), "sorsvd_run")
+    if check:
+        st, info = get_status(workspace, stream)
+        _check(st, "sorsvd_run (device)")
+    if trans:
+        U, V = V, U
+    return U, S, V
+
+
+def get_status(workspace: torch.Tensor, stream=None):
+    st, info = C.c_int(0), C.c_int(0)
+    _check(_lib.sorsvd_get_status(workspace.data_ptr(), C.byref(st), C.byref(info), _stream(stream)),
+           "sorsvd_get_status")
+    return st.value, info.value
+
+
+def gaussian(rows: int, cols: int, seed: int, stream_id: int = 0, dtype=F64, device="cuda", stream=None):
+    code = dtype_code(dtype)
+    out = colmajor_empty(rows, cols, _TORCH_OF[code], device)
+    _check(_lib.sorsvd_gaussian(out.data_ptr(), rows, cols, max(rows, 1), seed & 0xFFFFFFFFFFFFFFFF,
+                                stream_id, code, _stream(stream)), "sorsvd_gaussian")
+    return out
+
+
+def power_pass(A: torch.Tensor, X: torch.Tensor, k: int, p: int, dtype=None,
+               workspace: torch.Tensor | None = None, stream=None):
+    """T1 = A X, T2 = A^T T1 for column-major A (m x n) and X (n x l)."""
+    ptr, m, n, lda, trans = _colmajor(A)
+    if trans:
+        raise ValueError("power_pass needs a column-major A")
+    code = dtype_code(dtype if dtype is not None else A.dtype)
+    l = k + p
+    xp, xr, xc, ldx, xt = _colmajor(X)
+    if xt or xr != n or xc != l:
+        raise ValueError("X must be column-major n x l")
+    od = out_dtype(code)
+    T1 = colmajor_empty(m, l, od, A.device)
+    T2 = colmajor_empty(n, l, od, A.device)
+    if workspace is None:
+        workspace = alloc_workspace(m, n, k, p, code, 0, A.device)
+    _check(_lib.sorsvd_power_pass(ptr, m, n, lda, code, xp, ldx, l, T1.data_ptr(), m, T2.data_ptr(), n,
+                                  workspace.data_ptr(), workspace.numel(), _stream(stream)),
+           "sorsvd_power_pass")
+    return T1, T2
+
+
+def core(A: torch.Tensor, Q1: torch.Tensor, Q2: torch.Tensor, k: int, p: int, dtype=None, flags: int = 0,
+         workspace: torch.Tensor | None = None, stream=None):
+    """M = Q1^T A Q2 (binary64, l x l) for column-major A, Q1, Q2."""
+    ptr, m, n, lda, trans = _colmajor(A)
+    if trans:
+        raise ValueError("core needs a column-major A")
+    code = dtype_code(dtype if dtype is not None else A.dtype)
+    l = k + p
+    q1, r1, c1, ld1, t1 = _colmajor(Q1)
+    q2, r2, c2, ld2, t2 = _colmajor(Q2)
+    if t1 or t2 or (r1, c1, r2, c2) != (m, l, n, l):
+        raise ValueError("Q1 (m x l) and Q2 (n x l) must be column-major")
+    M = colmajor_empty(l, l, torch.float64, A.device)
+    if workspace is None:
+        workspace = alloc_workspace(m, n, k, p, code, flags, A.device)
+    _check(_lib.sorsvd_core(ptr, m, n, lda, code, flags, q1, ld1, q2, ld2, l, M.data_ptr(), l,
+                            workspace.data_ptr(), workspace.numel(), _stream(stream)), "sorsvd_core")
+    return M
+
+
+# ---- launch accounting ------------------------------------------------------
+NUM_KCLASS = 8
+KCLASS_NAMES = ("gaussian", "pass", "core_pass", "small_gemm", "reduce", "chol", "jacobi", "misc")
+_lib.sorsvd_launch_count.argtypes = []
+_lib.sorsvd_launch_count.restype = C.c_uint64
+_lib.sorsvd_profile_begin.argtypes = [_uint]
+_lib.sorsvd_profile_begin.restype = _int
+_lib.sorsvd_profile_end.argtypes = [C.POINTER(C.c_double), C.POINTER(_int), _int]
+_lib.sorsvd_profile_end.restype = _int
+
+
+def launch_count() -> int:
+    return int(_lib.sorsvd_launch_count())
+
+
+def profile_begin(classes=KCLASS_NAMES):
+    mask = 0
+    for c in classes:
+        mask |= 1 << KCLASS_NAMES.index(c)
+    _check(_lib.sorsvd_profile_begin(mask), "sorsvd_profile_begin")
+
+
+def profile_end():
+    """{class name: (total ms, launches)} of the launches since profile_begin."""
+    ms = (C.c_double * NUM_KCLASS)()
+    ln = (_int * NUM_KCLASS)()
+    _check(_lib.sorsvd_profile_end(ms, ln, NUM_KCLASS), "sorsvd_profile_end")
+    return {KCLASS_NAMES[i]: (ms[i], ln[i]) for i in range(NUM_KCLASS)}

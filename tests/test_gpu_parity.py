@@ -1,0 +1,235 @@
+"""Parity of the CUDA path (through the C ABI) with the binary64 CPU oracle.
+
+Gates (relative Frobenius reconstruction error r = ||A - U S V^T||_F / ||A||_F
+and singular values, on the same seeded input and the same Omega):
+  |r_gpu - r_oracle| <= tol  and  max_j |S_gpu_j - S_oracle_j| / S_oracle_1 <= tol
+with tol = 1e-10 (F64), 1e-5 (F32 / TF32-free fp32 path), 1e-2 (BF16 / F16
+without refinement).  Stage-level checks compare the Gaussian test matrix bit
+for bit and the pass / core products element by element.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from oracle import philox as oph  # noqa: E402
+from paper_1804_00462_gb300 import inputs  # noqa: E402
+
+TOL = {"f64": 1e-10, "f32": 1e-5, "tf32": 1e-5, "bf16": 1e-2, "f16": 1e-2}
+
+
+@pytest.fixture(scope="module")
+def nat():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1804_00462_gb300 import native
+    return native
+
+
+def cuda_colmajor(store: np.ndarray, dtype: str):
+    """Fortran-ordered numpy storage -> column-major CUDA tensor (m x n)."""
+    t = np.ascontiguousarray(store.T)
+    if dtype == "bf16":
+        x = torch.from_numpy(t.view(np.int16)).cuda().view(torch.bfloat16)
+    else:
+        x = torch.from_numpy(t).cuda()
+    return x.T
+
+
+def to_np(x):
+    return x.detach().double().cpu().numpy()
+
+
+def gates(exact, got, ref):
+    nA = np.linalg.norm(exact)
+    U, S, V = (to_np(t) for t in got)
+    Uo, So, Vo = ref
+    r_gpu = oracle.recon_error_fro(exact, U, S, V) / nA
+    r_orc = oracle.recon_error_fro(exact, Uo, So, Vo) / nA
+    ds = float(np.max(np.abs(S - So)) / So[0]) if So[0] > 0 else float(np.max(np.abs(S)))
+    return r_gpu, r_orc, ds
+
+
+def run_both(nat, A64, k, p, q, seed, dt, flags=0, mode="stabilised"):
+    store, exact = inputs.to_storage(A64, dt)
+    A = cuda_colmajor(store, dt)
+    got = nat.run(A, k, p, q, seed=seed, dtype=dt, flags=flags, check=True)
+    torch.cuda.synchronize()
+    ref = oracle.sorsvd(exact, k, p, q, seed, omega_dtype=dt, mode=mode)
+    return exact, got, ref
+
+
+# ---------------------------------------------------------------------------
+# stage 1: Omega
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("rows,cols", [(1, 1), (7, 3), (333, 27), (1000, 25), (10000, 110)])
+@pytest.mark.parametrize("dt", ["f64", "f32", "bf16", "f16"])
+def test_gaussian_bit_exact(nat, rows, cols, dt):
+    for seed, sid in ((0, 0), (2**64 - 5, 0), (123456789, 3)):
+        g = nat.gaussian(rows, cols, seed, sid, dtype=dt)
+        ref = oph.gaussian_matrix(rows, cols, seed, sid, dtype=dt)
+        assert np.array_equal(to_np(g), ref), (rows, cols, dt, seed)
+
+
+def test_gaussian_leading_dimension(nat):
+    rows, cols, ld = 37, 5, 50
+    buf = torch.full((cols, ld), 7.0, dtype=torch.float64, device="cuda")
+    r = nat.lib.sorsvd_gaussian(buf.data_ptr(), rows, cols, ld, 99, 0, nat.F64,
+                                torch.cuda.current_stream().cuda_stream)
+    assert r == 0
+    torch.cuda.synchronize()
+    b = buf.cpu().numpy()
+    assert np.array_equal(b[:, :rows].T, oph.gaussian_matrix(rows, cols, 99))
+    assert np.all(b[:, rows:] == 7.0)
+
+
+# ---------------------------------------------------------------------------
+# stage 2: power pass T1 = A X, T2 = A^T T1
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dt", ["f64", "f32", "bf16", "f16"])
+@pytest.mark.parametrize("m,n,k,p", [(333, 517, 20, 7), (1025, 130, 60, 4), (129, 2049, 9, 1)])
+def test_power_pass_elementwise(nat, dt, m, n, k, p):
+    l = k + p
+    g = np.random.default_rng(m + n)
+    A64 = g.standard_normal((m, n))
+    store, exact = inputs.to_storage(A64, dt)
+    X64 = g.standard_normal((n, l))
+    xd = torch.float64 if dt == "f64" else torch.float32
+    X = torch.from_numpy(np.ascontiguousarray(X64.T)).to(xd).cuda().T
+    T1, T2 = nat.power_pass(cuda_colmajor(store, dt), X, k, p, dtype=dt)
+    torch.cuda.synchronize()
+    Xr = oph.round_to(to_np(X), dt)                       # the operand the GPU multiplies by
+    T1o = exact @ Xr
+    T2o = exact.T @ oph.round_to(T1o, dt)
+    e1 = np.linalg.norm(to_np(T1) - T1o) / np.linalg.norm(T1o)
+    e2 = np.linalg.norm(to_np(T2) - T2o) / np.linalg.norm(T2o)
+    tol1 = 1e-14 if dt == "f64" else 1e-6
+    tol2 = 1e-14 if dt == "f64" else (1e-6 if dt == "f32" else 2e-3)   # 16-bit T1 operand
+    assert e1 <= tol1 and e2 <= tol2, (e1, e2)
+
+
+# ---------------------------------------------------------------------------
+# stage 4: core M = Q1^T A Q2
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dt,flags,tol", [("f64", 0, 1e-13), ("f32", 0, 2e-6), ("bf16", 0, 6e-3),
+                                          ("bf16", 2, 2e-6), ("f16", 0, 1e-3), ("f16", 2, 2e-6)])
+def test_core_elementwise(nat, dt, flags, tol):
+    m, n, k, p = 700, 300, 30, 5
+    l = k + p
+    g = np.random.default_rng(5)
+    store, exact = inputs.to_storage(g.standard_normal((m, n)), dt)
+    Q1, _ = np.linalg.qr(g.standard_normal((m, l)))
+    Q2, _ = np.linalg.qr(g.standard_normal((n, l)))
+    qd = torch.float64 if dt == "f64" else torch.float32
+    tq1 = torch.from_numpy(np.ascontiguousarray(Q1.T)).to(qd).cuda().T
+    tq2 = torch.from_numpy(np.ascontiguousarray(Q2.T)).to(qd).cuda().T
+    M = nat.core(cuda_colmajor(store, dt), tq1, tq2, k, p, dtype=dt, flags=flags)
+    torch.cuda.synchronize()
+    Mo = to_np(tq1).T @ exact @ to_np(tq2)
+    err = np.linalg.norm(to_np(M) - Mo) / np.linalg.norm(Mo)
+    assert err <= tol, err
+
+
+# ---------------------------------------------------------------------------
+# whole path
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("q", [0, 1])
+def test_run_cfg1_f64(nat, q):
+    A64, s, _, _ = inputs.cfg1(seed=0)
+    exact, got, ref = run_both(nat, A64, 20, 5, q, 0, "f64")
+    r_gpu, r_orc, ds = gates(exact, got, ref)
+    assert abs(r_gpu - r_orc) <= TOL["f64"] and ds <= TOL["f64"], (r_gpu, r_orc, ds)
+    assert r_orc >= oracle.eckart_young(s, 20)[1] / np.linalg.norm(exact) * (1 - 1e-12)
+
+
+def test_run_literal_power_f64(nat):
+    A64, s, _, _ = inputs.cfg1(seed=1, n=600)
+    exact, got, ref = run_both(nat, A64, 20, 5, 1, 4, "f64", flags=nat.FLAG_LITERAL_POWER, mode="literal")
+    r_gpu, r_orc, ds = gates(exact, got, ref)
+    assert abs(r_gpu - r_orc) <= 1e-10 and ds <= 1e-10
+
+
+@pytest.mark.parametrize("dt", ["f32", "tf32"])
+def test_run_noisy_poly_fp32(nat, dt):
+    A64, s, _, _ = inputs.noisy_poly(3000, 1500, 200, 1e-3, seed=2)
+    exact, got, ref = run_both(nat, A64, 40, 10, 1, 7, dt)
+    r_gpu, r_orc, ds = gates(exact, got, ref)
+    assert abs(r_gpu - r_orc) <= TOL[dt] and ds <= TOL[dt], (r_gpu, r_orc, ds)
+
+
+@pytest.mark.parametrize("dt", ["bf16", "f16"])
+@pytest.mark.parametrize("refine", [False, True])
+def test_run_16bit(nat, dt, refine):
+    A64, s, _, _ = inputs.spectral(2048, 1024, inputs.sigma_exp(300, 20.0), seed=3)
+    flags = nat.FLAG_REFINE if refine else 0
+    exact, got, ref = run_both(nat, A64, 32, 8, 2, 1, dt, flags=flags)
+    r_gpu, r_orc, ds = gates(exact, got, ref)
+    assert abs(r_gpu - r_orc) <= TOL[dt] and ds <= TOL[dt], (r_gpu, r_orc, ds)
+
+
+@pytest.mark.parametrize("dt,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_run_exact_recovery(nat, dt, tol):
+    A64 = inputs.exact_rank(900, 700, 10, seed=8)
+    exact, got, ref = run_both(nat, A64, 10, 6, 1, 2, dt)
+    r_gpu, r_orc, ds = gates(exact, got, ref)
+    assert r_gpu <= tol and ds <= tol, (r_gpu, ds)
+
+
+@pytest.mark.parametrize("m,n,k,p,q", [(300, 200, 1, 0, 0), (150, 150, 100, 50, 1), (200, 900, 17, 3, 2),
+                                       (1, 1, 1, 0, 0), (257, 65, 64, 1, 1)])
+def test_run_edge_shapes_f64(nat, m, n, k, p, q):
+    g = np.random.default_rng(m * n + k)
+    A64 = g.standard_normal((m, n)) * np.logspace(0, -4, n)[None, :]
+    exact, got, ref = run_both(nat, A64, k, p, q, 5, "f64")
+    r_gpu, r_orc, ds = gates(exact, got, ref)
+    assert abs(r_gpu - r_orc) <= 1e-10 and ds <= 1e-10, (r_gpu, r_orc, ds)
+
+
+def test_run_row_major_input_swaps_factors(nat):
+    A64, s, _, _ = inputs.spectral(500, 800, inputs.sigma_poly(500), seed=4)
+    At = torch.from_numpy(A64).cuda()                    # row-major m x n
+    U, S, V = nat.run(At, 10, 5, 1, seed=3, check=True)
+    assert U.shape == (500, 10) and V.shape == (800, 10)
+    # the row-major tensor is stored as A^T column-major: the oracle of A^T
+    Uo, So, Vo = oracle.sorsvd(A64.T, 10, 5, 1, 3)
+    r = oracle.recon_error_fro(A64, to_np(U), to_np(S), to_np(V)) / np.linalg.norm(A64)
+    r_o = oracle.recon_error_fro(A64.T, Uo, So, Vo) / np.linalg.norm(A64)
+    assert abs(r - r_o) <= 1e-10
+
+
+def test_device_status_clean_and_sweeps_reported(nat):
+    A64, s, _, _ = inputs.cfg1(seed=0, n=400)
+    A = cuda_colmajor(np.asfortranarray(A64), "f64")
+    ws = nat.alloc_workspace(400, 400, 10, 5, "f64")
+    nat.run(A, 10, 5, 1, seed=0, workspace=ws)
+    st, info = nat.get_status(ws)
+    assert st == 0
+    assert 1 <= (info >> 8) & 0xFF < 40
+
+
+def test_workspace_errors(nat):
+    A = torch.zeros(100, 80, dtype=torch.float64, device="cuda").T.contiguous().T
+    ws = torch.empty(64, dtype=torch.uint8, device="cuda")
+    with pytest.raises(nat.SorsvdError) as e:
+        nat.run(A, 5, 5, 0, workspace=ws)
+    assert e.value.code == 7
+
+
+# ---------------------------------------------------------------------------
+# full size: the configuration bench.py times (20000 x 10000 fp32, k=100,
+# p=10, q=1), whole oracle in binary64 on the host
+# ---------------------------------------------------------------------------
+
+def test_run_cfg2_full_size(nat):
+    A64, s, _, _ = inputs.cfg2(seed=0)
+    exact, got, ref = run_both(nat, A64, 100, 10, 1, 0, "f32")
+    r_gpu, r_orc, ds = gates(exact, got, ref)
+    assert abs(r_gpu - r_orc) <= 1e-5 and ds <= 1e-5, (r_gpu, r_orc, ds)
