@@ -10,9 +10,16 @@
 // not safely positive restarts the factorisation with a larger shift
 // (recorded in the status info bits); zero columns of T stay zero.
 //
-// One thread block; L is kept packed (row-major lower triangle) in shared
-// memory in the factor precision F (binary64 or fp32):
-// l <= SORSVD_MAX_L_F64 / SORSVD_MAX_L.
+// One thread block, the factor packed (row-major lower triangle) in shared
+// memory in the factor precision F (binary64 or fp32);
+// l <= SORSVD_MAX_L_F64 / SORSVD_MAX_L.  Both phases need one block-wide
+// barrier per column:
+//   factorisation, right-looking without the square roots:
+//     a_ic -= a_ij a_cj / a_jj  (j < c <= i),  then l_ij = a_ij / sqrt(a_jj);
+//   inverse, in place, row-oriented: with X = L^{-1} diag(L) kept unscaled
+//   (unit diagonal), after row i of X is final every later row r takes
+//     x_rj -= (l_ri / l_ii) x_ij  (j <= i),
+//   and finally Linv_ij = x_ij / l_ii.
 #include "internal.cuh"
 
 namespace sorsvd {
@@ -27,14 +34,14 @@ __global__ void __launch_bounds__(CT)
 chol_inv_kernel(const double* __restrict__ G, int l, double shift_rel, F* __restrict__ Rinv,
                 DeviceStatus* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  F* L = reinterpret_cast<F*>(smem_raw);
-  F* tmp = L + (l * (l + 1) / 2);
+  F* P = reinterpret_cast<F*>(smem_raw);
+  F* dg = P + (l * (l + 1) / 2);                                  // diagonal of L
   const size_t dofs = (sizeof(F) * ((size_t)l * (l + 1) / 2 + l + 2) + 7) & ~(size_t)7;
-  double* dscale = reinterpret_cast<double*>(smem_raw + dofs);  // D^{-1/2}
-  __shared__ int s_fail;
+  double* dscale = reinterpret_cast<double*>(smem_raw + dofs);     // D^{-1/2}
   __shared__ int s_retry;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarps = CT / 32;
-  const double eps = sizeof(F) == 8 ? 2.220446049250313e-16 : 1.1920928955078125e-07;
+  const F eps = sizeof(F) == 8 ? (F)2.220446049250313e-16 : (F)1.1920928955078125e-07;
+  const F thr = (F)4 * eps;
 
   for (int i = t; i < l; i += CT) {
     double d = G[i + (int64_t)i * l];
@@ -47,46 +54,34 @@ chol_inv_kernel(const double* __restrict__ G, int l, double shift_rel, F* __rest
   const int max_try = 12;
   int attempt = 0;
   for (; attempt < max_try; ++attempt) {
-    for (int e = t; e < l * (l + 1) / 2; e += CT) {
-      // packed (i, c), c <= i
-      int i = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
-      while (i * (i + 1) / 2 > e) --i;
-      while ((i + 1) * (i + 2) / 2 <= e) ++i;
-      int c = e - i * (i + 1) / 2;
-      double v;
-      if (dscale[i] == 0.0 || dscale[c] == 0.0) v = (i == c) ? 1.0 : 0.0;   // zero column
-      else v = G[i + (int64_t)c * l] * dscale[i] * dscale[c] + (i == c ? shift : 0.0);
-      L[e] = (F)v;
+    for (int i = warp; i < l; i += nwarps) {
+      const double si = dscale[i];
+      F* row = P + pidx(i, 0);
+      for (int c = lane; c <= i; c += 32) {
+        const double sc = dscale[c];
+        double v;
+        if (si == 0.0 || sc == 0.0) v = (i == c) ? 1.0 : 0.0;       // zero column of T
+        else v = G[i + (int64_t)c * l] * si * sc + (i == c ? shift : 0.0);
+        row[c] = (F)v;
+      }
     }
-    if (t == 0) s_fail = 0;
     __syncthreads();
+    bool fail = false;
     for (int j = 0; j < l; ++j) {
-      if (t == 0) {
-        F d = L[pidx(j, j)];
-        if (!(d > (F)(4.0 * eps))) s_fail = 1;
-        else L[pidx(j, j)] = sqrt(d);
-      }
-      __syncthreads();
-      if (s_fail) break;
-      F piv = L[pidx(j, j)];
-      for (int i = j + 1 + t; i < l; i += CT) {
-        F v = L[pidx(i, j)] / piv;
-        L[pidx(i, j)] = v;
-        tmp[i] = v;
-      }
-      __syncthreads();
-      // trailing update: L[i][c] -= L[i][j] L[c][j], j < c <= i
+      const F d = P[pidx(j, j)];          // final since the previous barrier
+      if (!(d > thr)) { fail = true; break; }   // same decision in every thread
+      const F rinv = (F)1 / d;
       for (int i = j + 1 + warp; i < l; i += nwarps) {
-        F lij = tmp[i];
-        F* row = L + pidx(i, 0);
-        for (int c = j + 1 + lane; c <= i; c += 32) row[c] -= lij * tmp[c];
+        F* row = P + pidx(i, 0);
+        const F aij = row[j] * rinv;
+        for (int c = j + 1 + lane; c <= i; c += 32) row[c] -= aij * P[pidx(c, j)];
       }
       __syncthreads();
     }
-    if (!s_fail) break;
-    shift = fmax(shift * 16.0, 64.0 * eps);
-    if (t == 0) s_retry = 1;
+    if (!fail) break;
     __syncthreads();
+    shift = fmax(shift * 16.0, 64.0 * (double)eps);
+    if (t == 0) s_retry = 1;
   }
   if (attempt == max_try) {
     if (t == 0) raise_status(status, SORSVD_ERR_BREAKDOWN);
@@ -95,30 +90,36 @@ chol_inv_kernel(const double* __restrict__ G, int l, double shift_rel, F* __rest
   }
   if (t == 0 && s_retry) atomicOr(&status->info, 1);
 
-  // in-place inverse of the lower factor, last column first:
-  // Linv[j][j] = 1/L[j][j];  Linv[i][j] = -(sum_{k=j+1}^{i} Linv[i][k] L[k][j]) / L[j][j]
-  for (int j = l - 1; j >= 0; --j) {
-    for (int k = j + 1 + t; k < l; k += CT) tmp[k] = L[pidx(k, j)];
-    F dinv = (F)1 / L[pidx(j, j)];
-    __syncthreads();
-    for (int i = j + 1 + warp; i < l; i += nwarps) {
-      const F* row = L + pidx(i, 0);
-      F s = 0;
-      for (int k = j + 1 + lane; k <= i; k += 32) s += row[k] * tmp[k];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) L[pidx(i, j)] = -s * dinv;
+  // scale the columns: l_ij = a_ij / sqrt(a_jj); keep diag(L) aside and put
+  // the unit diagonal of X in its place
+  for (int j = t; j < l; j += CT) dg[j] = sqrt(P[pidx(j, j)]);
+  __syncthreads();
+  for (int i = warp; i < l; i += nwarps) {
+    F* row = P + pidx(i, 0);
+    for (int c = lane; c < i; c += 32) row[c] = row[c] / dg[c];
+    if (lane == 0) row[i] = (F)1;
+  }
+  __syncthreads();
+  // in-place inverse, row i of X final at step i
+  for (int i = 0; i + 1 < l; ++i) {
+    const F dinv = (F)1 / dg[i];
+    const F* xi = P + pidx(i, 0);
+    for (int r = i + 1 + warp; r < l; r += nwarps) {
+      F* row = P + pidx(r, 0);
+      const F f = row[i] * dinv;         // l_ri / l_ii, read before the row changes
+      __syncwarp();
+      for (int j = lane; j <= i; j += 32) row[j] = (j == i ? (F)0 : row[j]) - f * xi[j];
     }
-    if (t == 0) L[pidx(j, j)] = dinv;
     __syncthreads();
   }
-  // R^{-1} = D^{-1/2} Linv^T : upper triangular, column-major
+  // R^{-1} = D^{-1/2} Linv^T : upper triangular, column-major;
+  // Linv_cr = x_cr / l_cc
   for (int e = t; e < l * l; e += CT) {
-    int r = e % l, c = e / l;
+    const int r = e % l, c = e / l;
     F v = 0;
     if (r <= c) {
-      double sc = dscale[r] == 0.0 ? 1.0 : dscale[r];
-      v = (F)((double)L[pidx(c, r)] * sc);
+      const double sc = dscale[r] == 0.0 ? 1.0 : dscale[r];
+      v = (F)((double)(P[pidx(c, r)] / dg[c]) * sc);
     }
     Rinv[e] = v;
   }

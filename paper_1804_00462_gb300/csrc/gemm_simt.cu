@@ -156,6 +156,28 @@ __global__ void copy2d_kernel(const T* __restrict__ x, int64_t ldx, T* __restric
   }
 }
 
+// At (cols x rows, ldt) = A^T for column-major A (rows x cols, lda): 32 x 32
+// tiles through shared memory (padded against bank conflicts), coalesced on
+// both sides.
+__global__ void __launch_bounds__(256)
+transpose32_kernel(const float* __restrict__ A, int64_t lda, int64_t rows, int64_t cols, float* __restrict__ At,
+                   int64_t ldt) {
+  __shared__ float tile[32][33];
+  const int64_t r0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+#pragma unroll
+  for (int k = 0; k < 32; k += 8) {
+    const int64_t r = r0 + tx, c = c0 + ty + k;
+    tile[ty + k][tx] = (r < rows && c < cols) ? A[r + c * lda] : 0.f;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 32; k += 8) {
+    const int64_t c = c0 + tx, r = r0 + ty + k;
+    if (c < cols && r < rows) At[c + r * ldt] = tile[tx][ty + k];
+  }
+}
+
 inline int grid_for(int64_t total) {
   int64_t b = (total + 255) / 256;
   int64_t cap = (int64_t)num_sms() * 16;
@@ -209,6 +231,15 @@ cudaError_t launch_convert_f32(const float* x, int64_t ldx, int64_t rows, int64_
     convert_kernel<f16><<<g, 256, 0, st>>>(x, ldx, rows, cols, (f16*)y, ldy, (f16*)lo);
   else
     return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transpose_f32(const float* A, int64_t lda, int64_t rows, int64_t cols, float* At, int64_t ldt,
+                                 cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((cols + 31) / 32));
+  if (grid.y > 65535) return cudaErrorInvalidValue;
+  transpose32_kernel<<<grid, 256, 0, st>>>(A, lda, rows, cols, At, ldt);
   return cudaGetLastError();
 }
 

@@ -92,6 +92,9 @@ cudaError_t launch_reduce_splits(const void* parts, bool parts_f64, int splits, 
 // When `lo` is non-null it also receives round(x - float(y)) (hi/lo split).
 cudaError_t launch_convert_f32(const float* x, int64_t ldx, int64_t rows, int64_t cols,
                                void* y, int64_t ldy, int y_dt, void* lo, cudaStream_t st);
+// At (cols x rows, ldt) = A^T of a column-major fp32 matrix
+cudaError_t launch_transpose_f32(const float* A, int64_t lda, int64_t rows, int64_t cols, float* At, int64_t ldt,
+                                 cudaStream_t st);
 // copy with leading dimensions (same element size)
 cudaError_t launch_copy2d(const void* x, int64_t ldx, void* y, int64_t ldy,
                           int64_t rows, int64_t cols, size_t elem, cudaStream_t st);
@@ -102,11 +105,24 @@ cudaError_t launch_copy2d(const void* x, int64_t ldx, void* y, int64_t ldy,
 cudaError_t launch_chol_inv(const double* G, int l, double shift_rel, void* Rinv, bool f64,
                             DeviceStatus* status, cudaStream_t st);
 
-// jacobi.cu: SVD of the l x l matrix M (binary64 input) by one-sided Jacobi
-// in binary64 (f64) or fp32.  Writes sigma (descending) to S (k entries,
-// S_f64 selects its type), U~ and V~ (l x l, ld = l, same precision as the
-// sweep) with the sign convention of the oracle.  Work buffer: 2 l^2 words.
+// jacobi.cu: SVD of the l x l matrix M (binary64 input): one-sided Jacobi
+// sweeps in binary64 (f64) or fp32, binary64 finish.  Writes sigma
+// (descending) to S (k entries, S_f64 selects its type), U~ and V~ (l x l,
+// ld = l, sweep precision) with the sign convention of the oracle.  Work
+// buffer: jacobi_work_bytes(l).
 cudaError_t launch_jacobi(const double* M, int l, int k, bool f64, void* Ut, void* Vt,
                           void* S, bool S_f64, void* work, DeviceStatus* status, cudaStream_t st);
+size_t jacobi_work_bytes(int l);
+
+// gemm_tc.cu: tensor-core pass over A (tcgen05 + TMA), op(A) = A^T when
+// trans_a.  elt: 0 bf16, 1 fp16, 2 tf32 (fp32 containers).  B is K x N
+// column-major of the same element type.  Writes fp32 C (ldo) and, when
+// out16 is non-null, its 16-bit rounding (out16_kind 1 bf16, 2 fp16).
+// Needs tc_supported() and tc_parts_bytes() of scratch in `parts`.
+bool tc_supported(int elt, const void* A, int64_t lda, const void* B, int64_t ldb, int l);
+size_t tc_parts_bytes(int elt, int64_t M, int64_t N, int64_t K);
+cudaError_t launch_tc_gemm(bool trans_a, int elt, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
+                           const void* B, int64_t ldb, float* out, int64_t ldo, void* out16, int64_t ld16,
+                           int out16_kind, float* parts, DeviceStatus* status, int kcls, cudaStream_t st);
 
 }  // namespace sorsvd

@@ -18,9 +18,18 @@
 #include "profile.cuh"
 
 #include <algorithm>
+#include <cstdlib>
 
 namespace sorsvd {
 namespace {
+
+// Dispatch knob read once from the environment: SORSVD_TC=0 sends every pass
+// to the CUDA-core kernels.
+int env_flag(const char* name, int dflt) {
+  const char* v = std::getenv(name);
+  return v ? std::atoi(v) : dflt;
+}
+bool tc_enabled() { static const int v = env_flag("SORSVD_TC", 1); return v != 0; }
 
 constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
@@ -40,28 +49,51 @@ int splits_for(int64_t M, int64_t N, int64_t K, int cap) {
 }
 constexpr int kCapBig = 16, kCapSmall = 256;
 
+inline int64_t pad16(int64_t x) { return (x + 15) / 16 * 16; }
+
+// Tensor-core element kind of the passes over A for a dtype: 0 bf16, 1 fp16,
+// 2 tf32 (F32 and TF32 both keep fp32 containers), -1 none (binary64).
+inline int elt_of(int dt) {
+  switch (dt) {
+    case SORSVD_BF16: return 0;
+    case SORSVD_F16: return 1;
+    case SORSVD_TF32: case SORSVD_F32: return 2;
+    default: return -1;
+  }
+}
+
 struct Layout {
-  size_t status, t2op, t2, t1, t1op, q2op, tmp, parts, G, Rinv, M, Ut, Vt, jwork, total;
+  int64_t ldm, ldn;      // leading dimensions of the m x l / n x l sketches
+  size_t status, at, t2op, t2, t1, t1op, q2op, tmp, parts, G, Rinv, M, Ut, Vt, jwork, total;
+  bool has_at;           // fp32 containers: A^T kept for the products A X
 };
 
 Layout make_layout(int64_t m, int64_t n, int l, int dt) {
   Layout L{};
   const size_t acc = acc_size(dt), op = dtype_size(dt);
   const bool h16 = dtype_is_16(dt);
-  const int64_t mx = std::max(m, n);
+  L.ldm = pad16(m);
+  L.ldn = pad16(n);
+  const int64_t ldx = std::max(L.ldm, L.ldn);
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
   L.status = take(sizeof(DeviceStatus));
-  L.t2op = h16 ? take((size_t)n * l * op) : 0;
-  L.t2 = take((size_t)n * l * acc);
+  // TF32 tensor cores read A only K-major (an MN-major TF32 operand gave
+  // all-zero products on GB300), so the fp32-container dtypes keep a
+  // transposed copy A^T (n x m, ld ldn) for T1 = A T2 and W = A Q2.
+  L.has_at = (dt == SORSVD_F32 || dt == SORSVD_TF32);
+  L.at = L.has_at ? take((size_t)L.ldn * m * 4) : 0;
+  L.t2op = h16 ? take((size_t)L.ldn * l * op) : 0;
+  L.t2 = take((size_t)L.ldn * l * acc);
   if (!h16) L.t2op = L.t2;
-  L.t1 = take((size_t)m * l * acc);
-  L.t1op = h16 ? take((size_t)m * l * op) : L.t1;
-  L.q2op = h16 ? take((size_t)2 * n * l * op) : 0;
-  L.tmp = take((size_t)mx * l * acc);
-  // split-K partials: the largest of the big passes and the l x l products
-  // (every gemm() call of the pipeline is listed; an l x l product always
-  // goes through the buffer because its binary64 result is a reduction)
+  L.t1 = take((size_t)L.ldm * l * acc);
+  L.t1op = h16 ? take((size_t)L.ldm * l * op) : L.t1;
+  L.q2op = h16 ? take((size_t)2 * L.ldn * l * op) : 0;
+  L.tmp = take((size_t)ldx * l * acc);
+  // split-K partials of the CUDA-core products and the stream-K partials of
+  // the tensor-core passes share one buffer (never live at the same time);
+  // an l x l product always goes through it because its binary64 result is
+  // a reduction.
   size_t pb = 0;
   auto need = [&](int64_t M, int64_t N, int64_t K, int cap, bool always) {
     int s = splits_for(M, N, K, cap);
@@ -77,13 +109,18 @@ Layout make_layout(int64_t m, int64_t n, int l, int dt) {
     need(m, k, l, kCapBig, false);
     need(n, k, l, kCapBig, false);
   }
+  const int elt = elt_of(dt);
+  if (elt >= 0) {
+    pb = std::max(pb, tc_parts_bytes(elt, m, l, n));
+    pb = std::max(pb, tc_parts_bytes(elt, n, l, m));
+  }
   L.parts = take(pb);
   L.G = take((size_t)l * l * 8);
   L.Rinv = take((size_t)l * l * acc);
   L.M = take((size_t)l * l * 8);
   L.Ut = take((size_t)l * l * acc);
   L.Vt = take((size_t)l * l * acc);
-  L.jwork = take((size_t)2 * l * l * acc);
+  L.jwork = take(jacobi_work_bytes(l));
   L.total = off;
   return L;
 }
@@ -100,7 +137,8 @@ struct Ctx {
 
 #define CK(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) return SORSVD_ERR_CUDA; } while (0)
 
-// C (M x N, ldc) = op(A) B, with split-K through the partial buffer when useful.
+// C (M x N, ldc) = op(A) B on CUDA cores, with split-K through the partial
+// buffer when useful.
 int gemm(const Ctx& c, int kcls, bool trans, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
          int adt, const void* B, int64_t ldb, int bdt, void* C, int64_t ldc, bool c_f64, int cap) {
   const bool accf = c.f64;
@@ -123,60 +161,88 @@ int gemm(const Ctx& c, int kcls, bool trans, int64_t M, int64_t N, int64_t K, co
 // a single launch of class `kcls`
 #define LAUNCH(kcls, expr) do { ProfScope ps_(kcls, c.st); CK(expr); } while (0)
 
-// T (rows x l, ld = rows, accumulator type) <- T R^{-1}, repeated `passes`
-// times (CholeskyQR); the first pass is shifted by shift0.
-int orth(const Ctx& c, void* T, int64_t rows, int l, int passes, double shift0) {
+// One pass over A: C (fp32, M x N) = op(A) B with B in the pass element type,
+// plus an optional 16-bit copy of C.  Tensor cores when the operands allow
+// TMA (16-byte aligned bases and strides), CUDA cores otherwise.
+int pass(const Ctx& c, int kcls, bool trans, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
+         const void* B, int64_t ldb, int bdt, void* C, int64_t ldc, void* C16, int64_t ld16) {
+  const int dt = c.dt;
+  const int elt = elt_of(dt);
+  const bool b_ok = (elt == 2) ? (bdt == SORSVD_F32 || bdt == SORSVD_TF32) : (bdt == dt);
+  if (elt >= 0 && b_ok && tc_enabled()) {
+    // fp32 containers: A X = (A^T)^T X through the transposed copy
+    const bool use_at = (elt == 2 && !trans);
+    const void* Aop = use_at ? c.at(c.L.at) : A;
+    const int64_t ldop = use_at ? c.L.ldn : lda;
+    if ((!use_at || c.L.has_at) && tc_supported(elt, Aop, ldop, B, ldb, (int)N)) {
+      CK(launch_tc_gemm(trans || use_at, elt, M, N, K, Aop, ldop, B, ldb, (float*)C, ldc, C16, ld16,
+                        dt == SORSVD_BF16 ? 1 : 2, (float*)c.at(c.L.parts), c.status(), kcls, c.st));
+      return SORSVD_OK;
+    }
+  }
+  int r = gemm(c, kcls, trans, M, N, K, A, lda, dt, B, ldb, bdt, C, ldc, c.f64, kCapBig);
+  if (r) return r;
+  if (C16) LAUNCH(K_MISC, launch_convert_f32((const float*)C, ldc, M, N, C16, ld16, dt, nullptr, c.st));
+  return SORSVD_OK;
+}
+
+// A^T into the workspace (fp32 containers), once per call that passes over A
+int prepare_at(const Ctx& c, const void* A, int64_t m, int64_t n, int64_t lda) {
+  if (!c.L.has_at || !tc_enabled()) return SORSVD_OK;
+  LAUNCH(K_MISC, launch_transpose_f32((const float*)A, lda, m, n, (float*)c.at(c.L.at), c.L.ldn, c.st));
+  return SORSVD_OK;
+}
+
+// T (rows x l, ld, accumulator type) <- T R^{-1}, repeated `passes` times
+// (CholeskyQR); the first pass is shifted by shift0.
+int orth(const Ctx& c, void* T, int64_t rows, int64_t ld, int l, int passes, double shift0) {
   const int adt = c.f64 ? SORSVD_F64 : SORSVD_F32;
   for (int p = 0; p < passes; ++p) {
-    int r = gemm(c, K_SMALL_GEMM, true, l, l, rows, T, rows, adt, T, rows, adt, c.at(c.L.G), l, true, kCapSmall);
+    int r = gemm(c, K_SMALL_GEMM, true, l, l, rows, T, ld, adt, T, ld, adt, c.at(c.L.G), l, true, kCapSmall);
     if (r) return r;
     LAUNCH(K_CHOL, launch_chol_inv((const double*)c.at(c.L.G), l, p == 0 ? shift0 : 0.0, c.at(c.L.Rinv), c.f64,
                                    c.status(), c.st));
-    r = gemm(c, K_SMALL_GEMM, false, rows, l, l, T, rows, adt, c.at(c.L.Rinv), l, adt, c.at(c.L.tmp), rows, c.f64,
+    r = gemm(c, K_SMALL_GEMM, false, rows, l, l, T, ld, adt, c.at(c.L.Rinv), l, adt, c.at(c.L.tmp), ld, c.f64,
              kCapBig);
     if (r) return r;
-    LAUNCH(K_MISC, launch_copy2d(c.at(c.L.tmp), rows, T, rows, rows, l, acc_size(c.dt), c.st));
+    LAUNCH(K_MISC, launch_copy2d(c.at(c.L.tmp), ld, T, ld, rows, l, acc_size(c.dt), c.st));
   }
   return SORSVD_OK;
 }
 
-// T1 = A X (X given as the operand buffer xop, type of the passes), then
-// T2 = A^T T1 (rounded to 16 bits first for BF16/F16).
+// T1 = A X (X: the operand buffer of the pass type), then T2 = A^T T1 (the
+// 16-bit rounding of T1 for BF16/F16, kept in t1op).
 int power_pass_impl(const Ctx& c, const void* A, int64_t m, int64_t n, int64_t lda, const void* xop,
                     int64_t ldx, int l, void* T1, int64_t ldt1, void* T2, int64_t ldt2) {
-  const int dt = c.dt, adt = c.f64 ? SORSVD_F64 : SORSVD_F32;
-  int r = gemm(c, K_PASS, false, m, l, n, A, lda, dt, xop, ldx, dt, T1, ldt1, c.f64, kCapBig);
+  const int dt = c.dt;
+  const bool h16 = dtype_is_16(dt);
+  const int opdt = c.f64 ? SORSVD_F64 : (h16 ? dt : SORSVD_F32);
+  void* t1op = h16 ? c.at(c.L.t1op) : nullptr;
+  int r = pass(c, K_PASS, false, m, l, n, A, lda, xop, ldx, opdt, T1, ldt1, t1op, c.L.ldm);
   if (r) return r;
-  const void* t1op = T1;
-  int64_t ldop = ldt1;
-  int opdt = adt;
-  if (dtype_is_16(dt)) {
-    LAUNCH(K_MISC, launch_convert_f32((const float*)T1, ldt1, m, l, c.at(c.L.t1op), m, dt, nullptr, c.st));
-    t1op = c.at(c.L.t1op);
-    ldop = m;
-    opdt = dt;
-  }
-  return gemm(c, K_PASS, true, n, l, m, A, lda, dt, t1op, ldop, opdt, T2, ldt2, c.f64, kCapBig);
+  const void* y = h16 ? t1op : T1;
+  const int64_t ldy = h16 ? c.L.ldm : ldt1;
+  return pass(c, K_PASS, true, n, l, m, A, lda, y, ldy, opdt, T2, ldt2, nullptr, 0);
 }
 
 // M (l x l, f64, ldm) = Q1^T (A Q2)
 int core_impl(const Ctx& c, const void* A, int64_t m, int64_t n, int64_t lda, unsigned flags,
               const void* Q1, int64_t ldq1, const void* Q2, int64_t ldq2, int l, double* M, int64_t ldm) {
   const int dt = c.dt, adt = c.f64 ? SORSVD_F64 : SORSVD_F32;
-  const void* q2 = Q2;
-  int64_t ldq = ldq2;
-  int qdt = adt;
+  const int64_t ldw = c.L.ldm;
+  int r;
   if (dtype_is_16(dt) && !(flags & SORSVD_FLAG_REFINE)) {
-    LAUNCH(K_MISC, launch_convert_f32((const float*)Q2, ldq2, n, l, c.at(c.L.q2op), n, dt, nullptr, c.st));
-    q2 = c.at(c.L.q2op);
-    ldq = n;
-    qdt = dt;
+    LAUNCH(K_MISC, launch_convert_f32((const float*)Q2, ldq2, n, l, c.at(c.L.q2op), c.L.ldn, dt, nullptr, c.st));
+    r = pass(c, K_CORE, false, m, l, n, A, lda, c.at(c.L.q2op), c.L.ldn, dt, c.at(c.L.tmp), ldw, nullptr, 0);
+  } else if (dt == SORSVD_TF32) {
+    r = pass(c, K_CORE, false, m, l, n, A, lda, Q2, ldq2, SORSVD_F32, c.at(c.L.tmp), ldw, nullptr, 0);
+  } else {
+    // fp32-accurate product (F32, and BF16/F16 with REFINE: the fp32 Q2
+    // multiplies the stored A exactly, at least as accurate as a hi+lo pair)
+    r = gemm(c, K_CORE, false, m, l, n, A, lda, dt, Q2, ldq2, adt, c.at(c.L.tmp), ldw, c.f64, kCapBig);
   }
-  // With REFINE the CUDA-core path multiplies by the fp32 Q2 directly, which
-  // is at least as accurate as the hi+lo pair of the tensor-core path.
-  int r = gemm(c, K_CORE, false, m, l, n, A, lda, dt, q2, ldq, qdt, c.at(c.L.tmp), m, c.f64, kCapBig);
   if (r) return r;
-  return gemm(c, K_SMALL_GEMM, true, l, l, m, Q1, ldq1, adt, c.at(c.L.tmp), m, adt, M, ldm, true, kCapSmall);
+  return gemm(c, K_SMALL_GEMM, true, l, l, m, Q1, ldq1, adt, c.at(c.L.tmp), ldw, adt, M, ldm, true, kCapSmall);
 }
 
 int check_dtype(int dt) { return (dt >= SORSVD_F64 && dt <= SORSVD_F16) ? SORSVD_OK : SORSVD_ERR_DTYPE; }
@@ -251,12 +317,13 @@ int sorsvd_power_pass(const void* A, int64_t m, int64_t n, int64_t lda, int dtyp
   Layout L = make_layout(m, n, l, dtype);
   if (int r = check_ws(workspace, ws_bytes, L)) return r;
   Ctx c{(char*)workspace, L, dtype, dtype == SORSVD_F64, (cudaStream_t)stream};
+  if (int r = prepare_at(c, A, m, n, lda)) return r;
   const void* xop = X;
   int64_t ldop = ldx;
   if (dtype_is_16(dtype)) {
-    LAUNCH(K_MISC, launch_convert_f32((const float*)X, ldx, n, l, c.at(L.t2op), n, dtype, nullptr, c.st));
+    LAUNCH(K_MISC, launch_convert_f32((const float*)X, ldx, n, l, c.at(L.t2op), L.ldn, dtype, nullptr, c.st));
     xop = c.at(L.t2op);
-    ldop = n;
+    ldop = L.ldn;
   }
   return power_pass_impl(c, A, m, n, lda, xop, ldop, l, T1, ldt1, T2, ldt2);
 }
@@ -272,6 +339,7 @@ int sorsvd_core(const void* A, int64_t m, int64_t n, int64_t lda, int dtype, uns
   Layout L = make_layout(m, n, l, dtype);
   if (int r = check_ws(workspace, ws_bytes, L)) return r;
   Ctx c{(char*)workspace, L, dtype, dtype == SORSVD_F64, (cudaStream_t)stream};
+  if (int r = prepare_at(c, A, m, n, lda)) return r;
   return core_impl(c, A, m, n, lda, flags, Q1, ldq1, Q2, ldq2, l, M, ldm);
 }
 
@@ -294,29 +362,33 @@ int sorsvd_run(const void* A, int64_t m, int64_t n, int64_t lda, int k, int p, i
   int r;
 
   CK(cudaMemsetAsync(c.status(), 0, sizeof(DeviceStatus), c.st));
-  LAUNCH(K_GAUSSIAN, launch_gaussian(c.at(L.t2op), n, l, n, seed, 0, dtype, c.st));
+  r = prepare_at(c, A, m, n, lda);
+  if (r) return r;
+  LAUNCH(K_GAUSSIAN, launch_gaussian(c.at(L.t2op), n, l, L.ldn, seed, 0, dtype, c.st));
   for (int i = 1; i <= q + 1; ++i) {
     if (i > 1) {
       if (!(flags & SORSVD_FLAG_LITERAL_POWER)) {
-        r = orth(c, c.at(L.t2), n, l, 1, first_shift(dtype));
+        r = orth(c, c.at(L.t2), n, L.ldn, l, 1, first_shift(dtype));
         if (r) return r;
       }
-      if (h16) LAUNCH(K_MISC, launch_convert_f32((const float*)c.at(L.t2), n, n, l, c.at(L.t2op), n, dtype, nullptr, c.st));
+      if (h16)
+        LAUNCH(K_MISC, launch_convert_f32((const float*)c.at(L.t2), L.ldn, n, l, c.at(L.t2op), L.ldn, dtype, nullptr,
+                                          c.st));
     }
-    r = power_pass_impl(c, A, m, n, lda, c.at(L.t2op), n, l, c.at(L.t1), m, c.at(L.t2), n);
+    r = power_pass_impl(c, A, m, n, lda, c.at(L.t2op), L.ldn, l, c.at(L.t1), L.ldm, c.at(L.t2), L.ldn);
     if (r) return r;
   }
-  r = orth(c, c.at(L.t1), m, l, 3, first_shift(dtype));
+  r = orth(c, c.at(L.t1), m, L.ldm, l, 3, first_shift(dtype));
   if (r) return r;
-  r = orth(c, c.at(L.t2), n, l, 3, first_shift(dtype));
+  r = orth(c, c.at(L.t2), n, L.ldn, l, 3, first_shift(dtype));
   if (r) return r;
-  r = core_impl(c, A, m, n, lda, flags, c.at(L.t1), m, c.at(L.t2), n, l, (double*)c.at(L.M), l);
+  r = core_impl(c, A, m, n, lda, flags, c.at(L.t1), L.ldm, c.at(L.t2), L.ldn, l, (double*)c.at(L.M), l);
   if (r) return r;
   LAUNCH(K_JACOBI, launch_jacobi((const double*)c.at(L.M), l, k, c.f64, c.at(L.Ut), c.at(L.Vt), S, c.f64,
                                   c.at(L.jwork), c.status(), c.st));
-  r = gemm(c, K_SMALL_GEMM, false, m, k, l, c.at(L.t1), m, adt, c.at(L.Ut), l, adt, U, ldu, c.f64, kCapBig);
+  r = gemm(c, K_SMALL_GEMM, false, m, k, l, c.at(L.t1), L.ldm, adt, c.at(L.Ut), l, adt, U, ldu, c.f64, kCapBig);
   if (r) return r;
-  r = gemm(c, K_SMALL_GEMM, false, n, k, l, c.at(L.t2), n, adt, c.at(L.Vt), l, adt, V, ldv, c.f64, kCapBig);
+  r = gemm(c, K_SMALL_GEMM, false, n, k, l, c.at(L.t2), L.ldn, adt, c.at(L.Vt), l, adt, V, ldv, c.f64, kCapBig);
   if (r) return r;
   return SORSVD_OK;
 }

@@ -156,19 +156,12 @@ def to_storage(A: np.ndarray, dtype: str):
 # large builders on the GPU (torch), for full-size runs
 # ----------------------------------------------------------------------------
 
-def _torch_haar(rows, cols, gen, device):
-    import torch
-    Z = torch.randn(rows, cols, generator=gen, device=device, dtype=torch.float32)
-    Q, R = torch.linalg.qr(Z)
-    d = torch.sign(torch.diagonal(R))
-    d[d == 0] = 1
-    return Q * d[None, :]
-
-
 def spectral_torch(m: int, n: int, sigma: np.ndarray, seed: int, device="cuda",
                    noise: float = 0.0, out_dtype=None, chunk: int = 8192):
-    """Column-major A = U diag(sigma) V^T (+ noise) built on the GPU in fp32.
+    """Column-major A = U diag(sigma) V^T (+ noise), product formed on the GPU.
 
+    The Haar factors U (m x r), V (n x r) come from ``haar`` on the host
+    (numpy); the product and the noise are formed on the GPU in fp32.
     Returns a torch tensor ``At`` of shape (n, m), contiguous: the column-major
     storage of A with lda = m, in ``out_dtype`` (default fp32).
     """
@@ -176,8 +169,9 @@ def spectral_torch(m: int, n: int, sigma: np.ndarray, seed: int, device="cuda",
     gen = torch.Generator(device=device)
     gen.manual_seed(seed)
     r = len(sigma)
-    U = _torch_haar(m, r, gen, device)
-    V = _torch_haar(n, r, gen, device)
+    g = rng(seed, 1)
+    U = torch.from_numpy(haar(m, r, g).astype(np.float32)).to(device)
+    V = torch.from_numpy(haar(n, r, g).astype(np.float32)).to(device)
     Vs = V * torch.as_tensor(np.asarray(sigma, np.float32), device=device)[None, :]
     out_dtype = out_dtype or torch.float32
     At = torch.empty(n, m, device=device, dtype=out_dtype)
