@@ -32,10 +32,12 @@ extern "C" {
 #endif
 
 /* Storage / arithmetic type of the passes over A.
- *   F64  : A binary64; every stage in binary64.
- *   F32  : A binary32; passes with fp32-accurate products and fp32
- *          accumulation; Gram partials combined in binary64.
- *   TF32 : A binary32; passes on tensor cores in TF32 with fp32 accumulation.
+ *   F64  : A binary64; every stage in binary64 (CUDA cores).
+ *   F32  : A binary32; the power passes that only steer the subspace run as
+ *          TF32 tensor-core products, the last power pass and the core
+ *          product as fp32-accurate split TF32 products (hi*hi + hi*lo +
+ *          lo*hi); fp32 accumulation, Gram partials combined in binary64.
+ *   TF32 : A binary32; every pass a TF32 tensor-core product.
  *   BF16 : A bfloat16; passes on tensor cores, fp32 accumulation.
  *   F16  : A binary16; as BF16.
  * Outputs U, S, V are binary64 for F64 and binary32 otherwise. */
@@ -109,8 +111,9 @@ int sorsvd_gaussian(void* out, int64_t rows, int64_t cols, int64_t ld,
  *   T1 = A X (m x l),  T2 = A^T T1 (n x l).
  * X is n x l (ldx >= n); X, T1, T2 are binary64 for F64 and binary32
  * otherwise; for BF16/F16 X and T1 are rounded to the 16-bit type before
- * they multiply A, exactly as inside sorsvd_run.  Uses the same workspace
- * as sorsvd_run for the same (m, n, k, p, dtype) with l = k + p. */
+ * they multiply A, exactly as inside sorsvd_run; F32 uses the fp32-accurate
+ * products of the last power pass, TF32 plain TF32 products.  Uses the same
+ * workspace as sorsvd_run for the same (m, n, k, p, dtype) with l = k + p. */
 int sorsvd_power_pass(const void* A, int64_t m, int64_t n, int64_t lda, int dtype,
                       const void* X, int64_t ldx, int l,
                       void* T1, int64_t ldt1, void* T2, int64_t ldt2,

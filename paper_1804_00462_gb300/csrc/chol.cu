@@ -39,11 +39,12 @@ chol_inv_kernel(const double* __restrict__ G, int l, double shift_rel, F* __rest
   const size_t dofs = (sizeof(F) * ((size_t)l * (l + 1) / 2 + l + 2) + 7) & ~(size_t)7;
   double* dscale = reinterpret_cast<double*>(smem_raw + dofs);     // D^{-1/2}
   __shared__ int s_retry;
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarps = CT / 32;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarps = blockDim.x >> 5;
+  const int NT = blockDim.x;
   const F eps = sizeof(F) == 8 ? (F)2.220446049250313e-16 : (F)1.1920928955078125e-07;
   const F thr = (F)4 * eps;
 
-  for (int i = t; i < l; i += CT) {
+  for (int i = t; i < l; i += NT) {
     double d = G[i + (int64_t)i * l];
     dscale[i] = d > 0.0 ? 1.0 / sqrt(d) : 0.0;
   }
@@ -85,14 +86,14 @@ chol_inv_kernel(const double* __restrict__ G, int l, double shift_rel, F* __rest
   }
   if (attempt == max_try) {
     if (t == 0) raise_status(status, SORSVD_ERR_BREAKDOWN);
-    for (int e = t; e < l * l; e += CT) Rinv[e] = (e % l == e / l) ? (F)1 : (F)0;
+    for (int e = t; e < l * l; e += NT) Rinv[e] = (e % l == e / l) ? (F)1 : (F)0;
     return;
   }
   if (t == 0 && s_retry) atomicOr(&status->info, 1);
 
   // scale the columns: l_ij = a_ij / sqrt(a_jj); keep diag(L) aside and put
   // the unit diagonal of X in its place
-  for (int j = t; j < l; j += CT) dg[j] = sqrt(P[pidx(j, j)]);
+  for (int j = t; j < l; j += NT) dg[j] = sqrt(P[pidx(j, j)]);
   __syncthreads();
   for (int i = warp; i < l; i += nwarps) {
     F* row = P + pidx(i, 0);
@@ -114,7 +115,7 @@ chol_inv_kernel(const double* __restrict__ G, int l, double shift_rel, F* __rest
   }
   // R^{-1} = D^{-1/2} Linv^T : upper triangular, column-major;
   // Linv_cr = x_cr / l_cc
-  for (int e = t; e < l * l; e += CT) {
+  for (int e = t; e < l * l; e += NT) {
     const int r = e % l, c = e / l;
     F v = 0;
     if (r <= c) {

@@ -1,12 +1,18 @@
 // Tensor-core passes over A (the dense contractions of Algorithm 3):
 //   T1 = A T2 and W = A Q2   (op(A) = A:   A is MN-major for the MMA)
 //   T2 = A^T T1              (op(A) = A^T: A is K-major for the MMA)
-// D[128 x Npad] tiles accumulate in tensor memory (TMEM) through
-// tcgen05.mma (kind::f16 for bf16/fp16 operands, kind::tf32 for fp32
-// containers), fed by TMA loads into 128-byte-swizzled shared-memory stages.
+// Output tiles of MT x 128 rows x Npad columns accumulate in tensor memory
+// (TMEM) through tcgen05.mma (kind::f16 for bf16/fp16 operands, kind::tf32
+// for fp32 containers), fed by TMA loads into 128-byte-swizzled
+// shared-memory stages.  A stage holds KA "atoms" along K (one atom = one
+// 128-byte swizzle row per matrix row: 64 bf16 / 32 fp32 elements) for each
+// of the MT row blocks, and the matching KA atoms of the skinny operand B,
+// which all MT row blocks share.  KA sets the contiguous run read from each
+// column of a column-major A per stage (KA x 128 bytes); MT = 2 halves the
+// re-reads of B from L2.
 //
 // Work decomposition: a persistent grid of G <= #SM CTAs splits the
-// tiles x K-blocks iteration space into G contiguous ranges ("stream-K"),
+// tiles x K-stages iteration space into G contiguous ranges ("stream-K"),
 // so every SM streams the same share of A whatever the tile count.  A CTA
 // walks its range as segments (one per output tile it touches).  A segment
 // that covers a whole tile is written straight to the output; the at most
@@ -14,11 +20,20 @@
 // per-CTA partial buffer and a fix-up kernel sums them per tile in CTA
 // order: the result is deterministic and uses no atomics.
 //
-// Warp roles (192 threads): warp 0 issues TMA (one lane), warp 1 owns the
-// TMEM allocation and issues MMAs (one lane), warps 2-5 drain accumulators
-// (tcgen05.ld, 32 TMEM lanes per warp) into fp32 output and, optionally, a
-// 16-bit copy used as the next pass's operand.  Accumulators are
-// double-buffered in TMEM when 2 Npad <= 512 columns, so the epilogue of
+// Split mode (ELT 3, fp32 containers, K-major only, MT = 1): a fourth
+// warpgroup splits each staged fp32 tile x into hi = RN_tf32(x), rewritten
+// in place, and lo = x - hi (exact in fp32) next to it, and every K step
+// issues hi*hi + hi*lo + lo*hi TF32 MMAs.  The neglected lo*lo term and the
+// TF32 truncation of lo are below 2^-21 relative and of random sign, so the
+// products carry fp32-level error.
+//
+// Warp roles (224 threads): warp 0 issues the TMA loads of A into a deep
+// ring (HBM latency), warp 6 those of B into a short ring (B is re-read
+// from L2), warp 1 owns the TMEM allocation and issues MMAs (one lane),
+// warps 2-5 drain accumulators (tcgen05.ld, 32 TMEM lanes per warp) into
+// fp32 output and, optionally, a 16-bit copy used as the next pass's
+// operand; in split mode warps 7-10 convert.  Accumulators are
+// double-buffered in TMEM when 2 MT Npad <= 512 columns, so the epilogue of
 // one segment overlaps the MMAs of the next.  Every mbarrier wait is
 // bounded (tc::kWaitCycles); a timeout records SORSVD_ERR_TIMEOUT, stops all
 // roles, waits for the copies and MMAs already issued, frees TMEM and exits.
@@ -27,30 +42,52 @@
 #include "tc_ptx.cuh"
 
 #include <algorithm>
+#include <cstdlib>
 
 namespace sorsvd {
 
 struct TcParams {
   int64_t M, K;          // output rows, reduction length
   int N, Npad, nch, ch0; // output columns, padded, N-chunks of ch0 rows
+  int KA, MT;            // K atoms per stage, 128-row blocks per tile
   int64_t tiles, ipt, total;
   int G;
   int nbuf;
   uint32_t tmem_cols;
-  int stages;
-  uint32_t stage_bytes, a_bytes, tx_bytes;
+  int stages, bstages;   // ring depths: A (from HBM), B (from L2)
+  uint32_t stage_bytes, a_bytes, b_atom, b_bytes, bstage_bytes;
   float* out;
   int64_t ldo;
   void* out16;           // optional 16-bit copy of the output (bf16 / fp16)
   int64_t ld16;
   int out16_kind;        // 0 none, 1 bf16, 2 fp16
-  float* parts;          // G x 2 x 128 x Npad fp32
+  float* parts;          // G x 2 x (128 MT) x Npad fp32
   DeviceStatus* status;
 };
 
 namespace {
 
-constexpr int kThreads = 192;
+constexpr int kThreads = 224;
+constexpr int kThreadsSplit = 352;
+// Split mode drains TMEM every kDrainAtoms K atoms into fp32 registers
+// (round-to-nearest adds): tensor-core accumulation truncates, which over
+// thousands of MMA steps biases long fp32 sums by ~1e-5; short fills bound
+// that bias.  The register accumulator holds up to kAccCols columns.
+constexpr int kDrainAtoms = 4;
+constexpr int kAccCols = 128;
+constexpr uint32_t kAtomBytes = 128u * 128u;   // 128 rows x 128 bytes
+
+// round-to-nearest-even of an fp32 value to TF32 (10 explicit mantissa bits);
+// finite inputs
+__device__ __forceinline__ float rn_tf32(float x) {
+  uint32_t u = __float_as_uint(x);
+  u = (u + 0xFFFu + ((u >> 13) & 1u)) & 0xFFFFE000u;
+  return __uint_as_float(u);
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
 
 __host__ __device__ __forceinline__ int64_t cta_of(int64_t x, int64_t total, int64_t G) {
   // the CTA whose iteration range [c*total/G, (c+1)*total/G) holds x
@@ -63,34 +100,45 @@ __device__ __forceinline__ void store_out(const TcParams& P, int64_t grow, int c
   else if (P.out16_kind == 2) reinterpret_cast<f16*>(P.out16)[grow + (int64_t)col * P.ld16] = __float2half_rn(v);
 }
 
-// ELT: 0 bf16, 1 fp16, 2 tf32.  A_MN: A operand MN-major (op(A) = A).
+// ELT: 0 bf16, 1 fp16, 2 tf32, 3 tf32 split (3 MMAs).  A_MN: A operand
+// MN-major (op(A) = A).
 template <int ELT, bool A_MN>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__((ELT == 3 ? kThreadsSplit : kThreads), 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const TcParams P) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)P.stages * P.stage_bytes);
+  uint8_t* bring = smem + (size_t)P.stages * P.stage_bytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(bring + (size_t)P.bstages * P.bstage_bytes);
   uint64_t* empty = full + P.stages;
-  uint64_t* tfull = empty + P.stages;
+  uint64_t* bfull = empty + P.stages;
+  uint64_t* bempty = bfull + P.bstages;
+  uint64_t* tfull = bempty + P.bstages;
   uint64_t* tempty = tfull + 2;
   uint64_t* done = tempty + 2;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* conv = done + 1;          // split mode: low parts written (per A stage)
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(conv + P.stages);
   volatile int* abortp = reinterpret_cast<volatile int*>(tslot + 1);
 
-  // K elements per stage (one 128-byte swizzle row), K per MMA, MN width of
-  // one swizzle row for the MN-major A boxes
-  constexpr int BK = (ELT == 2) ? 32 : 64;
-  constexpr int KMMA = (ELT == 2) ? 8 : 16;
-  constexpr int AMN = (ELT == 2) ? 32 : 64;
-  constexpr uint32_t AMN_BOX = (uint32_t)BK * 128u;     // bytes of one MN-major A box
+  constexpr bool SPLIT = (ELT == 3);
+  constexpr int AK = (ELT >= 2) ? 32 : 64;              // K elements per atom
+  constexpr int KMMA = (ELT >= 2) ? 8 : 16;             // K per MMA
+  constexpr int AMN = (ELT >= 2) ? 32 : 64;             // MN width of an MN-major box
+  constexpr uint32_t AMN_BOX = (uint32_t)AK * 128u;     // bytes of one MN-major A box
   constexpr uint32_t FMT = (ELT == 0) ? 1u : (ELT == 1 ? 0u : 2u);
+  // accumulator fill length in stages (split mode drains every kDrainAtoms atoms)
+  const int64_t CHUNK = SPLIT ? (int64_t)((kDrainAtoms + P.KA - 1) / P.KA) : ((int64_t)1 << 40);
+  // split mode: the low parts sit right after the hi tiles of each stage
+  const int mrows = 128 * P.MT;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < P.stages; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
+    for (int s = 0; s < P.bstages; ++s) { tc::mbar_init(&bfull[s], 1); tc::mbar_init(&bempty[s], 1); }
     for (int b = 0; b < 2; ++b) { tc::mbar_init(&tfull[b], 1); tc::mbar_init(&tempty[b], 128); }
     tc::mbar_init(done, 1);
+    if (SPLIT)
+      for (int s2 = 0; s2 < P.stages; ++s2) tc::mbar_init(&conv[s2], 4);
     *abortp = 0;
     tc::fence_barrier_init();
   }
@@ -98,7 +146,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     tc::tmem_alloc(tslot, P.tmem_cols);
     tc::tmem_relinquish();
   }
-  if (warp == 0 && lane == 0) { tc::prefetch_tmap(&tmA); tc::prefetch_tmap(&tmB); }
+  if (warp == 0 && lane == 0) tc::prefetch_tmap(&tmA);
+  if (warp == 6 && lane == 0) tc::prefetch_tmap(&tmB);
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = *tslot;
@@ -107,9 +156,9 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   const int64_t it0 = cta * P.total / P.G, it1 = (cta + 1) * P.total / P.G;
 
   if (warp == 0) {
-    // ------------------------------------------------------------ producer
+    // ------------------------------------------------------------ producer of A
     if (lane == 0) {
-      const uint64_t polA = tc::policy_evict_first(), polB = tc::policy_evict_last();
+      const uint64_t polA = tc::policy_evict_first();
       uint32_t stage = 0, phase = 0;
       uint32_t armed = 0;          // bit s: stage s armed and not yet seen consumed
       uint32_t armed_par = 0;      // parity of that armed phase
@@ -119,22 +168,24 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         const int64_t gend = min(it1, (t + 1) * P.ipt);
         for (int64_t kb = g - t * P.ipt; kb < gend - t * P.ipt; ++kb) {
           if (!tc::mbar_wait(&empty[stage], phase ^ 1, abortp)) { ok = false; break; }
-          armed &= ~(1u << stage);
-          tc::mbar_arrive_expect_tx(&full[stage], P.tx_bytes);
+          tc::mbar_arrive_expect_tx(&full[stage], P.a_bytes);
           armed |= 1u << stage;
           armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
           uint8_t* sa = smem + (size_t)stage * P.stage_bytes;
-          uint8_t* sb = sa + P.a_bytes;
-          const int k0 = (int)(kb * BK);
-          if (A_MN) {
+          for (int j = 0; j < P.KA; ++j) {
+            const int k = (int)((kb * P.KA + j) * AK);
+            for (int mt = 0; mt < P.MT; ++mt) {
+              uint8_t* dst = sa + (size_t)(mt * P.KA + j) * kAtomBytes;
+              const int row0 = (int)(t * mrows) + mt * 128;
+              if (A_MN) {
 #pragma unroll
-            for (int j = 0; j < 128 / AMN; ++j)
-              tc::tma_load_2d_hint(sa + j * AMN_BOX, &tmA, &full[stage], (int)(t * 128) + j * AMN, k0, polA);
-          } else {
-            tc::tma_load_2d_hint(sa, &tmA, &full[stage], k0, (int)(t * 128), polA);
+                for (int h = 0; h < 128 / AMN; ++h)
+                  tc::tma_load_2d_hint(dst + h * AMN_BOX, &tmA, &full[stage], row0 + h * AMN, k, polA);
+              } else {
+                tc::tma_load_2d_hint(dst, &tmA, &full[stage], k, row0, polA);
+              }
+            }
           }
-          for (int ch = 0; ch < P.nch; ++ch)
-            tc::tma_load_2d_hint(sb + (size_t)ch * P.ch0 * 128, &tmB, &full[stage], k0, ch * P.ch0, polB);
           if (++stage == (uint32_t)P.stages) { stage = 0; phase ^= 1; }
         }
         g = gend;
@@ -148,46 +199,104 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           }
       }
     }
+  } else if (warp == 6) {
+    // ------------------------------------------------------------ producer of B
+    // the skinny operand comes from L2: a short ring suffices
+    if (lane == 0) {
+      const uint64_t polB = tc::policy_evict_last();
+      uint32_t stage = 0, phase = 0;
+      uint32_t armed = 0, armed_par = 0;
+      bool ok = true;
+      for (int64_t g = it0; g < it1 && ok;) {
+        const int64_t t = g / P.ipt;
+        const int64_t gend = min(it1, (t + 1) * P.ipt);
+        for (int64_t kb = g - t * P.ipt; kb < gend - t * P.ipt; ++kb) {
+          if (!tc::mbar_wait(&bempty[stage], phase ^ 1, abortp)) { ok = false; break; }
+          tc::mbar_arrive_expect_tx(&bfull[stage], P.b_bytes);
+          armed |= 1u << stage;
+          armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
+          uint8_t* sb = bring + (size_t)stage * P.bstage_bytes;
+          for (int j = 0; j < P.KA; ++j) {
+            const int k = (int)((kb * P.KA + j) * AK);
+            for (int ch = 0; ch < P.nch; ++ch)
+              tc::tma_load_2d_hint(sb + (size_t)j * P.b_atom + (size_t)ch * P.ch0 * 128, &tmB, &bfull[stage], k,
+                                   ch * P.ch0, polB);
+          }
+          if (++stage == (uint32_t)P.bstages) { stage = 0; phase ^= 1; }
+        }
+        g = gend;
+      }
+      if (!ok) {
+        for (int s2 = 0; s2 < P.bstages; ++s2)
+          if (armed & (1u << s2)) {
+            const long long t0 = clock64();
+            while (!tc::mbar_try_wait(&bfull[s2], (armed_par >> s2) & 1u) && clock64() - t0 < tc::kWaitCycles) {}
+          }
+      }
+    }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       uint32_t idesc[2];
       idesc[0] = tc::idesc_make(FMT, A_MN, false, 128, P.ch0);
       idesc[1] = tc::idesc_make(FMT, A_MN, false, 128, P.Npad - P.ch0);
-      uint32_t stage = 0, phase = 0;
-      int seg = 0;
+      uint32_t stage = 0, phase = 0, bstage = 0, bphase = 0;
+      int chunk = 0;                 // accumulator fills (TMEM buffer alternation)
       bool ok = true;
       for (int64_t g = it0; g < it1 && ok;) {
         const int64_t t = g / P.ipt;
         const int64_t gend = min(it1, (t + 1) * P.ipt);
-        const int b = (P.nbuf == 2) ? (seg & 1) : 0;
-        const uint32_t use = (P.nbuf == 2) ? (uint32_t)(seg >> 1) : (uint32_t)seg;
-        if (!tc::mbar_wait(&tempty[b], (use & 1u) ^ 1u, abortp)) { ok = false; break; }
-        tc::fence_after_sync();
-        const uint32_t dcol = tbase + (uint32_t)(b * P.Npad);
         const int64_t kb0 = g - t * P.ipt, kb1 = gend - t * P.ipt;
-        for (int64_t kb = kb0; kb < kb1; ++kb) {
-          if (!tc::mbar_wait(&full[stage], phase, abortp)) { ok = false; break; }
+        for (int64_t c0 = kb0; c0 < kb1 && ok; c0 += CHUNK) {
+          const int64_t c1 = min(kb1, c0 + CHUNK);
+          const int b = (P.nbuf == 2) ? (chunk & 1) : 0;
+          const uint32_t use = (P.nbuf == 2) ? (uint32_t)(chunk >> 1) : (uint32_t)chunk;
+          if (!tc::mbar_wait(&tempty[b], (use & 1u) ^ 1u, abortp)) { ok = false; break; }
           tc::fence_after_sync();
-          const uint32_t sa = tc::smem_u32(smem + (size_t)stage * P.stage_bytes);
-          const uint32_t sb = sa + P.a_bytes;
+          const uint32_t dcol = tbase + (uint32_t)(b * P.MT * P.Npad);
+          for (int64_t kb = c0; kb < c1; ++kb) {
+            if (!tc::mbar_wait(&full[stage], phase, abortp)) { ok = false; break; }
+            if (!tc::mbar_wait(&bfull[bstage], bphase, abortp)) { ok = false; break; }
+            if (SPLIT && !tc::mbar_wait(&conv[stage], phase, abortp)) { ok = false; break; }
+            tc::fence_after_sync();
+            const uint32_t sa = tc::smem_u32(smem + (size_t)stage * P.stage_bytes);
+            const uint32_t sb = tc::smem_u32(bring + (size_t)bstage * P.bstage_bytes);
+            for (int j = 0; j < P.KA; ++j) {
 #pragma unroll
-          for (int ks = 0; ks < BK / KMMA; ++ks) {
-            const uint64_t ad = A_MN ? tc::desc_sw128(sa + ks * KMMA * 128, AMN_BOX, 1024)
-                                     : tc::desc_sw128(sa + ks * 32, 16, 1024);
-            const uint32_t acc = (kb > kb0 || ks > 0) ? 1u : 0u;
-            for (int ch = 0; ch < P.nch; ++ch) {
-              const uint64_t bd = tc::desc_sw128(sb + ch * P.ch0 * 128 + ks * 32, 16, 1024);
-              if (ELT == 2) tc::mma_tf32(dcol + ch * P.ch0, ad, bd, idesc[ch], acc);
-              else tc::mma_f16(dcol + ch * P.ch0, ad, bd, idesc[ch], acc);
+              for (int ks = 0; ks < AK / KMMA; ++ks) {
+                const uint32_t acc = (kb > c0 || j > 0 || ks > 0) ? 1u : 0u;
+                for (int mt = 0; mt < P.MT; ++mt) {
+                  const uint32_t aat = sa + (uint32_t)(mt * P.KA + j) * kAtomBytes;
+                  const uint64_t ad = A_MN ? tc::desc_sw128(aat + ks * KMMA * 128, AMN_BOX, 1024)
+                                           : tc::desc_sw128(aat + ks * 32, 16, 1024);
+                  const uint32_t dm = dcol + (uint32_t)(mt * P.Npad);
+                  for (int ch = 0; ch < P.nch; ++ch) {
+                    const uint32_t bat = sb + (uint32_t)j * P.b_atom + (uint32_t)(ch * P.ch0 * 128);
+                    const uint64_t bd = tc::desc_sw128(bat + ks * 32, 16, 1024);
+                    if (SPLIT) {
+                      const uint64_t ad_lo = tc::desc_sw128(aat + P.a_bytes + ks * 32, 16, 1024);
+                      const uint64_t bd_lo = tc::desc_sw128(bat + P.b_bytes + ks * 32, 16, 1024);
+                      tc::mma_tf32(dm + ch * P.ch0, ad, bd, idesc[ch], acc);
+                      tc::mma_tf32(dm + ch * P.ch0, ad, bd_lo, idesc[ch], 1u);
+                      tc::mma_tf32(dm + ch * P.ch0, ad_lo, bd, idesc[ch], 1u);
+                    } else if (ELT == 2) {
+                      tc::mma_tf32(dm + ch * P.ch0, ad, bd, idesc[ch], acc);
+                    } else {
+                      tc::mma_f16(dm + ch * P.ch0, ad, bd, idesc[ch], acc);
+                    }
+                  }
+                }
+              }
             }
+            tc::mma_commit(&empty[stage]);
+            tc::mma_commit(&bempty[bstage]);
+            if (++stage == (uint32_t)P.stages) { stage = 0; phase ^= 1; }
+            if (++bstage == (uint32_t)P.bstages) { bstage = 0; bphase ^= 1; }
           }
-          tc::mma_commit(&empty[stage]);
-          if (++stage == (uint32_t)P.stages) { stage = 0; phase ^= 1; }
+          if (!ok) break;
+          tc::mma_commit(&tfull[b]);
+          ++chunk;
         }
-        if (!ok) break;
-        tc::mma_commit(&tfull[b]);
-        ++seg;
         g = gend;
       }
       // every MMA issued by this thread has completed once `done` flips
@@ -195,45 +304,119 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       const long long t0 = clock64();
       while (!tc::mbar_try_wait(done, 0) && clock64() - t0 < tc::kWaitCycles) {}
     }
-  } else {
-    // ------------------------------------------------------------ epilogue
-    const int q = warp & 3;                    // TMEM lane quarter of this warp
-    const int row = q * 32 + lane;
-    int seg = 0;
-    for (int64_t g = it0; g < it1;) {
+  } else if (SPLIT && warp >= 7) {
+    // ------------------------------------------------------------ converter
+    // hi = RN_tf32(x) rewritten in place (exactly representable, so the MMA
+    // reads it without truncation) and lo = x - hi (exact in fp32) right
+    // after the hi tiles of the stage, for the A and the B tiles of every
+    // K-stage; elementwise, so the 128-byte swizzle of the copies carries over
+    const int ct = threadIdx.x - 224;          // 0..127
+    uint32_t stage = 0, phase = 0, bstage = 0, bphase = 0;
+    bool ok = true;
+    for (int64_t g = it0; g < it1 && ok;) {
       const int64_t t = g / P.ipt;
       const int64_t gend = min(it1, (t + 1) * P.ipt);
-      const int b = (P.nbuf == 2) ? (seg & 1) : 0;
-      const uint32_t use = (P.nbuf == 2) ? (uint32_t)(seg >> 1) : (uint32_t)seg;
-      if (!tc::mbar_wait(&tfull[b], use & 1u, abortp)) break;
-      tc::fence_after_sync();
+      for (int64_t kb = g - t * P.ipt; kb < gend - t * P.ipt; ++kb) {
+        if (!tc::mbar_wait(&full[stage], phase, abortp)) { ok = false; break; }
+        if (!tc::mbar_wait(&bfull[bstage], bphase, abortp)) { ok = false; break; }
+        for (int part = 0; part < 2; ++part) {
+          uint8_t* base = part == 0 ? smem + (size_t)stage * P.stage_bytes : bring + (size_t)bstage * P.bstage_bytes;
+          const uint32_t bytes = part == 0 ? P.a_bytes : P.b_bytes;
+          float4* src = reinterpret_cast<float4*>(base);
+          float4* dst = reinterpret_cast<float4*>(base + bytes);
+          for (uint32_t v = ct; v < bytes / 16; v += 128) {
+            float4 x = src[v], h, r;
+            h.x = rn_tf32(x.x); h.y = rn_tf32(x.y); h.z = rn_tf32(x.z); h.w = rn_tf32(x.w);
+            r.x = x.x - h.x; r.y = x.y - h.y; r.z = x.z - h.z; r.w = x.w - h.w;
+            src[v] = h;
+            dst[v] = r;
+          }
+        }
+        fence_proxy_async();                   // generic writes -> tensor-core reads
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&conv[stage]);
+        if (++stage == (uint32_t)P.stages) { stage = 0; phase ^= 1; }
+        if (++bstage == (uint32_t)P.bstages) { bstage = 0; bphase ^= 1; }
+      }
+      g = gend;
+    }
+  } else if (warp >= 2 && warp <= 5) {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3;                    // TMEM lane quarter of this warp
+    int chunk = 0;
+    bool ok = true;
+    for (int64_t g = it0; g < it1 && ok;) {
+      const int64_t t = g / P.ipt;
+      const int64_t gend = min(it1, (t + 1) * P.ipt);
+      const int64_t kb0 = g - t * P.ipt, kb1 = gend - t * P.ipt;
       const bool whole = (g == t * P.ipt) && (gend == (t + 1) * P.ipt);
-      const int64_t grow = t * 128 + row;
-      const uint32_t taddr = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * P.Npad);
       float* pdst = nullptr;
       if (!whole) {
         const int slot = (t == it0 / P.ipt) ? 0 : 1;
-        pdst = P.parts + ((size_t)cta * 2 + slot) * 128 * P.Npad;
+        pdst = P.parts + ((size_t)cta * 2 + slot) * mrows * P.Npad;
       }
-      for (int c0 = 0; c0 < P.N; c0 += 16) {
-        float v[16];
-        tc::tmem_ld16(taddr + c0, v);
-        tc::tmem_ld_wait();
-        if (whole) {
-          if (grow < P.M) {
+      float accum[SPLIT ? kAccCols : 1];
+      if (SPLIT) {
 #pragma unroll
-            for (int i = 0; i < 16; ++i)
-              if (c0 + i < P.N) store_out(P, grow, c0 + i, v[i]);
+        for (int i = 0; i < (SPLIT ? kAccCols : 1); ++i) accum[i] = 0.f;
+      }
+      for (int64_t c0 = kb0; c0 < kb1; c0 += CHUNK) {
+        const int b = (P.nbuf == 2) ? (chunk & 1) : 0;
+        const uint32_t use = (P.nbuf == 2) ? (uint32_t)(chunk >> 1) : (uint32_t)chunk;
+        if (!tc::mbar_wait(&tfull[b], use & 1u, abortp)) { ok = false; break; }
+        tc::fence_after_sync();
+        for (int mt = 0; mt < P.MT; ++mt) {
+          const uint32_t taddr =
+              tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * P.MT * P.Npad + mt * P.Npad);
+          const int row = mt * 128 + q * 32 + lane;
+          const int64_t grow = t * mrows + row;
+          if (SPLIT) {
+            // drain: round-to-nearest fp32 adds of the partial accumulator
+#pragma unroll
+            for (int cc = 0; cc < (SPLIT ? kAccCols / 16 : 1); ++cc) {
+              if (cc * 16 < P.Npad) {
+                float v[16];
+                tc::tmem_ld16(taddr + cc * 16, v);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int i = 0; i < 16; ++i) accum[cc * 16 + i] += v[i];
+              }
+            }
+          } else {
+            for (int cb = 0; cb < P.N; cb += 16) {
+              float v[16];
+              tc::tmem_ld16(taddr + cb, v);
+              tc::tmem_ld_wait();
+              if (whole) {
+                if (grow < P.M) {
+#pragma unroll
+                  for (int i = 0; i < 16; ++i)
+                    if (cb + i < P.N) store_out(P, grow, cb + i, v[i]);
+                }
+              } else {
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                  if (cb + i < P.N) pdst[row + (size_t)(cb + i) * mrows] = v[i];
+              }
+            }
           }
-        } else {
+        }
+        tc::fence_before_sync();
+        tc::mbar_arrive(&tempty[b]);
+        ++chunk;
+      }
+      if (SPLIT && ok) {
+        // split mode runs with MT = 1
+        const int row = q * 32 + lane;
+        const int64_t grow = t * mrows + row;
 #pragma unroll
-          for (int i = 0; i < 16; ++i)
-            if (c0 + i < P.N) pdst[row + (size_t)(c0 + i) * 128] = v[i];
+        for (int i = 0; i < (SPLIT ? kAccCols : 1); ++i) {
+          if (i < P.N) {
+            if (whole) { if (grow < P.M) store_out(P, grow, i, accum[i]); }
+            else pdst[row + (size_t)i * mrows] = accum[i];
+          }
         }
       }
-      tc::fence_before_sync();
-      tc::mbar_arrive(&tempty[b]);
-      ++seg;
       g = gend;
     }
   }
@@ -248,14 +431,15 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 // Sum the partial segments of every tile touched by more than one CTA, in
 // CTA order, and write the tile to the output.
 __global__ void tc_fixup_kernel(const TcParams P) {
-  const int64_t per_tile = 128 * (int64_t)P.N;
+  const int mrows = 128 * P.MT;
+  const int64_t per_tile = (int64_t)mrows * P.N;
   const int64_t total = P.tiles * per_tile;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t t = e / per_tile;
     const int64_t r = e - t * per_tile;
-    const int col = (int)(r / 128), row = (int)(r - (int64_t)col * 128);
-    const int64_t grow = t * 128 + row;
+    const int col = (int)(r / mrows), row = (int)(r - (int64_t)col * mrows);
+    const int64_t grow = t * mrows + row;
     if (grow >= P.M) continue;
     const int64_t c_first = cta_of(t * P.ipt, P.total, P.G);
     const int64_t c_last = cta_of(t * P.ipt + P.ipt - 1, P.total, P.G);
@@ -264,7 +448,7 @@ __global__ void tc_fixup_kernel(const TcParams P) {
     for (int64_t c = c_first; c <= c_last; ++c) {
       const int64_t head_tile = (c * P.total / P.G) / P.ipt;
       const int slot = (t == head_tile) ? 0 : 1;
-      s += (double)P.parts[((size_t)c * 2 + slot) * 128 * P.Npad + row + (size_t)col * 128];
+      s += (double)P.parts[((size_t)c * 2 + slot) * mrows * P.Npad + row + (size_t)col * mrows];
     }
     store_out(P, grow, col, (float)s);
   }
@@ -314,48 +498,85 @@ cudaError_t launch_typed(const CUtensorMap& ma, const CUtensorMap& mb, const TcP
   cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<ELT, A_MN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  tc_gemm_kernel<ELT, A_MN><<<P.G, kThreads, smem, st>>>(ma, mb, P);
+  tc_gemm_kernel<ELT, A_MN><<<P.G, ELT == 3 ? kThreadsSplit : kThreads, smem, st>>>(ma, mb, P);
   return cudaGetLastError();
 }
 
-}  // namespace
-
-bool tc_supported(int elt, const void* A, int64_t lda, const void* B, int64_t ldb, int l) {
-  const int64_t esz = elt == 2 ? 4 : 2;
-  if (l < 1 || l > 512) return false;
-  if ((reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15)) return false;
-  if ((lda * esz) % 16 || (ldb * esz) % 16) return false;
-  return encode_fn() != nullptr;
+int env_int(const char* name, int dflt) {
+  const char* v = std::getenv(name);
+  return v ? std::atoi(v) : dflt;
 }
 
-// Planned shape of a launch (shared by the launcher and the workspace size).
-TcParams tc_plan(int elt, int64_t M, int64_t N, int64_t K) {
+constexpr uint32_t kSmemBudget = 220u * 1024u;
+
+// Shape of a launch for a given (KA, MT); stages = 0 when it does not fit.
+TcParams shape(int elt, int64_t M, int64_t N, int64_t K, int KA, int MT) {
   TcParams P{};
   P.M = M; P.K = K; P.N = (int)N;
   P.Npad = (int)((N + 15) / 16 * 16);
   if (P.Npad <= 256) { P.nch = 1; P.ch0 = P.Npad; }
   else { P.nch = 2; P.ch0 = (P.Npad / 2 + 15) / 16 * 16; }
-  const int BK = elt == 2 ? 32 : 64;
-  P.tiles = (M + 127) / 128;
-  P.ipt = (K + BK - 1) / BK;
+  P.KA = KA; P.MT = MT;
+  const int AK = elt >= 2 ? 32 : 64;
+  P.tiles = (M + 128 * MT - 1) / (128 * MT);
+  P.ipt = (K + (int64_t)AK * KA - 1) / ((int64_t)AK * KA);
   P.total = P.tiles * P.ipt;
   P.G = (int)std::min<int64_t>(num_sms(), P.total);
   if (P.G < 1) P.G = 1;
-  P.nbuf = (2 * P.Npad <= 512) ? 2 : 1;
+  P.nbuf = (2 * MT * P.Npad <= 512) ? 2 : 1;
   uint32_t cols = 32;
-  while (cols < (uint32_t)(P.nbuf * P.Npad)) cols <<= 1;
+  while (cols < (uint32_t)(P.nbuf * MT * P.Npad)) cols <<= 1;
   P.tmem_cols = cols;
-  P.a_bytes = 128u * 128u;                                   // 128 rows x 128 bytes
-  P.stage_bytes = P.a_bytes + (uint32_t)P.nch * (uint32_t)P.ch0 * 128u;
-  P.tx_bytes = P.stage_bytes;
-  const uint32_t budget = 220u * 1024u;
-  P.stages = (int)std::min<uint32_t>(8u, budget / P.stage_bytes);
+  P.a_bytes = (uint32_t)(MT * KA) * kAtomBytes;
+  P.b_atom = (uint32_t)P.nch * (uint32_t)P.ch0 * 128u;
+  P.b_bytes = (uint32_t)KA * P.b_atom;
+  const uint32_t mult = (elt == 3 ? 2u : 1u);                             // + low parts in split mode
+  P.stage_bytes = mult * P.a_bytes;
+  P.bstage_bytes = mult * P.b_bytes;
+  P.bstages = 2;
+  const uint32_t left = kSmemBudget > P.bstages * P.bstage_bytes ? kSmemBudget - P.bstages * P.bstage_bytes : 0;
+  P.stages = (int)std::min<uint32_t>(12u, left / P.stage_bytes);
+  if (MT * P.Npad > 512 || cols > 512) P.stages = 0;
+  if (elt == 3 && MT != 1) P.stages = 0;
   return P;
+}
+
+}  // namespace
+
+// Planned shape of a launch (shared by the launcher and the workspace size).
+// Default tiling: two 128-row blocks per tile when they fit in TMEM
+// double-buffered (not in split mode), then the most K atoms per stage (the
+// longest contiguous run per column of A, up to 4) that still leaves >= 3
+// stages.  SORSVD_TC_KATOMS and SORSVD_TC_MTILES override the choice.
+TcParams tc_plan(int elt, int64_t M, int64_t N, int64_t K) {
+  const int envKA = env_int("SORSVD_TC_KATOMS", 0), envMT = env_int("SORSVD_TC_MTILES", 0);
+  const int64_t Npad = (N + 15) / 16 * 16;
+  int MT = envMT > 0 ? envMT : ((elt != 3 && 4 * Npad <= 512) ? 2 : 1);
+  if (elt == 3 || MT * Npad > 512 || MT < 1 || MT > 2) MT = 1;
+  TcParams best = shape(elt, M, N, K, 1, MT);
+  if (envKA > 0) {
+    TcParams P = shape(elt, M, N, K, envKA, MT);
+    return P.stages >= 2 ? P : best;
+  }
+  for (int KA = 2; KA <= 4; ++KA) {
+    TcParams P = shape(elt, M, N, K, KA, MT);
+    if (P.stages >= 4) best = P;
+  }
+  return best;
+}
+
+bool tc_supported(int elt, const void* A, int64_t lda, const void* B, int64_t ldb, int l) {
+  const int64_t esz = elt >= 2 ? 4 : 2;
+  if (l < 1 || l > 512) return false;
+  if (elt == 3 && l > kAccCols) return false;       // split mode: register accumulator
+  if ((reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15)) return false;
+  if ((lda * esz) % 16 || (ldb * esz) % 16) return false;
+  return encode_fn() != nullptr;
 }
 
 size_t tc_parts_bytes(int elt, int64_t M, int64_t N, int64_t K) {
   TcParams P = tc_plan(elt, M, N, K);
-  return (size_t)P.G * 2 * 128 * P.Npad * sizeof(float);
+  return (size_t)P.G * 2 * 128 * P.MT * P.Npad * sizeof(float);
 }
 
 cudaError_t launch_tc_gemm(bool trans_a, int elt, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
@@ -364,31 +585,33 @@ cudaError_t launch_tc_gemm(bool trans_a, int elt, int64_t M, int64_t N, int64_t 
   if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
   // an MN-major TF32 operand gave all-zero products on GB300: fp32 products
   // of the form A X go through a transposed copy of A instead
-  if (elt == 2 && !trans_a) return cudaErrorInvalidValue;
+  if (elt >= 2 && !trans_a) return cudaErrorInvalidValue;
   TcParams P = tc_plan(elt, M, N, K);
   if (P.stages < 2) return cudaErrorInvalidValue;
   P.out = out; P.ldo = ldo; P.out16 = out16; P.ld16 = ld16; P.out16_kind = out16 ? out16_kind : 0;
   P.parts = parts; P.status = status;
-  const int BK = elt == 2 ? 32 : 64, AMN = elt == 2 ? 32 : 64;
+  const int AK = elt >= 2 ? 32 : 64, AMN = elt >= 2 ? 32 : 64;
+  const int map_elt = elt == 3 ? 2 : elt;
   CUtensorMap ma, mb;
   // A is stored column-major (inner = rows of A).  op(A) = A^T: MMA rows are
   // columns of A, K runs along A's rows.  op(A) = A: MMA rows are A's rows.
   const int64_t a_rows = trans_a ? K : M, a_cols = trans_a ? M : K;
-  const bool okA = trans_a ? make_map(&ma, A, elt, a_rows, a_cols, lda, (uint32_t)BK, 128u)
-                           : make_map(&ma, A, elt, a_rows, a_cols, lda, (uint32_t)AMN, (uint32_t)BK);
-  const bool okB = make_map(&mb, B, elt, K, N, ldb, (uint32_t)BK, (uint32_t)P.ch0);
+  const bool okA = trans_a ? make_map(&ma, A, map_elt, a_rows, a_cols, lda, (uint32_t)AK, 128u)
+                           : make_map(&ma, A, map_elt, a_rows, a_cols, lda, (uint32_t)AMN, (uint32_t)AK);
+  const bool okB = make_map(&mb, B, map_elt, K, N, ldb, (uint32_t)AK, (uint32_t)P.ch0);
   if (!okA || !okB) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)P.stages * P.stage_bytes + 1024 + 256;
+  const size_t smem = (size_t)P.stages * P.stage_bytes + (size_t)P.bstages * P.bstage_bytes + 1024 + 512;
   cudaError_t e;
   {
     ProfScope ps(kcls, st);
     if (elt == 0) e = trans_a ? launch_typed<0, false>(ma, mb, P, smem, st) : launch_typed<0, true>(ma, mb, P, smem, st);
     else if (elt == 1) e = trans_a ? launch_typed<1, false>(ma, mb, P, smem, st) : launch_typed<1, true>(ma, mb, P, smem, st);
-    else e = launch_typed<2, false>(ma, mb, P, smem, st);
+    else if (elt == 2) e = launch_typed<2, false>(ma, mb, P, smem, st);
+    else e = launch_typed<3, false>(ma, mb, P, smem, st);
   }
   if (e != cudaSuccess) return e;
   // fix-up of tiles split across CTAs (a no-op grid when every tile is whole)
-  const int64_t work = P.tiles * 128 * P.N;
+  const int64_t work = P.tiles * 128 * P.MT * P.N;
   int64_t blocks = (work + 255) / 256;
   if (blocks > (int64_t)num_sms() * 8) blocks = (int64_t)num_sms() * 8;
   ProfScope ps2(K_REDUCE, st);

@@ -4,23 +4,20 @@
 // a relative tolerance; then sigma_j = ||M v_j|| / ||v_j||, U~ = M V diag(sigma)^{-1}.
 //
 // Three kernels:
-//  1. sweeps (one block): W and V in shared memory when 2 l^2 words fit, else
-//     in the caller's work buffer.  Pair schedule: round-robin tournament
-//     (circle method); in each of the N - 1 rounds (N = l rounded up to even)
-//     the N/2 disjoint pairs are independent, one 8-lane group of a warp
-//     rotates each pair, one barrier separates rounds.  Rotations are applied
-//     while a pair's cosine exceeds l * eps of the sweep precision.  The
-//     sweep count is capped; hitting the cap with a cosine above 32 l eps
-//     raises SORSVD_ERR_NOT_CONVERGED.
-//  2. finish (one block per column), binary64: w_j = M v_j, sigma_j =
-//     ||w_j|| / ||v_j||.  sigma_j is a Rayleigh quotient of M^T M, so its error
-//     is quadratic in the departure of v_j from a singular vector: fp32 sweeps
-//     followed by this step give singular values to about 1e-8 of sigma_1,
-//     while fp32 rotations alone leak about 1e-5 of sigma_1 into the small
-//     columns.
-//  3. order (one block): sigma descending (ties by column index), U~ =
-//     w / ||w||, V~ = v / ||v||; sign: the largest-magnitude entry of each
-//     column of U~ is made positive and the matching column of V~ follows.
+//  1. sweeps (one block): W in shared memory when l^2 words fit, else in the
+//     caller's work buffer; round-robin pair schedule (see the kernel).
+//     Rotations are applied while a pair's cosine exceeds l * eps of the
+//     sweep precision.  The sweep count is capped; hitting the cap with a
+//     cosine above 32 l eps raises SORSVD_ERR_NOT_CONVERGED.
+//  2. finish (one block per column), binary64: from the rotated column
+//     w ~ sigma u: z = M^T u, sigma = ||z||, v = z / sigma, u = M v / sigma.
+//     sigma is a Rayleigh quotient of M M^T, so its error is quadratic in the
+//     departure of u from a singular vector: fp32 sweeps followed by this step
+//     give singular values to about 1e-8 of sigma_1, while fp32 rotations
+//     alone leak about 1e-5 of sigma_1 into the small columns.
+//  3. order (one block): sigma descending (ties by column index); sign: the
+//     largest-magnitude entry of each column of U~ is made positive and the
+//     matching column of V~ follows.
 #include "internal.cuh"
 
 namespace sorsvd {
@@ -37,6 +34,28 @@ __device__ __forceinline__ int rr_player(int pos, int round, int N) {
   return 1 + x;
 }
 
+// Jacobi rotation (c, s) that orthogonalises two columns with squared norms
+// al, be and inner product ga: t = sign(z) / (|z| + sqrt(1 + z^2)),
+// z = (be - al) / (2 ga), c = 1 / sqrt(1 + t^2), s = c t.  For |z| beyond
+// 1e18 (fp32) 1 + z^2 overflows, t becomes 0 and the pair is left as is.
+__device__ __forceinline__ void rotation(float al, float be, float ga, float* c, float* s) {
+  const float z = __fdividef(be - al, 2.f * ga);
+  const float az = fabsf(z);
+  const float t = copysignf(__fdividef(1.f, az + sqrtf(fmaf(az, az, 1.f))), z);
+  const float cs = rsqrtf(fmaf(t, t, 1.f));
+  *c = cs;
+  *s = cs * t;
+}
+__device__ __forceinline__ void rotation(double al, double be, double ga, double* c, double* s) {
+  const double z = (be - al) / (2.0 * ga);
+  const double az = fabs(z);
+  const double root = az > 1.0 ? az * sqrt(1.0 + (1.0 / az) * (1.0 / az)) : sqrt(1.0 + az * az);
+  const double t = (z >= 0.0 ? 1.0 : -1.0) / (az + root);
+  const double cs = 1.0 / sqrt(1.0 + t * t);
+  *c = cs;
+  *s = cs * t;
+}
+
 template <typename J>
 __device__ __forceinline__ J group8_sum(J v, unsigned mask) {
   v += __shfl_xor_sync(mask, v, 4);
@@ -45,28 +64,29 @@ __device__ __forceinline__ J group8_sum(J v, unsigned mask) {
   return v;
 }
 
-template <typename J>
-__global__ void __launch_bounds__(JT)
-jacobi_sweep_kernel(const double* __restrict__ Min, int l, J* __restrict__ Vout, J* __restrict__ gwork,
-                    int in_smem, DeviceStatus* status) {
+// Sweep kernel.  Only W = M V is rotated: the right factor is recovered in
+// binary64 by the finish kernel (v = M^T u / sigma), which halves the work of
+// a rotation.  Pairs follow the round-robin tournament (circle method): in
+// each of the N - 1 rounds of a sweep (N = l rounded up to even) the N/2
+// disjoint pairs are rotated concurrently, one 8-lane group per pair, which
+// keeps the pair's two columns in registers between the inner products and
+// the update; one barrier separates rounds.  EPL: elements per lane (>= l/8).
+template <typename J, bool IN_SMEM, int EPL, int NT>
+__global__ void __launch_bounds__(NT)
+jacobi_sweep_kernel(const double* __restrict__ Min, int l, J* __restrict__ Wout, J* __restrict__ gwork,
+                    DeviceStatus* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_rot, s_big;
-  J* W;
-  J* V;
-  if (in_smem) { W = reinterpret_cast<J*>(smem_raw); V = W + (size_t)l * l; }
-  else { W = gwork; V = gwork + (size_t)l * l; }
+  J* W = IN_SMEM ? reinterpret_cast<J*>(smem_raw) : gwork;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int grp = lane >> 3, gl = lane & 7;
+  const int ngroups = (blockDim.x >> 5) * 4;
   const unsigned gmask = 0xFFu << (grp * 8);
-  const int ngroups = (JT / 32) * 4;
   const J eps = sizeof(J) == 8 ? (J)2.220446049250313e-16 : (J)1.1920928955078125e-07;
   const J tol = (J)l * eps, tol2 = tol * tol;
   const J big = (J)32 * tol, big2 = big * big;
 
-  for (int e = t; e < l * l; e += JT) {
-    W[e] = (J)Min[e];
-    V[e] = (e % l == e / l) ? (J)1 : (J)0;
-  }
+  for (int e = t; e < l * l; e += blockDim.x) W[e] = (J)Min[e];
   __syncthreads();
 
   const int N = (l + 1) & ~1;
@@ -74,45 +94,44 @@ jacobi_sweep_kernel(const double* __restrict__ Min, int l, J* __restrict__ Vout,
   for (sweep = 1; sweep <= kMaxSweeps; ++sweep) {
     if (t == 0) { s_rot = 0; s_big = 0; }
     __syncthreads();
+    int rot_local = 0, big_local = 0;
     for (int r = 0; r < N - 1; ++r) {
       for (int pr = warp * 4 + grp; pr < N / 2; pr += ngroups) {
         const int a = rr_player(pr, r, N), b = rr_player(N - 1 - pr, r, N);
         if (a >= l || b >= l) continue;                // bye (whole group)
-        const int p = min(a, b), q = max(a, b);
-        J* wp = W + (size_t)p * l;
-        J* wq = W + (size_t)q * l;
+        J* wp = W + (size_t)min(a, b) * l;
+        J* wq = W + (size_t)max(a, b) * l;
+        J x[EPL], y[EPL];
         J al = 0, be = 0, ga = 0;
-        for (int i = gl; i < l; i += 8) {
-          const J x = wp[i], y = wq[i];
-          al += x * x; be += y * y; ga += x * y;
+#pragma unroll
+        for (int e = 0; e < EPL; ++e) {
+          const int i = gl + 8 * e;
+          x[e] = (i < l) ? wp[i] : (J)0;
+          y[e] = (i < l) ? wq[i] : (J)0;
+          al += x[e] * x[e]; be += y[e] * y[e]; ga += x[e] * y[e];
         }
-        // xor butterflies leave bitwise-identical sums in all 8 lanes, so
-        // the group takes one decision and one rotation
+        // xor butterflies leave bitwise-identical sums in all 8 lanes, so the
+        // group takes one decision and one rotation
         al = group8_sum(al, gmask); be = group8_sum(be, gmask); ga = group8_sum(ga, gmask);
         if (!(ga * ga > tol2 * al * be)) continue;
-        if (gl == 0 && ga * ga > big2 * al * be) s_big = 1;
-        const J zeta = (be - al) / ((J)2 * ga);
-        const J az = fabs(zeta);
-        const J root = az > (J)1 ? az * sqrt((J)1 + ((J)1 / az) * ((J)1 / az)) : sqrt((J)1 + az * az);
-        const J tt = (zeta >= (J)0 ? (J)1 : (J)-1) / (az + root);
-        const J cs = (J)1 / sqrt((J)1 + tt * tt);
-        const J sn = cs * tt;
-        for (int i = gl; i < l; i += 8) {
-          const J x = wp[i], y = wq[i];
-          wp[i] = cs * x - sn * y;
-          wq[i] = sn * x + cs * y;
+        if (ga * ga > big2 * al * be) big_local = 1;
+        J cs, sn;
+        rotation(al, be, ga, &cs, &sn);
+#pragma unroll
+        for (int e = 0; e < EPL; ++e) {
+          const int i = gl + 8 * e;
+          if (i < l) {
+            wp[i] = cs * x[e] - sn * y[e];
+            wq[i] = sn * x[e] + cs * y[e];
+          }
         }
-        J* vp = V + (size_t)p * l;
-        J* vq = V + (size_t)q * l;
-        for (int i = gl; i < l; i += 8) {
-          const J x = vp[i], y = vq[i];
-          vp[i] = cs * x - sn * y;
-          vq[i] = sn * x + cs * y;
-        }
-        if (gl == 0) s_rot = 1;
+        rot_local = 1;
       }
       __syncthreads();
     }
+    if (rot_local) s_rot = 1;
+    if (big_local) s_big = 1;
+    __syncthreads();
     const int rot = s_rot, bg = s_big;
     __syncthreads();
     if (!rot) break;
@@ -122,7 +141,7 @@ jacobi_sweep_kernel(const double* __restrict__ Min, int l, J* __restrict__ Vout,
     }
   }
   if (t == 0) atomicOr(&status->info, (min(sweep, kMaxSweeps)) << 8);
-  for (int e = t; e < l * l; e += JT) Vout[e] = V[e];
+  for (int e = t; e < l * l; e += blockDim.x) Wout[e] = W[e];
 }
 
 template <typename J>
@@ -138,41 +157,53 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;
 }
 
-// w_j = M v_j (binary64), sigma_j = ||w_j|| / ||v_j||
+// From a rotated column w_j ~ sigma_j u_j (sweep precision): u = w / ||w||,
+// z = M^T u, sigma_j = ||z||, v_j = z / sigma_j, and the left vector again
+// as M v_j / sigma_j, all in binary64.  sigma_j is a Rayleigh quotient of
+// M M^T, so its error is quadratic in the departure of u from a singular
+// vector.
 template <typename J>
 __global__ void __launch_bounds__(256)
-jacobi_finish_kernel(const double* __restrict__ M, int l, const J* __restrict__ Vin, double* __restrict__ W64,
-                     double* __restrict__ sig, double* __restrict__ vnorm) {
-  __shared__ double v[SORSVD_MAX_L];
+jacobi_finish_kernel(const double* __restrict__ M, int l, const J* __restrict__ Win, double* __restrict__ U64,
+                     double* __restrict__ V64, double* __restrict__ sig) {
+  __shared__ double u[SORSVD_MAX_L];
+  __shared__ double z[SORSVD_MAX_L];
   __shared__ double red[32];
   const int j = blockIdx.x;
-  double nv = 0;
-  for (int i = threadIdx.x; i < l; i += blockDim.x) {
-    const double x = (double)Vin[i + (size_t)j * l];
-    v[i] = x;
-    nv += x * x;
-  }
-  nv = block_sum<J>(nv, red);
   double nw = 0;
   for (int i = threadIdx.x; i < l; i += blockDim.x) {
-    double s = 0;
-    for (int c = 0; c < l; ++c) s += M[i + (size_t)c * l] * v[c];
-    W64[i + (size_t)j * l] = s;
-    nw += s * s;
+    const double x = (double)Win[i + (size_t)j * l];
+    u[i] = x;
+    nw += x * x;
   }
   nw = block_sum<J>(nw, red);
-  if (threadIdx.x == 0) {
-    const double n_v = sqrt(nv);
-    sig[j] = n_v > 0 ? sqrt(nw) / n_v : 0.0;
-    vnorm[j] = n_v;
+  const double inv_nw = nw > 0 ? 1.0 / sqrt(nw) : 0.0;
+  double nz = 0;
+  for (int c = threadIdx.x; c < l; c += blockDim.x) {       // z_c = sum_i M_ic u_i
+    double s = 0;
+    const double* mc = M + (size_t)c * l;
+    for (int i = 0; i < l; ++i) s += mc[i] * u[i];
+    s *= inv_nw;
+    z[c] = s;
+    nz += s * s;
   }
+  nz = block_sum<J>(nz, red);
+  const double sg = sqrt(nz);
+  const double inv_sg = sg > 0 ? 1.0 / sg : 0.0;
+  for (int c = threadIdx.x; c < l; c += blockDim.x) V64[c + (size_t)j * l] = z[c] * inv_sg;
+  __syncthreads();
+  for (int i = threadIdx.x; i < l; i += blockDim.x) {       // u_i = (M v)_i / sigma
+    double s = 0;
+    for (int c = 0; c < l; ++c) s += M[i + (size_t)c * l] * z[c];
+    U64[i + (size_t)j * l] = s * inv_sg * inv_sg;
+  }
+  if (threadIdx.x == 0) sig[j] = sg;
 }
 
 template <typename J, typename TS>
 __global__ void __launch_bounds__(JT)
-jacobi_order_kernel(int l, int k, const double* __restrict__ W64, const J* __restrict__ Vin,
-                    const double* __restrict__ sig, const double* __restrict__ vnorm, J* __restrict__ Ut,
-                    J* __restrict__ Vt, TS* __restrict__ S) {
+jacobi_order_kernel(int l, int k, const double* __restrict__ U64, const double* __restrict__ V64,
+                    const double* __restrict__ sig, J* __restrict__ Ut, J* __restrict__ Vt, TS* __restrict__ S) {
   __shared__ int s_order[SORSVD_MAX_L];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarps = JT / 32;
   for (int c = t; c < l; c += JT) {
@@ -187,14 +218,12 @@ jacobi_order_kernel(int l, int k, const double* __restrict__ W64, const J* __res
   __syncthreads();
   for (int j = warp; j < l; j += nwarps) {
     const int c = s_order[j];
-    const double sg = sig[c], nv = vnorm[c];
-    const double uinv = (sg > 0.0 && nv > 0.0) ? 1.0 / (sg * nv) : 0.0;
-    const double vinv = nv > 0.0 ? 1.0 / nv : 0.0;
-    const double* wc = W64 + (size_t)c * l;
+    const double* uc = U64 + (size_t)c * l;
+    const double* vc = V64 + (size_t)c * l;
     double best = -1;
     int bi = l;
     for (int i = lane; i < l; i += 32) {
-      const double a = fabs(wc[i]);
+      const double a = fabs(uc[i]);
       if (a > best) { best = a; bi = i; }
     }
 #pragma unroll
@@ -203,40 +232,63 @@ jacobi_order_kernel(int l, int k, const double* __restrict__ W64, const J* __res
       const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
       if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
     }
-    const double sgn = (bi < l && wc[bi] < 0.0) ? -1.0 : 1.0;
+    const double sgn = (bi < l && uc[bi] < 0.0) ? -1.0 : 1.0;
     for (int i = lane; i < l; i += 32) {
-      Ut[(size_t)j * l + i] = (J)(sgn * wc[i] * uinv);
-      Vt[(size_t)j * l + i] = (J)(sgn * (double)Vin[(size_t)c * l + i] * vinv);
+      Ut[(size_t)j * l + i] = (J)(sgn * uc[i]);
+      Vt[(size_t)j * l + i] = (J)(sgn * vc[i]);
     }
-    if (lane == 0 && j < k) S[j] = (TS)sg;
+    if (lane == 0 && j < k) S[j] = (TS)sig[c];
   }
+}
+
+template <typename J, bool IN_SMEM>
+cudaError_t launch_sweep(const double* M, int l, J* wout, J* gwork, size_t smem, DeviceStatus* status,
+                         cudaStream_t st) {
+  const int epl = (l + 7) / 8;
+  // block size from the per-lane register footprint (2 EPL words per lane)
+#define SWEEP(E)                                                                                      \
+  {                                                                                                   \
+    constexpr int NT = (E * sizeof(J) <= 64) ? 1024 : ((E * sizeof(J) <= 160) ? 512 : 256);          \
+    if (IN_SMEM) {                                                                                    \
+      cudaError_t e = cudaFuncSetAttribute(jacobi_sweep_kernel<J, IN_SMEM, E, NT>,                   \
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); \
+      if (e != cudaSuccess) return e;                                                                 \
+    }                                                                                                 \
+    jacobi_sweep_kernel<J, IN_SMEM, E, NT><<<1, NT, smem, st>>>(M, l, wout, gwork, status);          \
+    return cudaGetLastError();                                                                        \
+  }
+  if (epl <= 4) SWEEP(4)
+  if (epl <= 8) SWEEP(8)
+  if (epl <= 16) SWEEP(16)
+  if (epl <= 24) SWEEP(24)
+  if (epl <= 32) SWEEP(32)
+  SWEEP(40)
+#undef SWEEP
 }
 
 template <typename J, typename TS>
 cudaError_t run_all(const double* M, int l, int k, void* Ut, void* Vt, void* S, void* work, DeviceStatus* status,
                     cudaStream_t st) {
-  // work: [sweep W,V fallback: 2 l^2 J][V out: l^2 J][W64: l^2 f64][sig, vnorm: 2 l f64]
+  // work: [sweep W fallback: l^2 J][W out: l^2 J][U64, V64: 2 l^2 f64][sig: l f64]
   char* w = static_cast<char*>(work);
   J* gwork = reinterpret_cast<J*>(w);
-  J* vout = gwork + 2 * (size_t)l * l;
-  double* w64 = reinterpret_cast<double*>(w + ((3 * (size_t)l * l * sizeof(J) + 15) & ~(size_t)15));
-  double* sig = w64 + (size_t)l * l;
-  double* vn = sig + l;
-  const size_t need = 2 * (size_t)l * l * sizeof(J);
-  const int in_smem = need <= 200 * 1024 ? 1 : 0;
-  cudaError_t e = cudaFuncSetAttribute(jacobi_sweep_kernel<J>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       200 * 1024);
+  J* wout = gwork + (size_t)l * l;
+  double* u64 = reinterpret_cast<double*>(w + ((2 * (size_t)l * l * sizeof(J) + 15) & ~(size_t)15));
+  double* v64 = u64 + (size_t)l * l;
+  double* sig = v64 + (size_t)l * l;
+  const size_t need = (size_t)l * l * sizeof(J);
+  cudaError_t e = (need <= 200 * 1024) ? launch_sweep<J, true>(M, l, wout, gwork, need, status, st)
+                                       : launch_sweep<J, false>(M, l, wout, gwork, 0, status, st);
   if (e != cudaSuccess) return e;
-  jacobi_sweep_kernel<J><<<1, JT, in_smem ? need : 0, st>>>(M, l, vout, gwork, in_smem, status);
-  jacobi_finish_kernel<J><<<l, 256, 0, st>>>(M, l, vout, w64, sig, vn);
-  jacobi_order_kernel<J, TS><<<1, JT, 0, st>>>(l, k, w64, vout, sig, vn, (J*)Ut, (J*)Vt, (TS*)S);
+  jacobi_finish_kernel<J><<<l, 256, 0, st>>>(M, l, wout, u64, v64, sig);
+  jacobi_order_kernel<J, TS><<<1, JT, 0, st>>>(l, k, u64, v64, sig, (J*)Ut, (J*)Vt, (TS*)S);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 size_t jacobi_work_bytes(int l) {
-  return ((3 * (size_t)l * l * sizeof(double) + 15) & ~(size_t)15) + (size_t)l * l * 8 + 2 * (size_t)l * 8;
+  return ((2 * (size_t)l * l * sizeof(double) + 15) & ~(size_t)15) + 2 * (size_t)l * l * 8 + (size_t)l * 8;
 }
 
 cudaError_t launch_jacobi(const double* M, int l, int k, bool f64, void* Ut, void* Vt, void* S, bool S_f64,

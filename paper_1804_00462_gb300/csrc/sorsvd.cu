@@ -164,14 +164,16 @@ int gemm(const Ctx& c, int kcls, bool trans, int64_t M, int64_t N, int64_t K, co
 // One pass over A: C (fp32, M x N) = op(A) B with B in the pass element type,
 // plus an optional 16-bit copy of C.  Tensor cores when the operands allow
 // TMA (16-byte aligned bases and strides), CUDA cores otherwise.
+// `precise` asks fp32 containers (F32) for fp32-accurate products: the split
+// tensor-core mode (hi*hi + hi*lo + lo*hi TF32 MMAs).
 int pass(const Ctx& c, int kcls, bool trans, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
-         const void* B, int64_t ldb, int bdt, void* C, int64_t ldc, void* C16, int64_t ld16) {
+         const void* B, int64_t ldb, int bdt, void* C, int64_t ldc, void* C16, int64_t ld16, bool precise) {
   const int dt = c.dt;
-  const int elt = elt_of(dt);
-  const bool b_ok = (elt == 2) ? (bdt == SORSVD_F32 || bdt == SORSVD_TF32) : (bdt == dt);
+  const int elt = (precise && dt == SORSVD_F32) ? 3 : elt_of(dt);
+  const bool b_ok = (elt >= 2) ? (bdt == SORSVD_F32 || bdt == SORSVD_TF32) : (bdt == dt);
   if (elt >= 0 && b_ok && tc_enabled()) {
     // fp32 containers: A X = (A^T)^T X through the transposed copy
-    const bool use_at = (elt == 2 && !trans);
+    const bool use_at = (elt >= 2 && !trans);
     const void* Aop = use_at ? c.at(c.L.at) : A;
     const int64_t ldop = use_at ? c.L.ldn : lda;
     if ((!use_at || c.L.has_at) && tc_supported(elt, Aop, ldop, B, ldb, (int)N)) {
@@ -213,16 +215,16 @@ int orth(const Ctx& c, void* T, int64_t rows, int64_t ld, int l, int passes, dou
 // T1 = A X (X: the operand buffer of the pass type), then T2 = A^T T1 (the
 // 16-bit rounding of T1 for BF16/F16, kept in t1op).
 int power_pass_impl(const Ctx& c, const void* A, int64_t m, int64_t n, int64_t lda, const void* xop,
-                    int64_t ldx, int l, void* T1, int64_t ldt1, void* T2, int64_t ldt2) {
+                    int64_t ldx, int l, void* T1, int64_t ldt1, void* T2, int64_t ldt2, bool precise) {
   const int dt = c.dt;
   const bool h16 = dtype_is_16(dt);
   const int opdt = c.f64 ? SORSVD_F64 : (h16 ? dt : SORSVD_F32);
   void* t1op = h16 ? c.at(c.L.t1op) : nullptr;
-  int r = pass(c, K_PASS, false, m, l, n, A, lda, xop, ldx, opdt, T1, ldt1, t1op, c.L.ldm);
+  int r = pass(c, K_PASS, false, m, l, n, A, lda, xop, ldx, opdt, T1, ldt1, t1op, c.L.ldm, precise);
   if (r) return r;
   const void* y = h16 ? t1op : T1;
   const int64_t ldy = h16 ? c.L.ldm : ldt1;
-  return pass(c, K_PASS, true, n, l, m, A, lda, y, ldy, opdt, T2, ldt2, nullptr, 0);
+  return pass(c, K_PASS, true, n, l, m, A, lda, y, ldy, opdt, T2, ldt2, nullptr, 0, precise);
 }
 
 // M (l x l, f64, ldm) = Q1^T (A Q2)
@@ -233,12 +235,13 @@ int core_impl(const Ctx& c, const void* A, int64_t m, int64_t n, int64_t lda, un
   int r;
   if (dtype_is_16(dt) && !(flags & SORSVD_FLAG_REFINE)) {
     LAUNCH(K_MISC, launch_convert_f32((const float*)Q2, ldq2, n, l, c.at(c.L.q2op), c.L.ldn, dt, nullptr, c.st));
-    r = pass(c, K_CORE, false, m, l, n, A, lda, c.at(c.L.q2op), c.L.ldn, dt, c.at(c.L.tmp), ldw, nullptr, 0);
-  } else if (dt == SORSVD_TF32) {
-    r = pass(c, K_CORE, false, m, l, n, A, lda, Q2, ldq2, SORSVD_F32, c.at(c.L.tmp), ldw, nullptr, 0);
+    r = pass(c, K_CORE, false, m, l, n, A, lda, c.at(c.L.q2op), c.L.ldn, dt, c.at(c.L.tmp), ldw, nullptr, 0, false);
+  } else if (dt == SORSVD_TF32 || dt == SORSVD_F32) {
+    // TF32: one TF32 product; F32: the split (fp32-accurate) product
+    r = pass(c, K_CORE, false, m, l, n, A, lda, Q2, ldq2, SORSVD_F32, c.at(c.L.tmp), ldw, nullptr, 0, true);
   } else {
-    // fp32-accurate product (F32, and BF16/F16 with REFINE: the fp32 Q2
-    // multiplies the stored A exactly, at least as accurate as a hi+lo pair)
+    // binary64, and BF16/F16 with REFINE: the fp32 Q2 multiplies the stored
+    // A exactly on CUDA cores
     r = gemm(c, K_CORE, false, m, l, n, A, lda, dt, Q2, ldq2, adt, c.at(c.L.tmp), ldw, c.f64, kCapBig);
   }
   if (r) return r;
@@ -325,7 +328,7 @@ int sorsvd_power_pass(const void* A, int64_t m, int64_t n, int64_t lda, int dtyp
     xop = c.at(L.t2op);
     ldop = L.ldn;
   }
-  return power_pass_impl(c, A, m, n, lda, xop, ldop, l, T1, ldt1, T2, ldt2);
+  return power_pass_impl(c, A, m, n, lda, xop, ldop, l, T1, ldt1, T2, ldt2, true);
 }
 
 int sorsvd_core(const void* A, int64_t m, int64_t n, int64_t lda, int dtype, unsigned flags, const void* Q1,
@@ -375,7 +378,9 @@ int sorsvd_run(const void* A, int64_t m, int64_t n, int64_t lda, int k, int p, i
         LAUNCH(K_MISC, launch_convert_f32((const float*)c.at(L.t2), L.ldn, n, l, c.at(L.t2op), L.ldn, dtype, nullptr,
                                           c.st));
     }
-    r = power_pass_impl(c, A, m, n, lda, c.at(L.t2op), L.ldn, l, c.at(L.t1), L.ldm, c.at(L.t2), L.ldn);
+    // F32: TF32 products while the power loop only steers the subspace, the
+    // fp32-accurate split products in the last pass that fixes Q1 and Q2
+    r = power_pass_impl(c, A, m, n, lda, c.at(L.t2op), L.ldn, l, c.at(L.t1), L.ldm, c.at(L.t2), L.ldn, i == q + 1);
     if (r) return r;
   }
   r = orth(c, c.at(L.t1), m, L.ldm, l, 3, first_shift(dtype));

@@ -120,10 +120,12 @@ def test_power_pass_elementwise(nat, dt, m, n, k, p):
     # (CUDA-core fallback - TMA needs 16-byte aligned strides - is exact fp32).
     # fp32 products A X read a transposed copy of A (aligned by the library),
     # so only X's leading dimension n decides.
-    fp32c = dt in ("f32", "tf32")
-    esz = 4 if fp32c else 2
+    fp32c = dt == "tf32"            # F32 passes are fp32-accurate (split products)
+    esz = 4 if dt in ("f32", "tf32") else 2
     nn_tc = TC_ON and dt != "f64" and ((n * 4) % 16 == 0 if fp32c else (m * esz) % 16 == 0)
     tn_tc = TC_ON and dt != "f64" and (m * esz) % 16 == 0
+    if dt == "f32":
+        nn_tc = tn_tc = False
     t_nn = trunc_tf32 if (fp32c and nn_tc) else (lambda x: x)
     t_tn = trunc_tf32 if (fp32c and tn_tc) else (lambda x: x)
     Xr = oph.round_to(to_np(X), dt)
@@ -131,8 +133,10 @@ def test_power_pass_elementwise(nat, dt, m, n, k, p):
     T2o = t_tn(exact).T @ t_tn(oph.round_to(T1o, dt))
     e1 = np.linalg.norm(to_np(T1) - T1o) / np.linalg.norm(T1o)
     e2 = np.linalg.norm(to_np(T2) - T2o) / np.linalg.norm(T2o)
-    tol1 = 1e-14 if dt == "f64" else max(1e-6, 5e-8 * np.sqrt(n))    # fp32 accumulation over n
-    tol2 = {"f64": 1e-14, "f32": 1e-4, "tf32": 1e-4, "bf16": 2e-3, "f16": 1e-3}[dt]
+    # fp32 accumulation over K terms: relative error ~ sqrt(K) eps_32
+    tol1 = 1e-14 if dt == "f64" else max(2e-6, 1.5e-7 * np.sqrt(n))
+    tol2 = {"f64": 1e-14, "f32": max(2e-6, 1.5e-7 * (np.sqrt(m) + np.sqrt(n))), "tf32": 1e-4, "bf16": 2e-3,
+            "f16": 1e-3}[dt]
     assert e1 <= tol1 and e2 <= tol2, (e1, e2)
 
 
@@ -140,7 +144,7 @@ def test_power_pass_elementwise(nat, dt, m, n, k, p):
 # stage 4: core M = Q1^T A Q2
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("dt,flags,tol", [("f64", 0, 1e-13), ("f32", 0, 2e-6), ("tf32", 0, 2e-6),
+@pytest.mark.parametrize("dt,flags,tol", [("f64", 0, 1e-13), ("f32", 0, 3e-6), ("tf32", 0, 2e-6),
                                           ("bf16", 0, 6e-3), ("bf16", 2, 2e-6), ("f16", 0, 1e-3),
                                           ("f16", 2, 2e-6)])
 def test_core_elementwise(nat, dt, flags, tol):
