@@ -89,6 +89,29 @@ int sorsvd_run(const void* A, int64_t m, int64_t n, int64_t lda,
                void* U, int64_t ldu, void* S, void* V, int64_t ldv,
                void* workspace, size_t ws_bytes, void* stream);
 
+/* Maximum scratch of sorsvd_run_noalloc: 32 MiB of device memory, held by
+ * every GPU that loads the library for the life of the process. */
+#define SORSVD_NOALLOC_MAX_BYTES 33554432u
+
+/* sorsvd_run without a caller workspace.  The paper has no counterpart: it
+ * is an interface convenience for callers that cannot allocate device
+ * memory when they call - for example code inside a host application that
+ * owns all device memory through its own fixed pool, or latency-critical
+ * loops that cannot afford cudaMalloc's possible device synchronisation.
+ * The caller still provides A, U, S and V (same meaning, layout and errors
+ * as sorsvd_run).  Scratch comes from one library-owned device array of
+ * SORSVD_NOALLOC_MAX_BYTES: problems whose sorsvd_workspace_size exceeds it
+ * return SORSVD_ERR_UNSUPPORTED.  The first call on each device looks the
+ * array up (cudaGetSymbolAddress) with that device current; make it before
+ * any stream capture.  Nothing is allocated or freed.  Every call shares the
+ * array and leaves its contents behind: calls that may overlap on the GPU
+ * (different streams or host threads) race and must be serialised by the
+ * caller.  Device-side status: sorsvd_get_status is not available for this
+ * entry point (the workspace is internal); check the outputs. */
+int sorsvd_run_noalloc(const void* A, int64_t m, int64_t n, int64_t lda,
+                       int k, int p, int q, uint64_t seed, int dtype, unsigned flags,
+                       void* U, int64_t ldu, void* S, void* V, int64_t ldv, void* stream);
+
 /* Copies the device status word of a workspace to the host (synchronous on
  * `stream`).  *device_status receives a sorsvd_status code (SORSVD_OK when
  * the last call finished cleanly); *info receives diagnostic bits
