@@ -149,13 +149,124 @@ int sorsvd_core(const void* A, int64_t m, int64_t n, int64_t lda, int dtype, uns
                 const void* Q1, int64_t ldq1, const void* Q2, int64_t ldq2, int l,
                 double* M, int64_t ldm, void* workspace, size_t ws_bytes, void* stream);
 
+/* R^{-1} of one CholeskyQR step (the QR of the sketches, Sec. III): with
+ * D = diag(G) and G' = D^{-1/2} G D^{-1/2} + s I (s = shift_rel, relative to
+ * the unit diagonal of G'), G' = L L^T and R^{-1} = D^{-1/2} L^{-T}, so that
+ * T R^{-1} has orthonormal columns up to the conditioning of T when
+ * G = T^T T.  A pivot that is not safely positive restarts with a 16x larger
+ * shift (status info bit 0), at most 12 times, then SORSVD_ERR_BREAKDOWN
+ * (R^{-1} = I).  G: l x l binary64, column-major, ld = l.  Rinv: l x l
+ * upper triangular, ld = l, binary64 for dtype F64 and fp32 otherwise.
+ * status: device memory of at least 64 bytes receiving the device status
+ * word (read it with sorsvd_get_status; the call clears it first).
+ * 1 <= l <= SORSVD_MAX_L (SORSVD_MAX_L_F64 for F64). */
+int sorsvd_chol_inv(const double* G, int l, double shift_rel, int dtype, void* Rinv, void* status, void* stream);
+
+/* ---- batched SOR-SVD -------------------------------------------------------
+ * Many independent problems of uneven shape (m, n, k, p, q may all differ)
+ * in one sequence of grouped launches: each launch runs one stage of
+ * Algorithm 3 for every problem, from per-problem job descriptors that a
+ * plan uploads into the workspace once; the plan can capture the launches
+ * in a CUDA graph.  The paper has no batched form: this is the same
+ * algorithm per problem (same Omega, same results up to rounding order as
+ * sorsvd_run with the same arguments, except that every product runs on
+ * CUDA cores in the accumulator precision and the passes over A are not
+ * split into TF32 parts).  dtype: SORSVD_F64, SORSVD_F32 or SORSVD_TF32 (A
+ * binary64 or fp32; U, S, V in the same type).  flags: 0 or
+ * SORSVD_FLAG_LITERAL_POWER.  l = k + p <= min(m, n) and l <= 128 (F64) /
+ * 160 (fp32), else SORSVD_ERR_UNSUPPORTED. */
+typedef struct {
+  const void* A; int64_t m, n, lda;   /* device, column-major */
+  int k, p, q;
+  uint64_t seed;                      /* Omega of this problem (stream 0) */
+  void* U; int64_t ldu;               /* device outputs, as sorsvd_run */
+  void* S;
+  void* V; int64_t ldv;
+} sorsvd_problem;
+
+typedef struct sorsvd_batch_plan sorsvd_batch_plan;
+
+/* Workspace bytes for a batch (host array of descriptors); 0 on bad
+ * arguments.  256-byte aligned device memory. */
+size_t sorsvd_batched_workspace_size(const sorsvd_problem* probs, int batch, int dtype, unsigned flags);
+
+/* Builds a plan: checks every descriptor, lays out the workspace, uploads
+ * the job descriptors (synchronous on `stream`) and, when use_graph != 0,
+ * captures the launches in a CUDA graph (on a private stream).  The plan
+ * keeps pointers to the problems' A, U, S, V and to the workspace: they
+ * must stay valid while the plan is used.  *plan is NULL on error. */
+int sorsvd_batched_plan_create(sorsvd_batch_plan** plan, const sorsvd_problem* probs, int batch, int dtype,
+                               unsigned flags, int use_graph, void* workspace, size_t ws_bytes, void* stream);
+/* Runs the batch on `stream` (graph replay or direct launches); async. */
+int sorsvd_batched_plan_launch(sorsvd_batch_plan* plan, void* stream);
+/* Device status of every problem of the last run (synchronous): codes has
+ * `batch` entries. */
+int sorsvd_batched_plan_status(const sorsvd_batch_plan* plan, int* codes, void* stream);
+/* Kernel launches per run (for accounting). */
+int sorsvd_batched_plan_launches(const sorsvd_batch_plan* plan);
+void sorsvd_batched_plan_destroy(sorsvd_batch_plan* plan);
+/* One-shot: plan (no graph), launch, destroy.  Asynchronous except for the
+ * descriptor upload. */
+int sorsvd_run_batched(const sorsvd_problem* probs, int batch, int dtype, unsigned flags, void* workspace,
+                       size_t ws_bytes, void* stream);
+
+/* ---- robust PCA (Sec. V-C, Table 3) ---------------------------------------
+ * Inexact augmented-Lagrange-multiplier RPCA with SOR-SVD as the low-rank
+ * step ("ALM-SOR-SVD"): splits X = L + S, L of rank <= k and S sparse.  Per
+ * iteration j (mu_j the penalty, lambda = 1 / sqrt(max(m, n))):
+ *   (U, Z, V) = sorsvd_run(X - S_j + Y_j / mu_j; k, p, q, seed + j - 1)
+ *   L = U shrink_{1/mu_j}(Z) V^T ;  S = shrink_{lambda/mu_j}(X - L + Y_j / mu_j)
+ *   Y += mu_j (X - L - S) ;  mu_{j+1} = min(rho mu_j, 1e7 mu_0)
+ * with shrink_e(x) = sgn(x) max(|x| - e, 0), stopping after the first
+ * iteration with ||X - L - S||_F < tol ||X||_F, or after max_iter.  Start:
+ * S = 0, Y = X / max(||X||_2, ||X||_inf / lambda), mu_0 = 1.25 / ||X||_2
+ * (the paper defers these choices to the inexact-ALM literature; the table
+ * prints the mu cap as a maximum, read here as the usual minimum). */
+typedef struct {
+  const float* X;  int64_t m, n, ldx;  /* input, m x n fp32, m, n >= 2 */
+  float* L;        int64_t ldl;        /* output low-rank part, m x n */
+  float* S;        int64_t lds;        /* output sparse part, m x n */
+  double norm2;    /* ||X||_2 if > 0; otherwise estimated on the device by a
+                      rank-1 SOR-SVD of X (p = 9, q = 2) */
+  uint64_t seed;   /* Gaussian seed of the first inner SOR-SVD */
+} sorsvd_rpca_problem;
+
+/* Flag of sorsvd_rpca: run the inner SOR-SVD in `dtype` while the residual
+ * is large and in binary64 once ||X - L - S||_F / ||X||_F < 30 tol.  An
+ * fp32 SOR-SVD leaves about 1e-7 relative error in L, where the iteration
+ * stalls (the ALM residual cannot fall below the error of the low-rank
+ * step); the binary64 finish costs a few iterations. */
+#define SORSVD_RPCA_FINISH_F64 0x100u
+
+/* Workspace bytes for sorsvd_rpca on `batch` problems (host array); 0 on
+ * bad arguments.  256-byte aligned device memory. */
+size_t sorsvd_rpca_workspace_size(const sorsvd_rpca_problem* probs, int batch, int k, int p, int dtype,
+                                  unsigned flags);
+
+/* Runs RPCA on `batch` independent problems (host array of descriptors whose
+ * X, L, S point to device memory).  dtype: the type of the inner SOR-SVD,
+ * SORSVD_F32, SORSVD_TF32 or SORSVD_F64 (its input G = X - S + Y / mu is
+ * then kept in that precision); the RPCA state S, Y is fp32 either way and
+ * the elementwise updates use double-fp32 arithmetic.  flags: 0 or
+ * SORSVD_RPCA_FINISH_F64.  k, p, q as in sorsvd_run (l = k + p <= min(m, n)).
+ * tol > 0, max_iter >= 1, rho >= 1.  SYNCHRONOUS: the host drives the loop
+ * and reads one residual per problem per iteration; returns when every
+ * problem has stopped.  Host outputs: iters[b] iterations run, xi[b] the
+ * last ||X - L - S||_F / ||X||_F, xi_history (optional, batch x max_iter,
+ * row b = problem b) every iteration's value.  Returns SORSVD_OK, an
+ * argument error, or the first device status an inner SOR-SVD raised. */
+int sorsvd_rpca(const sorsvd_rpca_problem* probs, int batch, int k, int p, int q, int dtype, unsigned flags,
+                double tol, int max_iter, double rho, int* iters, double* xi, double* xi_history,
+                void* workspace, size_t ws_bytes, void* stream);
+
 /* ---- launch accounting (host side, no device work) -----------------------
  * Kernel classes: 0 Gaussian, 1 pass over A in the power loop (T1 = A T2 or
  * T2 = A^T T1), 2 pass over A in the core product (A Q2), 3 small
  * tall-skinny products (Gram, T R^{-1}, Q1^T W, output assembly),
- * 4 split-K reductions, 5 Cholesky/inverse, 6 Jacobi SVD, 7 conversions
- * and copies. */
-#define SORSVD_NUM_KCLASS 8
+ * 4 split-K reductions and tile fix-ups, 5 Cholesky/inverse, 6 Jacobi SVD,
+ * 7 conversions, copies and the transposed copy of A, 8 fp32-accurate
+ * (split) power passes, 9 RPCA elementwise kernels. */
+#define SORSVD_NUM_KCLASS 10
 
 /* Number of kernel launches the library has issued in this process. */
 uint64_t sorsvd_launch_count(void);

@@ -18,6 +18,8 @@
 //          then rotated by the quadrant q mod 4.
 #include "internal.cuh"
 
+#include <algorithm>
+
 namespace sorsvd {
 namespace {
 
@@ -95,8 +97,8 @@ __device__ __forceinline__ void sincos_2pi(double u, double* sn, double* cs) {
 }
 
 template <typename T>
-__global__ void gaussian_kernel(T* __restrict__ out, int64_t rows, int64_t cols, int64_t ld,
-                                uint64_t seed, uint64_t stream_id) {
+__device__ __forceinline__ void gaussian_body(T* __restrict__ out, int64_t rows, int64_t cols, int64_t ld,
+                                              uint64_t seed, uint64_t stream_id) {
   const int64_t total = rows * cols;
   const int64_t groups = (total + 3) / 4;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < groups;
@@ -124,6 +126,19 @@ __global__ void gaussian_kernel(T* __restrict__ out, int64_t rows, int64_t cols,
   }
 }
 
+template <typename T>
+__global__ void gaussian_kernel(T* __restrict__ out, int64_t rows, int64_t cols, int64_t ld,
+                                uint64_t seed, uint64_t stream_id) {
+  gaussian_body<T>(out, rows, cols, ld, seed, stream_id);
+}
+
+// blockIdx.y = job; Omega of each problem from stream 0
+template <typename T>
+__global__ void gaussian_batched_kernel(const GaussJob* __restrict__ jobs) {
+  const GaussJob& j = jobs[blockIdx.y];
+  gaussian_body<T>((T*)j.out, j.rows, j.cols, j.ld, j.seed, 0ull);
+}
+
 }  // namespace
 
 cudaError_t launch_gaussian(void* out, int64_t rows, int64_t cols, int64_t ld, uint64_t seed,
@@ -139,6 +154,20 @@ cudaError_t launch_gaussian(void* out, int64_t rows, int64_t cols, int64_t ld, u
     case SORSVD_F32: case SORSVD_TF32: gaussian_kernel<float><<<(int)blocks, threads, 0, st>>>((float*)out, rows, cols, ld, seed, stream_id); break;
     case SORSVD_BF16: gaussian_kernel<bf16><<<(int)blocks, threads, 0, st>>>((bf16*)out, rows, cols, ld, seed, stream_id); break;
     case SORSVD_F16: gaussian_kernel<f16><<<(int)blocks, threads, 0, st>>>((f16*)out, rows, cols, ld, seed, stream_id); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gaussian_batched(const GaussJob* jobs, int njobs, int64_t max_elems, int dtype,
+                                    cudaStream_t st) {
+  if (njobs <= 0 || max_elems <= 0) return cudaSuccess;
+  const int64_t groups = (max_elems + 3) / 4;
+  const int64_t bx = std::min<int64_t>((groups + 255) / 256, 64);
+  dim3 grid((unsigned)bx, (unsigned)njobs);
+  switch (dtype) {
+    case SORSVD_F64: gaussian_batched_kernel<double><<<grid, 256, 0, st>>>(jobs); break;
+    case SORSVD_F32: case SORSVD_TF32: gaussian_batched_kernel<float><<<grid, 256, 0, st>>>(jobs); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

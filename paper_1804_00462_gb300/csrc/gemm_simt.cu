@@ -11,6 +11,8 @@
 // reduce_splits in a fixed order (no atomics, deterministic results).
 #include "internal.cuh"
 
+#include <algorithm>
+
 namespace sorsvd {
 
 int num_sms() {
@@ -32,19 +34,15 @@ constexpr int BM = 128, BN = 64, BK = 16, TM = 8, TN = 4, NT = 256;
 
 template <typename Acc, typename T> __device__ __forceinline__ Acc ld_as(const T* p) { return to_acc<Acc, T>(*p); }
 
+// One BM x BN tile of C = op(A) B over the K range [kbeg, kend).
 template <typename TA, typename TB, typename Acc, bool TRANS>
-__global__ void __launch_bounds__(NT)
-gemm_kernel(int64_t M, int64_t N, int64_t K, const TA* __restrict__ A, int64_t lda,
-            const TB* __restrict__ B, int64_t ldb, Acc* __restrict__ C, int64_t ldc,
-            int64_t k_chunk, int64_t split_stride) {
+__device__ __forceinline__ void gemm_tile(int64_t M, int64_t N, const TA* __restrict__ A, int64_t lda,
+                                          const TB* __restrict__ B, int64_t ldb, Acc* __restrict__ C,
+                                          int64_t ldc, int64_t row0, int64_t col0, int64_t kbeg, int64_t kend) {
   __shared__ Acc As[BK][BM];
   __shared__ Acc Bs[BK][BN];
   const int t = threadIdx.x;
   const int tx = t % (BN / TN), ty = t / (BN / TN);
-  const int64_t row0 = (int64_t)blockIdx.x * BM, col0 = (int64_t)blockIdx.y * BN;
-  const int64_t kbeg = (int64_t)blockIdx.z * k_chunk;
-  const int64_t kend = min(K, kbeg + k_chunk);
-  C += (int64_t)blockIdx.z * split_stride;
 
   Acc acc[TM][TN];
 #pragma unroll
@@ -99,6 +97,29 @@ gemm_kernel(int64_t M, int64_t N, int64_t K, const TA* __restrict__ A, int64_t l
   }
 }
 
+template <typename TA, typename TB, typename Acc, bool TRANS>
+__global__ void __launch_bounds__(NT)
+gemm_kernel(int64_t M, int64_t N, int64_t K, const TA* __restrict__ A, int64_t lda,
+            const TB* __restrict__ B, int64_t ldb, Acc* __restrict__ C, int64_t ldc,
+            int64_t k_chunk, int64_t split_stride) {
+  const int64_t kbeg = (int64_t)blockIdx.z * k_chunk;
+  gemm_tile<TA, TB, Acc, TRANS>(M, N, A, lda, B, ldb, C + (int64_t)blockIdx.z * split_stride, ldc,
+                                (int64_t)blockIdx.x * BM, (int64_t)blockIdx.y * BN, kbeg, min(K, kbeg + k_chunk));
+}
+
+// Grouped form: block b computes unit units[b] = (job, m-tile, n-tile,
+// k-split) of jobs[job]; one launch covers a stage of every problem.
+template <typename Acc, bool TRANS>
+__global__ void __launch_bounds__(NT)
+gemm_batched_kernel(const GemmJob* __restrict__ jobs, const int4* __restrict__ units) {
+  const int4 u = units[blockIdx.x];
+  const GemmJob& j = jobs[u.x];
+  const int64_t kbeg = (int64_t)u.w * j.k_chunk;
+  gemm_tile<Acc, Acc, Acc, TRANS>(j.M, j.N, (const Acc*)j.A, j.lda, (const Acc*)j.B, j.ldb,
+                                  (Acc*)j.C + (int64_t)u.w * j.split_stride, j.ldc, (int64_t)u.y * BM,
+                                  (int64_t)u.z * BN, kbeg, min(j.K, kbeg + j.k_chunk));
+}
+
 template <typename TA, typename TB, typename Acc>
 cudaError_t gemm_dispatch(bool trans, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
                           const void* B, int64_t ldb, void* C, int64_t ldc, int splits,
@@ -118,6 +139,27 @@ cudaError_t gemm_dispatch(bool trans, int64_t M, int64_t N, int64_t K, const voi
   return cudaGetLastError();
 }
 
+// Fixed-order sum of split partials.  fp32 partials are summed with
+// Neumaier's compensated summation in fp32 (error about 2 eps of the sum of
+// magnitudes, independent of the split count) and the pair is combined in
+// binary64 once: binary64 adds run at a small fraction of the fp32 rate on
+// this GPU.  Binary64 partials are summed in binary64.
+__device__ __forceinline__ double sum_parts(const float* __restrict__ p, int splits, int64_t stride) {
+  float s = 0.f, c = 0.f;
+  for (int q = 0; q < splits; ++q) {
+    const float x = p[q * stride];
+    const float t = __fadd_rn(s, x);
+    c = __fadd_rn(c, fabsf(s) >= fabsf(x) ? __fadd_rn(__fsub_rn(s, t), x) : __fadd_rn(__fsub_rn(x, t), s));
+    s = t;
+  }
+  return (double)s + (double)c;
+}
+__device__ __forceinline__ double sum_parts(const double* __restrict__ p, int splits, int64_t stride) {
+  double s = 0.0;
+  for (int q = 0; q < splits; ++q) s += p[q * stride];
+  return s;
+}
+
 template <typename TP, typename TO>
 __global__ void reduce_kernel(const TP* __restrict__ parts, int splits, int64_t stride, int64_t rows,
                               int64_t cols, int64_t ldp, TO* __restrict__ out, int64_t ldo) {
@@ -125,9 +167,23 @@ __global__ void reduce_kernel(const TP* __restrict__ parts, int splits, int64_t 
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     int64_t j = e / rows, i = e - j * rows;
-    double s = 0.0;
-    for (int p = 0; p < splits; ++p) s += (double)parts[p * stride + i + j * ldp];
-    out[i + j * ldo] = (TO)s;
+    out[i + j * ldo] = (TO)sum_parts(parts + i + j * ldp, splits, stride);
+  }
+}
+
+// Grouped reduce: blockIdx.y = job; parts fp32 or binary64 (Acc), out binary64
+// or the accumulator type.
+template <typename TP>
+__global__ void reduce_batched_kernel(const ReduceJob* __restrict__ jobs) {
+  const ReduceJob& j = jobs[blockIdx.y];
+  const int64_t total = j.rows * j.cols;
+  const TP* parts = (const TP*)j.parts;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t c = e / j.rows, i = e - c * j.rows;
+    const double s = sum_parts(parts + i + c * j.ldp, j.splits, j.stride);
+    if (j.out_f64) ((double*)j.out)[i + c * j.ldo] = s;
+    else ((TP*)j.out)[i + c * j.ldo] = (TP)s;
   }
 }
 
@@ -253,5 +309,31 @@ cudaError_t launch_copy2d(const void* x, int64_t ldx, void* y, int64_t ldy, int6
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
+
+cudaError_t launch_gemm_batched(bool trans_a, bool f64, const GemmJob* jobs, const int4* units, int nunits,
+                                cudaStream_t st) {
+  if (nunits <= 0) return cudaSuccess;
+  if (f64) {
+    if (trans_a) gemm_batched_kernel<double, true><<<nunits, NT, 0, st>>>(jobs, units);
+    else gemm_batched_kernel<double, false><<<nunits, NT, 0, st>>>(jobs, units);
+  } else {
+    if (trans_a) gemm_batched_kernel<float, true><<<nunits, NT, 0, st>>>(jobs, units);
+    else gemm_batched_kernel<float, false><<<nunits, NT, 0, st>>>(jobs, units);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_batched(bool parts_f64, const ReduceJob* jobs, int njobs, int64_t max_elems,
+                                  cudaStream_t st) {
+  if (njobs <= 0 || max_elems <= 0) return cudaSuccess;
+  const int64_t bx = std::min<int64_t>((max_elems + 255) / 256, 64);
+  dim3 grid((unsigned)bx, (unsigned)njobs);
+  if (parts_f64) reduce_batched_kernel<double><<<grid, 256, 0, st>>>(jobs);
+  else reduce_batched_kernel<float><<<grid, 256, 0, st>>>(jobs);
+  return cudaGetLastError();
+}
+
+// the tile shape of the grouped kernel (units are counted in these tiles)
+void gemm_tile_shape(int* bm, int* bn, int* bk) { *bm = BM; *bn = BN; *bk = BK; }
 
 }  // namespace sorsvd

@@ -21,8 +21,9 @@
 // order: the result is deterministic and uses no atomics.
 //
 // Split mode (ELT 3, fp32 containers, K-major only, MT = 1): a fourth
-// warpgroup splits each staged fp32 tile x into hi = RN_tf32(x), rewritten
-// in place, and lo = x - hi (exact in fp32) next to it, and every K step
+// warpgroup splits each staged fp32 tile x of A into hi = RN_tf32(x),
+// rewritten in place, and lo = x - hi (exact in fp32) next to it; B comes
+// split the same way from two tensors prepared by the caller; every K step
 // issues hi*hi + hi*lo + lo*hi TF32 MMAs.  The neglected lo*lo term and the
 // TF32 truncation of lo are below 2^-21 relative and of random sign, so the
 // products carry fp32-level error.
@@ -69,10 +70,11 @@ namespace {
 
 constexpr int kThreads = 224;
 constexpr int kThreadsSplit = 352;
-// Split mode drains TMEM every kDrainAtoms K atoms into fp32 registers
-// (round-to-nearest adds): tensor-core accumulation truncates, which over
-// thousands of MMA steps biases long fp32 sums by ~1e-5; short fills bound
-// that bias.  The register accumulator holds up to kAccCols columns.
+// Split mode drains each accumulator fill of kDrainAtoms K atoms into a
+// running sum kept in TMEM (round-to-nearest fp32 adds in registers):
+// tensor-core accumulation truncates, which over thousands of MMA steps
+// biases long fp32 sums by ~1e-5; short fills bound that bias.  Two fills
+// and the running sum need 3 Npad <= 512 TMEM columns (l <= kAccCols).
 constexpr int kDrainAtoms = 4;
 constexpr int kAccCols = 128;
 constexpr uint32_t kAtomBytes = 128u * 128u;   // 128 rows x 128 bytes
@@ -105,7 +107,7 @@ __device__ __forceinline__ void store_out(const TcParams& P, int64_t grow, int c
 template <int ELT, bool A_MN>
 __global__ void __launch_bounds__((ELT == 3 ? kThreadsSplit : kThreads), 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-               const TcParams P) {
+               const __grid_constant__ CUtensorMap tmBlo, const TcParams P) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint8_t* bring = smem + (size_t)P.stages * P.stage_bytes;
@@ -147,7 +149,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     tc::tmem_relinquish();
   }
   if (warp == 0 && lane == 0) tc::prefetch_tmap(&tmA);
-  if (warp == 6 && lane == 0) tc::prefetch_tmap(&tmB);
+  if (warp == 6 && lane == 0) { tc::prefetch_tmap(&tmB); if (SPLIT) tc::prefetch_tmap(&tmBlo); }
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = *tslot;
@@ -212,15 +214,17 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         const int64_t gend = min(it1, (t + 1) * P.ipt);
         for (int64_t kb = g - t * P.ipt; kb < gend - t * P.ipt; ++kb) {
           if (!tc::mbar_wait(&bempty[stage], phase ^ 1, abortp)) { ok = false; break; }
-          tc::mbar_arrive_expect_tx(&bfull[stage], P.b_bytes);
+          tc::mbar_arrive_expect_tx(&bfull[stage], (SPLIT ? 2u : 1u) * P.b_bytes);
           armed |= 1u << stage;
           armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
           uint8_t* sb = bring + (size_t)stage * P.bstage_bytes;
           for (int j = 0; j < P.KA; ++j) {
             const int k = (int)((kb * P.KA + j) * AK);
-            for (int ch = 0; ch < P.nch; ++ch)
-              tc::tma_load_2d_hint(sb + (size_t)j * P.b_atom + (size_t)ch * P.ch0 * 128, &tmB, &bfull[stage], k,
-                                   ch * P.ch0, polB);
+            for (int ch = 0; ch < P.nch; ++ch) {
+              const size_t off = (size_t)j * P.b_atom + (size_t)ch * P.ch0 * 128;
+              tc::tma_load_2d_hint(sb + off, &tmB, &bfull[stage], k, ch * P.ch0, polB);
+              if (SPLIT) tc::tma_load_2d_hint(sb + P.b_bytes + off, &tmBlo, &bfull[stage], k, ch * P.ch0, polB);
+            }
           }
           if (++stage == (uint32_t)P.bstages) { stage = 0; phase ^= 1; }
         }
@@ -308,35 +312,29 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     // ------------------------------------------------------------ converter
     // hi = RN_tf32(x) rewritten in place (exactly representable, so the MMA
     // reads it without truncation) and lo = x - hi (exact in fp32) right
-    // after the hi tiles of the stage, for the A and the B tiles of every
-    // K-stage; elementwise, so the 128-byte swizzle of the copies carries over
+    // after the A tiles of the stage; elementwise, so the 128-byte swizzle of
+    // the copies carries over.  B arrives already split (hi and lo tensors).
     const int ct = threadIdx.x - 224;          // 0..127
-    uint32_t stage = 0, phase = 0, bstage = 0, bphase = 0;
+    uint32_t stage = 0, phase = 0;
     bool ok = true;
     for (int64_t g = it0; g < it1 && ok;) {
       const int64_t t = g / P.ipt;
       const int64_t gend = min(it1, (t + 1) * P.ipt);
       for (int64_t kb = g - t * P.ipt; kb < gend - t * P.ipt; ++kb) {
         if (!tc::mbar_wait(&full[stage], phase, abortp)) { ok = false; break; }
-        if (!tc::mbar_wait(&bfull[bstage], bphase, abortp)) { ok = false; break; }
-        for (int part = 0; part < 2; ++part) {
-          uint8_t* base = part == 0 ? smem + (size_t)stage * P.stage_bytes : bring + (size_t)bstage * P.bstage_bytes;
-          const uint32_t bytes = part == 0 ? P.a_bytes : P.b_bytes;
-          float4* src = reinterpret_cast<float4*>(base);
-          float4* dst = reinterpret_cast<float4*>(base + bytes);
-          for (uint32_t v = ct; v < bytes / 16; v += 128) {
-            float4 x = src[v], h, r;
-            h.x = rn_tf32(x.x); h.y = rn_tf32(x.y); h.z = rn_tf32(x.z); h.w = rn_tf32(x.w);
-            r.x = x.x - h.x; r.y = x.y - h.y; r.z = x.z - h.z; r.w = x.w - h.w;
-            src[v] = h;
-            dst[v] = r;
-          }
+        float4* src = reinterpret_cast<float4*>(smem + (size_t)stage * P.stage_bytes);
+        float4* dst = reinterpret_cast<float4*>(smem + (size_t)stage * P.stage_bytes + P.a_bytes);
+        for (uint32_t v = ct; v < P.a_bytes / 16; v += 128) {
+          float4 x = src[v], h, r;
+          h.x = rn_tf32(x.x); h.y = rn_tf32(x.y); h.z = rn_tf32(x.z); h.w = rn_tf32(x.w);
+          r.x = x.x - h.x; r.y = x.y - h.y; r.z = x.z - h.z; r.w = x.w - h.w;
+          src[v] = h;
+          dst[v] = r;
         }
         fence_proxy_async();                   // generic writes -> tensor-core reads
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&conv[stage]);
         if (++stage == (uint32_t)P.stages) { stage = 0; phase ^= 1; }
-        if (++bstage == (uint32_t)P.bstages) { bstage = 0; bphase ^= 1; }
       }
       g = gend;
     }
@@ -355,11 +353,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         const int slot = (t == it0 / P.ipt) ? 0 : 1;
         pdst = P.parts + ((size_t)cta * 2 + slot) * mrows * P.Npad;
       }
-      float accum[SPLIT ? kAccCols : 1];
-      if (SPLIT) {
-#pragma unroll
-        for (int i = 0; i < (SPLIT ? kAccCols : 1); ++i) accum[i] = 0.f;
-      }
+      // split mode: running sum in TMEM columns [2 Npad, 3 Npad) of this warp's lanes
+      const uint32_t tmaster = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(2 * P.Npad);
       for (int64_t c0 = kb0; c0 < kb1; c0 += CHUNK) {
         const int b = (P.nbuf == 2) ? (chunk & 1) : 0;
         const uint32_t use = (P.nbuf == 2) ? (uint32_t)(chunk >> 1) : (uint32_t)chunk;
@@ -371,17 +366,17 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           const int row = mt * 128 + q * 32 + lane;
           const int64_t grow = t * mrows + row;
           if (SPLIT) {
-            // drain: round-to-nearest fp32 adds of the partial accumulator
+            // drain: round-to-nearest fp32 adds of the fill into the running sum
+            for (int cc = 0; cc < P.Npad; cc += 16) {
+              float v[16], acc[16];
+              tc::tmem_ld16(taddr + cc, v);
+              if (c0 != kb0) tc::tmem_ld16(tmaster + cc, acc);
+              tc::tmem_ld_wait();
 #pragma unroll
-            for (int cc = 0; cc < (SPLIT ? kAccCols / 16 : 1); ++cc) {
-              if (cc * 16 < P.Npad) {
-                float v[16];
-                tc::tmem_ld16(taddr + cc * 16, v);
-                tc::tmem_ld_wait();
-#pragma unroll
-                for (int i = 0; i < 16; ++i) accum[cc * 16 + i] += v[i];
-              }
+              for (int i = 0; i < 16; ++i) acc[i] = (c0 != kb0) ? acc[i] + v[i] : v[i];
+              tc::tmem_st16(tmaster + cc, acc);
             }
+            tc::tmem_st_wait();
           } else {
             for (int cb = 0; cb < P.N; cb += 16) {
               float v[16];
@@ -409,11 +404,16 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         // split mode runs with MT = 1
         const int row = q * 32 + lane;
         const int64_t grow = t * mrows + row;
+        for (int cb = 0; cb < P.N; cb += 16) {
+          float v[16];
+          tc::tmem_ld16(tmaster + cb, v);
+          tc::tmem_ld_wait();
 #pragma unroll
-        for (int i = 0; i < (SPLIT ? kAccCols : 1); ++i) {
-          if (i < P.N) {
-            if (whole) { if (grow < P.M) store_out(P, grow, i, accum[i]); }
-            else pdst[row + (size_t)i * mrows] = accum[i];
+          for (int i = 0; i < 16; ++i) {
+            if (cb + i < P.N) {
+              if (whole) { if (grow < P.M) store_out(P, grow, cb + i, v[i]); }
+              else pdst[row + (size_t)(cb + i) * mrows] = v[i];
+            }
           }
         }
       }
@@ -429,28 +429,43 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 }
 
 // Sum the partial segments of every tile touched by more than one CTA, in
-// CTA order, and write the tile to the output.
+// CTA order (deterministic), and write the tile to the output.  Blocks walk tiles
+// (blockIdx.x) and split each tile's elements (blockIdx.y).  The CTAs that
+// cover tile t are c0..c1 (consecutive); tile t is the head segment (slot 0)
+// of each of them except c0 when c0's range starts inside an earlier tile
+// (then it is c0's tail, slot 1).
 __global__ void tc_fixup_kernel(const TcParams P) {
   const int mrows = 128 * P.MT;
-  const int64_t per_tile = (int64_t)mrows * P.N;
-  const int64_t total = P.tiles * per_tile;
+  const int per = mrows * P.N;
+  for (int64_t t = blockIdx.x; t < P.tiles; t += gridDim.x) {
+    const int64_t c0 = cta_of(t * P.ipt, P.total, P.G);
+    const int64_t c1 = cta_of(t * P.ipt + P.ipt - 1, P.total, P.G);
+    if (c0 == c1) continue;                       // written whole by its CTA
+    const int slot0 = (c0 * P.total / P.G < t * P.ipt) ? 1 : 0;
+    for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < per; e += gridDim.y * blockDim.x) {
+      const int col = e / mrows, row = e - col * mrows;
+      const int64_t grow = t * mrows + row;
+      if (grow >= P.M) continue;
+      const size_t off = (size_t)row + (size_t)col * mrows;
+      const size_t seg = (size_t)mrows * P.Npad;
+      // a handful of fp32 partials: fp32 sums (binary64 adds are slow here)
+      float s = P.parts[((size_t)c0 * 2 + slot0) * seg + off];
+      for (int64_t c = c0 + 1; c <= c1; ++c) s += P.parts[(size_t)c * 2 * seg + off];
+      store_out(P, grow, col, s);
+    }
+  }
+}
+
+__global__ void split_tf32_kernel(const float* __restrict__ X, int64_t ldx, int64_t rows, int64_t cols,
+                                  float* __restrict__ hi, float* __restrict__ lo, int64_t ldh) {
+  const int64_t total = rows * cols;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t t = e / per_tile;
-    const int64_t r = e - t * per_tile;
-    const int col = (int)(r / mrows), row = (int)(r - (int64_t)col * mrows);
-    const int64_t grow = t * mrows + row;
-    if (grow >= P.M) continue;
-    const int64_t c_first = cta_of(t * P.ipt, P.total, P.G);
-    const int64_t c_last = cta_of(t * P.ipt + P.ipt - 1, P.total, P.G);
-    if (c_first == c_last) continue;
-    double s = 0.0;
-    for (int64_t c = c_first; c <= c_last; ++c) {
-      const int64_t head_tile = (c * P.total / P.G) / P.ipt;
-      const int slot = (t == head_tile) ? 0 : 1;
-      s += (double)P.parts[((size_t)c * 2 + slot) * mrows * P.Npad + row + (size_t)col * mrows];
-    }
-    store_out(P, grow, col, (float)s);
+    const int64_t c = e / rows, r = e - c * rows;
+    const float x = X[r + c * ldx];
+    const float h = rn_tf32(x);
+    hi[r + c * ldh] = h;
+    lo[r + c * ldh] = x - h;
   }
 }
 
@@ -493,12 +508,12 @@ bool make_map(CUtensorMap* map, const void* ptr, int elt, int64_t rows, int64_t 
 }
 
 template <int ELT, bool A_MN>
-cudaError_t launch_typed(const CUtensorMap& ma, const CUtensorMap& mb, const TcParams& P, size_t smem,
-                         cudaStream_t st) {
+cudaError_t launch_typed(const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& mblo, const TcParams& P,
+                         size_t smem, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<ELT, A_MN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  tc_gemm_kernel<ELT, A_MN><<<P.G, ELT == 3 ? kThreadsSplit : kThreads, smem, st>>>(ma, mb, P);
+  tc_gemm_kernel<ELT, A_MN><<<P.G, ELT == 3 ? kThreadsSplit : kThreads, smem, st>>>(ma, mb, mblo, P);
   return cudaGetLastError();
 }
 
@@ -525,7 +540,9 @@ TcParams shape(int elt, int64_t M, int64_t N, int64_t K, int KA, int MT) {
   if (P.G < 1) P.G = 1;
   P.nbuf = (2 * MT * P.Npad <= 512) ? 2 : 1;
   uint32_t cols = 32;
-  while (cols < (uint32_t)(P.nbuf * MT * P.Npad)) cols <<= 1;
+  // split mode keeps its running sum in a third block of Npad columns
+  const uint32_t need_cols = (uint32_t)(P.nbuf * MT * P.Npad + (elt == 3 ? P.Npad : 0));
+  while (cols < need_cols) cols <<= 1;
   P.tmem_cols = cols;
   P.a_bytes = (uint32_t)(MT * KA) * kAtomBytes;
   P.b_atom = (uint32_t)P.nch * (uint32_t)P.ch0 * 128u;
@@ -537,7 +554,7 @@ TcParams shape(int elt, int64_t M, int64_t N, int64_t K, int KA, int MT) {
   const uint32_t left = kSmemBudget > P.bstages * P.bstage_bytes ? kSmemBudget - P.bstages * P.bstage_bytes : 0;
   P.stages = (int)std::min<uint32_t>(12u, left / P.stage_bytes);
   if (MT * P.Npad > 512 || cols > 512) P.stages = 0;
-  if (elt == 3 && MT != 1) P.stages = 0;
+  if (elt == 3 && (MT != 1 || P.nbuf != 2 || need_cols > 512)) P.stages = 0;
   return P;
 }
 
@@ -568,7 +585,7 @@ TcParams tc_plan(int elt, int64_t M, int64_t N, int64_t K) {
 bool tc_supported(int elt, const void* A, int64_t lda, const void* B, int64_t ldb, int l) {
   const int64_t esz = elt >= 2 ? 4 : 2;
   if (l < 1 || l > 512) return false;
-  if (elt == 3 && l > kAccCols) return false;       // split mode: register accumulator
+  if (elt == 3 && l > kAccCols) return false;       // split mode: 3 Npad TMEM columns
   if ((reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15)) return false;
   if ((lda * esz) % 16 || (ldb * esz) % 16) return false;
   return encode_fn() != nullptr;
@@ -580,9 +597,11 @@ size_t tc_parts_bytes(int elt, int64_t M, int64_t N, int64_t K) {
 }
 
 cudaError_t launch_tc_gemm(bool trans_a, int elt, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
-                           const void* B, int64_t ldb, float* out, int64_t ldo, void* out16, int64_t ld16,
-                           int out16_kind, float* parts, DeviceStatus* status, int kcls, cudaStream_t st) {
+                           const void* B, int64_t ldb, const void* Blo, float* out, int64_t ldo, void* out16,
+                           int64_t ld16, int out16_kind, float* parts, DeviceStatus* status, int kcls,
+                           cudaStream_t st) {
   if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+  if (elt == 3 && (!Blo || (reinterpret_cast<uintptr_t>(Blo) & 15))) return cudaErrorInvalidValue;
   // an MN-major TF32 operand gave all-zero products on GB300: fp32 products
   // of the form A X go through a transposed copy of A instead
   if (elt >= 2 && !trans_a) return cudaErrorInvalidValue;
@@ -599,23 +618,36 @@ cudaError_t launch_tc_gemm(bool trans_a, int elt, int64_t M, int64_t N, int64_t 
   const bool okA = trans_a ? make_map(&ma, A, map_elt, a_rows, a_cols, lda, (uint32_t)AK, 128u)
                            : make_map(&ma, A, map_elt, a_rows, a_cols, lda, (uint32_t)AMN, (uint32_t)AK);
   const bool okB = make_map(&mb, B, map_elt, K, N, ldb, (uint32_t)AK, (uint32_t)P.ch0);
-  if (!okA || !okB) return cudaErrorInvalidValue;
+  CUtensorMap mblo = mb;
+  const bool okBlo = elt != 3 || make_map(&mblo, Blo, map_elt, K, N, ldb, (uint32_t)AK, (uint32_t)P.ch0);
+  if (!okA || !okB || !okBlo) return cudaErrorInvalidValue;
   const size_t smem = (size_t)P.stages * P.stage_bytes + (size_t)P.bstages * P.bstage_bytes + 1024 + 512;
   cudaError_t e;
   {
     ProfScope ps(kcls, st);
-    if (elt == 0) e = trans_a ? launch_typed<0, false>(ma, mb, P, smem, st) : launch_typed<0, true>(ma, mb, P, smem, st);
-    else if (elt == 1) e = trans_a ? launch_typed<1, false>(ma, mb, P, smem, st) : launch_typed<1, true>(ma, mb, P, smem, st);
-    else if (elt == 2) e = launch_typed<2, false>(ma, mb, P, smem, st);
-    else e = launch_typed<3, false>(ma, mb, P, smem, st);
+    if (elt == 0) e = trans_a ? launch_typed<0, false>(ma, mb, mblo, P, smem, st) : launch_typed<0, true>(ma, mb, mblo, P, smem, st);
+    else if (elt == 1) e = trans_a ? launch_typed<1, false>(ma, mb, mblo, P, smem, st) : launch_typed<1, true>(ma, mb, mblo, P, smem, st);
+    else if (elt == 2) e = launch_typed<2, false>(ma, mb, mblo, P, smem, st);
+    else e = launch_typed<3, false>(ma, mb, mblo, P, smem, st);
   }
   if (e != cudaSuccess) return e;
-  // fix-up of tiles split across CTAs (a no-op grid when every tile is whole)
-  const int64_t work = P.tiles * 128 * P.MT * P.N;
-  int64_t blocks = (work + 255) / 256;
-  if (blocks > (int64_t)num_sms() * 8) blocks = (int64_t)num_sms() * 8;
+  // fix-up of tiles split across CTAs (blocks of whole tiles return at once)
+  const int64_t gx = std::min<int64_t>(P.tiles, 65535);
+  const int64_t per = (int64_t)128 * P.MT * P.N;
+  const int64_t gy = std::max<int64_t>(1, std::min<int64_t>((per + 255) / 256,
+                                                            ((int64_t)num_sms() * 8 + gx - 1) / gx));
   ProfScope ps2(K_REDUCE, st);
-  tc_fixup_kernel<<<(unsigned)blocks, 256, 0, st>>>(P);
+  tc_fixup_kernel<<<dim3((unsigned)gx, (unsigned)gy), 256, 0, st>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_tf32(const float* X, int64_t ldx, int64_t rows, int64_t cols, float* hi, float* lo,
+                              int64_t ldh, cudaStream_t st) {
+  const int64_t total = rows * cols;
+  if (total <= 0) return cudaSuccess;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > (int64_t)num_sms() * 8) blocks = (int64_t)num_sms() * 8;
+  split_tf32_kernel<<<(unsigned)blocks, 256, 0, st>>>(X, ldx, rows, cols, hi, lo, ldh);
   return cudaGetLastError();
 }
 

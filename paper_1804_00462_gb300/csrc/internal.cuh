@@ -99,6 +99,52 @@ cudaError_t launch_transpose_f32(const float* A, int64_t lda, int64_t rows, int6
 cudaError_t launch_copy2d(const void* x, int64_t ldx, void* y, int64_t ldy,
                           int64_t rows, int64_t cols, size_t elem, cudaStream_t st);
 
+// ---------------------------------------------------------------------------
+// grouped ("batched") launches: one launch runs one stage of many problems,
+// reading per-problem job descriptors from device memory
+// ---------------------------------------------------------------------------
+// C = op(A) B for job j, all operands of the accumulator type; K chunks of
+// k_chunk, chunk s written to C + s * split_stride.
+struct GemmJob {
+  const void* A; const void* B; void* C;
+  int64_t lda, ldb, ldc;
+  int64_t M, N, K;
+  int64_t k_chunk, split_stride;
+};
+// out = sum_{s < splits} parts[s * stride] (binary64 sums)
+struct ReduceJob {
+  const void* parts; void* out;
+  int64_t rows, cols, ldp, ldo, stride;
+  int splits, out_f64;
+};
+// Omega of one problem
+struct GaussJob {
+  void* out; int64_t rows, cols, ld; uint64_t seed;
+};
+// Cholesky inverse of one problem (chol.cu)
+struct CholJob {
+  const double* G; void* Rinv; DeviceStatus* status; int l; double shift;
+};
+// l x l SVD of one problem (jacobi.cu)
+struct JacobiJob {
+  const double* M; void* Ut; void* Vt; void* S; void* work; DeviceStatus* status; int l, k;
+};
+// units: int4 (job, m-tile, n-tile, k-split) in tiles of gemm_tile_shape()
+cudaError_t launch_gemm_batched(bool trans_a, bool f64, const GemmJob* jobs, const int4* units, int nunits,
+                                cudaStream_t st);
+void gemm_tile_shape(int* bm, int* bn, int* bk);
+cudaError_t launch_reduce_batched(bool parts_f64, const ReduceJob* jobs, int njobs, int64_t max_elems,
+                                  cudaStream_t st);
+cudaError_t launch_gaussian_batched(const GaussJob* jobs, int njobs, int64_t max_elems, int dtype,
+                                    cudaStream_t st);
+// largest l the one-block blocked Cholesky takes (shared-memory tiles)
+int chol_batched_max_l(bool f64);
+cudaError_t launch_chol_batched(const CholJob* jobs, int njobs, int max_l, bool f64, cudaStream_t st);
+// largest l of the batched Jacobi (W in shared memory)
+int jacobi_batched_max_l(bool f64);
+size_t jacobi_batched_work_bytes(int l);
+cudaError_t launch_jacobi_batched(const JacobiJob* jobs, int njobs, int max_l, bool f64, cudaStream_t st);
+
 // chol.cu: R^{-1} (upper triangular, l x l, column-major, ld = l) of the
 // Cholesky factor of G + s I, s = shift_rel * trace(G) / l.  G binary64.
 // Output in binary64 (f64 = true) or fp32.
@@ -114,15 +160,26 @@ cudaError_t launch_jacobi(const double* M, int l, int k, bool f64, void* Ut, voi
                           void* S, bool S_f64, void* work, DeviceStatus* status, cudaStream_t st);
 size_t jacobi_work_bytes(int l);
 
+// sorsvd.cu: the device status word of a sorsvd_run workspace
+DeviceStatus* workspace_status(void* ws);
+
 // gemm_tc.cu: tensor-core pass over A (tcgen05 + TMA), op(A) = A^T when
-// trans_a.  elt: 0 bf16, 1 fp16, 2 tf32 (fp32 containers).  B is K x N
-// column-major of the same element type.  Writes fp32 C (ldo) and, when
-// out16 is non-null, its 16-bit rounding (out16_kind 1 bf16, 2 fp16).
-// Needs tc_supported() and tc_parts_bytes() of scratch in `parts`.
+// trans_a.  elt: 0 bf16, 1 fp16, 2 tf32 (fp32 containers), 3 fp32-accurate
+// split products (fp32 containers, trans_a only).  B is K x N column-major
+// of the same element type; for elt 3, B and Blo are the hi / lo parts of
+// the operand written by launch_split_tf32 (Blo unused otherwise).  Writes
+// fp32 C (ldo) and, when out16 is non-null, its 16-bit rounding (out16_kind
+// 1 bf16, 2 fp16).  Needs tc_supported() and tc_parts_bytes() of scratch in
+// `parts`.
 bool tc_supported(int elt, const void* A, int64_t lda, const void* B, int64_t ldb, int l);
 size_t tc_parts_bytes(int elt, int64_t M, int64_t N, int64_t K);
 cudaError_t launch_tc_gemm(bool trans_a, int elt, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
-                           const void* B, int64_t ldb, float* out, int64_t ldo, void* out16, int64_t ld16,
-                           int out16_kind, float* parts, DeviceStatus* status, int kcls, cudaStream_t st);
+                           const void* B, int64_t ldb, const void* Blo, float* out, int64_t ldo, void* out16,
+                           int64_t ld16, int out16_kind, float* parts, DeviceStatus* status, int kcls,
+                           cudaStream_t st);
+// hi = RN_tf32(X), lo = X - hi (exact in fp32) of a rows x cols fp32 matrix
+// (column-major, ldx); hi and lo share the leading dimension ldh.
+cudaError_t launch_split_tf32(const float* X, int64_t ldx, int64_t rows, int64_t cols, float* hi, float* lo,
+                              int64_t ldh, cudaStream_t st);
 
 }  // namespace sorsvd

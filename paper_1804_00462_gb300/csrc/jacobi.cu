@@ -1,24 +1,30 @@
 // Truncated SVD of the small core matrix M (l x l) of Algorithm 3
 // ("compute the rank-k truncated SVD of M").  One-sided (Hestenes) Jacobi:
 // columns w_p, w_q of W = M V are rotated until every pair is orthogonal to
-// a relative tolerance; then sigma_j = ||M v_j|| / ||v_j||, U~ = M V diag(sigma)^{-1}.
+// a relative tolerance, the same rotations accumulating V; then
+// sigma_j = ||M v_j|| and u_j = M v_j / sigma_j.
 //
 // Three kernels:
-//  1. sweeps (one block): W in shared memory when l^2 words fit, else in the
-//     caller's work buffer; round-robin pair schedule (see the kernel).
-//     Rotations are applied while a pair's cosine exceeds l * eps of the
-//     sweep precision.  The sweep count is capped; hitting the cap with a
-//     cosine above 32 l eps raises SORSVD_ERR_NOT_CONVERGED.
-//  2. finish (one block per column), binary64: from the rotated column
-//     w ~ sigma u: z = M^T u, sigma = ||z||, v = z / sigma, u = M v / sigma.
-//     sigma is a Rayleigh quotient of M M^T, so its error is quadratic in the
-//     departure of u from a singular vector: fp32 sweeps followed by this step
-//     give singular values to about 1e-8 of sigma_1, while fp32 rotations
-//     alone leak about 1e-5 of sigma_1 into the small columns.
+//  1. sweeps (one block): W and V in shared memory when 2 l^2 words fit,
+//     else in the caller's work buffer; round-robin pair schedule (see the
+//     kernel).  Rotations are applied while a pair's cosine exceeds l * eps
+//     of the sweep precision.  The sweep count is capped; hitting the cap
+//     with a cosine above 32 l eps raises SORSVD_ERR_NOT_CONVERGED.
+//  2. finish (one block per column), binary64: v_j normalised (fp32
+//     rotations keep its norm only to a few ulps each), z = M v_j,
+//     sigma_j = ||z||, u_j = z / sigma_j.  V stays orthonormal to the sweep precision whatever
+//     the grading of M, so the rank-k result M V_k V_k^T is as accurate as
+//     the subspace of V_k; sigma_j is a Rayleigh quotient of M^T M (error
+//     quadratic in the error of v_j).  (Recovering v_j = M^T u_j / sigma_j
+//     from the rotated W instead multiplies the sweep's rounding in u_j by
+//     sigma_1 / sigma_j: with fp32 sweeps on a matrix graded like i^-2 the
+//     factors lost orthogonality at the 1e-2 level.)
 //  3. order (one block): sigma descending (ties by column index); sign: the
 //     largest-magnitude entry of each column of U~ is made positive and the
 //     matching column of V~ follows.
 #include "internal.cuh"
+
+#include <algorithm>
 
 namespace sorsvd {
 namespace {
@@ -64,20 +70,20 @@ __device__ __forceinline__ J group8_sum(J v, unsigned mask) {
   return v;
 }
 
-// Sweep kernel.  Only W = M V is rotated: the right factor is recovered in
-// binary64 by the finish kernel (v = M^T u / sigma), which halves the work of
-// a rotation.  Pairs follow the round-robin tournament (circle method): in
-// each of the N - 1 rounds of a sweep (N = l rounded up to even) the N/2
+// Sweep kernel.  Pairs follow the round-robin tournament (circle method):
+// in each of the N - 1 rounds of a sweep (N = l rounded up to even) the N/2
 // disjoint pairs are rotated concurrently, one 8-lane group per pair, which
-// keeps the pair's two columns in registers between the inner products and
-// the update; one barrier separates rounds.  EPL: elements per lane (>= l/8).
-template <typename J, bool IN_SMEM, int EPL, int NT>
-__global__ void __launch_bounds__(NT)
-jacobi_sweep_kernel(const double* __restrict__ Min, int l, J* __restrict__ Wout, J* __restrict__ gwork,
-                    DeviceStatus* status) {
+// keeps the pair's two W columns in registers between the inner products and
+// the update; the same rotation is applied to the two V columns.  One
+// barrier separates rounds.  EPL: elements per lane (>= l/8).  W (l x l) and
+// V (l x l) sit in shared memory (IN_SMEM) or in gwork; V is written to Vout.
+template <typename J, bool IN_SMEM, int EPL>
+__device__ __forceinline__ void jacobi_sweep_body(const double* __restrict__ Min, int l, J* __restrict__ Vout,
+                                                  J* __restrict__ gwork, DeviceStatus* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_rot, s_big;
   J* W = IN_SMEM ? reinterpret_cast<J*>(smem_raw) : gwork;
+  J* V = W + (size_t)l * l;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int grp = lane >> 3, gl = lane & 7;
   const int ngroups = (blockDim.x >> 5) * 4;
@@ -86,7 +92,10 @@ jacobi_sweep_kernel(const double* __restrict__ Min, int l, J* __restrict__ Wout,
   const J tol = (J)l * eps, tol2 = tol * tol;
   const J big = (J)32 * tol, big2 = big * big;
 
-  for (int e = t; e < l * l; e += blockDim.x) W[e] = (J)Min[e];
+  for (int e = t; e < l * l; e += blockDim.x) {
+    W[e] = (J)Min[e];
+    V[e] = (e % l == e / l) ? (J)1 : (J)0;
+  }
   __syncthreads();
 
   const int N = (l + 1) & ~1;
@@ -99,8 +108,9 @@ jacobi_sweep_kernel(const double* __restrict__ Min, int l, J* __restrict__ Wout,
       for (int pr = warp * 4 + grp; pr < N / 2; pr += ngroups) {
         const int a = rr_player(pr, r, N), b = rr_player(N - 1 - pr, r, N);
         if (a >= l || b >= l) continue;                // bye (whole group)
-        J* wp = W + (size_t)min(a, b) * l;
-        J* wq = W + (size_t)max(a, b) * l;
+        const size_t oa = (size_t)min(a, b) * l, ob = (size_t)max(a, b) * l;
+        J* wp = W + oa;
+        J* wq = W + ob;
         J x[EPL], y[EPL];
         J al = 0, be = 0, ga = 0;
 #pragma unroll
@@ -117,12 +127,17 @@ jacobi_sweep_kernel(const double* __restrict__ Min, int l, J* __restrict__ Wout,
         if (ga * ga > big2 * al * be) big_local = 1;
         J cs, sn;
         rotation(al, be, ga, &cs, &sn);
+        J* vp = V + oa;
+        J* vq = V + ob;
 #pragma unroll
         for (int e = 0; e < EPL; ++e) {
           const int i = gl + 8 * e;
           if (i < l) {
             wp[i] = cs * x[e] - sn * y[e];
             wq[i] = sn * x[e] + cs * y[e];
+            const J u = vp[i], v = vq[i];
+            vp[i] = cs * u - sn * v;
+            vq[i] = sn * u + cs * v;
           }
         }
         rot_local = 1;
@@ -141,7 +156,14 @@ jacobi_sweep_kernel(const double* __restrict__ Min, int l, J* __restrict__ Wout,
     }
   }
   if (t == 0) atomicOr(&status->info, (min(sweep, kMaxSweeps)) << 8);
-  for (int e = t; e < l * l; e += blockDim.x) Wout[e] = W[e];
+  for (int e = t; e < l * l; e += blockDim.x) Vout[e] = V[e];
+}
+
+template <typename J, bool IN_SMEM, int EPL, int NT>
+__global__ void __launch_bounds__(NT)
+jacobi_sweep_kernel(const double* __restrict__ Min, int l, J* __restrict__ Vout, J* __restrict__ gwork,
+                    DeviceStatus* status) {
+  jacobi_sweep_body<J, IN_SMEM, EPL>(Min, l, Vout, gwork, status);
 }
 
 template <typename J>
@@ -157,56 +179,61 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;
 }
 
-// From a rotated column w_j ~ sigma_j u_j (sweep precision): u = w / ||w||,
-// z = M^T u, sigma_j = ||z||, v_j = z / sigma_j, and the left vector again
-// as M v_j / sigma_j, all in binary64.  sigma_j is a Rayleigh quotient of
-// M M^T, so its error is quadratic in the departure of u from a singular
-// vector.
+// From the accumulated right vector v_j (sweep precision): z = M v_j,
+// sigma_j = ||z||, u_j = z / sigma_j, all in binary64.
 template <typename J>
-__global__ void __launch_bounds__(256)
-jacobi_finish_kernel(const double* __restrict__ M, int l, const J* __restrict__ Win, double* __restrict__ U64,
-                     double* __restrict__ V64, double* __restrict__ sig) {
-  __shared__ double u[SORSVD_MAX_L];
-  __shared__ double z[SORSVD_MAX_L];
+__device__ __forceinline__ void jacobi_finish_body(const double* __restrict__ M, int l, const J* __restrict__ Vin,
+                                                   double* __restrict__ U64, double* __restrict__ V64,
+                                                   double* __restrict__ sig, int j) {
+  __shared__ double v[SORSVD_MAX_L];
   __shared__ double red[32];
-  const int j = blockIdx.x;
-  double nw = 0;
+  // the rotations keep ||v_j|| = 1 only to a few ulps each: normalise first
+  double nv = 0;
   for (int i = threadIdx.x; i < l; i += blockDim.x) {
-    const double x = (double)Win[i + (size_t)j * l];
-    u[i] = x;
-    nw += x * x;
+    const double x = (double)Vin[i + (size_t)j * l];
+    v[i] = x;
+    nv += x * x;
   }
-  nw = block_sum<J>(nw, red);
-  const double inv_nw = nw > 0 ? 1.0 / sqrt(nw) : 0.0;
+  nv = block_sum<J>(nv, red);
+  const double inv_nv = nv > 0 ? 1.0 / sqrt(nv) : 0.0;
+  for (int i = threadIdx.x; i < l; i += blockDim.x) {
+    const double x = v[i] * inv_nv;
+    v[i] = x;
+    V64[i + (size_t)j * l] = x;
+  }
+  __syncthreads();
   double nz = 0;
-  for (int c = threadIdx.x; c < l; c += blockDim.x) {       // z_c = sum_i M_ic u_i
+  double zloc[(SORSVD_MAX_L + 255) / 256];
+  int q = 0;
+  for (int i = threadIdx.x; i < l; i += blockDim.x, ++q) {     // z_i = sum_c M_ic v_c
     double s = 0;
-    const double* mc = M + (size_t)c * l;
-    for (int i = 0; i < l; ++i) s += mc[i] * u[i];
-    s *= inv_nw;
-    z[c] = s;
+    for (int c = 0; c < l; ++c) s += M[i + (size_t)c * l] * v[c];
+    zloc[q] = s;
     nz += s * s;
   }
   nz = block_sum<J>(nz, red);
   const double sg = sqrt(nz);
   const double inv_sg = sg > 0 ? 1.0 / sg : 0.0;
-  for (int c = threadIdx.x; c < l; c += blockDim.x) V64[c + (size_t)j * l] = z[c] * inv_sg;
-  __syncthreads();
-  for (int i = threadIdx.x; i < l; i += blockDim.x) {       // u_i = (M v)_i / sigma
-    double s = 0;
-    for (int c = 0; c < l; ++c) s += M[i + (size_t)c * l] * z[c];
-    U64[i + (size_t)j * l] = s * inv_sg * inv_sg;
-  }
+  q = 0;
+  for (int i = threadIdx.x; i < l; i += blockDim.x, ++q) U64[i + (size_t)j * l] = zloc[q] * inv_sg;
   if (threadIdx.x == 0) sig[j] = sg;
 }
 
+template <typename J>
+__global__ void __launch_bounds__(256)
+jacobi_finish_kernel(const double* __restrict__ M, int l, const J* __restrict__ Vin, double* __restrict__ U64,
+                     double* __restrict__ V64, double* __restrict__ sig) {
+  jacobi_finish_body<J>(M, l, Vin, U64, V64, sig, blockIdx.x);
+}
+
 template <typename J, typename TS>
-__global__ void __launch_bounds__(JT)
-jacobi_order_kernel(int l, int k, const double* __restrict__ U64, const double* __restrict__ V64,
-                    const double* __restrict__ sig, J* __restrict__ Ut, J* __restrict__ Vt, TS* __restrict__ S) {
+__device__ __forceinline__ void jacobi_order_body(int l, int k, const double* __restrict__ U64,
+                                                  const double* __restrict__ V64, const double* __restrict__ sig,
+                                                  J* __restrict__ Ut, J* __restrict__ Vt, TS* __restrict__ S) {
   __shared__ int s_order[SORSVD_MAX_L];
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarps = JT / 32;
-  for (int c = t; c < l; c += JT) {
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarps = blockDim.x / 32;
+  const int NTH = blockDim.x;
+  for (int c = t; c < l; c += NTH) {
     const double sc = sig[c];
     int rank = 0;
     for (int d = 0; d < l; ++d) {
@@ -241,8 +268,51 @@ jacobi_order_kernel(int l, int k, const double* __restrict__ U64, const double* 
   }
 }
 
+template <typename J, typename TS>
+__global__ void __launch_bounds__(JT)
+jacobi_order_kernel(int l, int k, const double* __restrict__ U64, const double* __restrict__ V64,
+                    const double* __restrict__ sig, J* __restrict__ Ut, J* __restrict__ Vt, TS* __restrict__ S) {
+  jacobi_order_body<J, TS>(l, k, U64, V64, sig, Ut, Vt, S);
+}
+
+// ---------------------------------------------------------------- batched
+// work of one problem: [V out: l^2 J][U64, V64: 2 l^2 f64][sig: l f64]
+template <typename J>
+struct BatchedWork {
+  J* vout; double* u64; double* v64; double* sig;
+  __host__ __device__ BatchedWork(void* w, int l) {
+    char* c = static_cast<char*>(w);
+    vout = reinterpret_cast<J*>(c);
+    u64 = reinterpret_cast<double*>(c + (((size_t)l * l * sizeof(J) + 15) & ~(size_t)15));
+    v64 = u64 + (size_t)l * l;
+    sig = v64 + (size_t)l * l;
+  }
+};
+
+template <typename J, int EPL, int NT>
+__global__ void __launch_bounds__(NT) jacobi_sweep_batched_kernel(const JacobiJob* __restrict__ jobs) {
+  const JacobiJob& jb = jobs[blockIdx.x];
+  BatchedWork<J> w(jb.work, jb.l);
+  jacobi_sweep_body<J, true, EPL>(jb.M, jb.l, w.vout, nullptr, jb.status);
+}
+
+template <typename J>
+__global__ void __launch_bounds__(256) jacobi_finish_batched_kernel(const JacobiJob* __restrict__ jobs) {
+  const JacobiJob& jb = jobs[blockIdx.y];
+  if ((int)blockIdx.x >= jb.l) return;
+  BatchedWork<J> w(jb.work, jb.l);
+  jacobi_finish_body<J>(jb.M, jb.l, w.vout, w.u64, w.v64, w.sig, blockIdx.x);
+}
+
+template <typename J>
+__global__ void __launch_bounds__(256) jacobi_order_batched_kernel(const JacobiJob* __restrict__ jobs) {
+  const JacobiJob& jb = jobs[blockIdx.x];
+  BatchedWork<J> w(jb.work, jb.l);
+  jacobi_order_body<J, J>(jb.l, jb.k, w.u64, w.v64, w.sig, (J*)jb.Ut, (J*)jb.Vt, (J*)jb.S);
+}
+
 template <typename J, bool IN_SMEM>
-cudaError_t launch_sweep(const double* M, int l, J* wout, J* gwork, size_t smem, DeviceStatus* status,
+cudaError_t launch_sweep(const double* M, int l, J* vout, J* gwork, size_t smem, DeviceStatus* status,
                          cudaStream_t st) {
   const int epl = (l + 7) / 8;
   // block size from the per-lane register footprint (2 EPL words per lane)
@@ -251,10 +321,10 @@ cudaError_t launch_sweep(const double* M, int l, J* wout, J* gwork, size_t smem,
     constexpr int NT = (E * sizeof(J) <= 64) ? 1024 : ((E * sizeof(J) <= 160) ? 512 : 256);          \
     if (IN_SMEM) {                                                                                    \
       cudaError_t e = cudaFuncSetAttribute(jacobi_sweep_kernel<J, IN_SMEM, E, NT>,                   \
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); \
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
       if (e != cudaSuccess) return e;                                                                 \
     }                                                                                                 \
-    jacobi_sweep_kernel<J, IN_SMEM, E, NT><<<1, NT, smem, st>>>(M, l, wout, gwork, status);          \
+    jacobi_sweep_kernel<J, IN_SMEM, E, NT><<<1, NT, smem, st>>>(M, l, vout, gwork, status);          \
     return cudaGetLastError();                                                                        \
   }
   if (epl <= 4) SWEEP(4)
@@ -266,21 +336,23 @@ cudaError_t launch_sweep(const double* M, int l, J* wout, J* gwork, size_t smem,
 #undef SWEEP
 }
 
+constexpr size_t kSweepSmemMax = 200 * 1024;
+
 template <typename J, typename TS>
 cudaError_t run_all(const double* M, int l, int k, void* Ut, void* Vt, void* S, void* work, DeviceStatus* status,
                     cudaStream_t st) {
-  // work: [sweep W fallback: l^2 J][W out: l^2 J][U64, V64: 2 l^2 f64][sig: l f64]
+  // work: [W, V fallback: 2 l^2 J][V out: l^2 J][U64, V64: 2 l^2 f64][sig: l f64]
   char* w = static_cast<char*>(work);
   J* gwork = reinterpret_cast<J*>(w);
-  J* wout = gwork + (size_t)l * l;
-  double* u64 = reinterpret_cast<double*>(w + ((2 * (size_t)l * l * sizeof(J) + 15) & ~(size_t)15));
+  J* vout = gwork + 2 * (size_t)l * l;
+  double* u64 = reinterpret_cast<double*>(w + ((3 * (size_t)l * l * sizeof(J) + 15) & ~(size_t)15));
   double* v64 = u64 + (size_t)l * l;
   double* sig = v64 + (size_t)l * l;
-  const size_t need = (size_t)l * l * sizeof(J);
-  cudaError_t e = (need <= 200 * 1024) ? launch_sweep<J, true>(M, l, wout, gwork, need, status, st)
-                                       : launch_sweep<J, false>(M, l, wout, gwork, 0, status, st);
+  const size_t need = 2 * (size_t)l * l * sizeof(J);
+  cudaError_t e = (need <= kSweepSmemMax) ? launch_sweep<J, true>(M, l, vout, gwork, need, status, st)
+                                          : launch_sweep<J, false>(M, l, vout, gwork, 0, status, st);
   if (e != cudaSuccess) return e;
-  jacobi_finish_kernel<J><<<l, 256, 0, st>>>(M, l, wout, u64, v64, sig);
+  jacobi_finish_kernel<J><<<l, 256, 0, st>>>(M, l, vout, u64, v64, sig);
   jacobi_order_kernel<J, TS><<<1, JT, 0, st>>>(l, k, u64, v64, sig, (J*)Ut, (J*)Vt, (TS*)S);
   return cudaGetLastError();
 }
@@ -288,7 +360,7 @@ cudaError_t run_all(const double* M, int l, int k, void* Ut, void* Vt, void* S, 
 }  // namespace
 
 size_t jacobi_work_bytes(int l) {
-  return ((2 * (size_t)l * l * sizeof(double) + 15) & ~(size_t)15) + 2 * (size_t)l * l * 8 + (size_t)l * 8;
+  return ((3 * (size_t)l * l * sizeof(double) + 15) & ~(size_t)15) + 2 * (size_t)l * l * 8 + (size_t)l * 8;
 }
 
 cudaError_t launch_jacobi(const double* M, int l, int k, bool f64, void* Ut, void* Vt, void* S, bool S_f64,
@@ -296,6 +368,50 @@ cudaError_t launch_jacobi(const double* M, int l, int k, bool f64, void* Ut, voi
   if (f64) return run_all<double, double>(M, l, k, Ut, Vt, S, work, status, st);
   if (S_f64) return cudaErrorInvalidValue;
   return run_all<float, float>(M, l, k, Ut, Vt, S, work, status, st);
+}
+
+int jacobi_batched_max_l(bool f64) { return f64 ? 112 : 160; }
+
+size_t jacobi_batched_work_bytes(int l) {
+  return (((size_t)l * l * sizeof(double) + 15) & ~(size_t)15) + 2 * (size_t)l * l * 8 + (size_t)l * 8;
+}
+
+cudaError_t launch_jacobi_batched(const JacobiJob* jobs, int njobs, int max_l, bool f64, cudaStream_t st) {
+  if (njobs <= 0) return cudaSuccess;
+  if (max_l < 1 || max_l > jacobi_batched_max_l(f64)) return cudaErrorInvalidValue;
+  const size_t smem = 2 * (size_t)max_l * max_l * (f64 ? 8 : 4);
+  const int epl = (max_l + 7) / 8;
+  // one problem per block: (l/2 pairs) x 8 lanes, rounded up to whole warps
+  const int pairs = (max_l + 1) / 2;
+  int nt = ((pairs * 8 + 31) / 32) * 32;
+#define BSWEEP(J, E)                                                                                        \
+  {                                                                                                         \
+    cudaError_t e = cudaFuncSetAttribute(jacobi_sweep_batched_kernel<J, E, 512>,                            \
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);           \
+    if (e != cudaSuccess) return e;                                                                         \
+    jacobi_sweep_batched_kernel<J, E, 512><<<njobs, std::min(nt, 512), smem, st>>>(jobs);                   \
+  }
+  if (f64) {
+    if (epl <= 4) BSWEEP(double, 4)
+    else if (epl <= 8) BSWEEP(double, 8)
+    else BSWEEP(double, 16)
+  } else {
+    if (epl <= 4) BSWEEP(float, 4)
+    else if (epl <= 8) BSWEEP(float, 8)
+    else if (epl <= 16) BSWEEP(float, 16)
+    else BSWEEP(float, 20)
+  }
+#undef BSWEEP
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (f64) {
+    jacobi_finish_batched_kernel<double><<<dim3(max_l, njobs), 256, 0, st>>>(jobs);
+    jacobi_order_batched_kernel<double><<<njobs, 256, 0, st>>>(jobs);
+  } else {
+    jacobi_finish_batched_kernel<float><<<dim3(max_l, njobs), 256, 0, st>>>(jobs);
+    jacobi_order_batched_kernel<float><<<njobs, 256, 0, st>>>(jobs);
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace sorsvd

@@ -6,7 +6,7 @@ namespace sorsvd {
 
 // kernel classes reported by sorsvd_profile_end (same numbering as the header)
 enum KClass { K_GAUSSIAN = 0, K_PASS = 1, K_CORE = 2, K_SMALL_GEMM = 3, K_REDUCE = 4, K_CHOL = 5,
-              K_JACOBI = 6, K_MISC = 7, K_NCLASS = 8 };
+              K_JACOBI = 6, K_MISC = 7, K_PASS_SPLIT = 8, K_RPCA = 9, K_NCLASS = 10 };
 
 void count_launches(int n);
 int prof_start(int cls, cudaStream_t st);   // -1 when profiling is off

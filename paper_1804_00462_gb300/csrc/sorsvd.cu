@@ -64,7 +64,8 @@ inline int elt_of(int dt) {
 
 struct Layout {
   int64_t ldm, ldn;      // leading dimensions of the m x l / n x l sketches
-  size_t status, at, t2op, t2, t1, t1op, q2op, tmp, parts, G, Rinv, M, Ut, Vt, jwork, total;
+  size_t status, at, t2op, t2, t1, t1op, q2op, tmp, bhi, blo, parts, G, Rinv, M, Ut, Vt, jwork, total;
+  int64_t ldb;           // leading dimension of bhi / blo
   bool has_at;           // fp32 containers: A^T kept for the products A X
 };
 
@@ -90,6 +91,12 @@ Layout make_layout(int64_t m, int64_t n, int l, int dt) {
   L.t1op = h16 ? take((size_t)L.ldm * l * op) : L.t1;
   L.q2op = h16 ? take((size_t)2 * L.ldn * l * op) : 0;
   L.tmp = take((size_t)ldx * l * acc);
+  // F32: hi / lo TF32 parts of the skinny operand of the split products
+  L.ldb = ldx;
+  if (dt == SORSVD_F32) {
+    L.bhi = take((size_t)ldx * l * 4);
+    L.blo = take((size_t)ldx * l * 4);
+  }
   // split-K partials of the CUDA-core products and the stream-K partials of
   // the tensor-core passes share one buffer (never live at the same time);
   // an l x l product always goes through it because its binary64 result is
@@ -177,8 +184,17 @@ int pass(const Ctx& c, int kcls, bool trans, int64_t M, int64_t N, int64_t K, co
     const void* Aop = use_at ? c.at(c.L.at) : A;
     const int64_t ldop = use_at ? c.L.ldn : lda;
     if ((!use_at || c.L.has_at) && tc_supported(elt, Aop, ldop, B, ldb, (int)N)) {
-      CK(launch_tc_gemm(trans || use_at, elt, M, N, K, Aop, ldop, B, ldb, (float*)C, ldc, C16, ld16,
-                        dt == SORSVD_BF16 ? 1 : 2, (float*)c.at(c.L.parts), c.status(), kcls, c.st));
+      const void* Bop = B;
+      int64_t ldbop = ldb;
+      if (elt == 3) {
+        // the skinny operand is split once per pass, the A tiles in the kernel
+        LAUNCH(K_MISC, launch_split_tf32((const float*)B, ldb, K, N, (float*)c.at(c.L.bhi),
+                                         (float*)c.at(c.L.blo), c.L.ldb, c.st));
+        Bop = c.at(c.L.bhi);
+        ldbop = c.L.ldb;
+      }
+      CK(launch_tc_gemm(trans || use_at, elt, M, N, K, Aop, ldop, Bop, ldbop, c.at(c.L.blo), (float*)C, ldc, C16,
+                        ld16, dt == SORSVD_BF16 ? 1 : 2, (float*)c.at(c.L.parts), c.status(), kcls, c.st));
       return SORSVD_OK;
     }
   }
@@ -220,11 +236,12 @@ int power_pass_impl(const Ctx& c, const void* A, int64_t m, int64_t n, int64_t l
   const bool h16 = dtype_is_16(dt);
   const int opdt = c.f64 ? SORSVD_F64 : (h16 ? dt : SORSVD_F32);
   void* t1op = h16 ? c.at(c.L.t1op) : nullptr;
-  int r = pass(c, K_PASS, false, m, l, n, A, lda, xop, ldx, opdt, T1, ldt1, t1op, c.L.ldm, precise);
+  const int kc = (precise && c.dt == SORSVD_F32) ? K_PASS_SPLIT : K_PASS;
+  int r = pass(c, kc, false, m, l, n, A, lda, xop, ldx, opdt, T1, ldt1, t1op, c.L.ldm, precise);
   if (r) return r;
   const void* y = h16 ? t1op : T1;
   const int64_t ldy = h16 ? c.L.ldm : ldt1;
-  return pass(c, K_PASS, true, n, l, m, A, lda, y, ldy, opdt, T2, ldt2, nullptr, 0, precise);
+  return pass(c, kc, true, n, l, m, A, lda, y, ldy, opdt, T2, ldt2, nullptr, 0, precise);
 }
 
 // M (l x l, f64, ldm) = Q1^T (A Q2)
@@ -260,6 +277,10 @@ int check_ws(void* ws, size_t ws_bytes, const Layout& L) {
 int max_l(int dt) { return dt == SORSVD_F64 ? SORSVD_MAX_L_F64 : SORSVD_MAX_L; }
 
 }  // namespace
+
+// the status word is the first region of every workspace layout
+DeviceStatus* workspace_status(void* ws) { return reinterpret_cast<DeviceStatus*>(ws); }
+
 }  // namespace sorsvd
 
 using namespace sorsvd;
@@ -307,6 +328,17 @@ int sorsvd_gaussian(void* out, int64_t rows, int64_t cols, int64_t ld, uint64_t 
   ProfScope ps(K_GAUSSIAN, (cudaStream_t)stream);
   if (launch_gaussian(out, rows, cols, ld, seed, stream_id, dtype, (cudaStream_t)stream) != cudaSuccess)
     return SORSVD_ERR_CUDA;
+  return SORSVD_OK;
+}
+
+int sorsvd_chol_inv(const double* G, int l, double shift_rel, int dtype, void* Rinv, void* status, void* stream) {
+  if (check_dtype(dtype)) return SORSVD_ERR_DTYPE;
+  if (!G || !Rinv || !status || l < 1 || !(shift_rel >= 0.0)) return SORSVD_ERR_ARG;
+  if (l > max_l(dtype)) return SORSVD_ERR_UNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaMemsetAsync(status, 0, sizeof(DeviceStatus), st));
+  ProfScope ps(K_CHOL, st);
+  CK(launch_chol_inv(G, l, shift_rel, Rinv, dtype == SORSVD_F64, (DeviceStatus*)status, st));
   return SORSVD_OK;
 }
 
@@ -368,25 +400,52 @@ int sorsvd_run(const void* A, int64_t m, int64_t n, int64_t lda, int k, int p, i
   r = prepare_at(c, A, m, n, lda);
   if (r) return r;
   LAUNCH(K_GAUSSIAN, launch_gaussian(c.at(L.t2op), n, l, L.ldn, seed, 0, dtype, c.st));
-  for (int i = 1; i <= q + 1; ++i) {
-    if (i > 1) {
-      if (!(flags & SORSVD_FLAG_LITERAL_POWER)) {
-        r = orth(c, c.at(L.t2), n, L.ldn, l, 1, first_shift(dtype));
-        if (r) return r;
-      }
+  if (flags & SORSVD_FLAG_LITERAL_POWER) {
+    // Algorithm 3 as printed: the sketches are orthonormalised only at the end
+    for (int i = 1; i <= q + 1; ++i) {
+      if (i > 1 && h16)
+        LAUNCH(K_MISC, launch_convert_f32((const float*)c.at(L.t2), L.ldn, n, l, c.at(L.t2op), L.ldn, dtype, nullptr,
+                                          c.st));
+      r = power_pass_impl(c, A, m, n, lda, c.at(L.t2op), L.ldn, l, c.at(L.t1), L.ldm, c.at(L.t2), L.ldn,
+                          i == q + 1);
+      if (r) return r;
+    }
+    r = orth(c, c.at(L.t1), m, L.ldm, l, 3, first_shift(dtype));
+    if (r) return r;
+    r = orth(c, c.at(L.t2), n, L.ldn, l, 3, first_shift(dtype));
+    if (r) return r;
+  } else {
+    // Each sketch is orthonormalised as soon as it is formed: T1 before the
+    // product A^T T1 and T2 before the next A T2.  By Lemma 1 this leaves
+    // range(T1) and range(T2) - hence Q1, Q2 and the result - unchanged,
+    // while every product sees the conditioning of A instead of its square
+    // (the trailing directions of a fast-decaying spectrum survive fp32).
+    // One CholeskyQR pass while the loop only steers the subspace, three
+    // (CholeskyQR3) in the last iteration, which fixes Q1 and Q2.
+    const int kc = dtype == SORSVD_F32 ? K_PASS_SPLIT : K_PASS;
+    void* t1op = h16 ? c.at(L.t1op) : c.at(L.t1);
+    for (int i = 1; i <= q + 1; ++i) {
+      const bool last = (i == q + 1);
+      const int np = last ? 3 : 1;
+      // F32: TF32 products while the loop only steers the subspace, the
+      // fp32-accurate split products in the last iteration
+      r = pass(c, last ? kc : K_PASS, false, m, l, n, A, lda, c.at(L.t2op), L.ldn, h16 ? dtype : adt, c.at(L.t1),
+               L.ldm, nullptr, 0, last);
+      if (r) return r;
+      r = orth(c, c.at(L.t1), m, L.ldm, l, np, first_shift(dtype));
+      if (r) return r;
       if (h16)
+        LAUNCH(K_MISC, launch_convert_f32((const float*)c.at(L.t1), L.ldm, m, l, t1op, L.ldm, dtype, nullptr, c.st));
+      r = pass(c, last ? kc : K_PASS, true, n, l, m, A, lda, t1op, L.ldm, h16 ? dtype : adt, c.at(L.t2), L.ldn,
+               nullptr, 0, last);
+      if (r) return r;
+      r = orth(c, c.at(L.t2), n, L.ldn, l, np, first_shift(dtype));
+      if (r) return r;
+      if (!last && h16)
         LAUNCH(K_MISC, launch_convert_f32((const float*)c.at(L.t2), L.ldn, n, l, c.at(L.t2op), L.ldn, dtype, nullptr,
                                           c.st));
     }
-    // F32: TF32 products while the power loop only steers the subspace, the
-    // fp32-accurate split products in the last pass that fixes Q1 and Q2
-    r = power_pass_impl(c, A, m, n, lda, c.at(L.t2op), L.ldn, l, c.at(L.t1), L.ldm, c.at(L.t2), L.ldn, i == q + 1);
-    if (r) return r;
   }
-  r = orth(c, c.at(L.t1), m, L.ldm, l, 3, first_shift(dtype));
-  if (r) return r;
-  r = orth(c, c.at(L.t2), n, L.ldn, l, 3, first_shift(dtype));
-  if (r) return r;
   r = core_impl(c, A, m, n, lda, flags, c.at(L.t1), L.ldm, c.at(L.t2), L.ldn, l, (double*)c.at(L.M), l);
   if (r) return r;
   LAUNCH(K_JACOBI, launch_jacobi((const double*)c.at(L.M), l, k, c.f64, c.at(L.Ut), c.at(L.Vt), S, c.f64,

@@ -105,6 +105,21 @@ def batched_matrix(m: int, n: int, seed: int):
     return spectral(m, n, sigma_poly(min(m, n), 2.0), seed)
 
 
+def batched_matrix_torch(m: int, n: int, seed: int, width: int = 256, device="cuda", dtype=None):
+    """sigma_i = i^-2 for i <= min(m, n, width) (Haar factors of that width,
+    drawn on the host) multiplied out on the GPU; the tail beyond ``width``
+    (sigma < 1.6e-5 sigma_1) is left out to keep 512 problems cheap to draw.
+    Returns a column-major tensor."""
+    import torch
+    r = min(m, n, width)
+    g = rng(seed, 6)
+    U = torch.from_numpy(haar(m, r, g)).to(device)
+    V = torch.from_numpy(haar(n, r, g)).to(device)
+    s = torch.from_numpy(sigma_poly(r, 2.0)).to(device)
+    A = (V * s[None, :]) @ U.T                       # (n, m) row-major = A column-major
+    return A.to(dtype or torch.float64).T
+
+
 def rpca_problem(m: int = 25344, n: int = 400, rank: int = 5, density: float = 0.05,
                  lo: float = 1.0, hi: float = 10.0, seed: int = 0):
     """X = L + S: L = G H^T (Gaussian factors), S with Bernoulli(density)

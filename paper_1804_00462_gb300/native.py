@@ -53,6 +53,9 @@ _lib.sorsvd_core.argtypes = [_vp, _i64, _i64, _i64, _int, _uint, _vp, _i64, _vp,
                              _vp, _sz, _vp]
 _lib.sorsvd_core.restype = _int
 
+_lib.sorsvd_chol_inv.argtypes = [_vp, _int, C.c_double, _int, _vp, _vp, _vp]
+_lib.sorsvd_chol_inv.restype = _int
+
 lib = _lib
 
 
@@ -206,9 +209,205 @@ def core(A: torch.Tensor, Q1: torch.Tensor, Q2: torch.Tensor, k: int, p: int, dt
     return M
 
 
+def chol_inv(G: torch.Tensor, shift_rel: float, dtype=F32, stream=None):
+    """R^{-1} of a CholeskyQR step for the binary64 Gram G (l x l CUDA
+    tensor).  Returns (Rinv, status, info)."""
+    if G.dtype != torch.float64 or G.dim() != 2 or G.shape[0] != G.shape[1]:
+        raise ValueError("G must be a square binary64 CUDA tensor")
+    l = G.shape[0]
+    Gc = G.T.contiguous().T if G.stride(0) != 1 else G
+    code = dtype_code(dtype)
+    R = colmajor_empty(l, l, out_dtype(code), G.device)
+    st = torch.zeros(64, dtype=torch.uint8, device=G.device)
+    _check(_lib.sorsvd_chol_inv(Gc.data_ptr(), l, shift_rel, code, R.data_ptr(), st.data_ptr(), _stream(stream)),
+           "sorsvd_chol_inv")
+    s, info = get_status(st, stream)
+    return R, s, info
+
+
+# ---- batched SOR-SVD ----------------------------------------------------------
+class Problem(C.Structure):
+    """sorsvd_problem of the C header."""
+    _fields_ = [("A", _vp), ("m", _i64), ("n", _i64), ("lda", _i64), ("k", _int), ("p", _int), ("q", _int),
+                ("seed", _u64), ("U", _vp), ("ldu", _i64), ("S", _vp), ("V", _vp), ("ldv", _i64)]
+
+
+_lib.sorsvd_batched_workspace_size.argtypes = [C.POINTER(Problem), _int, _int, _uint]
+_lib.sorsvd_batched_workspace_size.restype = _sz
+_lib.sorsvd_batched_plan_create.argtypes = [C.POINTER(_vp), C.POINTER(Problem), _int, _int, _uint, _int, _vp, _sz,
+                                            _vp]
+_lib.sorsvd_batched_plan_create.restype = _int
+_lib.sorsvd_batched_plan_launch.argtypes = [_vp, _vp]
+_lib.sorsvd_batched_plan_launch.restype = _int
+_lib.sorsvd_batched_plan_status.argtypes = [_vp, C.POINTER(_int), _vp]
+_lib.sorsvd_batched_plan_status.restype = _int
+_lib.sorsvd_batched_plan_launches.argtypes = [_vp]
+_lib.sorsvd_batched_plan_launches.restype = _int
+_lib.sorsvd_batched_plan_destroy.argtypes = [_vp]
+_lib.sorsvd_batched_plan_destroy.restype = None
+_lib.sorsvd_run_batched.argtypes = [C.POINTER(Problem), _int, _int, _uint, _vp, _sz, _vp]
+_lib.sorsvd_run_batched.restype = _int
+
+
+def _per(v, n):
+    return list(v) if isinstance(v, (list, tuple)) else [v] * n
+
+
+class BatchedPlan:
+    """A batch of SOR-SVD problems (column-major CUDA matrices ``As`` of one
+    dtype, per-problem k, p, q, seed) with its outputs and workspace, planned
+    once (optionally captured in a CUDA graph) and run by ``launch``.
+    ``U[b]`` (m x k), ``S[b]`` (k), ``V[b]`` (n x k) hold problem b's result."""
+
+    def __init__(self, As, ks, p, q, seeds=0, dtype=None, flags: int = 0, use_graph: bool = True, stream=None):
+        nb = len(As)
+        ks, ps, qs, seeds = _per(ks, nb), _per(p, nb), _per(q, nb), _per(seeds, nb)
+        code = dtype_code(dtype if dtype is not None else As[0].dtype)
+        od = out_dtype(code)
+        self.As = list(As)
+        self.U, self.S, self.V = [], [], []
+        arr = (Problem * nb)()
+        for b, A in enumerate(self.As):
+            ptr, m, n, lda, trans = _colmajor(A)
+            if trans or A.dtype != _TORCH_OF[code]:
+                raise ValueError("batched problems need column-major matrices of the plan's dtype")
+            U = colmajor_empty(m, ks[b], od, A.device)
+            S = torch.empty(ks[b], dtype=od, device=A.device)
+            V = colmajor_empty(n, ks[b], od, A.device)
+            self.U.append(U); self.S.append(S); self.V.append(V)
+            arr[b] = Problem(ptr, m, n, lda, ks[b], ps[b], qs[b], int(seeds[b]) & 0xFFFFFFFFFFFFFFFF,
+                             U.data_ptr(), U.stride(1), S.data_ptr(), V.data_ptr(), V.stride(1))
+        need = int(_lib.sorsvd_batched_workspace_size(arr, nb, code, flags))
+        if need == 0:
+            raise SorsvdError(1, "sorsvd_batched_workspace_size")
+        self.workspace = torch.empty(need, dtype=torch.uint8, device=self.As[0].device)
+        self.batch = nb
+        self._arr = arr
+        h = _vp()
+        _check(_lib.sorsvd_batched_plan_create(C.byref(h), arr, nb, code, flags, 1 if use_graph else 0,
+                                               self.workspace.data_ptr(), need, _stream(stream)),
+               "sorsvd_batched_plan_create")
+        self._h = h
+
+    def launch(self, stream=None):
+        _check(_lib.sorsvd_batched_plan_launch(self._h, _stream(stream)), "sorsvd_batched_plan_launch")
+
+    def status(self, stream=None):
+        codes = (_int * self.batch)()
+        _check(_lib.sorsvd_batched_plan_status(self._h, codes, _stream(stream)), "sorsvd_batched_plan_status")
+        return list(codes)
+
+    @property
+    def launches(self) -> int:
+        return int(_lib.sorsvd_batched_plan_launches(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.sorsvd_batched_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def run_batched(As, ks, p, q, seeds=0, dtype=None, flags: int = 0, stream=None):
+    """One-shot batched SOR-SVD (no graph); returns [(U, S, V) per problem]."""
+    plan = BatchedPlan(As, ks, p, q, seeds, dtype, flags, use_graph=False, stream=stream)
+    plan.launch(stream)
+    out = list(zip(plan.U, plan.S, plan.V))
+    plan.close()
+    return out
+
+
+def batched_workspace_size(problems, dtype, flags: int = 0) -> int:
+    """Workspace bytes for a list of (m, n, k, p, q) (no device memory touched)."""
+    nb = len(problems)
+    arr = (Problem * nb)()
+    for b, (m, n, k, p, q) in enumerate(problems):
+        arr[b] = Problem(1, m, n, m, k, p, q, 0, 1, m, 1, 1, n)
+    return int(_lib.sorsvd_batched_workspace_size(arr, nb, dtype_code(dtype), flags))
+
+
+# ---- robust PCA ---------------------------------------------------------------
+class RpcaProblem(C.Structure):
+    """sorsvd_rpca_problem of the C header."""
+    _fields_ = [("X", _vp), ("m", _i64), ("n", _i64), ("ldx", _i64),
+                ("L", _vp), ("ldl", _i64), ("S", _vp), ("lds", _i64),
+                ("norm2", C.c_double), ("seed", _u64)]
+
+
+RPCA_FINISH_F64 = 0x100
+_lib.sorsvd_rpca_workspace_size.argtypes = [C.POINTER(RpcaProblem), _int, _int, _int, _int, _uint]
+_lib.sorsvd_rpca_workspace_size.restype = _sz
+_lib.sorsvd_rpca.argtypes = [C.POINTER(RpcaProblem), _int, _int, _int, _int, _int, _uint, C.c_double, _int,
+                             C.c_double, C.POINTER(_int), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                             _vp, _sz, _vp]
+_lib.sorsvd_rpca.restype = _int
+
+
+def _rpca_problems(Xs, Ls, Ss, seeds, norm2s):
+    arr = (RpcaProblem * len(Xs))()
+    for b, X in enumerate(Xs):
+        ptr, m, n, ldx, trans = _colmajor(X)
+        if trans or X.dtype != torch.float32:
+            raise ValueError("rpca needs column-major fp32 matrices")
+        arr[b] = RpcaProblem(ptr, m, n, ldx, Ls[b].data_ptr(), Ls[b].stride(1), Ss[b].data_ptr(),
+                             Ss[b].stride(1), float(norm2s[b]), int(seeds[b]) & 0xFFFFFFFFFFFFFFFF)
+    return arr
+
+
+def rpca(Xs, k: int, p: int, q: int, seeds=0, norm2=None, dtype=F32, finish_f64: bool = True,
+         tol: float = 1e-7, max_iter: int = 50, rho: float = 1.5, workspace: torch.Tensor | None = None,
+         stream=None):
+    """Robust PCA (inexact ALM with SOR-SVD, Table 3) of each column-major
+    fp32 matrix in ``Xs`` (a tensor or a list).  ``seeds`` / ``norm2``: one
+    value or one per problem (norm2 <= 0 or None: estimated on the device).
+    ``dtype``: inner SOR-SVD type; ``finish_f64``: switch it to binary64
+    near convergence (SORSVD_RPCA_FINISH_F64).
+    Returns (Ls, Ss, iters, xi, xi_history) with xi_history a (batch,
+    max_iter) CPU tensor (entries past iters[b] are zero)."""
+    single = isinstance(Xs, torch.Tensor)
+    Xs = [Xs] if single else list(Xs)
+    nb = len(Xs)
+    seeds = [seeds] * nb if isinstance(seeds, int) else list(seeds)
+    norm2s = [0.0 if norm2 is None else norm2] * nb if not isinstance(norm2, (list, tuple)) else list(norm2)
+    Ls = [colmajor_empty(X.shape[0], X.shape[1], torch.float32, X.device) for X in Xs]
+    Ss = [colmajor_empty(X.shape[0], X.shape[1], torch.float32, X.device) for X in Xs]
+    arr = _rpca_problems(Xs, Ls, Ss, seeds, norm2s)
+    code = dtype_code(dtype)
+    flags = RPCA_FINISH_F64 if finish_f64 else 0
+    need = int(_lib.sorsvd_rpca_workspace_size(arr, nb, k, p, code, flags))
+    if need == 0:
+        raise SorsvdError(1, "sorsvd_rpca_workspace_size")
+    if workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device=Xs[0].device)
+    iters = (_int * nb)()
+    xi = (C.c_double * nb)()
+    hist = (C.c_double * (nb * max_iter))()
+    _check(_lib.sorsvd_rpca(arr, nb, k, p, q, code, flags, tol, max_iter, rho, iters, xi, hist,
+                            workspace.data_ptr(), workspace.numel(), _stream(stream)), "sorsvd_rpca")
+    xh = torch.tensor(list(hist), dtype=torch.float64).reshape(nb, max_iter)
+    if single:
+        return Ls[0], Ss[0], iters[0], xi[0], xh[0]
+    return Ls, Ss, list(iters), list(xi), xh
+
+
+def rpca_workspace_size(Xs, k: int, p: int, dtype=F32, norm2=None, finish_f64: bool = True) -> int:
+    Xs = [Xs] if isinstance(Xs, torch.Tensor) else list(Xs)
+    nb = len(Xs)
+    norm2s = [0.0 if norm2 is None else norm2] * nb if not isinstance(norm2, (list, tuple)) else list(norm2)
+    arr = _rpca_problems(Xs, Xs, Xs, [0] * nb, norm2s)
+    return int(_lib.sorsvd_rpca_workspace_size(arr, nb, k, p, dtype_code(dtype),
+                                               RPCA_FINISH_F64 if finish_f64 else 0))
+
+
 # ---- launch accounting ------------------------------------------------------
-NUM_KCLASS = 8
-KCLASS_NAMES = ("gaussian", "pass", "core_pass", "small_gemm", "reduce", "chol", "jacobi", "misc")
+NUM_KCLASS = 10
+KCLASS_NAMES = ("gaussian", "pass", "core_pass", "small_gemm", "reduce", "chol", "jacobi", "misc", "pass_split",
+                "rpca")
 _lib.sorsvd_launch_count.argtypes = []
 _lib.sorsvd_launch_count.restype = C.c_uint64
 _lib.sorsvd_profile_begin.argtypes = [_uint]

@@ -80,3 +80,76 @@ def test_run_rejects_bad_arguments_before_any_device_work():
     assert call() == 7                              # no workspace
     assert call(ws=0x1010, wsb=1 << 30) == 7        # misaligned workspace
     assert call(ws=0x1000, wsb=16) == 7             # too small
+
+
+def test_rpca_rejects_bad_arguments_before_any_device_work():
+    from paper_1804_00462_gb300 import native as nat
+    lib = nat.lib
+    fake = 0x1000
+    prob = nat.RpcaProblem(fake, 1000, 100, 1000, fake, 1000, fake, 1000, 10.0, 0)
+    arr = (nat.RpcaProblem * 1)(prob)
+    it = (C.c_int * 1)()
+    xi = (C.c_double * 1)()
+
+    def call(arr=arr, batch=1, k=5, p=5, q=1, dt=nat.F32, fl=0, tol=1e-7, mi=50, rho=1.5, ws=None, wsb=0):
+        return lib.sorsvd_rpca(arr, batch, k, p, q, dt, fl, tol, mi, rho, it, xi, None, ws, wsb, None)
+    assert call(dt=nat.BF16) == 2
+    assert call(dt=nat.F16) == 2
+    assert call(fl=0x1) == 1
+    assert call(batch=0) == 1
+    assert call(tol=0.0) == 1
+    assert call(mi=0) == 1
+    assert call(rho=0.5) == 1
+    assert call(q=-1) == 1
+    assert call(k=0) == 1
+    assert call(k=96, p=5) == 1                    # l = 101 > min(m, n)
+    bad = (nat.RpcaProblem * 1)(nat.RpcaProblem(fake, 1000, 100, 999, fake, 1000, fake, 1000, 10.0, 0))
+    assert call(arr=bad) == 1                      # ldx < m
+    nul = (nat.RpcaProblem * 1)(nat.RpcaProblem(None, 1000, 100, 1000, fake, 1000, fake, 1000, 10.0, 0))
+    assert call(arr=nul) == 1
+    assert call() == 7                             # no workspace
+    need = lib.sorsvd_rpca_workspace_size(arr, 1, 5, 5, nat.F32, 0)
+    assert need > 2 * 1000 * 100 * 4
+    assert call(ws=256, wsb=need - 1) == 7
+    assert lib.sorsvd_rpca_workspace_size(arr, 1, 5, 5, nat.BF16, 0) == 0
+    mixed = lib.sorsvd_rpca_workspace_size(arr, 1, 5, 5, nat.F32, nat.RPCA_FINISH_F64)
+    assert mixed >= need + 1000 * 100 * 8          # + the binary64 copy of G
+    assert call(fl=nat.RPCA_FINISH_F64, ws=256, wsb=mixed - 1) == 7
+
+
+def test_batched_rejects_bad_arguments_before_any_device_work():
+    from paper_1804_00462_gb300 import native as nat
+    lib = nat.lib
+    fake = 0x1000
+
+    def prob(**kw):
+        d = dict(A=fake, m=300, n=200, lda=300, k=10, p=8, q=1, seed=0, U=fake, ldu=300, S=fake, V=fake, ldv=200)
+        d.update(kw)
+        return nat.Problem(d["A"], d["m"], d["n"], d["lda"], d["k"], d["p"], d["q"], d["seed"], d["U"], d["ldu"],
+                           d["S"], d["V"], d["ldv"])
+
+    def arr(*ps):
+        return (nat.Problem * len(ps))(*ps)
+    good = arr(prob(), prob(m=50, n=400, lda=50, ldu=50, ldv=400, k=3, p=2, q=0))
+    assert lib.sorsvd_batched_workspace_size(good, 2, nat.F32, 0) > 0
+    assert lib.sorsvd_batched_workspace_size(good, 2, nat.F64, 0) > lib.sorsvd_batched_workspace_size(good, 2, nat.F32, 0)
+    assert lib.sorsvd_batched_workspace_size(good, 0, nat.F32, 0) == 0
+    assert lib.sorsvd_batched_workspace_size(good, 2, nat.BF16, 0) == 0
+    assert lib.sorsvd_batched_workspace_size(good, 2, nat.F32, nat.FLAG_REFINE) == 0
+    assert lib.sorsvd_batched_workspace_size(arr(prob(lda=299)), 1, nat.F32, 0) == 0
+    assert lib.sorsvd_batched_workspace_size(arr(prob(k=195, p=10)), 1, nat.F32, 0) == 0   # l > min(m, n)
+    h = C.c_void_p()
+
+    def create(a, n, dt=nat.F32, fl=0, ws=None, wsb=0):
+        return lib.sorsvd_batched_plan_create(C.byref(h), a, n, dt, fl, 0, ws, wsb, None)
+    assert create(good, 2, dt=nat.F16) == 2
+    assert create(good, 2, fl=0x80) == 1
+    assert create(arr(prob(A=None)), 1) == 1
+    assert create(arr(prob(m=2000, n=2000, lda=2000, ldu=2000, ldv=2000, k=150, p=20)), 1) == 8   # l > 160
+    assert create(arr(prob(m=2000, n=2000, lda=2000, ldu=2000, ldv=2000, k=120, p=9)), 1, dt=nat.F64) == 8
+    assert create(good, 2) == 7                      # no workspace
+    assert h.value is None
+    need = lib.sorsvd_batched_workspace_size(good, 2, nat.F32, 0)
+    assert create(good, 2, ws=256, wsb=need - 1) == 7
+    assert lib.sorsvd_batched_plan_launch(None, None) == 1
+    lib.sorsvd_batched_plan_destroy(None)

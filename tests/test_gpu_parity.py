@@ -265,3 +265,45 @@ def test_run_cfg2_full_size(nat):
     exact, got, ref = run_both(nat, A64, 100, 10, 1, 0, "f32")
     r_gpu, r_orc, ds = gates(exact, got, ref)
     assert abs(r_gpu - r_orc) <= 1e-5 and ds <= 1e-5, (r_gpu, r_orc, ds)
+
+
+# ---- CholeskyQR building block ---------------------------------------------
+def _rinv_ref(G, shift):
+    d = 1.0 / np.sqrt(np.diag(G))
+    Gs = G * d[:, None] * d[None, :] + shift * np.eye(G.shape[0])
+    L = np.linalg.cholesky(Gs)
+    return d[:, None] * np.linalg.inv(L).T
+
+
+@pytest.mark.parametrize("dt,l", [("f32", 1), ("f32", 7), ("f32", 32), ("f32", 33), ("f32", 110), ("f32", 266),
+                                  ("f32", 300), ("f64", 25), ("f64", 150), ("f64", 224)])
+def test_chol_inv_matches_numpy(nat, dt, l):
+    g = np.random.default_rng(l)
+    T = g.standard_normal((2 * l + 3, l)) * np.exp(np.linspace(0, -3, l))[None, :]
+    G = T.T @ T
+    R, st, info = nat.chol_inv(torch.from_numpy(G).cuda(), 1e-5 if dt == "f32" else 1e-13, dtype=dt)
+    torch.cuda.synchronize()
+    assert st == 0 and (info & 1) == 0
+    Rg = R.double().cpu().numpy()
+    Rr = _rinv_ref(G, 1e-5 if dt == "f32" else 1e-13)
+    assert np.array_equal(np.tril(Rg, -1), np.zeros_like(Rg))
+    tol = 2e-4 if dt == "f32" else 1e-10
+    assert np.linalg.norm(Rg - Rr) <= tol * np.linalg.norm(Rr)
+    Q = T @ Rg
+    assert np.abs(Q.T @ Q - np.eye(l)).max() <= (5e-3 if dt == "f32" else 1e-9)
+
+
+def test_chol_inv_retry_and_breakdown(nat):
+    g = np.random.default_rng(0)
+    T = g.standard_normal((50, 20))
+    T[:, 5] = T[:, 4]                               # rank deficient: the unshifted factorisation fails
+    G = T.T @ T
+    R, st, info = nat.chol_inv(torch.from_numpy(G).cuda(), 0.0, dtype="f32")
+    torch.cuda.synchronize()
+    assert st == 0 and (info & 1) == 1
+    assert np.all(np.isfinite(R.cpu().numpy()))
+    G[3, 4] = G[4, 3] = np.nan                      # no shift makes this factorisable
+    R, st, info = nat.chol_inv(torch.from_numpy(G).cuda(), 0.0, dtype="f32")
+    torch.cuda.synchronize()
+    assert st == 5                                  # SORSVD_ERR_BREAKDOWN
+    assert np.array_equal(R.cpu().numpy(), np.eye(20, dtype=np.float32))
