@@ -159,6 +159,105 @@ __device__ __forceinline__ void jacobi_sweep_body(const double* __restrict__ Min
   for (int e = t; e < l * l; e += blockDim.x) Vout[e] = V[e];
 }
 
+// fp32 sweeps with packed pairs: W and V columns are zero-padded to
+// ldw = 16 EP rows, lane gl of a pair's 8-lane group holds the element
+// pairs (2 (gl + 8 e), +1), e < EP, so the loops need no bounds tests, and
+// the inner products and the rotation run as paired fp32 operations
+// (__ffma2_rn / __fmul2_rn: two lanes of fp32 FMA per instruction, same
+// rounding as two fma calls).  Same pair schedule, tolerance and cap as the
+// generic body.
+template <int EP>
+__device__ __forceinline__ void jacobi_sweep_body_f2(const double* __restrict__ Min, int l, float* __restrict__ Vout,
+                                                     DeviceStatus* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_rot, s_big;
+  const int ldw = 16 * EP;
+  float* W = reinterpret_cast<float*>(smem_raw);
+  float* V = W + (size_t)ldw * l;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int grp = lane >> 3, gl = lane & 7;
+  const int ngroups = (blockDim.x >> 5) * 4;
+  const unsigned gmask = 0xFFu << (grp * 8);
+  const float eps = 1.1920928955078125e-07f;
+  const float tol = (float)l * eps, tol2 = tol * tol;
+  const float big = 32.f * tol, big2 = big * big;
+
+  for (int e = t; e < ldw * l; e += blockDim.x) {
+    const int c = e / ldw, i = e - c * ldw;
+    W[e] = i < l ? (float)Min[i + (size_t)c * l] : 0.f;
+    V[e] = (i == c) ? 1.f : 0.f;
+  }
+  __syncthreads();
+
+  const int N = (l + 1) & ~1;
+  int sweep;
+  for (sweep = 1; sweep <= kMaxSweeps; ++sweep) {
+    if (t == 0) { s_rot = 0; s_big = 0; }
+    __syncthreads();
+    int rot_local = 0, big_local = 0;
+    for (int r = 0; r < N - 1; ++r) {
+      for (int pr = warp * 4 + grp; pr < N / 2; pr += ngroups) {
+        const int a = rr_player(pr, r, N), b = rr_player(N - 1 - pr, r, N);
+        if (a >= l || b >= l) continue;                // bye (whole group)
+        const size_t oa = (size_t)min(a, b) * ldw, ob = (size_t)max(a, b) * ldw;
+        float2* wp = reinterpret_cast<float2*>(W + oa);
+        float2* wq = reinterpret_cast<float2*>(W + ob);
+        float2 x[EP], y[EP];
+        float2 al2 = make_float2(0.f, 0.f), be2 = al2, ga2 = al2;
+#pragma unroll
+        for (int e = 0; e < EP; ++e) {
+          x[e] = wp[gl + 8 * e];
+          y[e] = wq[gl + 8 * e];
+          al2 = __ffma2_rn(x[e], x[e], al2);
+          be2 = __ffma2_rn(y[e], y[e], be2);
+          ga2 = __ffma2_rn(x[e], y[e], ga2);
+        }
+        float al = al2.x + al2.y, be = be2.x + be2.y, ga = ga2.x + ga2.y;
+        al = group8_sum(al, gmask); be = group8_sum(be, gmask); ga = group8_sum(ga, gmask);
+        if (!(ga * ga > tol2 * al * be)) continue;
+        if (ga * ga > big2 * al * be) big_local = 1;
+        float cs, sn;
+        rotation(al, be, ga, &cs, &sn);
+        const float2 c2 = make_float2(cs, cs), s2 = make_float2(sn, sn), ns2 = make_float2(-sn, -sn);
+        float2* vp = reinterpret_cast<float2*>(V + oa);
+        float2* vq = reinterpret_cast<float2*>(V + ob);
+#pragma unroll
+        for (int e = 0; e < EP; ++e) {
+          const int i = gl + 8 * e;
+          wp[i] = __ffma2_rn(c2, x[e], __fmul2_rn(ns2, y[e]));
+          wq[i] = __ffma2_rn(s2, x[e], __fmul2_rn(c2, y[e]));
+          const float2 u = vp[i], v = vq[i];
+          vp[i] = __ffma2_rn(c2, u, __fmul2_rn(ns2, v));
+          vq[i] = __ffma2_rn(s2, u, __fmul2_rn(c2, v));
+        }
+        rot_local = 1;
+      }
+      __syncthreads();
+    }
+    if (rot_local) s_rot = 1;
+    if (big_local) s_big = 1;
+    __syncthreads();
+    const int rot = s_rot, bg = s_big;
+    __syncthreads();
+    if (!rot) break;
+    if (sweep == kMaxSweeps) {
+      if (bg && t == 0) raise_status(status, SORSVD_ERR_NOT_CONVERGED);
+      break;
+    }
+  }
+  if (t == 0) atomicOr(&status->info, (min(sweep, kMaxSweeps)) << 8);
+  for (int e = t; e < l * l; e += blockDim.x) {
+    const int c = e / l, i = e - c * l;
+    Vout[e] = V[i + (size_t)c * ldw];
+  }
+}
+
+template <int EP>
+__global__ void __launch_bounds__(512)
+jacobi_sweep_f2_kernel(const double* __restrict__ Min, int l, float* __restrict__ Vout, DeviceStatus* status) {
+  jacobi_sweep_body_f2<EP>(Min, l, Vout, status);
+}
+
 template <typename J, bool IN_SMEM, int EPL, int NT>
 __global__ void __launch_bounds__(NT)
 jacobi_sweep_kernel(const double* __restrict__ Min, int l, J* __restrict__ Vout, J* __restrict__ gwork,
@@ -338,6 +437,45 @@ cudaError_t launch_sweep(const double* M, int l, J* vout, J* gwork, size_t smem,
 
 constexpr size_t kSweepSmemMax = 200 * 1024;
 
+// template EP of the paired sweep for l (the kernel's row stride is 16 EP)
+inline int sweep_f2_ep(int l) {
+  const int need = (l + 15) / 16;
+  const int eps[] = {2, 4, 6, 7, 8, 10};
+  for (int e : eps)
+    if (need <= e) return e;
+  return 0;                                        // l > 160: not handled
+}
+inline size_t sweep_f2_smem(int l) {
+  const int ep = sweep_f2_ep(l);
+  return ep ? 2 * (size_t)16 * ep * l * sizeof(float) : (size_t)-1;
+}
+
+cudaError_t launch_sweep_f2(const double* M, int l, float* vout, DeviceStatus* status, cudaStream_t st) {
+  const int ep = sweep_f2_ep(l);
+  const size_t smem = sweep_f2_smem(l);            // sized with the same EP the kernel indexes with
+  if (!ep || smem > kSweepSmemMax) return cudaErrorInvalidValue;
+  // one 8-lane group per pair: (l/2 pairs) x 8 lanes, whole warps, <= 512
+  const int nt = std::min(512, (((l + 1) / 2 * 8 + 31) / 32) * 32);
+#define F2SWEEP(E)                                                                                  \
+  {                                                                                                 \
+    cudaError_t e = cudaFuncSetAttribute(jacobi_sweep_f2_kernel<E>,                                \
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
+    if (e != cudaSuccess) return e;                                                                 \
+    jacobi_sweep_f2_kernel<E><<<1, nt, smem, st>>>(M, l, vout, status);                            \
+    return cudaGetLastError();                                                                      \
+  }
+  switch (ep) {
+    case 2: F2SWEEP(2)
+    case 4: F2SWEEP(4)
+    case 6: F2SWEEP(6)
+    case 7: F2SWEEP(7)
+    case 8: F2SWEEP(8)
+    case 10: F2SWEEP(10)
+    default: return cudaErrorInvalidValue;
+  }
+#undef F2SWEEP
+}
+
 template <typename J, typename TS>
 cudaError_t run_all(const double* M, int l, int k, void* Ut, void* Vt, void* S, void* work, DeviceStatus* status,
                     cudaStream_t st) {
@@ -349,8 +487,12 @@ cudaError_t run_all(const double* M, int l, int k, void* Ut, void* Vt, void* S, 
   double* v64 = u64 + (size_t)l * l;
   double* sig = v64 + (size_t)l * l;
   const size_t need = 2 * (size_t)l * l * sizeof(J);
-  cudaError_t e = (need <= kSweepSmemMax) ? launch_sweep<J, true>(M, l, vout, gwork, need, status, st)
-                                          : launch_sweep<J, false>(M, l, vout, gwork, 0, status, st);
+  cudaError_t e;
+  if (sizeof(J) == 4 && sweep_f2_smem(l) <= kSweepSmemMax)
+    e = launch_sweep_f2(M, l, reinterpret_cast<float*>(vout), status, st);
+  else
+    e = (need <= kSweepSmemMax) ? launch_sweep<J, true>(M, l, vout, gwork, need, status, st)
+                                : launch_sweep<J, false>(M, l, vout, gwork, 0, status, st);
   if (e != cudaSuccess) return e;
   jacobi_finish_kernel<J><<<l, 256, 0, st>>>(M, l, vout, u64, v64, sig);
   jacobi_order_kernel<J, TS><<<1, JT, 0, st>>>(l, k, u64, v64, sig, (J*)Ut, (J*)Vt, (TS*)S);
