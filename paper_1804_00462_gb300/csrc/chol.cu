@@ -220,7 +220,8 @@ __device__ __forceinline__ F inv_col_warp(const F* D, int c, int lane, const F* 
 
 template <typename F>
 __device__ __forceinline__ void chol_inv_blocked_body(const double* __restrict__ G, int l, double shift_rel,
-                                                      F* __restrict__ Rinv, DeviceStatus* status) {
+                                                      F* __restrict__ Rinv, DeviceStatus* status,
+                                                      const int* skip_in, int* conv_out, float conv_tol) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nb = (l + TB - 1) / TB;
   const int ntile = nb * (nb + 1) / 2;
@@ -230,10 +231,17 @@ __device__ __forceinline__ void chol_inv_blocked_body(const double* __restrict__
   F* dsf = reinterpret_cast<F*>(dscale + nb * TB);                   // the same in F
   F* rdiag = dsf + nb * TB;                                          // 1 / L_jj
   __shared__ int s_fail, s_retry;
+  __shared__ unsigned s_offmax;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const F eps = sizeof(F) == 8 ? (F)2.220446049250313e-16 : (F)1.1920928955078125e-07;
   const F thr = (F)4 * eps;
   auto tile = [&](int I, int J) { return T + (size_t)tid_of(I, J) * TS; };
+  // an earlier pass found the columns orthonormal: R^{-1} = I
+  if (skip_in && *skip_in) {
+    for (int e = t; e < l * l; e += BT) Rinv[e] = (e % l == e / l) ? (F)1 : (F)0;
+    return;
+  }
+  if (t == 0) s_offmax = 0u;
 
   for (int i = t; i < nb * TB; i += BT) {
     double d = i < l ? G[i + (int64_t)i * l] : 0.0;
@@ -248,8 +256,10 @@ __device__ __forceinline__ void chol_inv_blocked_body(const double* __restrict__
   int attempt = 0;
   for (; attempt < max_try; ++attempt) {
     // equilibrated, shifted Gram in the lower tiles (factor precision);
-    // padding and zero columns of T become identity rows / columns
+    // padding and zero columns of T become identity rows / columns; the
+    // largest off-diagonal entry (a column cosine) is recorded for conv_out
     const F fshift = (F)shift;
+    float offmax = 0.f;
     for (int I = 0; I < nb; ++I)
       for (int J = 0; J <= I; ++J) {
         F* D = tile(I, J);
@@ -259,10 +269,15 @@ __device__ __forceinline__ void chol_inv_blocked_body(const double* __restrict__
           const F si = dsf[gi], sc = dsf[gc];
           F v;
           if (si == (F)0 || sc == (F)0) v = (gi == gc) ? (F)1 : (F)0;
-          else v = (F)G[gc + (int64_t)gi * l] * si * sc + (gi == gc ? fshift : (F)0);   // G symmetric: coalesced
+          else {
+            v = (F)G[gc + (int64_t)gi * l] * si * sc;   // G symmetric: coalesced
+            if (gi > gc) offmax = fmaxf(offmax, fabsf((float)v));
+            if (gi == gc) v += fshift;
+          }
           D[r * TLD + c] = v;
         }
       }
+    if (conv_out && attempt == 0) atomicMax(&s_offmax, __float_as_uint(offmax));
     if (t == 0) s_fail = 0;
     __syncthreads();
     for (int K = 0; K < nb && !s_fail; ++K) {
@@ -339,6 +354,7 @@ __device__ __forceinline__ void chol_inv_blocked_body(const double* __restrict__
     return;
   }
   if (t == 0 && s_retry) atomicOr(&status->info, 1);
+  if (conv_out && t == 0) *conv_out = (__uint_as_float(s_offmax) <= conv_tol && !s_retry) ? 1 : 0;
 
   // X_II = L_II^{-1}: warp w solves L x = e_c for the columns c = w, w + NW,
   // ... of every diagonal tile, all its columns' chains interleaved (lane =
@@ -458,15 +474,15 @@ __device__ __forceinline__ void chol_inv_blocked_body(const double* __restrict__
 template <typename F>
 __global__ void __launch_bounds__(BT)
 chol_inv_blocked_kernel(const double* __restrict__ G, int l, double shift_rel, F* __restrict__ Rinv,
-                        DeviceStatus* status) {
-  chol_inv_blocked_body<F>(G, l, shift_rel, Rinv, status);
+                        DeviceStatus* status, const int* skip_in, int* conv_out, float conv_tol) {
+  chol_inv_blocked_body<F>(G, l, shift_rel, Rinv, status, skip_in, conv_out, conv_tol);
 }
 
 // one problem per block
 template <typename F>
 __global__ void __launch_bounds__(BT) chol_batched_kernel(const CholJob* __restrict__ jobs) {
   const CholJob& j = jobs[blockIdx.x];
-  chol_inv_blocked_body<F>(j.G, j.l, j.shift, (F*)j.Rinv, j.status);
+  chol_inv_blocked_body<F>(j.G, j.l, j.shift, (F*)j.Rinv, j.status, nullptr, nullptr, 0.f);
 }
 
 template <typename F>
@@ -488,14 +504,16 @@ size_t chol_smem(int l) {
 }  // namespace
 
 cudaError_t launch_chol_inv(const double* G, int l, double shift_rel, void* Rinv, bool f64,
-                            DeviceStatus* status, cudaStream_t st) {
+                            DeviceStatus* status, cudaStream_t st, const int* skip_in, int* conv_out,
+                            float conv_tol) {
   if (f64) {
     size_t sb = chol_blocked_smem<double>(l);
     if (sb <= kCholSmemMax) {
       cudaError_t e = cudaFuncSetAttribute(chol_inv_blocked_kernel<double>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
       if (e != cudaSuccess) return e;
-      chol_inv_blocked_kernel<double><<<1, BT, sb, st>>>(G, l, shift_rel, (double*)Rinv, status);
+      chol_inv_blocked_kernel<double><<<1, BT, sb, st>>>(G, l, shift_rel, (double*)Rinv, status, skip_in, conv_out,
+                                                         conv_tol);
       return cudaGetLastError();
     }
     size_t sm = chol_smem<double>(l);
@@ -508,7 +526,8 @@ cudaError_t launch_chol_inv(const double* G, int l, double shift_rel, void* Rinv
       cudaError_t e = cudaFuncSetAttribute(chol_inv_blocked_kernel<float>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
       if (e != cudaSuccess) return e;
-      chol_inv_blocked_kernel<float><<<1, BT, sb, st>>>(G, l, shift_rel, (float*)Rinv, status);
+      chol_inv_blocked_kernel<float><<<1, BT, sb, st>>>(G, l, shift_rel, (float*)Rinv, status, skip_in, conv_out,
+                                                        conv_tol);
       return cudaGetLastError();
     }
     size_t sm = chol_smem<float>(l);

@@ -17,7 +17,7 @@ namespace sorsvd {
 struct DeviceStatus {
   int code;        // first non-OK sorsvd_status raised on the device
   int info;        // bit 0: shifted Cholesky retry; bits 8..15: Jacobi sweeps
-  int pad[14];
+  int pad[14];      // pad[0]: CholeskyQR3's second pass found Q orthonormal (the third is skipped)
 };
 
 __device__ __forceinline__ void raise_status(DeviceStatus* st, int code) {
@@ -148,8 +148,13 @@ cudaError_t launch_jacobi_batched(const JacobiJob* jobs, int njobs, int max_l, b
 // chol.cu: R^{-1} (upper triangular, l x l, column-major, ld = l) of the
 // Cholesky factor of G + s I, s = shift_rel * trace(G) / l.  G binary64.
 // Output in binary64 (f64 = true) or fp32.
+// Optional (blocked kernel only): skip_in non-null and *skip_in != 0 ->
+// R^{-1} = I without factorising; conv_out non-null -> *conv_out = 1 when
+// every off-diagonal entry of the equilibrated G is <= conv_tol (the columns
+// are orthonormal to that level) and no shifted retry was needed, else 0.
 cudaError_t launch_chol_inv(const double* G, int l, double shift_rel, void* Rinv, bool f64,
-                            DeviceStatus* status, cudaStream_t st);
+                            DeviceStatus* status, cudaStream_t st, const int* skip_in = nullptr,
+                            int* conv_out = nullptr, float conv_tol = 0.f);
 
 // jacobi.cu: SVD of the l x l matrix M (binary64 input): one-sided Jacobi
 // sweeps in binary64 (f64) or fp32, binary64 finish.  Writes sigma
@@ -159,6 +164,21 @@ cudaError_t launch_chol_inv(const double* G, int l, double shift_rel, void* Rinv
 cudaError_t launch_jacobi(const double* M, int l, int k, bool f64, void* Ut, void* Vt,
                           void* S, bool S_f64, void* work, DeviceStatus* status, cudaStream_t st);
 size_t jacobi_work_bytes(int l);
+
+// cholqr.cu: row-block CholeskyQR products for fp32 sketches, l <= kCqMaxL.
+// launch_cq_gram: parts[b] (l x l fp32) = T_b^T T_b for each block b of rows
+// (cq_blocks(rows) blocks; sum them with launch_reduce_splits, stride l*l).
+// launch_cq_apply: T <- T R^{-1} in place (Rinv l x l upper triangular,
+// ld = l, fp32); with parts non-null also the partial Grams of the result.
+constexpr int kCqMaxL = 128;
+int64_t cq_blocks(int64_t rows);
+cudaError_t launch_cq_gram(const float* T, int64_t ld, int64_t rows, int l, float* parts, cudaStream_t st);
+cudaError_t launch_cq_apply(float* T, int64_t ld, int64_t rows, int l, const float* Rinv, float* parts,
+                            cudaStream_t st);
+// out (binary64, rows x cols, ldo) = fixed-order sum of nparts fp32
+// partials (ld ldp, stride between partials), one warp per element
+cudaError_t launch_reduce_parts_warp(const float* parts, int nparts, int64_t stride, int rows, int cols, int ldp,
+                                     double* out, int ldo, cudaStream_t st);
 
 // sorsvd.cu: the device status word of a sorsvd_run workspace
 DeviceStatus* workspace_status(void* ws);

@@ -36,6 +36,10 @@ inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 // relative shift of the first CholeskyQR pass (unit-diagonal Gram)
 inline double first_shift(int dt) { return dt == SORSVD_F64 ? 1e-13 : 1e-5; }
+// largest column cosine of the second pass's input for which the third
+// CholeskyQR pass is skipped: the second pass then leaves Q orthonormal to
+// working precision (its error grows with cond(Q)^2 <= (1 + l tol) / (1 - l tol))
+constexpr float kOrthTol = 1e-4f;
 
 // K splits of a product with an M x N output and reduction length K
 int splits_for(int64_t M, int64_t N, int64_t K, int cap) {
@@ -121,6 +125,8 @@ Layout make_layout(int64_t m, int64_t n, int l, int dt) {
     pb = std::max(pb, tc_parts_bytes(elt, m, l, n));
     pb = std::max(pb, tc_parts_bytes(elt, n, l, m));
   }
+  if (dt != SORSVD_F64 && l <= kCqMaxL)              // row-block Gram partials
+    pb = std::max(pb, (size_t)cq_blocks(std::max(m, n)) * l * l * 4);
   L.parts = take(pb);
   L.G = take((size_t)l * l * 8);
   L.Rinv = take((size_t)l * l * acc);
@@ -212,8 +218,28 @@ int prepare_at(const Ctx& c, const void* A, int64_t m, int64_t n, int64_t lda) {
 }
 
 // T (rows x l, ld, accumulator type) <- T R^{-1}, repeated `passes` times
-// (CholeskyQR); the first pass is shifted by shift0.
+// (CholeskyQR); the first pass is shifted by shift0.  fp32 sketches with
+// l <= kCqMaxL use the row-block kernels (Gram partials, in-place T R^{-1}
+// fused with the next pass's Gram partials); binary64 and wider sketches
+// the CUDA-core GEMMs.
 int orth(const Ctx& c, void* T, int64_t rows, int64_t ld, int l, int passes, double shift0) {
+  if (!c.f64 && l <= kCqMaxL) {
+    float* parts = (float*)c.at(c.L.parts);
+    const int nb = (int)cq_blocks(rows);
+    LAUNCH(K_SMALL_GEMM, launch_cq_gram((const float*)T, ld, rows, l, parts, c.st));
+    // the third pass of CholeskyQR3 only runs when the second pass's Gram
+    // was not already within kOrthTol of the identity (decided on the
+    // device: the third pass's factorisation then returns R^{-1} = I)
+    int* conv = c.status()->pad;
+    for (int p = 0; p < passes; ++p) {
+      LAUNCH(K_REDUCE, launch_reduce_parts_warp(parts, nb, (int64_t)l * l, l, l, l, (double*)c.at(c.L.G), l, c.st));
+      LAUNCH(K_CHOL, launch_chol_inv((const double*)c.at(c.L.G), l, p == 0 ? shift0 : 0.0, c.at(c.L.Rinv), false,
+                                     c.status(), c.st, p == 2 ? conv : nullptr, p == 1 ? conv : nullptr, kOrthTol));
+      LAUNCH(K_SMALL_GEMM, launch_cq_apply((float*)T, ld, rows, l, (const float*)c.at(c.L.Rinv),
+                                           p + 1 < passes ? parts : nullptr, c.st));
+    }
+    return SORSVD_OK;
+  }
   const int adt = c.f64 ? SORSVD_F64 : SORSVD_F32;
   for (int p = 0; p < passes; ++p) {
     int r = gemm(c, K_SMALL_GEMM, true, l, l, rows, T, ld, adt, T, ld, adt, c.at(c.L.G), l, true, kCapSmall);
