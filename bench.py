@@ -294,7 +294,51 @@ def run_ours(args, w, rank, world, local_rank):
            "wall_s_timed": t_wall}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, args.cpu_rows)
+    if args.compare_precisions and dt in ("bf16", "f16"):
+        out["precision_comparison"] = compare_precisions(w, A, At, k, p, q, max(3, min(args.steps, 5)))
     return out
+
+
+def compare_precisions(w, A, At, k, p, q, steps):
+    """Time and accuracy of the 16-bit path (with and without REFINE) and of
+    the fp32 path on the same stored matrix: the fp32 run factors the 16-bit
+    values widened exactly to fp32, so both approximate the same A.
+    Accuracy: ||A - U S V^T||_F / sigma_{k+1}, sigma_{k+1} of the construction
+    (the storage rounding moves it by ~2^-9 relative)."""
+    import torch
+    from paper_1804_00462_gb300 import native
+    sig = sigma_of(w)
+    s_k1 = float(sig[k]) if k < len(sig) else float("nan")
+    A32t = At.float()                      # (n, m) row-major = A column-major, exact widening
+    res = {}
+    for name, mat, dt, fl in (("bf16", A, w["dtype"], 0), ("bf16_refine", A, w["dtype"], native.FLAG_REFINE),
+                              ("f32", A32t.T, "f32", 0)):
+        ws = native.alloc_workspace(w["m"], w["n"], k, p, dt, fl)
+        out = native.run(mat, k, p, q, seed=0, dtype=dt, flags=fl, workspace=ws)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for i in range(steps):
+            out = native.run(mat, k, p, q, seed=i, dtype=dt, flags=fl, workspace=ws)
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / steps
+        U, S, V = out
+        # ||A - U S V^T||_F by row blocks of A (fp32 on the GPU)
+        err2 = 0.0
+        for c0 in range(0, w["n"], 2048):
+            c1 = min(w["n"], c0 + 2048)
+            blk = A32t[c0:c1].T - (U * S[None, :]) @ V[c0:c1].T
+            err2 += float((blk.double() ** 2).sum())
+        st, _ = native.get_status(ws)
+        res[name] = {"ms": ms, "err_over_sigma_k1": err2 ** 0.5 / s_k1, "status": st}
+        del ws
+    res["speedup_bf16_vs_f32"] = res["f32"]["ms"] / res["bf16"]["ms"]
+    res["speedup_bf16_refine_vs_f32"] = res["f32"]["ms"] / res["bf16_refine"]["ms"]
+    res["note"] = ("same stored matrix; err = ||A - U S V^T||_F / sigma_{k+1}; the Eckart-Young floor "
+                   "is ||sigma_{k+1:}||_2 / sigma_{k+1}")
+    res["eckart_young_floor"] = float((sig[k:] ** 2).sum() ** 0.5 / s_k1)
+    return res
 
 
 def _timed(args, world, fn, stream):
@@ -481,6 +525,8 @@ def main():
     ap.add_argument("--workload", choices=tuple(WORKLOADS), default="cfg2")
     ap.add_argument("--cpu-rows", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--compare-precisions", action="store_true",
+                    help="16-bit workloads: also time the fp32 and REFINE paths on the same matrix")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

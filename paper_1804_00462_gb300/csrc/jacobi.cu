@@ -24,6 +24,8 @@
 //     matching column of V~ follows.
 #include "internal.cuh"
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cstdlib>
 
@@ -363,6 +365,100 @@ jacobi_sweep_g_kernel(const double* __restrict__ Min, int l, float* __restrict__
   jacobi_sweep_body_g<G, EP>(Min, l, Vout, status);
 }
 
+// Large l (W and V do not fit one SM's shared memory): the same sweep as
+// one cooperative grid, W and V in global memory (they stay in L2), 16-lane
+// groups, kCoopPairsPerCta pairs per CTA, one grid-wide barrier per round.
+// The "any rotation" / "large cosine" flags of sweep s live in
+// flags[2 s], flags[2 s + 1] (zeroed by the launcher), so no flag is
+// reused within the kernel.
+constexpr int kCoopPairsPerCta = 8;
+constexpr int kCoopThreads = kCoopPairsPerCta * 16;
+
+template <int EP>
+__global__ void __launch_bounds__(kCoopThreads)
+jacobi_sweep_coop_kernel(const double* __restrict__ Min, int l, int ldw, float* __restrict__ W, float* __restrict__ V,
+                         float* __restrict__ Vout, int* __restrict__ flags, DeviceStatus* status) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  const int t = threadIdx.x, lane = t & 31;
+  const int grp = t >> 4, gl = lane & 15;
+  const unsigned gmask = 0xFFFFu << ((lane >> 4) * 16);
+  const float eps = 1.1920928955078125e-07f;
+  const float tol = (float)l * eps, tol2 = tol * tol;
+  const float big = 32.f * tol, big2 = big * big;
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + t, gn = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = gt; e < (int64_t)ldw * l; e += gn) {
+    const int c = (int)(e / ldw), i = (int)(e - (int64_t)c * ldw);
+    W[e] = i < l ? (float)Min[i + (size_t)c * l] : 0.f;
+    V[e] = (i == c) ? 1.f : 0.f;
+  }
+  grid.sync();
+  const int N = (l + 1) & ~1;
+  const int pr_base = blockIdx.x * kCoopPairsPerCta + grp;
+  int sweep;
+  for (sweep = 1; sweep <= kMaxSweeps; ++sweep) {
+    int rot_local = 0, big_local = 0;
+    for (int r = 0; r < N - 1; ++r) {
+      for (int pr = pr_base; pr < N / 2; pr += gridDim.x * kCoopPairsPerCta) {
+        const int a0 = rr_player(pr, r, N), b0 = rr_player(N - 1 - pr, r, N);
+        const int a = min(a0, b0), b = max(a0, b0);
+        if (b >= l) continue;                          // bye (whole group)
+        float2* wp = reinterpret_cast<float2*>(W + (size_t)a * ldw);
+        float2* wq = reinterpret_cast<float2*>(W + (size_t)b * ldw);
+        float2 x[EP], y[EP];
+        float2 al2 = make_float2(0.f, 0.f), be2 = al2, ga2 = al2;
+#pragma unroll
+        for (int e = 0; e < EP; ++e) {
+          x[e] = wp[gl + 16 * e];
+          y[e] = wq[gl + 16 * e];
+          al2 = __ffma2_rn(x[e], x[e], al2);
+          be2 = __ffma2_rn(y[e], y[e], be2);
+          ga2 = __ffma2_rn(x[e], y[e], ga2);
+        }
+        float al = al2.x + al2.y, be = be2.x + be2.y, ga = ga2.x + ga2.y;
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(gmask, al, o);
+          be += __shfl_xor_sync(gmask, be, o);
+          ga += __shfl_xor_sync(gmask, ga, o);
+        }
+        if (!(ga * ga > tol2 * al * be)) continue;
+        if (ga * ga > big2 * al * be) big_local = 1;
+        float cs, sn;
+        rotation(al, be, ga, &cs, &sn);
+        const float2 c2 = make_float2(cs, cs), s2 = make_float2(sn, sn), ns2 = make_float2(-sn, -sn);
+        float2* vp = reinterpret_cast<float2*>(V + (size_t)a * ldw);
+        float2* vq = reinterpret_cast<float2*>(V + (size_t)b * ldw);
+#pragma unroll
+        for (int e = 0; e < EP; ++e) {
+          const int i = gl + 16 * e;
+          wp[i] = __ffma2_rn(c2, x[e], __fmul2_rn(ns2, y[e]));
+          wq[i] = __ffma2_rn(s2, x[e], __fmul2_rn(c2, y[e]));
+          const float2 u = vp[i], v = vq[i];
+          vp[i] = __ffma2_rn(c2, u, __fmul2_rn(ns2, v));
+          vq[i] = __ffma2_rn(s2, u, __fmul2_rn(c2, v));
+        }
+        rot_local = 1;
+      }
+      grid.sync();                                     // the round's columns are final
+    }
+    if (rot_local) atomicOr(&flags[2 * sweep], 1);
+    if (big_local) atomicOr(&flags[2 * sweep + 1], 1);
+    grid.sync();
+    const int rot = *((volatile int*)&flags[2 * sweep]), bg = *((volatile int*)&flags[2 * sweep + 1]);
+    if (!rot) break;
+    if (sweep == kMaxSweeps) {
+      if (bg && gt == 0) raise_status(status, SORSVD_ERR_NOT_CONVERGED);
+      break;
+    }
+  }
+  if (gt == 0) atomicOr(&status->info, (min(sweep, kMaxSweeps)) << 8);
+  for (int64_t e = gt; e < (int64_t)l * l; e += gn) {
+    const int c = (int)(e / l), i = (int)(e - (int64_t)c * l);
+    Vout[e] = V[i + (size_t)c * ldw];
+  }
+}
+
 template <int EP>
 __global__ void __launch_bounds__(512)
 jacobi_sweep_f2_kernel(const double* __restrict__ Min, int l, float* __restrict__ Vout, DeviceStatus* status) {
@@ -548,6 +644,12 @@ cudaError_t launch_sweep(const double* M, int l, J* vout, J* gwork, size_t smem,
 
 constexpr size_t kSweepSmemMax = 200 * 1024;
 
+// [W, V fallback: 2 l^2 J][V out: l^2 J][U64, V64: 2 l^2 f64][sig: l f64], sized for J = double;
+// the cooperative sweep's own W, V and flags follow (256-aligned)
+inline size_t jacobi_base_bytes(int l) {
+  return ((3 * (size_t)l * l * sizeof(double) + 15) & ~(size_t)15) + 2 * (size_t)l * l * 8 + (size_t)l * 8;
+}
+
 // template EP of the paired sweep for l (the kernel's row stride is 16 EP)
 inline int sweep_f2_ep(int l) {
   const int need = (l + 15) / 16;
@@ -570,6 +672,48 @@ inline size_t sweep_g_smem(int l) {
   const int ep = sweep_g_ep(l);
   const int N = (l + 1) & ~1;
   return ep ? 2 * (size_t)32 * ep * l * sizeof(float) + (size_t)(N - 1) * (N / 2) * 4 : (size_t)-1;
+}
+
+// cooperative sweep: ldw = 32 EP rows; work = [W ldw*l][V ldw*l][flags 2*(kMaxSweeps+1) ints]
+inline int sweep_coop_ep(int l) {
+  const int need = (l + 31) / 32;
+  return need <= 10 ? need : 0;
+}
+size_t sweep_coop_work_bytes(int l) {
+  const int ep = std::max(1, sweep_coop_ep(l));
+  return 2 * (size_t)32 * ep * l * sizeof(float) + 2 * (kMaxSweeps + 1) * sizeof(int) + 256;
+}
+
+cudaError_t launch_sweep_coop(const double* M, int l, float* vout, void* work, DeviceStatus* status, cudaStream_t st) {
+  const int ep = sweep_coop_ep(l);
+  if (!ep) return cudaErrorInvalidValue;
+  int ldw = 32 * ep;
+  float* W = reinterpret_cast<float*>(work);
+  float* V = W + (size_t)ldw * l;
+  int* flags = reinterpret_cast<int*>(V + (size_t)ldw * l);
+  cudaError_t e = cudaMemsetAsync(flags, 0, 2 * (kMaxSweeps + 1) * sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  const int npairs = (l + 1) / 2;
+  int grid = (npairs + kCoopPairsPerCta - 1) / kCoopPairsPerCta;
+  grid = std::min(grid, num_sms());
+  void* args[] = {(void*)&M, (void*)&l, (void*)&ldw, (void*)&W, (void*)&V, (void*)&vout, (void*)&flags, (void*)&status};
+#define COOP(E)                                                                                                    \
+  return cudaLaunchCooperativeKernel((const void*)jacobi_sweep_coop_kernel<E>, dim3(grid), dim3(kCoopThreads), args, \
+                                     0, st);
+  switch (ep) {
+    case 1: COOP(1)
+    case 2: COOP(2)
+    case 3: COOP(3)
+    case 4: COOP(4)
+    case 5: COOP(5)
+    case 6: COOP(6)
+    case 7: COOP(7)
+    case 8: COOP(8)
+    case 9: COOP(9)
+    case 10: COOP(10)
+    default: return cudaErrorInvalidValue;
+  }
+#undef COOP
 }
 
 cudaError_t launch_sweep_g(const double* M, int l, float* vout, DeviceStatus* status, cudaStream_t st) {
@@ -638,6 +782,9 @@ cudaError_t run_all(const double* M, int l, int k, void* Ut, void* Vt, void* S, 
   static const int lanes = [] { const char* v = std::getenv("SORSVD_JACOBI_LANES"); return v ? std::atoi(v) : 16; }();
   if (sizeof(J) == 4 && lanes == 16 && sweep_g_smem(l) <= kSweepSmemMax)
     e = launch_sweep_g(M, l, reinterpret_cast<float*>(vout), status, st);
+  else if (sizeof(J) == 4 && sweep_coop_ep(l) && sweep_f2_smem(l) > kSweepSmemMax)
+    e = launch_sweep_coop(M, l, reinterpret_cast<float*>(vout), w + ((jacobi_base_bytes(l) + 255) & ~(size_t)255),
+                          status, st);
   else if (sizeof(J) == 4 && sweep_f2_smem(l) <= kSweepSmemMax)
     e = launch_sweep_f2(M, l, reinterpret_cast<float*>(vout), status, st);
   else
@@ -652,7 +799,7 @@ cudaError_t run_all(const double* M, int l, int k, void* Ut, void* Vt, void* S, 
 }  // namespace
 
 size_t jacobi_work_bytes(int l) {
-  return ((3 * (size_t)l * l * sizeof(double) + 15) & ~(size_t)15) + 2 * (size_t)l * l * 8 + (size_t)l * 8;
+  return ((jacobi_base_bytes(l) + 255) & ~(size_t)255) + sweep_coop_work_bytes(l);
 }
 
 cudaError_t launch_jacobi(const double* M, int l, int k, bool f64, void* Ut, void* Vt, void* S, bool S_f64,

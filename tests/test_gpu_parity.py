@@ -307,3 +307,15 @@ def test_chol_inv_retry_and_breakdown(nat):
     torch.cuda.synchronize()
     assert st == 5                                  # SORSVD_ERR_BREAKDOWN
     assert np.array_equal(R.cpu().numpy(), np.eye(20, dtype=np.float32))
+
+
+@pytest.mark.parametrize("dt,l", [("f32", 200), ("bf16", 266)])
+def test_run_large_sketch(nat, dt, l):
+    """l beyond one SM's shared memory for the Jacobi sweep (cooperative grid
+    sweep) and for the row-block CholeskyQR (CUDA-core products)."""
+    k = l - 10
+    A64, s, _, _ = inputs.spectral(1200, 700, inputs.sigma_exp(600, 64.0), seed=8)
+    exact, got, ref = run_both(nat, A64, k, 10, 1, 2, dt)
+    r_gpu, r_orc, ds = gates(exact, got, ref)
+    tol = TOL[dt]
+    assert abs(r_gpu - r_orc) <= tol and ds <= tol, (r_gpu, r_orc, ds)
