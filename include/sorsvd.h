@@ -62,7 +62,9 @@ typedef enum {
                                           Algorithm 3 (no re-orthonormalisation
                                           of T2 between passes) */
 #define SORSVD_FLAG_REFINE        0x2u /* BF16/F16: Q2 enters the core pass as a
-                                          hi+lo pair of 16-bit operands */
+                                          hi+lo pair of 16-bit operands (two
+                                          tensor-core passes over A, combined
+                                          in binary64) */
 
 /* Largest sketch width l = k + p supported (the small l x l factorisations
  * run in one thread block with the factor in shared memory). */

@@ -279,12 +279,29 @@ int core_impl(const Ctx& c, const void* A, int64_t m, int64_t n, int64_t lda, un
   if (dtype_is_16(dt) && !(flags & SORSVD_FLAG_REFINE)) {
     LAUNCH(K_MISC, launch_convert_f32((const float*)Q2, ldq2, n, l, c.at(c.L.q2op), c.L.ldn, dt, nullptr, c.st));
     r = pass(c, K_CORE, false, m, l, n, A, lda, c.at(c.L.q2op), c.L.ldn, dt, c.at(c.L.tmp), ldw, nullptr, 0, false);
+  } else if (dtype_is_16(dt) && tc_enabled()) {
+    // REFINE: Q2 = hi + lo as a pair of 16-bit operands (lo = round(Q2 - hi)
+    // carries the next 8-11 bits), two tensor-core passes over A, and
+    // M = Q1^T (A hi) + Q1^T (A lo) combined in binary64
+    char* hi = (char*)c.at(c.L.q2op);
+    char* lo = hi + (size_t)c.L.ldn * l * dtype_size(dt);
+    LAUNCH(K_MISC, launch_convert_f32((const float*)Q2, ldq2, n, l, hi, c.L.ldn, dt, lo, c.st));
+    r = pass(c, K_CORE, false, m, l, n, A, lda, hi, c.L.ldn, dt, c.at(c.L.tmp), ldw, nullptr, 0, false);
+    if (r) return r;
+    r = gemm(c, K_SMALL_GEMM, true, l, l, m, Q1, ldq1, adt, c.at(c.L.tmp), ldw, adt, M, ldm, true, kCapSmall);
+    if (r) return r;
+    r = pass(c, K_CORE, false, m, l, n, A, lda, lo, c.L.ldn, dt, c.at(c.L.tmp), ldw, nullptr, 0, false);
+    if (r) return r;
+    r = gemm(c, K_SMALL_GEMM, true, l, l, m, Q1, ldq1, adt, c.at(c.L.tmp), ldw, adt, c.at(c.L.G), l, true, kCapSmall);
+    if (r) return r;
+    LAUNCH(K_MISC, launch_add_f64((const double*)c.at(c.L.G), l, M, ldm, l, l, c.st));
+    return SORSVD_OK;
   } else if (dt == SORSVD_TF32 || dt == SORSVD_F32) {
     // TF32: one TF32 product; F32: the split (fp32-accurate) product
     r = pass(c, K_CORE, false, m, l, n, A, lda, Q2, ldq2, SORSVD_F32, c.at(c.L.tmp), ldw, nullptr, 0, true);
   } else {
-    // binary64, and BF16/F16 with REFINE: the fp32 Q2 multiplies the stored
-    // A exactly on CUDA cores
+    // binary64, and BF16/F16 with REFINE when tensor cores are switched
+    // off: the fp32 Q2 multiplies the stored A exactly on CUDA cores
     r = gemm(c, K_CORE, false, m, l, n, A, lda, dt, Q2, ldq2, adt, c.at(c.L.tmp), ldw, c.f64, kCapBig);
   }
   if (r) return r;
