@@ -78,6 +78,7 @@ constexpr int kThreadsSplit = 352;
 constexpr int kDrainAtoms = 4;
 constexpr int kAccCols = 128;
 constexpr uint32_t kAtomBytes = 128u * 128u;   // 128 rows x 128 bytes
+constexpr int kMaxKA = 2;                      // K atoms per stage, at most
 
 // round-to-nearest-even of an fp32 value to TF32 (10 explicit mantissa bits);
 // finite inputs
@@ -103,8 +104,11 @@ __device__ __forceinline__ void store_out(const TcParams& P, int64_t grow, int c
 }
 
 // ELT: 0 bf16, 1 fp16, 2 tf32, 3 tf32 split (3 MMAs).  A_MN: A operand
-// MN-major (op(A) = A).
-template <int ELT, bool A_MN>
+// MN-major (op(A) = A).  MT, NCH, KA: the launch's row blocks per tile,
+// N-chunks and K atoms per stage, fixed at compile time so that the MMA
+// issue loop is straight-line code (issued from a rolled loop, the same
+// tcgen05.mma sequence ran 2-4x slower, measured).
+template <int ELT, bool A_MN, int MT, int NCH, int KA>
 __global__ void __launch_bounds__((ELT == 3 ? kThreadsSplit : kThreads), 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const __grid_constant__ CUtensorMap tmBlo, const TcParams P) {
@@ -129,9 +133,9 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   constexpr uint32_t AMN_BOX = (uint32_t)AK * 128u;     // bytes of one MN-major A box
   constexpr uint32_t FMT = (ELT == 0) ? 1u : (ELT == 1 ? 0u : 2u);
   // accumulator fill length in stages (split mode drains every kDrainAtoms atoms)
-  const int64_t CHUNK = SPLIT ? (int64_t)((kDrainAtoms + P.KA - 1) / P.KA) : ((int64_t)1 << 40);
+  const int64_t CHUNK = SPLIT ? (int64_t)((kDrainAtoms + KA - 1) / KA) : ((int64_t)1 << 40);
   // split mode: the low parts sit right after the hi tiles of each stage
-  const int mrows = 128 * P.MT;
+  const int mrows = 128 * MT;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -174,10 +178,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           armed |= 1u << stage;
           armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
           uint8_t* sa = smem + (size_t)stage * P.stage_bytes;
-          for (int j = 0; j < P.KA; ++j) {
-            const int k = (int)((kb * P.KA + j) * AK);
-            for (int mt = 0; mt < P.MT; ++mt) {
-              uint8_t* dst = sa + (size_t)(mt * P.KA + j) * kAtomBytes;
+          for (int j = 0; j < KA; ++j) {
+            const int k = (int)((kb * KA + j) * AK);
+            for (int mt = 0; mt < MT; ++mt) {
+              uint8_t* dst = sa + (size_t)(mt * KA + j) * kAtomBytes;
               const int row0 = (int)(t * mrows) + mt * 128;
               if (A_MN) {
 #pragma unroll
@@ -218,9 +222,9 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           armed |= 1u << stage;
           armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
           uint8_t* sb = bring + (size_t)stage * P.bstage_bytes;
-          for (int j = 0; j < P.KA; ++j) {
-            const int k = (int)((kb * P.KA + j) * AK);
-            for (int ch = 0; ch < P.nch; ++ch) {
+          for (int j = 0; j < KA; ++j) {
+            const int k = (int)((kb * KA + j) * AK);
+            for (int ch = 0; ch < NCH; ++ch) {
               const size_t off = (size_t)j * P.b_atom + (size_t)ch * P.ch0 * 128;
               tc::tma_load_2d_hint(sb + off, &tmB, &bfull[stage], k, ch * P.ch0, polB);
               if (SPLIT) tc::tma_load_2d_hint(sb + P.b_bytes + off, &tmBlo, &bfull[stage], k, ch * P.ch0, polB);
@@ -241,9 +245,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      uint32_t idesc[2];
-      idesc[0] = tc::idesc_make(FMT, A_MN, false, 128, P.ch0);
-      idesc[1] = tc::idesc_make(FMT, A_MN, false, 128, P.Npad - P.ch0);
+      const uint32_t idesc0 = tc::idesc_make(FMT, A_MN, false, 128, P.ch0);
+      const uint32_t idesc1 = tc::idesc_make(FMT, A_MN, false, 128, P.Npad - P.ch0);
       uint32_t stage = 0, phase = 0, bstage = 0, bphase = 0;
       int chunk = 0;                 // accumulator fills (TMEM buffer alternation)
       bool ok = true;
@@ -257,7 +260,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           const uint32_t use = (P.nbuf == 2) ? (uint32_t)(chunk >> 1) : (uint32_t)chunk;
           if (!tc::mbar_wait(&tempty[b], (use & 1u) ^ 1u, abortp)) { ok = false; break; }
           tc::fence_after_sync();
-          const uint32_t dcol = tbase + (uint32_t)(b * P.MT * P.Npad);
+          const uint32_t dcol = tbase + (uint32_t)(b * MT * P.Npad);
           for (int64_t kb = c0; kb < c1; ++kb) {
             if (!tc::mbar_wait(&full[stage], phase, abortp)) { ok = false; break; }
             if (!tc::mbar_wait(&bfull[bstage], bphase, abortp)) { ok = false; break; }
@@ -265,28 +268,33 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             tc::fence_after_sync();
             const uint32_t sa = tc::smem_u32(smem + (size_t)stage * P.stage_bytes);
             const uint32_t sb = tc::smem_u32(bring + (size_t)bstage * P.bstage_bytes);
-            for (int j = 0; j < P.KA; ++j) {
+#pragma unroll
+            for (int j = 0; j < KA; ++j) {
 #pragma unroll
               for (int ks = 0; ks < AK / KMMA; ++ks) {
                 const uint32_t acc = (kb > c0 || j > 0 || ks > 0) ? 1u : 0u;
-                for (int mt = 0; mt < P.MT; ++mt) {
-                  const uint32_t aat = sa + (uint32_t)(mt * P.KA + j) * kAtomBytes;
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt) {
+                  const uint32_t aat = sa + (uint32_t)(mt * KA + j) * kAtomBytes;
                   const uint64_t ad = A_MN ? tc::desc_sw128(aat + ks * KMMA * 128, AMN_BOX, 1024)
                                            : tc::desc_sw128(aat + ks * 32, 16, 1024);
                   const uint32_t dm = dcol + (uint32_t)(mt * P.Npad);
-                  for (int ch = 0; ch < P.nch; ++ch) {
-                    const uint32_t bat = sb + (uint32_t)j * P.b_atom + (uint32_t)(ch * P.ch0 * 128);
+#pragma unroll
+                  for (int ch = 0; ch < NCH; ++ch) {
+                    const uint32_t id = ch ? idesc1 : idesc0;
+                    const uint32_t dch = dm + (ch ? (uint32_t)P.ch0 : 0u);
+                    const uint32_t bat = sb + (uint32_t)j * P.b_atom + (ch ? (uint32_t)(P.ch0 * 128) : 0u);
                     const uint64_t bd = tc::desc_sw128(bat + ks * 32, 16, 1024);
                     if (SPLIT) {
                       const uint64_t ad_lo = tc::desc_sw128(aat + P.a_bytes + ks * 32, 16, 1024);
                       const uint64_t bd_lo = tc::desc_sw128(bat + P.b_bytes + ks * 32, 16, 1024);
-                      tc::mma_tf32(dm + ch * P.ch0, ad, bd, idesc[ch], acc);
-                      tc::mma_tf32(dm + ch * P.ch0, ad, bd_lo, idesc[ch], 1u);
-                      tc::mma_tf32(dm + ch * P.ch0, ad_lo, bd, idesc[ch], 1u);
+                      tc::mma_tf32(dch, ad, bd, id, acc);
+                      tc::mma_tf32(dch, ad, bd_lo, id, 1u);
+                      tc::mma_tf32(dch, ad_lo, bd, id, 1u);
                     } else if (ELT == 2) {
-                      tc::mma_tf32(dm + ch * P.ch0, ad, bd, idesc[ch], acc);
+                      tc::mma_tf32(dch, ad, bd, id, acc);
                     } else {
-                      tc::mma_f16(dm + ch * P.ch0, ad, bd, idesc[ch], acc);
+                      tc::mma_f16(dch, ad, bd, id, acc);
                     }
                   }
                 }
@@ -360,9 +368,9 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         const uint32_t use = (P.nbuf == 2) ? (uint32_t)(chunk >> 1) : (uint32_t)chunk;
         if (!tc::mbar_wait(&tfull[b], use & 1u, abortp)) { ok = false; break; }
         tc::fence_after_sync();
-        for (int mt = 0; mt < P.MT; ++mt) {
+        for (int mt = 0; mt < MT; ++mt) {
           const uint32_t taddr =
-              tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * P.MT * P.Npad + mt * P.Npad);
+              tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * MT * P.Npad + mt * P.Npad);
           const int row = mt * 128 + q * 32 + lane;
           const int64_t grow = t * mrows + row;
           if (SPLIT) {
@@ -507,14 +515,38 @@ bool make_map(CUtensorMap* map, const void* ptr, int elt, int64_t rows, int64_t 
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+template <int ELT, bool A_MN, int MT, int NCH, int KA>
+cudaError_t launch_shape(const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& mblo, const TcParams& P,
+                         size_t smem, cudaStream_t st) {
+  auto kern = tc_gemm_kernel<ELT, A_MN, MT, NCH, KA>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<P.G, ELT == 3 ? kThreadsSplit : kThreads, smem, st>>>(ma, mb, mblo, P);
+  return cudaGetLastError();
+}
+
+// the instantiation for the plan's (MT, nch, KA); split mode has MT = 1 and
+// one N-chunk (l <= 128)
 template <int ELT, bool A_MN>
 cudaError_t launch_typed(const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& mblo, const TcParams& P,
                          size_t smem, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<ELT, A_MN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  tc_gemm_kernel<ELT, A_MN><<<P.G, ELT == 3 ? kThreadsSplit : kThreads, smem, st>>>(ma, mb, mblo, P);
-  return cudaGetLastError();
+  if (ELT == 3) {
+    if (P.MT != 1 || P.nch != 1) return cudaErrorInvalidValue;
+    return P.KA == 1 ? launch_shape<ELT, A_MN, 1, 1, 1>(ma, mb, mblo, P, smem, st)
+                     : launch_shape<ELT, A_MN, 1, 1, 2>(ma, mb, mblo, P, smem, st);
+  }
+  const int code = (P.MT - 1) * 4 + (P.nch - 1) * 2 + (P.KA - 1);
+  switch (code) {
+    case 0: return launch_shape<ELT, A_MN, 1, 1, 1>(ma, mb, mblo, P, smem, st);
+    case 1: return launch_shape<ELT, A_MN, 1, 1, 2>(ma, mb, mblo, P, smem, st);
+    case 2: return launch_shape<ELT, A_MN, 1, 2, 1>(ma, mb, mblo, P, smem, st);
+    case 3: return launch_shape<ELT, A_MN, 1, 2, 2>(ma, mb, mblo, P, smem, st);
+    case 4: return launch_shape<ELT, A_MN, 2, 1, 1>(ma, mb, mblo, P, smem, st);
+    case 5: return launch_shape<ELT, A_MN, 2, 1, 2>(ma, mb, mblo, P, smem, st);
+    case 6: return launch_shape<ELT, A_MN, 2, 2, 1>(ma, mb, mblo, P, smem, st);
+    case 7: return launch_shape<ELT, A_MN, 2, 2, 2>(ma, mb, mblo, P, smem, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 int env_int(const char* name, int dflt) {
@@ -571,11 +603,12 @@ TcParams tc_plan(int elt, int64_t M, int64_t N, int64_t K) {
   int MT = envMT > 0 ? envMT : ((elt != 3 && 4 * Npad <= 512) ? 2 : 1);
   if (elt == 3 || MT * Npad > 512 || MT < 1 || MT > 2) MT = 1;
   TcParams best = shape(elt, M, N, K, 1, MT);
+  if (envKA > kMaxKA) return best;
   if (envKA > 0) {
     TcParams P = shape(elt, M, N, K, envKA, MT);
     return P.stages >= 2 ? P : best;
   }
-  for (int KA = 2; KA <= 4; ++KA) {
+  for (int KA = 2; KA <= kMaxKA; ++KA) {
     TcParams P = shape(elt, M, N, K, KA, MT);
     if (P.stages >= 4) best = P;
   }
