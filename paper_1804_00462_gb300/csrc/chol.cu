@@ -516,6 +516,9 @@ cudaError_t launch_chol_inv(const double* G, int l, double shift_rel, void* Rinv
                                                          conv_tol);
       return cudaGetLastError();
     }
+    // the packed kernel always factorises and reports no convergence (the
+    // caller's next pass then runs)
+    if (conv_out && cudaMemsetAsync(conv_out, 0, sizeof(int), st) != cudaSuccess) return cudaErrorUnknown;
     size_t sm = chol_smem<double>(l);
     cudaError_t e = cudaFuncSetAttribute(chol_inv_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
@@ -530,6 +533,7 @@ cudaError_t launch_chol_inv(const double* G, int l, double shift_rel, void* Rinv
                                                         conv_tol);
       return cudaGetLastError();
     }
+    if (conv_out && cudaMemsetAsync(conv_out, 0, sizeof(int), st) != cudaSuccess) return cudaErrorUnknown;
     size_t sm = chol_smem<float>(l);
     cudaError_t e = cudaFuncSetAttribute(chol_inv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;

@@ -195,6 +195,155 @@ cq_apply_kernel(float* __restrict__ T, int64_t ld, int64_t rows, int l, const fl
   if (parts) cq_gram_store(l, lp, gacc, parts + (size_t)blockIdx.x * l * l);
 }
 
+// ---------------------------------------------------------------- wide
+// kCqMaxL < l <= SORSVD_MAX_L: the Gram and the product no longer fit one
+// CTA's registers / shared memory whole, so both are tiled.
+//
+//   cq_gram_wide_kernel:  grid (x: row chunks, y: groups of kCqThreads 8 x 8
+//       blocks of the lower triangle); a thread accumulates one 8 x 8 block
+//       over the CTA's chunks (the whole row chunk is staged, every column);
+//       partial Grams per grid column x, both halves written.
+//   cq_apply_wide_kernel: T_b <- T_b R^{-1} in place, panels of 128 output
+//       columns from the last to the first (a panel only reads columns to
+//       its left and its own, so it can overwrite itself in shared memory),
+//       R^{-1} streamed through a 32 x 128 shared tile (zero below the
+//       diagonal and past l).
+constexpr int kWideKT = 32;                  // k rows per R^{-1} tile
+constexpr int kWidePW = 128;                 // output columns per panel
+constexpr int kWideRS = kWidePW + 4;         // R^{-1} tile row stride
+
+__host__ __device__ inline int cq_lp8(int l) { return (l + 7) & ~7; }
+inline int cq_wide_groups(int l) {
+  const int nb = cq_lp8(l) / 8;
+  return (nb * (nb + 1) / 2 + kCqThreads - 1) / kCqThreads;
+}
+inline size_t cq_wide_gram_smem(int l) { return (size_t)kCqRows * cq_xs(cq_lp8(l)) * 4; }
+inline size_t cq_wide_apply_smem(int l) {
+  return (size_t)kCqRows * cq_xs(cq_lp8(l)) * 4 + (size_t)kWideKT * kWideRS * 4;
+}
+
+__global__ void __launch_bounds__(kCqThreads, 2)
+cq_gram_wide_kernel(const float* __restrict__ T, int64_t ld, int64_t rows, int l, float* __restrict__ parts,
+                    const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  extern __shared__ __align__(16) float sm[];
+  const int lp = cq_lp8(l), xs = cq_xs(lp);
+  const int nb = lp / 8, nblk = nb * (nb + 1) / 2;
+  const int q = blockIdx.y * kCqThreads + threadIdx.x;
+  const bool act = q < nblk;
+  int i0 = 0, j0 = 0;
+  if (act) {
+    cq_block_of(q, &i0, &j0);                 // 4 x (block row, block column)
+    i0 *= 2;
+    j0 *= 2;
+  }
+  float acc[8][8] = {};
+  const int64_t nchunk = (rows + kCqRows - 1) / kCqRows;
+  for (int64_t ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
+    __syncthreads();
+    cq_load_block(T, ld, rows, l, lp, ch * kCqRows, sm);
+    __syncthreads();
+    if (!act) continue;
+    for (int r = 0; r < kCqRows; ++r) {
+      const float* xr = sm + r * xs;
+      const float4 a0 = *reinterpret_cast<const float4*>(xr + i0);
+      const float4 a1 = *reinterpret_cast<const float4*>(xr + i0 + 4);
+      const float4 b0 = *reinterpret_cast<const float4*>(xr + j0);
+      const float4 b1 = *reinterpret_cast<const float4*>(xr + j0 + 4);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+    }
+  }
+  if (!act) return;
+  float* out = parts + (size_t)blockIdx.x * l * l;
+#pragma unroll
+  for (int u = 0; u < 8; ++u)
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+      const int i = i0 + u, j = j0 + v;
+      if (i < l && j < l) {
+        out[i + (size_t)j * l] = acc[u][v];
+        out[j + (size_t)i * l] = acc[u][v];
+      }
+    }
+}
+
+__global__ void __launch_bounds__(kCqThreads, 2)
+cq_apply_wide_kernel(float* __restrict__ T, int64_t ld, int64_t rows, int l, const float* __restrict__ Rinv,
+                     const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  extern __shared__ __align__(16) float sm[];
+  const int lp = cq_lp8(l), xs = cq_xs(lp);
+  float* X = sm;
+  float* Rs = sm + (size_t)kCqRows * xs;      // Rs[kk * kWideRS + jj] = R^{-1}(k0 + kk, j0 + jj)
+  // thread: rows 4 tr .. 4 tr + 3 of the chunk, panel columns 4 tc .. 4 tc + 3
+  // and 64 + 4 tc .. 64 + 4 tc + 3 (a warp's R loads are two contiguous
+  // 256-byte runs)
+  const int tr = threadIdx.x / 16, tc = threadIdx.x % 16;
+  const int npan = (lp + kWidePW - 1) / kWidePW;
+  const int64_t nchunk = (rows + kCqRows - 1) / kCqRows;
+  for (int64_t ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
+    const int64_t r0 = ch * kCqRows;
+    __syncthreads();
+    cq_load_block(T, ld, rows, l, lp, r0, X);
+    for (int J = npan - 1; J >= 0; --J) {
+      const int j0 = J * kWidePW, pw = min(kWidePW, lp - j0), kend = j0 + pw;
+      const bool act = 4 * tc < pw;
+      float acc[4][8] = {};
+      for (int k0 = 0; k0 < kend; k0 += kWideKT) {
+        __syncthreads();                      // X staged / previous tile consumed
+        for (int e = threadIdx.x; e < kWideKT * kWidePW; e += blockDim.x) {
+          const int jj = e / kWideKT, kk = e - jj * kWideKT;
+          const int k = k0 + kk, j = j0 + jj;
+          Rs[kk * kWideRS + jj] = (j < l && k <= j) ? Rinv[k + (size_t)j * l] : 0.f;
+        }
+        __syncthreads();
+        if (!act) continue;
+        const int kn = min(kWideKT, kend - k0);   // a multiple of 8
+        for (int kk = 0; kk < kn; kk += 4) {
+          float xv[4][4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float4 x = *reinterpret_cast<const float4*>(X + (4 * tr + u) * xs + k0 + kk);
+            xv[u][0] = x.x; xv[u][1] = x.y; xv[u][2] = x.z; xv[u][3] = x.w;
+          }
+#pragma unroll
+          for (int qq = 0; qq < 4; ++qq) {
+            const float* rr = Rs + (kk + qq) * kWideRS;
+            const float4 ra = *reinterpret_cast<const float4*>(rr + 4 * tc);
+            const float4 rb = *reinterpret_cast<const float4*>(rr + 64 + 4 * tc);
+            const float rv[8] = {ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+              for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(xv[u][qq], rv[v], acc[u][v]);
+          }
+        }
+      }
+      __syncthreads();                        // every read of this panel's columns is done
+      if (act) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          float* xr = X + (4 * tr + u) * xs + j0;
+          *reinterpret_cast<float4*>(xr + 4 * tc) = make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
+          if (64 + 4 * tc < pw)
+            *reinterpret_cast<float4*>(xr + 64 + 4 * tc) = make_float4(acc[u][4], acc[u][5], acc[u][6], acc[u][7]);
+        }
+      }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < l * kCqRows; e += blockDim.x) {
+      const int c = e / kCqRows, r = e - c * kCqRows;
+      const int64_t gr = r0 + r;
+      if (gr < rows) T[gr + (int64_t)c * ld] = X[r * xs + c];
+    }
+  }
+}
+
 // out[i + j ldo] = sum_s parts[s * stride + i + j ldp] (binary64) for an
 // rows x cols result: one warp per element, lane t takes the partials
 // t, t + 32, ... (Neumaier compensated fp32 sums), then a fixed xor tree
@@ -235,6 +384,37 @@ cudaError_t launch_reduce_parts_warp(const float* parts, int nparts, int64_t str
 int64_t cq_blocks(int64_t rows) {
   const int64_t nchunk = (rows + kCqRows - 1) / kCqRows;
   return std::max<int64_t>(1, std::min<int64_t>(nchunk, (int64_t)num_sms()));
+}
+
+// wide Gram: grid columns (= partial Grams), about two CTAs per SM in all
+int64_t cq_wide_blocks(int64_t rows, int l) {
+  const int64_t nchunk = (rows + kCqRows - 1) / kCqRows;
+  const int64_t gy = cq_wide_groups(l);
+  const int64_t want = (2 * (int64_t)num_sms() + gy - 1) / gy;
+  return std::max<int64_t>(1, std::min<int64_t>(nchunk, want));
+}
+
+cudaError_t launch_cq_gram_wide(const float* T, int64_t ld, int64_t rows, int l, float* parts, const int* skip,
+                                cudaStream_t st) {
+  if (l <= kCqMaxL || l > SORSVD_MAX_L || rows < 1) return cudaErrorInvalidValue;
+  const size_t sm = cq_wide_gram_smem(l);
+  cudaError_t e = cudaFuncSetAttribute(cq_gram_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  const dim3 grid((unsigned)cq_wide_blocks(rows, l), (unsigned)cq_wide_groups(l));
+  cq_gram_wide_kernel<<<grid, kCqThreads, sm, st>>>(T, ld, rows, l, parts, skip);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cq_apply_wide(float* T, int64_t ld, int64_t rows, int l, const float* Rinv, const int* skip,
+                                 cudaStream_t st) {
+  if (l <= kCqMaxL || l > SORSVD_MAX_L || rows < 1) return cudaErrorInvalidValue;
+  const size_t sm = cq_wide_apply_smem(l);
+  cudaError_t e = cudaFuncSetAttribute(cq_apply_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  const int64_t nchunk = (rows + kCqRows - 1) / kCqRows;
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(nchunk, 2 * (int64_t)num_sms()));
+  cq_apply_wide_kernel<<<(unsigned)grid, kCqThreads, sm, st>>>(T, ld, rows, l, Rinv, skip);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_cq_gram(const float* T, int64_t ld, int64_t rows, int l, float* parts, cudaStream_t st) {

@@ -178,6 +178,15 @@ int64_t cq_blocks(int64_t rows);
 cudaError_t launch_cq_gram(const float* T, int64_t ld, int64_t rows, int l, float* parts, cudaStream_t st);
 cudaError_t launch_cq_apply(float* T, int64_t ld, int64_t rows, int l, const float* Rinv, float* parts,
                             cudaStream_t st);
+// Wide sketches (kCqMaxL < l <= SORSVD_MAX_L): launch_cq_gram_wide writes
+// cq_wide_blocks(rows, l) partial Grams (l x l fp32, stride l*l) to parts;
+// launch_cq_apply_wide: T <- T R^{-1} in place.  Both return at once when
+// skip is non-null and *skip is set (on the device).
+int64_t cq_wide_blocks(int64_t rows, int l);
+cudaError_t launch_cq_gram_wide(const float* T, int64_t ld, int64_t rows, int l, float* parts, const int* skip,
+                                cudaStream_t st);
+cudaError_t launch_cq_apply_wide(float* T, int64_t ld, int64_t rows, int l, const float* Rinv, const int* skip,
+                                 cudaStream_t st);
 // out (binary64, rows x cols, ldo) = fixed-order sum of nparts fp32
 // partials (ld ldp, stride between partials), one warp per element
 cudaError_t launch_reduce_parts_warp(const float* parts, int nparts, int64_t stride, int rows, int cols, int ldp,

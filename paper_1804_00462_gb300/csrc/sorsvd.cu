@@ -127,6 +127,8 @@ Layout make_layout(int64_t m, int64_t n, int l, int dt) {
   }
   if (dt != SORSVD_F64 && l <= kCqMaxL)              // row-block Gram partials
     pb = std::max(pb, (size_t)cq_blocks(std::max(m, n)) * l * l * 4);
+  else if (dt != SORSVD_F64)
+    pb = std::max(pb, (size_t)std::max(cq_wide_blocks(m, l), cq_wide_blocks(n, l)) * l * l * 4);
   L.parts = take(pb);
   L.G = take((size_t)l * l * 8);
   L.Rinv = take((size_t)l * l * acc);
@@ -237,6 +239,22 @@ int orth(const Ctx& c, void* T, int64_t rows, int64_t ld, int l, int passes, dou
                                      c.status(), c.st, p == 2 ? conv : nullptr, p == 1 ? conv : nullptr, kOrthTol));
       LAUNCH(K_SMALL_GEMM, launch_cq_apply((float*)T, ld, rows, l, (const float*)c.at(c.L.Rinv),
                                            p + 1 < passes ? parts : nullptr, c.st));
+    }
+    return SORSVD_OK;
+  }
+  if (!c.f64 && l <= SORSVD_MAX_L) {
+    // wider fp32 sketches: tiled Gram and in-place product kernels; the
+    // third pass is skipped on the device in the same way
+    float* parts = (float*)c.at(c.L.parts);
+    const int nb = (int)cq_wide_blocks(rows, l);
+    int* conv = c.status()->pad;
+    for (int p = 0; p < passes; ++p) {
+      const int* skip = p == 2 ? conv : nullptr;
+      LAUNCH(K_SMALL_GEMM, launch_cq_gram_wide((const float*)T, ld, rows, l, parts, skip, c.st));
+      LAUNCH(K_REDUCE, launch_reduce_parts_warp(parts, nb, (int64_t)l * l, l, l, l, (double*)c.at(c.L.G), l, c.st));
+      LAUNCH(K_CHOL, launch_chol_inv((const double*)c.at(c.L.G), l, p == 0 ? shift0 : 0.0, c.at(c.L.Rinv), false,
+                                     c.status(), c.st, skip, p == 1 ? conv : nullptr, kOrthTol));
+      LAUNCH(K_SMALL_GEMM, launch_cq_apply_wide((float*)T, ld, rows, l, (const float*)c.at(c.L.Rinv), skip, c.st));
     }
     return SORSVD_OK;
   }

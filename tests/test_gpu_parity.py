@@ -312,13 +312,19 @@ def test_chol_inv_retry_and_breakdown(nat):
     assert np.array_equal(R.cpu().numpy(), np.eye(20, dtype=np.float32))
 
 
-@pytest.mark.parametrize("dt,l", [("f32", 200), ("bf16", 266)])
+@pytest.mark.parametrize("dt,l", [("f32", 129), ("f32", 200), ("bf16", 266), ("tf32", 288), ("f32", 320)])
 def test_run_large_sketch(nat, dt, l):
     """l beyond one SM's shared memory for the Jacobi sweep (cooperative grid
-    sweep) and for the row-block CholeskyQR (CUDA-core products)."""
+    sweep) and beyond the whole-panel CholeskyQR kernels (tiled Gram and
+    product kernels, l > 128); rows 1200 and 700 leave ragged row chunks."""
     k = l - 10
     A64, s, _, _ = inputs.spectral(1200, 700, inputs.sigma_exp(600, 64.0), seed=8)
     exact, got, ref = run_both(nat, A64, k, 10, 1, 2, dt)
     r_gpu, r_orc, ds = gates(exact, got, ref)
     tol = TOL[dt]
     assert abs(r_gpu - r_orc) <= tol and ds <= tol, (r_gpu, r_orc, ds)
+    U, S, V = (to_np(t) for t in got)
+    # the sketches are fp32 for every storage type: CholeskyQR3 leaves them
+    # orthonormal to fp32 level, and U~, V~ come from the binary64 finish
+    assert np.abs(U.T @ U - np.eye(k)).max() <= 1e-4
+    assert np.abs(V.T @ V - np.eye(k)).max() <= 1e-4
