@@ -437,18 +437,24 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 }
 
 // Sum the partial segments of every tile touched by more than one CTA, in
-// CTA order (deterministic), and write the tile to the output.  Blocks walk tiles
-// (blockIdx.x) and split each tile's elements (blockIdx.y).  The CTAs that
-// cover tile t are c0..c1 (consecutive); tile t is the head segment (slot 0)
-// of each of them except c0 when c0's range starts inside an earlier tile
-// (then it is c0's tail, slot 1).
+// CTA order (deterministic), and write the tile to the output.  Only split
+// tiles need work, and each holds at least one CTA boundary: block x takes
+// the boundary of CTA b = x + 1 and handles the tile that boundary falls
+// in when b is the first CTA boundary inside it; blockIdx.y splits the
+// tile's elements.  The CTAs that cover tile t are c0..c1 (consecutive);
+// tile t is the head segment (slot 0) of each of them except c0 when c0's
+// range starts inside an earlier tile (then it is c0's tail, slot 1).
 __global__ void tc_fixup_kernel(const TcParams P) {
   const int mrows = 128 * P.MT;
   const int per = mrows * P.N;
-  for (int64_t t = blockIdx.x; t < P.tiles; t += gridDim.x) {
-    const int64_t c0 = cta_of(t * P.ipt, P.total, P.G);
+  const int64_t b = (int64_t)blockIdx.x + 1;
+  const int64_t x = b * P.total / P.G;           // first iteration of CTA b
+  const int64_t t = x / P.ipt;
+  if (x == t * P.ipt || t >= P.tiles) return;     // the boundary is a tile start
+  const int64_t c0 = cta_of(t * P.ipt, P.total, P.G);
+  if (c0 != b - 1) return;                        // an earlier boundary handles tile t
+  {
     const int64_t c1 = cta_of(t * P.ipt + P.ipt - 1, P.total, P.G);
-    if (c0 == c1) continue;                       // written whole by its CTA
     const int slot0 = (c0 * P.total / P.G < t * P.ipt) ? 1 : 0;
     for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < per; e += gridDim.y * blockDim.x) {
       const int col = e / mrows, row = e - col * mrows;
@@ -664,13 +670,13 @@ cudaError_t launch_tc_gemm(bool trans_a, int elt, int64_t M, int64_t N, int64_t 
     else e = launch_typed<3, false>(ma, mb, mblo, P, smem, st);
   }
   if (e != cudaSuccess) return e;
-  // fix-up of tiles split across CTAs (blocks of whole tiles return at once)
-  const int64_t gx = std::min<int64_t>(P.tiles, 65535);
+  // fix-up of the tiles split across CTAs: one block row per CTA boundary,
+  // about 4 elements of the tile per thread
+  if (P.G < 2) return cudaSuccess;
   const int64_t per = (int64_t)128 * P.MT * P.N;
-  const int64_t gy = std::max<int64_t>(1, std::min<int64_t>((per + 255) / 256,
-                                                            ((int64_t)num_sms() * 8 + gx - 1) / gx));
+  const int64_t gy = std::max<int64_t>(1, std::min<int64_t>((per + 1023) / 1024, 65535));
   ProfScope ps2(K_REDUCE, st);
-  tc_fixup_kernel<<<dim3((unsigned)gx, (unsigned)gy), 256, 0, st>>>(P);
+  tc_fixup_kernel<<<dim3((unsigned)(P.G - 1), (unsigned)gy), 256, 0, st>>>(P);
   return cudaGetLastError();
 }
 

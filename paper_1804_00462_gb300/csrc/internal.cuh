@@ -168,28 +168,26 @@ cudaError_t launch_jacobi(const double* M, int l, int k, bool f64, void* Ut, voi
                           void* S, bool S_f64, void* work, DeviceStatus* status, cudaStream_t st);
 size_t jacobi_work_bytes(int l);
 
-// cholqr.cu: row-block CholeskyQR products for fp32 sketches, l <= kCqMaxL.
-// launch_cq_gram: parts[b] (l x l fp32) = T_b^T T_b for each block b of rows
-// (cq_blocks(rows) blocks; sum them with launch_reduce_splits, stride l*l).
-// launch_cq_apply: T <- T R^{-1} in place (Rinv l x l upper triangular,
-// ld = l, fp32); with parts non-null also the partial Grams of the result.
-constexpr int kCqMaxL = 128;
-int64_t cq_blocks(int64_t rows);
-cudaError_t launch_cq_gram(const float* T, int64_t ld, int64_t rows, int l, float* parts, cudaStream_t st);
-cudaError_t launch_cq_apply(float* T, int64_t ld, int64_t rows, int l, const float* Rinv, float* parts,
+// rowblock.cu: fp32 row-block products (l <= SORSVD_MAX_L columns).
+// launch_rb_gram: rb_gram_blocks(rows, lx, ly, sym) partials (lx x ly, ld lx,
+// stride lx*ly) of X^T Y over the rows (sym: Y = X, both halves written);
+// returns at once when *skip is set.  launch_rb_apply: Y = X B (X rows x K,
+// B K x N, ld ldb; tri: B upper triangular), out of place, with an optional
+// 16-bit rounding (kind16 1 bf16, 2 fp16); X 16-byte aligned, ldx % 4 == 0.
+// launch_rb_copy: dst = src (rows x l, ld) plus the 16-bit rounding; with
+// *skip set only the rounding of dst.
+int64_t rb_gram_blocks(int64_t rows, int lx, int ly, bool sym);
+size_t rb_gram_parts_bytes(int64_t rows, int lx, int ly, bool sym);
+cudaError_t launch_rb_gram(const float* X, int64_t ldx, const float* Y, int64_t ldy, int64_t rows, int lx, int ly,
+                           bool sym, float* parts, const int* skip, cudaStream_t st);
+cudaError_t launch_rb_apply(const float* X, int64_t ldx, int64_t rows, int K, const float* B, int64_t ldb, int N,
+                            bool tri, float* Y, int64_t ldy, void* Y16, int64_t ld16, int kind16, const int* skip,
                             cudaStream_t st);
-// Wide sketches (kCqMaxL < l <= SORSVD_MAX_L): launch_cq_gram_wide writes
-// cq_wide_blocks(rows, l) partial Grams (l x l fp32, stride l*l) to parts;
-// launch_cq_apply_wide: T <- T R^{-1} in place.  Both return at once when
-// skip is non-null and *skip is set (on the device).
-int64_t cq_wide_blocks(int64_t rows, int l);
-cudaError_t launch_cq_gram_wide(const float* T, int64_t ld, int64_t rows, int l, float* parts, const int* skip,
-                                cudaStream_t st);
-cudaError_t launch_cq_apply_wide(float* T, int64_t ld, int64_t rows, int l, const float* Rinv, const int* skip,
-                                 cudaStream_t st);
+cudaError_t launch_rb_copy(const float* src, float* dst, int64_t ld, int64_t rows, int l, void* Y16, int64_t ld16,
+                           int kind16, const int* skip, cudaStream_t st);
 // out (binary64, rows x cols, ldo) = fixed-order sum of nparts fp32
-// partials (ld ldp, stride between partials), one warp per element
-cudaError_t launch_reduce_parts_warp(const float* parts, int nparts, int64_t stride, int rows, int cols, int ldp,
+// partials (ld ldp, stride between partials), one thread per element
+cudaError_t launch_reduce_parts(const float* parts, int nparts, int64_t stride, int rows, int cols, int ldp,
                                      double* out, int ldo, cudaStream_t st);
 
 // sorsvd.cu: the device status word of a sorsvd_run workspace

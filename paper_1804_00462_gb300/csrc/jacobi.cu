@@ -574,11 +574,54 @@ __device__ __forceinline__ void jacobi_order_body(int l, int k, const double* __
   }
 }
 
+
+// The same ordering and sign convention with one block per column c of the
+// finish (the rank of sigma_c and the sign are block reductions, then the
+// block writes its column to position rank): the binary64 compares and
+// conversions spread over l blocks instead of one.
 template <typename J, typename TS>
-__global__ void __launch_bounds__(JT)
-jacobi_order_kernel(int l, int k, const double* __restrict__ U64, const double* __restrict__ V64,
-                    const double* __restrict__ sig, J* __restrict__ Ut, J* __restrict__ Vt, TS* __restrict__ S) {
-  jacobi_order_body<J, TS>(l, k, U64, V64, sig, Ut, Vt, S);
+__global__ void __launch_bounds__(256)
+jacobi_order_col_kernel(int l, int k, const double* __restrict__ U64, const double* __restrict__ V64,
+                        const double* __restrict__ sig, J* __restrict__ Ut, J* __restrict__ Vt, TS* __restrict__ S) {
+  __shared__ int s_rank[8], s_bi[8];
+  __shared__ double s_best[8];
+  const int c = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
+  const double sc = sig[c];
+  int rank = 0;
+  for (int d = t; d < l; d += blockDim.x) {
+    const double sd = sig[d];
+    rank += (sd > sc) || (sd == sc && d < c);
+  }
+  const double* uc = U64 + (size_t)c * l;
+  double best = -1;
+  int bi = l;
+  for (int i = t; i < l; i += blockDim.x) {
+    const double a = fabs(uc[i]);
+    if (a > best) { best = a; bi = i; }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    rank += __shfl_xor_sync(0xffffffffu, rank, o);
+    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+  }
+  if (lane == 0) { s_rank[warp] = rank; s_best[warp] = best; s_bi[warp] = bi; }
+  __syncthreads();
+  rank = 0;
+  best = -1;
+  bi = l;
+  for (int w = 0; w < nw; ++w) {
+    rank += s_rank[w];
+    if (s_best[w] > best || (s_best[w] == best && s_bi[w] < bi)) { best = s_best[w]; bi = s_bi[w]; }
+  }
+  const double sgn = (bi < l && uc[bi] < 0.0) ? -1.0 : 1.0;
+  const double* vc = V64 + (size_t)c * l;
+  for (int i = t; i < l; i += blockDim.x) {
+    Ut[(size_t)rank * l + i] = (J)(sgn * uc[i]);
+    Vt[(size_t)rank * l + i] = (J)(sgn * vc[i]);
+  }
+  if (t == 0 && rank < k) S[rank] = (TS)sc;
 }
 
 // ---------------------------------------------------------------- batched
@@ -792,7 +835,7 @@ cudaError_t run_all(const double* M, int l, int k, void* Ut, void* Vt, void* S, 
                                 : launch_sweep<J, false>(M, l, vout, gwork, 0, status, st);
   if (e != cudaSuccess) return e;
   jacobi_finish_kernel<J><<<l, 256, 0, st>>>(M, l, vout, u64, v64, sig);
-  jacobi_order_kernel<J, TS><<<1, JT, 0, st>>>(l, k, u64, v64, sig, (J*)Ut, (J*)Vt, (TS*)S);
+  jacobi_order_col_kernel<J, TS><<<l, 256, 0, st>>>(l, k, u64, v64, sig, (J*)Ut, (J*)Vt, (TS*)S);
   return cudaGetLastError();
 }
 

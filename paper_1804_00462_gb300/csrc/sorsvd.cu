@@ -125,10 +125,11 @@ Layout make_layout(int64_t m, int64_t n, int l, int dt) {
     pb = std::max(pb, tc_parts_bytes(elt, m, l, n));
     pb = std::max(pb, tc_parts_bytes(elt, n, l, m));
   }
-  if (dt != SORSVD_F64 && l <= kCqMaxL)              // row-block Gram partials
-    pb = std::max(pb, (size_t)cq_blocks(std::max(m, n)) * l * l * 4);
-  else if (dt != SORSVD_F64)
-    pb = std::max(pb, (size_t)std::max(cq_wide_blocks(m, l), cq_wide_blocks(n, l)) * l * l * 4);
+  if (dt != SORSVD_F64) {                           // row-block Gram partials
+    pb = std::max(pb, rb_gram_parts_bytes(m, l, l, true));
+    pb = std::max(pb, rb_gram_parts_bytes(n, l, l, true));
+    pb = std::max(pb, rb_gram_parts_bytes(m, l, l, false));
+  }
   L.parts = take(pb);
   L.G = take((size_t)l * l * 8);
   L.Rinv = take((size_t)l * l * acc);
@@ -220,45 +221,39 @@ int prepare_at(const Ctx& c, const void* A, int64_t m, int64_t n, int64_t lda) {
 }
 
 // T (rows x l, ld, accumulator type) <- T R^{-1}, repeated `passes` times
-// (CholeskyQR); the first pass is shifted by shift0.  fp32 sketches with
-// l <= kCqMaxL use the row-block kernels (Gram partials, in-place T R^{-1}
-// fused with the next pass's Gram partials); binary64 and wider sketches
-// the CUDA-core GEMMs.
-int orth(const Ctx& c, void* T, int64_t rows, int64_t ld, int l, int passes, double shift0) {
-  if (!c.f64 && l <= kCqMaxL) {
+// (CholeskyQR); the first pass is shifted by shift0.  fp32 sketches use the
+// row-block kernels: the products ping-pong between T and the tmp buffer
+// (same ld) and the result is copied back to T after an odd number of
+// passes; the third pass of CholeskyQR3 only runs when the second pass's
+// Gram was not already within kOrthTol of the identity (decided on the
+// device; a skipped pass leaves the result in T).  out16, when non-null,
+// receives the 16-bit rounding of the result (the operand of the next
+// BF16 / F16 pass).  binary64 sketches use the CUDA-core GEMMs.
+int orth(const Ctx& c, void* T, int64_t rows, int64_t ld, int l, int passes, double shift0, void* out16 = nullptr,
+         int64_t ld16 = 0) {
+  const int kind16 = out16 ? (c.dt == SORSVD_BF16 ? 1 : 2) : 0;
+  if (!c.f64) {
     float* parts = (float*)c.at(c.L.parts);
-    const int nb = (int)cq_blocks(rows);
-    LAUNCH(K_SMALL_GEMM, launch_cq_gram((const float*)T, ld, rows, l, parts, c.st));
-    // the third pass of CholeskyQR3 only runs when the second pass's Gram
-    // was not already within kOrthTol of the identity (decided on the
-    // device: the third pass's factorisation then returns R^{-1} = I)
+    const int nb = (int)rb_gram_blocks(rows, l, l, true);
     int* conv = c.status()->pad;
-    for (int p = 0; p < passes; ++p) {
-      LAUNCH(K_REDUCE, launch_reduce_parts_warp(parts, nb, (int64_t)l * l, l, l, l, (double*)c.at(c.L.G), l, c.st));
-      LAUNCH(K_CHOL, launch_chol_inv((const double*)c.at(c.L.G), l, p == 0 ? shift0 : 0.0, c.at(c.L.Rinv), false,
-                                     c.status(), c.st, p == 2 ? conv : nullptr, p == 1 ? conv : nullptr, kOrthTol));
-      LAUNCH(K_SMALL_GEMM, launch_cq_apply((float*)T, ld, rows, l, (const float*)c.at(c.L.Rinv),
-                                           p + 1 < passes ? parts : nullptr, c.st));
-    }
-    return SORSVD_OK;
-  }
-  if (!c.f64 && l <= SORSVD_MAX_L) {
-    // wider fp32 sketches: tiled Gram and in-place product kernels; the
-    // third pass is skipped on the device in the same way
-    float* parts = (float*)c.at(c.L.parts);
-    const int nb = (int)cq_wide_blocks(rows, l);
-    int* conv = c.status()->pad;
+    float* X = (float*)T;
+    float* Y = (float*)c.at(c.L.tmp);
     for (int p = 0; p < passes; ++p) {
       const int* skip = p == 2 ? conv : nullptr;
-      LAUNCH(K_SMALL_GEMM, launch_cq_gram_wide((const float*)T, ld, rows, l, parts, skip, c.st));
-      LAUNCH(K_REDUCE, launch_reduce_parts_warp(parts, nb, (int64_t)l * l, l, l, l, (double*)c.at(c.L.G), l, c.st));
+      LAUNCH(K_SMALL_GEMM, launch_rb_gram(X, ld, X, ld, rows, l, l, true, parts, skip, c.st));
+      LAUNCH(K_REDUCE, launch_reduce_parts(parts, nb, (int64_t)l * l, l, l, l, (double*)c.at(c.L.G), l, c.st));
       LAUNCH(K_CHOL, launch_chol_inv((const double*)c.at(c.L.G), l, p == 0 ? shift0 : 0.0, c.at(c.L.Rinv), false,
                                      c.status(), c.st, skip, p == 1 ? conv : nullptr, kOrthTol));
-      LAUNCH(K_SMALL_GEMM, launch_cq_apply_wide((float*)T, ld, rows, l, (const float*)c.at(c.L.Rinv), skip, c.st));
+      LAUNCH(K_SMALL_GEMM, launch_rb_apply(X, ld, rows, l, (const float*)c.at(c.L.Rinv), l, l, true, Y, ld, nullptr,
+                                           0, 0, skip, c.st));
+      std::swap(X, Y);
     }
+    if (X != (float*)T || kind16)
+      LAUNCH(K_MISC, launch_rb_copy(X, (float*)T, ld, rows, l, out16, ld16, kind16,
+                                    (passes == 3 && X != (float*)T) ? conv : nullptr, c.st));
     return SORSVD_OK;
   }
-  const int adt = c.f64 ? SORSVD_F64 : SORSVD_F32;
+  const int adt = SORSVD_F64;
   for (int p = 0; p < passes; ++p) {
     int r = gemm(c, K_SMALL_GEMM, true, l, l, rows, T, ld, adt, T, ld, adt, c.at(c.L.G), l, true, kCapSmall);
     if (r) return r;
@@ -269,6 +264,33 @@ int orth(const Ctx& c, void* T, int64_t rows, int64_t ld, int l, int passes, dou
     if (r) return r;
     LAUNCH(K_MISC, launch_copy2d(c.at(c.L.tmp), ld, T, ld, rows, l, acc_size(c.dt), c.st));
   }
+  return SORSVD_OK;
+}
+
+// M (l x l, binary64, ldm) = X^T Y for X, Y rows x l in the accumulator type
+int cross_gram(const Ctx& c, const void* X, int64_t ldx, const void* Y, int64_t ldy, int64_t rows, int l, double* M,
+               int64_t ldm) {
+  const bool aligned = !((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Y)) & 15) && !((ldx | ldy) & 3);
+  if (c.f64 || !aligned) {
+    const int adt = c.f64 ? SORSVD_F64 : SORSVD_F32;
+    return gemm(c, K_SMALL_GEMM, true, l, l, rows, X, ldx, adt, Y, ldy, adt, M, ldm, true, kCapSmall);
+  }
+  float* parts = (float*)c.at(c.L.parts);
+  LAUNCH(K_SMALL_GEMM, launch_rb_gram((const float*)X, ldx, (const float*)Y, ldy, rows, l, l, false, parts, nullptr,
+                                      c.st));
+  LAUNCH(K_REDUCE, launch_reduce_parts(parts, (int)rb_gram_blocks(rows, l, l, false), (int64_t)l * l, l, l, l, M,
+                                       (int)ldm, c.st));
+  return SORSVD_OK;
+}
+
+// C (rows x k, ldc) = Q (rows x l) B (l x k, ld l), accumulator type
+int assemble(const Ctx& c, const void* Q, int64_t ldq, int64_t rows, int l, const void* B, int k, void* C,
+             int64_t ldc) {
+  if (c.f64 || (reinterpret_cast<uintptr_t>(Q) & 15) || (ldq & 3))
+    return gemm(c, K_SMALL_GEMM, false, rows, k, l, Q, ldq, c.f64 ? SORSVD_F64 : SORSVD_F32, B, l,
+                c.f64 ? SORSVD_F64 : SORSVD_F32, C, ldc, c.f64, kCapBig);
+  LAUNCH(K_SMALL_GEMM, launch_rb_apply((const float*)Q, ldq, rows, l, (const float*)B, l, k, false, (float*)C, ldc,
+                                       nullptr, 0, 0, nullptr, c.st));
   return SORSVD_OK;
 }
 
@@ -306,11 +328,11 @@ int core_impl(const Ctx& c, const void* A, int64_t m, int64_t n, int64_t lda, un
     LAUNCH(K_MISC, launch_convert_f32((const float*)Q2, ldq2, n, l, hi, c.L.ldn, dt, lo, c.st));
     r = pass(c, K_CORE, false, m, l, n, A, lda, hi, c.L.ldn, dt, c.at(c.L.tmp), ldw, nullptr, 0, false);
     if (r) return r;
-    r = gemm(c, K_SMALL_GEMM, true, l, l, m, Q1, ldq1, adt, c.at(c.L.tmp), ldw, adt, M, ldm, true, kCapSmall);
+    r = cross_gram(c, Q1, ldq1, c.at(c.L.tmp), ldw, m, l, M, ldm);
     if (r) return r;
     r = pass(c, K_CORE, false, m, l, n, A, lda, lo, c.L.ldn, dt, c.at(c.L.tmp), ldw, nullptr, 0, false);
     if (r) return r;
-    r = gemm(c, K_SMALL_GEMM, true, l, l, m, Q1, ldq1, adt, c.at(c.L.tmp), ldw, adt, c.at(c.L.G), l, true, kCapSmall);
+    r = cross_gram(c, Q1, ldq1, c.at(c.L.tmp), ldw, m, l, (double*)c.at(c.L.G), l);
     if (r) return r;
     LAUNCH(K_MISC, launch_add_f64((const double*)c.at(c.L.G), l, M, ldm, l, l, c.st));
     return SORSVD_OK;
@@ -323,7 +345,7 @@ int core_impl(const Ctx& c, const void* A, int64_t m, int64_t n, int64_t lda, un
     r = gemm(c, K_CORE, false, m, l, n, A, lda, dt, Q2, ldq2, adt, c.at(c.L.tmp), ldw, c.f64, kCapBig);
   }
   if (r) return r;
-  return gemm(c, K_SMALL_GEMM, true, l, l, m, Q1, ldq1, adt, c.at(c.L.tmp), ldw, adt, M, ldm, true, kCapSmall);
+  return cross_gram(c, Q1, ldq1, c.at(c.L.tmp), ldw, m, l, M, ldm);
 }
 
 int check_dtype(int dt) { return (dt >= SORSVD_F64 && dt <= SORSVD_F16) ? SORSVD_OK : SORSVD_ERR_DTYPE; }
@@ -493,27 +515,22 @@ int sorsvd_run(const void* A, int64_t m, int64_t n, int64_t lda, int k, int p, i
       r = pass(c, last ? kc : K_PASS, false, m, l, n, A, lda, c.at(L.t2op), L.ldn, h16 ? dtype : adt, c.at(L.t1),
                L.ldm, nullptr, 0, last);
       if (r) return r;
-      r = orth(c, c.at(L.t1), m, L.ldm, l, np, first_shift(dtype));
+      r = orth(c, c.at(L.t1), m, L.ldm, l, np, first_shift(dtype), h16 ? t1op : nullptr, L.ldm);
       if (r) return r;
-      if (h16)
-        LAUNCH(K_MISC, launch_convert_f32((const float*)c.at(L.t1), L.ldm, m, l, t1op, L.ldm, dtype, nullptr, c.st));
       r = pass(c, last ? kc : K_PASS, true, n, l, m, A, lda, t1op, L.ldm, h16 ? dtype : adt, c.at(L.t2), L.ldn,
                nullptr, 0, last);
       if (r) return r;
-      r = orth(c, c.at(L.t2), n, L.ldn, l, np, first_shift(dtype));
+      r = orth(c, c.at(L.t2), n, L.ldn, l, np, first_shift(dtype), (!last && h16) ? c.at(L.t2op) : nullptr, L.ldn);
       if (r) return r;
-      if (!last && h16)
-        LAUNCH(K_MISC, launch_convert_f32((const float*)c.at(L.t2), L.ldn, n, l, c.at(L.t2op), L.ldn, dtype, nullptr,
-                                          c.st));
     }
   }
   r = core_impl(c, A, m, n, lda, flags, c.at(L.t1), L.ldm, c.at(L.t2), L.ldn, l, (double*)c.at(L.M), l);
   if (r) return r;
   LAUNCH(K_JACOBI, launch_jacobi((const double*)c.at(L.M), l, k, c.f64, c.at(L.Ut), c.at(L.Vt), S, c.f64,
                                   c.at(L.jwork), c.status(), c.st));
-  r = gemm(c, K_SMALL_GEMM, false, m, k, l, c.at(L.t1), L.ldm, adt, c.at(L.Ut), l, adt, U, ldu, c.f64, kCapBig);
+  r = assemble(c, c.at(L.t1), L.ldm, m, l, c.at(L.Ut), k, U, ldu);
   if (r) return r;
-  r = gemm(c, K_SMALL_GEMM, false, n, k, l, c.at(L.t2), L.ldn, adt, c.at(L.Vt), l, adt, V, ldv, c.f64, kCapBig);
+  r = assemble(c, c.at(L.t2), L.ldn, n, l, c.at(L.Vt), k, V, ldv);
   if (r) return r;
   return SORSVD_OK;
 }
