@@ -485,6 +485,167 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;
 }
 
+// ---------------------------------------------------------------- cluster
+// Sweeps on a thread-block cluster of kClusterCtas CTAs (one per SM).  The
+// N/2 pairs of a round are spread over the CTAs, gpc per CTA, one 16-lane
+// group each with the arithmetic of the one-block 16-lane sweep.  A group's
+// two slots hold the W and V columns of the round-robin positions g and
+// N - 1 - g; after the rotation each column is written to the slot of its
+// next position, in the other of two slot buffers (in another CTA's shared
+// memory when that position belongs to it).  One cluster barrier per round:
+// shared memory bandwidth and the per-round latency scale with the CTAs
+// instead of queueing on one SM, and no round trip goes through L2.  The
+// convergence flags of a sweep are OR-ed into CTA 0 and read back by all
+// CTAs before any of them decides, so every CTA runs the same barriers.
+constexpr int kClusterCtas = 16;
+constexpr int kClusterMinL = 48;                 // below: the one-block sweeps
+
+__device__ __forceinline__ int next_pos(int p, int N) { return p == 0 ? 0 : (p == N - 1 ? 1 : p + 1); }
+
+template <int EP>
+__global__ void __launch_bounds__(512)
+jacobi_sweep_cluster_kernel(const double* __restrict__ Min, int l, int gpc, float* __restrict__ Vout,
+                            DeviceStatus* status) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int LDW = 32 * EP;                       // floats per column slot
+  float* S = reinterpret_cast<float*>(smem_raw);     // [buffer 2][slot 2 gpc][W, V][LDW]
+  __shared__ int s_flag[2], s_big[2];                // used in CTA 0, by sweep parity
+  const int N = (l + 1) & ~1, G = N / 2;
+  const int t = threadIdx.x, lane = t & 31;
+  const int lg = t >> 4, gl = t & 15;
+  const int gg = rank * gpc + lg;
+  const bool act = gg < G;
+  const unsigned gmask = 0xFFFFu << ((lane >> 4) * 16);
+  const float eps = 1.1920928955078125e-07f;
+  const float tol = (float)l * eps, tol2 = tol * tol;
+  const float big = 32.f * tol, big2 = big * big;
+  auto slot = [&](int b, int sl) { return S + ((size_t)(b * 2 * gpc + sl) * 2) * LDW; };
+
+  // round 0: position p holds column p (zero columns past l)
+  for (int e = t; e < 2 * gpc * LDW; e += blockDim.x) {
+    const int sl = e / LDW, i = e - sl * LDW;
+    const int g = rank * gpc + (sl >> 1);
+    const int j = g < G ? ((sl & 1) ? N - 1 - g : g) : N;
+    float* w = slot(0, sl);
+    w[i] = (i < l && j < l) ? (float)Min[i + (size_t)j * l] : 0.f;
+    w[LDW + i] = (i == j && j < l) ? 1.f : 0.f;
+  }
+  if (rank == 0 && t == 0) { s_flag[0] = s_flag[1] = 0; s_big[0] = s_big[1] = 0; }
+  cluster.sync();
+
+  // the next positions of a group's slots do not change from round to
+  // round: their slots (and whether they are local) are fixed per group
+  const int pa = gg, pb = N - 1 - gg;
+  int dsl[2], dcta[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int q = next_pos(h ? pb : pa, N);
+    const int g2 = q < G ? q : N - 1 - q;
+    dsl[h] = 2 * (g2 % gpc) + (q < G ? 0 : 1);
+    dcta[h] = g2 / gpc;
+  }
+  int buf = 0, sweep;
+  for (sweep = 1; sweep <= kMaxSweeps; ++sweep) {
+    const int par = sweep & 1;
+    int rot_local = 0, big_local = 0;
+    // players at the group's positions: rr_player(p, r, N) = 1 + (p - 1 - r) mod (N - 1), stepped down per round
+    int ia = pa == 0 ? 0 : pa, ib = pb;
+    for (int r = 0; r < N - 1; ++r) {
+      if (act) {
+        const bool sw = ia > ib;                     // x: the smaller column index
+        float* sx = slot(buf, 2 * lg + (sw ? 1 : 0));
+        float* sy = slot(buf, 2 * lg + (sw ? 0 : 1));
+        const float2* wx = reinterpret_cast<const float2*>(sx);
+        const float2* wy = reinterpret_cast<const float2*>(sy);
+        const float2* vx = reinterpret_cast<const float2*>(sx + LDW);
+        const float2* vy = reinterpret_cast<const float2*>(sy + LDW);
+        float2 x[EP], y[EP], u[EP], v[EP];
+        float2 al2 = make_float2(0.f, 0.f), be2 = al2, ga2 = al2;
+#pragma unroll
+        for (int e = 0; e < EP; ++e) {
+          x[e] = wx[gl + 16 * e];
+          y[e] = wy[gl + 16 * e];
+          u[e] = vx[gl + 16 * e];
+          v[e] = vy[gl + 16 * e];
+          al2 = __ffma2_rn(x[e], x[e], al2);
+          be2 = __ffma2_rn(y[e], y[e], be2);
+          ga2 = __ffma2_rn(x[e], y[e], ga2);
+        }
+        float al = al2.x + al2.y, be = be2.x + be2.y, ga = ga2.x + ga2.y;
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(gmask, al, o);
+          be += __shfl_xor_sync(gmask, be, o);
+          ga += __shfl_xor_sync(gmask, ga, o);
+        }
+        if (ga * ga > tol2 * al * be) {
+          if (ga * ga > big2 * al * be) big_local = 1;
+          float cs, sn;
+          rotation(al, be, ga, &cs, &sn);
+          const float2 c2 = make_float2(cs, cs), s2 = make_float2(sn, sn), ns2 = make_float2(-sn, -sn);
+#pragma unroll
+          for (int e = 0; e < EP; ++e) {
+            const float2 xn = __ffma2_rn(c2, x[e], __fmul2_rn(ns2, y[e]));
+            const float2 yn = __ffma2_rn(s2, x[e], __fmul2_rn(c2, y[e]));
+            const float2 un = __ffma2_rn(c2, u[e], __fmul2_rn(ns2, v[e]));
+            const float2 vn = __ffma2_rn(s2, u[e], __fmul2_rn(c2, v[e]));
+            x[e] = xn; y[e] = yn; u[e] = un; v[e] = vn;
+          }
+          rot_local = 1;
+        }
+        // each column to the slot of its next position (buffer buf ^ 1)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          float* dst = slot(buf ^ 1, dsl[h]);
+          if (dcta[h] != rank) dst = cluster.map_shared_rank(dst, dcta[h]);
+          float2* dw = reinterpret_cast<float2*>(dst);
+          float2* dv = reinterpret_cast<float2*>(dst + LDW);
+          const bool is_x = (h == 0) != sw;          // the slot at pa holds x unless swapped
+#pragma unroll
+          for (int e = 0; e < EP; ++e) {
+            dw[gl + 16 * e] = is_x ? x[e] : y[e];
+            dv[gl + 16 * e] = is_x ? u[e] : v[e];
+          }
+        }
+      }
+      cluster.sync();
+      buf ^= 1;
+      if (pa != 0) ia = ia == 1 ? N - 1 : ia - 1;
+      ib = ib == 1 ? N - 1 : ib - 1;
+      // the next sweep's flags: every CTA read them for the previous sweep
+      // before this round's barrier
+      if (r == 0 && rank == 0 && t == 0) { s_flag[par ^ 1] = 0; s_big[par ^ 1] = 0; }
+    }
+    rot_local = __syncthreads_or(rot_local);
+    big_local = __syncthreads_or(big_local);
+    if (t == 0) {
+      if (rot_local) atomicOr(cluster.map_shared_rank(&s_flag[par], 0), 1);
+      if (big_local) atomicOr(cluster.map_shared_rank(&s_big[par], 0), 1);
+    }
+    cluster.sync();
+    const int rot = *cluster.map_shared_rank(&s_flag[par], 0);
+    const int bg = *cluster.map_shared_rank(&s_big[par], 0);
+    cluster.sync();                                  // every CTA has read CTA 0's flags
+    if (!rot) break;
+    if (sweep == kMaxSweeps) {
+      if (bg && rank == 0 && t == 0) raise_status(status, SORSVD_ERR_NOT_CONVERGED);
+      break;
+    }
+  }
+  if (rank == 0 && t == 0) atomicOr(&status->info, (min(sweep, kMaxSweeps)) << 8);
+  // a sweep ends where it began: position p holds column p
+  for (int e = t; e < 2 * gpc * LDW; e += blockDim.x) {
+    const int sl = e / LDW, i = e - sl * LDW;
+    const int g = rank * gpc + (sl >> 1);
+    if (g >= G || i >= l) continue;
+    const int j = (sl & 1) ? N - 1 - g : g;
+    if (j < l) Vout[i + (size_t)j * l] = slot(buf, sl)[LDW + i];
+  }
+}
+
 // From the accumulated right vector v_j (sweep precision): z = M v_j,
 // sigma_j = ||z||, u_j = z / sigma_j, all in binary64.
 template <typename J>
@@ -759,6 +920,60 @@ cudaError_t launch_sweep_coop(const double* M, int l, float* vout, void* work, D
 #undef COOP
 }
 
+// cluster sweep: 16 lanes x gpc pairs per CTA, kClusterCtas CTAs
+inline int sweep_cluster_ep(int l) {
+  const int need = (l + 31) / 32;
+  return need <= 10 ? need : 0;
+}
+inline int sweep_cluster_gpc(int l) {
+  const int G = (l + 1) / 2;
+  return (G + kClusterCtas - 1) / kClusterCtas;
+}
+inline size_t sweep_cluster_smem(int l) {
+  return (size_t)2 * 2 * sweep_cluster_gpc(l) * 2 * 32 * std::max(1, sweep_cluster_ep(l)) * sizeof(float);
+}
+
+cudaError_t launch_sweep_cluster(const double* M, int l, float* vout, DeviceStatus* status, cudaStream_t st) {
+  const int ep = sweep_cluster_ep(l), gpc = sweep_cluster_gpc(l);
+  const size_t smem = sweep_cluster_smem(l);
+  if (!ep || gpc * 16 > 512 || smem > kSweepSmemMax) return cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kClusterCtas, 1, 1);
+  cfg.blockDim = dim3(gpc * 16, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kClusterCtas;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+#define CLSWEEP(E)                                                                                  \
+  {                                                                                                 \
+    auto kern = jacobi_sweep_cluster_kernel<E>;                                                     \
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);  \
+    if (e == cudaSuccess)                                                                           \
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);       \
+    if (e != cudaSuccess) return e;                                                                 \
+    return cudaLaunchKernelEx(&cfg, kern, M, l, gpc, vout, status);                                 \
+  }
+  switch (ep) {
+    case 1: CLSWEEP(1)
+    case 2: CLSWEEP(2)
+    case 3: CLSWEEP(3)
+    case 4: CLSWEEP(4)
+    case 5: CLSWEEP(5)
+    case 6: CLSWEEP(6)
+    case 7: CLSWEEP(7)
+    case 8: CLSWEEP(8)
+    case 9: CLSWEEP(9)
+    case 10: CLSWEEP(10)
+    default: return cudaErrorInvalidValue;
+  }
+#undef CLSWEEP
+}
+
 cudaError_t launch_sweep_g(const double* M, int l, float* vout, DeviceStatus* status, cudaStream_t st) {
   const int ep = sweep_g_ep(l);
   const size_t smem = sweep_g_smem(l);
@@ -823,7 +1038,10 @@ cudaError_t run_all(const double* M, int l, int k, void* Ut, void* Vt, void* S, 
   const size_t need = 2 * (size_t)l * l * sizeof(J);
   cudaError_t e;
   static const int lanes = [] { const char* v = std::getenv("SORSVD_JACOBI_LANES"); return v ? std::atoi(v) : 16; }();
-  if (sizeof(J) == 4 && lanes == 16 && sweep_g_smem(l) <= kSweepSmemMax)
+  if (sizeof(J) == 4 && lanes == 16 && l >= kClusterMinL && sweep_cluster_ep(l) &&
+      sweep_cluster_smem(l) <= kSweepSmemMax)
+    e = launch_sweep_cluster(M, l, reinterpret_cast<float*>(vout), status, st);
+  else if (sizeof(J) == 4 && lanes == 16 && sweep_g_smem(l) <= kSweepSmemMax)
     e = launch_sweep_g(M, l, reinterpret_cast<float*>(vout), status, st);
   else if (sizeof(J) == 4 && sweep_coop_ep(l) && sweep_f2_smem(l) > kSweepSmemMax)
     e = launch_sweep_coop(M, l, reinterpret_cast<float*>(vout), w + ((jacobi_base_bytes(l) + 255) & ~(size_t)255),
