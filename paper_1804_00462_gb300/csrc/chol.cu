@@ -150,6 +150,14 @@ constexpr int TLD = TB + 1;       // tile row stride
 constexpr int TS = TB * TLD;      // elements per tile
 
 __device__ __forceinline__ int tid_of(int I, int J) { return I * (I + 1) / 2 + J; }
+// q -> (i, j), j <= i, for q = i (i + 1) / 2 + j
+__device__ __forceinline__ void tri_index(int q, int* i, int* j) {
+  int b = (int)((sqrtf(8.f * q + 1.f) - 1.f) * 0.5f);
+  while ((b + 1) * (b + 2) / 2 <= q) ++b;
+  while (b * (b + 1) / 2 > q) --b;
+  *i = b;
+  *j = q - b * (b + 1) / 2;
+}
 
 constexpr int BT = 512;           // threads of the blocked kernel
 
@@ -325,22 +333,38 @@ __device__ __forceinline__ void chol_inv_blocked_body(const double* __restrict__
         }
       }
       if (s_fail) break;
-      // A_IJ -= L_IK L_JK^T for K < J <= I
-      for (int I = K + 1; I < nb; ++I)
-        for (int J = K + 1; J <= I; ++J) {
-          F* out = tile(I, J);
-          const F* a0 = tile(I, K);
-          const F* b0 = tile(J, K);
-          for (int e = t; e < TB * TB; e += BT) {
-            const int r = e >> 5, c = e & 31;
-            const F* a = a0 + r * TLD;
-            const F* b = b0 + c * TLD;
-            F s = 0;
-#pragma unroll 8
-            for (int k = 0; k < TB; ++k) s += a[k] * b[k];
-            out[r * TLD + c] -= s;
+      // A_IJ -= L_IK L_JK^T for K < J <= I: 64 threads per tile, a 4 x 4
+      // block of it each (8 row and column values per k for 16 FMAs)
+      {
+        const int nrem = nb - K - 1, ntr = nrem * (nrem + 1) / 2;
+        const int sub = t & 63, r0 = 4 * (sub >> 3), c0 = 4 * (sub & 7);
+        for (int q = t >> 6; q < ntr; q += BT / 64) {
+          int bi, bj;
+          tri_index(q, &bi, &bj);
+          const F* a = tile(K + 1 + bi, K) + r0 * TLD;
+          const F* b = tile(K + 1 + bj, K) + c0 * TLD;
+          F acc[4][4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = (F)0;
+#pragma unroll 4
+          for (int k = 0; k < TB; ++k) {
+            F av[4], bv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) { av[u] = a[u * TLD + k]; bv[u] = b[u * TLD + k]; }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+              for (int v = 0; v < 4; ++v) acc[u][v] += av[u] * bv[v];
           }
+          F* out = tile(K + 1 + bi, K + 1 + bj) + r0 * TLD + c0;
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) out[u * TLD + v] -= acc[u][v];
         }
+      }
       __syncthreads();
     }
     if (!s_fail) break;
@@ -395,65 +419,90 @@ __device__ __forceinline__ void chol_inv_blocked_body(const double* __restrict__
   // Off-diagonal blocks one block row I at a time: X_IJ = -X_II S_IJ with
   // S_IJ = sum_{K=J}^{I-1} L_IK X_KJ for every J < I at once (block rows
   // above I are final); all S_IJ are formed before any X_IJ overwrites the
-  // L_IJ they read.
+  // L_IJ they read.  64 threads per tile, a 4 x 4 block each; the I tiles
+  // of a block row take ceil(I / 8) waves of the 512 threads.
   {
-    constexpr int EPT = TB * TB / BT;             // elements of a tile per thread
-    constexpr int NBM = (SORSVD_MAX_L + TB - 1) / TB;
+    constexpr int NWAVE = ((SORSVD_MAX_L + TB - 1) / TB + 7) / 8;
+    const int sub = t & 63, r0 = 4 * (sub >> 3), c0 = 4 * (sub & 7), slot = t >> 6;
     for (int I = 1; I < nb; ++I) {
-      F acc[NBM * EPT];
+      F acc[NWAVE][4][4];
 #pragma unroll
-      for (int J = 0; J < NBM; ++J) {
+      for (int w = 0; w < NWAVE; ++w) {
+        const int J = slot + 8 * w;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[w][u][v] = (F)0;
         if (J < I) {
+          for (int K = J; K < I; ++K) {
+            const F* a = tile(I, K) + r0 * TLD;          // L_IK (rows r0..)
+            const F* bb = tile(K, J) + c0;               // X_KJ (X_JJ, lower, when K == J)
+#pragma unroll 4
+            for (int k = 0; k < TB; ++k) {
+              F av[4], bv[4];
 #pragma unroll
-          for (int q = 0; q < EPT; ++q) {
-            const int e = t + q * BT, r = e >> 5, c = e & 31;
-            F s = 0;
-            for (int K = J; K < I; ++K) {
-              const F* a = tile(I, K) + r * TLD;   // L_IK (X_JJ when K == J is lower)
-              const F* bb = tile(K, J);
-#pragma unroll 8
-              for (int k = 0; k < TB; ++k) s += a[k] * bb[k * TLD + c];
+              for (int u = 0; u < 4; ++u) { av[u] = a[u * TLD + k]; bv[u] = bb[k * TLD + u]; }
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[w][u][v] += av[u] * bv[v];
             }
-            acc[J * EPT + q] = s;
           }
         }
       }
       __syncthreads();
 #pragma unroll
-      for (int J = 0; J < NBM; ++J) {
+      for (int w = 0; w < NWAVE; ++w) {
+        const int J = slot + 8 * w;
         if (J < I) {
+          F* o = tile(I, J) + r0 * TLD + c0;
 #pragma unroll
-          for (int q = 0; q < EPT; ++q) {
-            const int e = t + q * BT;
-            tile(I, J)[(e >> 5) * TLD + (e & 31)] = acc[J * EPT + q];
-          }
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) o[u * TLD + v] = acc[w][u][v];
         }
       }
       __syncthreads();
+      // X_IJ = -X_II S_IJ, X_II lower triangular (k <= row)
       const F* xi0 = tile(I, I);
 #pragma unroll
-      for (int J = 0; J < NBM; ++J) {
+      for (int w = 0; w < NWAVE; ++w) {
+        const int J = slot + 8 * w;
         if (J < I) {
-          const F* sm = tile(I, J);
+          const F* sm = tile(I, J) + c0;
+          F x[4][4];
 #pragma unroll
-          for (int q = 0; q < EPT; ++q) {
-            const int e = t + q * BT, r = e >> 5, c = e & 31;
-            const F* xi = xi0 + r * TLD;
-            F x = 0;
-            for (int k = 0; k <= r; ++k) x += xi[k] * sm[k * TLD + c];
-            acc[J * EPT + q] = -x;
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) x[u][v] = (F)0;
+          for (int k = 0; k < r0 + 4; ++k) {
+            F av[4], bv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              av[u] = k <= r0 + u ? xi0[(r0 + u) * TLD + k] : (F)0;
+              bv[u] = sm[k * TLD + u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+              for (int v = 0; v < 4; ++v) x[u][v] += av[u] * bv[v];
           }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[w][u][v] = -x[u][v];
         }
       }
       __syncthreads();
 #pragma unroll
-      for (int J = 0; J < NBM; ++J) {
+      for (int w = 0; w < NWAVE; ++w) {
+        const int J = slot + 8 * w;
         if (J < I) {
+          F* o = tile(I, J) + r0 * TLD + c0;
 #pragma unroll
-          for (int q = 0; q < EPT; ++q) {
-            const int e = t + q * BT;
-            tile(I, J)[(e >> 5) * TLD + (e & 31)] = acc[J * EPT + q];
-          }
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) o[u * TLD + v] = acc[w][u][v];
         }
       }
       __syncthreads();
