@@ -509,15 +509,15 @@ __device__ __forceinline__ void chol_inv_blocked_body(const double* __restrict__
     }
   }
   // R^{-1} = D^{-1/2} X^T: upper triangular, column-major
-  for (int e = t; e < l * l; e += BT) {
-    const int r = e % l, c = e / l;
-    F v = 0;
-    if (r <= c) {
-      const F sc = dsf[r] == (F)0 ? (F)1 : dsf[r];
-      v = tile(c / TB, r / TB)[(c % TB) * TLD + (r % TB)] * sc;
+  for (int c = warp; c < l; c += BT / 32)
+    for (int r = lane; r < l; r += 32) {
+      F v = 0;
+      if (r <= c) {
+        const F sc = dsf[r] == (F)0 ? (F)1 : dsf[r];
+        v = tile(c / TB, r / TB)[(c % TB) * TLD + (r % TB)] * sc;
+      }
+      Rinv[r + (size_t)c * l] = v;
     }
-    Rinv[e] = v;
-  }
 }
 
 template <typename F>
