@@ -492,15 +492,56 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 // two slots hold the W and V columns of the round-robin positions g and
 // N - 1 - g; after the rotation each column is written to the slot of its
 // next position, in the other of two slot buffers (in another CTA's shared
-// memory when that position belongs to it).  One cluster barrier per round:
-// shared memory bandwidth and the per-round latency scale with the CTAs
-// instead of queueing on one SM, and no round trip goes through L2.  The
+// memory when that position belongs to it, by asynchronous stores that the
+// receiving CTA's mbarrier counts).  A round ends with a CTA barrier and a
+// wait for the neighbours' columns, no cluster-wide barrier: shared memory
+// bandwidth and the per-round latency scale with the CTAs instead of
+// queueing on one SM, and no round trip goes through L2.  Only neighbouring
+// CTAs exchange columns, and a CTA can run at most one round ahead of a
+// neighbour (it needs that neighbour's columns), so with two slot buffers
+// no column is overwritten before it has been read.  The
 // convergence flags of a sweep are OR-ed into CTA 0 and read back by all
 // CTAs before any of them decides, so every CTA runs the same barriers.
 constexpr int kClusterCtas = 16;
 constexpr int kClusterMinL = 48;                 // below: the one-block sweeps
 
 __device__ __forceinline__ int next_pos(int p, int N) { return p == 0 ? 0 : (p == N - 1 ? 1 : p + 1); }
+__device__ __forceinline__ int prev_pos(int q, int N) { return q == 0 ? 0 : (q == 1 ? N - 1 : q - 1); }
+
+__device__ __forceinline__ uint32_t cl_smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+// shared::cluster address of the same variable in CTA `rank`
+__device__ __forceinline__ uint32_t cl_mapa(uint32_t a, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+// 8-byte store into another CTA's shared memory that reports its bytes to
+// that CTA's mbarrier when they land
+__device__ __forceinline__ void cl_st_async(uint32_t addr, float2 v, uint32_t mbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(addr),
+               "f"(v.x), "f"(v.y), "r"(mbar)
+               : "memory");
+}
+__device__ __forceinline__ void cl_mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(cl_smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void cl_mbar_arm(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(cl_smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool cl_mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.b32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(cl_smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+constexpr long long kClusterWaitCycles = 4000000000ll;   // about 2 s
 
 template <int EP>
 __global__ void __launch_bounds__(512)
@@ -513,6 +554,7 @@ jacobi_sweep_cluster_kernel(const double* __restrict__ Min, int l, int gpc, floa
   constexpr int LDW = 32 * EP;                       // floats per column slot
   float* S = reinterpret_cast<float*>(smem_raw);     // [buffer 2][slot 2 gpc][W, V][LDW]
   __shared__ int s_flag[2], s_big[2];                // used in CTA 0, by sweep parity
+  __shared__ __align__(8) uint64_t s_mbar[2];        // incoming remote columns, by buffer
   const int N = (l + 1) & ~1, G = N / 2;
   const int t = threadIdx.x, lane = t & 31;
   const int lg = t >> 4, gl = t & 15;
@@ -534,6 +576,23 @@ jacobi_sweep_cluster_kernel(const double* __restrict__ Min, int l, int gpc, floa
     w[LDW + i] = (i == j && j < l) ? 1.f : 0.f;
   }
   if (rank == 0 && t == 0) { s_flag[0] = s_flag[1] = 0; s_big[0] = s_big[1] = 0; }
+  if (t == 0) {
+    cl_mbar_init(&s_mbar[0], 1);
+    cl_mbar_init(&s_mbar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // bytes this CTA receives from other CTAs per round: its slots whose
+  // previous position belongs to another CTA
+  int rem_cols = 0;
+  for (int sl = 0; sl < 2 * gpc; ++sl) {
+    const int g = rank * gpc + (sl >> 1);
+    if (g >= G) continue;
+    const int p = prev_pos((sl & 1) ? N - 1 - g : g, N);
+    const int gs = p < G ? p : N - 1 - p;
+    if (gs / gpc != rank) ++rem_cols;
+  }
+  uint32_t rem_bytes = (uint32_t)rem_cols * 2u * LDW * (uint32_t)sizeof(float);
+  uint32_t mpar0 = 0u, mpar1 = 0u;                 // phase parity of s_mbar[0], s_mbar[1]
   cluster.sync();
 
   // the next positions of a group's slots do not change from round to
@@ -554,6 +613,8 @@ jacobi_sweep_cluster_kernel(const double* __restrict__ Min, int l, int gpc, floa
     // players at the group's positions: rr_player(p, r, N) = 1 + (p - 1 - r) mod (N - 1), stepped down per round
     int ia = pa == 0 ? 0 : pa, ib = pb;
     for (int r = 0; r < N - 1; ++r) {
+      // the columns written this round land in buffer buf ^ 1
+      if (t == 0 && rem_bytes) cl_mbar_arm(&s_mbar[buf ^ 1], rem_bytes);
       if (act) {
         const bool sw = ia > ib;                     // x: the smaller column index
         float* sx = slot(buf, 2 * lg + (sw ? 1 : 0));
@@ -600,24 +661,49 @@ jacobi_sweep_cluster_kernel(const double* __restrict__ Min, int l, int gpc, floa
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           float* dst = slot(buf ^ 1, dsl[h]);
-          if (dcta[h] != rank) dst = cluster.map_shared_rank(dst, dcta[h]);
-          float2* dw = reinterpret_cast<float2*>(dst);
-          float2* dv = reinterpret_cast<float2*>(dst + LDW);
           const bool is_x = (h == 0) != sw;          // the slot at pa holds x unless swapped
+          if (dcta[h] == rank) {
+            float2* dw = reinterpret_cast<float2*>(dst);
+            float2* dv = reinterpret_cast<float2*>(dst + LDW);
 #pragma unroll
-          for (int e = 0; e < EP; ++e) {
-            dw[gl + 16 * e] = is_x ? x[e] : y[e];
-            dv[gl + 16 * e] = is_x ? u[e] : v[e];
+            for (int e = 0; e < EP; ++e) {
+              dw[gl + 16 * e] = is_x ? x[e] : y[e];
+              dv[gl + 16 * e] = is_x ? u[e] : v[e];
+            }
+          } else {
+            // a neighbouring CTA's slot: asynchronous stores counted by its mbarrier
+            const uint32_t rd = cl_mapa(cl_smem_u32(dst), dcta[h]);
+            const uint32_t rb = cl_mapa(cl_smem_u32(&s_mbar[buf ^ 1]), dcta[h]);
+#pragma unroll
+            for (int e = 0; e < EP; ++e) {
+              cl_st_async(rd + 8u * (gl + 16 * e), is_x ? x[e] : y[e], rb);
+              cl_st_async(rd + 4u * LDW + 8u * (gl + 16 * e), is_x ? u[e] : v[e], rb);
+            }
           }
         }
       }
-      cluster.sync();
+      __syncthreads();                               // this CTA's own column moves
+      if (rem_bytes) {
+        // the neighbours' columns (bounded wait: on a timeout the status
+        // records it and the sweeps run on without waiting, so every CTA
+        // still meets every cluster barrier)
+        const uint32_t ph = (buf ^ 1) ? mpar1 : mpar0;
+        if (!cl_mbar_try_wait(&s_mbar[buf ^ 1], ph)) {
+          const long long t0 = clock64();
+          while (!cl_mbar_try_wait(&s_mbar[buf ^ 1], ph)) {
+            if (clock64() - t0 > kClusterWaitCycles) {
+              if (t == 0) raise_status(status, SORSVD_ERR_TIMEOUT);
+              rem_bytes = 0;
+              break;
+            }
+          }
+        }
+        if (buf ^ 1) mpar1 ^= 1u;
+        else mpar0 ^= 1u;
+      }
       buf ^= 1;
       if (pa != 0) ia = ia == 1 ? N - 1 : ia - 1;
       ib = ib == 1 ? N - 1 : ib - 1;
-      // the next sweep's flags: every CTA read them for the previous sweep
-      // before this round's barrier
-      if (r == 0 && rank == 0 && t == 0) { s_flag[par ^ 1] = 0; s_big[par ^ 1] = 0; }
     }
     rot_local = __syncthreads_or(rot_local);
     big_local = __syncthreads_or(big_local);
@@ -629,6 +715,8 @@ jacobi_sweep_cluster_kernel(const double* __restrict__ Min, int l, int gpc, floa
     const int rot = *cluster.map_shared_rank(&s_flag[par], 0);
     const int bg = *cluster.map_shared_rank(&s_big[par], 0);
     cluster.sync();                                  // every CTA has read CTA 0's flags
+    // this parity's flags are next used two sweeps on, after two more barriers
+    if (rank == 0 && t == 0) { s_flag[par] = 0; s_big[par] = 0; }
     if (!rot) break;
     if (sweep == kMaxSweeps) {
       if (bg && rank == 0 && t == 0) raise_status(status, SORSVD_ERR_NOT_CONVERGED);
