@@ -147,7 +147,9 @@ cudaError_t launch_gaussian(void* out, int64_t rows, int64_t cols, int64_t ld, u
   int64_t groups = (rows * cols + 3) / 4;
   int threads = 256;
   int64_t blocks = (groups + threads - 1) / threads;
-  int cap = num_sms() * 8;
+  // binary64-ALU bound: two blocks per SM keep the FP64 pipes busy and
+  // leave the SMs' other thread slots to a memory-bound kernel beside it
+  int cap = num_sms() * 2;
   if (blocks > cap) blocks = cap;
   switch (dtype) {
     case SORSVD_F64: gaussian_kernel<double><<<(int)blocks, threads, 0, st>>>((double*)out, rows, cols, ld, seed, stream_id); break;

@@ -63,6 +63,7 @@ struct TcParams {
   int64_t ld16;
   int out16_kind;        // 0 none, 1 bf16, 2 fp16
   float* parts;          // G x 2 x (128 MT) x Npad fp32
+  int* tilecnt;          // per tile: shares written so far (zero between launches), or null
   DeviceStatus* status;
 };
 
@@ -125,6 +126,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   uint64_t* conv = done + 1;          // split mode: low parts written (per A stage)
   uint32_t* tslot = reinterpret_cast<uint32_t*>(conv + P.stages);
   volatile int* abortp = reinterpret_cast<volatile int*>(tslot + 1);
+  volatile int* lastp = abortp + 1;   // split tiles this CTA finishes: bit 0 head, bit 1 tail
 
   constexpr bool SPLIT = (ELT == 3);
   constexpr int AK = (ELT >= 2) ? 32 : 64;              // K elements per atom
@@ -428,11 +430,86 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       g = gend;
     }
   }
+  // every share of a split tile is in memory before its counter moves
+  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0 && *abortp) raise_status(P.status, SORSVD_ERR_TIMEOUT);
   if (warp == 1) {
     tc::fence_after_sync();
     tc::tmem_dealloc(tbase, P.tmem_cols);
+  }
+  // Split tiles: the CTA that writes the last share of a tile sums the
+  // shares in CTA order (as the separate fix-up kernel does) and writes the
+  // tile; no CTA waits for another.
+  if (P.tilecnt && !*abortp) {
+    const int64_t th = it0 / P.ipt, tt = (it1 - 1) / P.ipt;
+    const bool head_split = (it0 % P.ipt != 0) || (it1 < (th + 1) * P.ipt);
+    const bool tail_split = tt != th && (it1 % P.ipt != 0);
+    if (threadIdx.x == 0) {
+      int bits = 0;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const bool split = h ? tail_split : head_split;
+        if (!split) continue;
+        const int64_t t = h ? tt : th;
+        const int64_t c0 = cta_of(t * P.ipt, P.total, P.G), c1 = cta_of(t * P.ipt + P.ipt - 1, P.total, P.G);
+        if (atomicAdd(&P.tilecnt[t], 1) == (int)(c1 - c0)) bits |= 1 << h;
+      }
+      *lastp = bits;
+    }
+    __syncthreads();
+    const int bits = *lastp;
+    if (bits) {
+      __threadfence();
+      const int mrows = 128 * MT;
+      const int per = mrows * P.N;
+      const size_t seg = (size_t)mrows * P.Npad;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (!((bits >> h) & 1)) continue;
+        const int64_t t = h ? tt : th;
+        const int64_t c0 = cta_of(t * P.ipt, P.total, P.G), c1 = cta_of(t * P.ipt + P.ipt - 1, P.total, P.G);
+        const int slot0 = (c0 * P.total / P.G < t * P.ipt) ? 1 : 0;
+        // 4 consecutive rows per float4, 4 float4 per thread in flight
+        const int q4 = mrows / 4, nv = per / 4;
+        const float4* first = reinterpret_cast<const float4*>(P.parts + ((size_t)c0 * 2 + slot0) * seg);
+        for (int f0 = threadIdx.x; f0 < nv; f0 += 4 * blockDim.x) {
+          float4 acc[4];
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int f = f0 + b * blockDim.x;
+            if (f < nv) {
+              const int col = f / q4, r4 = f - col * q4;
+              acc[b] = first[(size_t)r4 + (size_t)col * q4];
+            }
+          }
+          for (int64_t cc = c0 + 1; cc <= c1; ++cc) {
+            const float4* pc = reinterpret_cast<const float4*>(P.parts + (size_t)cc * 2 * seg);
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+              const int f = f0 + b * blockDim.x;
+              if (f < nv) {
+                const int col = f / q4, r4 = f - col * q4;
+                const float4 x = pc[(size_t)r4 + (size_t)col * q4];
+                acc[b].x += x.x; acc[b].y += x.y; acc[b].z += x.z; acc[b].w += x.w;
+              }
+            }
+          }
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int f = f0 + b * blockDim.x;
+            if (f >= nv) continue;
+            const int col = f / q4, r4 = f - col * q4;
+            const int64_t grow = t * mrows + 4 * r4;
+            const float v[4] = {acc[b].x, acc[b].y, acc[b].z, acc[b].w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (grow + u < P.M) store_out(P, grow + u, col, v[u]);
+          }
+        }
+        if (threadIdx.x == 0) P.tilecnt[t] = 0;     // ready for the next launch
+      }
+    }
   }
 }
 
@@ -637,8 +714,8 @@ size_t tc_parts_bytes(int elt, int64_t M, int64_t N, int64_t K) {
 
 cudaError_t launch_tc_gemm(bool trans_a, int elt, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
                            const void* B, int64_t ldb, const void* Blo, float* out, int64_t ldo, void* out16,
-                           int64_t ld16, int out16_kind, float* parts, DeviceStatus* status, int kcls,
-                           cudaStream_t st) {
+                           int64_t ld16, int out16_kind, float* parts, int* tilecnt, int64_t ntilecnt,
+                           DeviceStatus* status, int kcls, cudaStream_t st) {
   if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
   if (elt == 3 && (!Blo || (reinterpret_cast<uintptr_t>(Blo) & 15))) return cudaErrorInvalidValue;
   // an MN-major TF32 operand gave all-zero products on GB300: fp32 products
@@ -648,6 +725,7 @@ cudaError_t launch_tc_gemm(bool trans_a, int elt, int64_t M, int64_t N, int64_t 
   if (P.stages < 2) return cudaErrorInvalidValue;
   P.out = out; P.ldo = ldo; P.out16 = out16; P.ld16 = ld16; P.out16_kind = out16 ? out16_kind : 0;
   P.parts = parts; P.status = status;
+  P.tilecnt = (tilecnt && P.tiles <= ntilecnt) ? tilecnt : nullptr;
   const int AK = elt >= 2 ? 32 : 64, AMN = elt >= 2 ? 32 : 64;
   const int map_elt = elt == 3 ? 2 : elt;
   CUtensorMap ma, mb;
@@ -670,9 +748,9 @@ cudaError_t launch_tc_gemm(bool trans_a, int elt, int64_t M, int64_t N, int64_t 
     else e = launch_typed<3, false>(ma, mb, mblo, P, smem, st);
   }
   if (e != cudaSuccess) return e;
-  // fix-up of the tiles split across CTAs: one block row per CTA boundary,
-  // about 4 elements of the tile per thread
-  if (P.G < 2) return cudaSuccess;
+  // fix-up of the tiles split across CTAs (when no counters were given):
+  // one block row per CTA boundary, about 4 elements of the tile per thread
+  if (P.G < 2 || P.tilecnt) return cudaSuccess;
   const int64_t per = (int64_t)128 * P.MT * P.N;
   const int64_t gy = std::max<int64_t>(1, std::min<int64_t>((per + 1023) / 1024, 65535));
   ProfScope ps2(K_REDUCE, st);

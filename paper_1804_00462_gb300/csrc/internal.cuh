@@ -205,8 +205,8 @@ bool tc_supported(int elt, const void* A, int64_t lda, const void* B, int64_t ld
 size_t tc_parts_bytes(int elt, int64_t M, int64_t N, int64_t K);
 cudaError_t launch_tc_gemm(bool trans_a, int elt, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
                            const void* B, int64_t ldb, const void* Blo, float* out, int64_t ldo, void* out16,
-                           int64_t ld16, int out16_kind, float* parts, DeviceStatus* status, int kcls,
-                           cudaStream_t st);
+                           int64_t ld16, int out16_kind, float* parts, int* tilecnt, int64_t ntilecnt,
+                           DeviceStatus* status, int kcls, cudaStream_t st);
 // hi = RN_tf32(X), lo = X - hi (exact in fp32) of a rows x cols fp32 matrix
 // (column-major, ldx); hi and lo share the leading dimension ldh.
 cudaError_t launch_split_tf32(const float* X, int64_t ldx, int64_t rows, int64_t cols, float* hi, float* lo,

@@ -68,7 +68,8 @@ inline int elt_of(int dt) {
 
 struct Layout {
   int64_t ldm, ldn;      // leading dimensions of the m x l / n x l sketches
-  size_t status, at, t2op, t2, t1, t1op, q2op, tmp, bhi, blo, parts, G, Rinv, M, Ut, Vt, jwork, total;
+  size_t status, tilecnt, at, t2op, t2, t1, t1op, q2op, tmp, bhi, blo, parts, G, Rinv, M, Ut, Vt, jwork, total;
+  int64_t ntilecnt;      // counters of the split tiles of a tensor-core pass
   int64_t ldb;           // leading dimension of bhi / blo
   bool has_at;           // fp32 containers: A^T kept for the products A X
 };
@@ -83,6 +84,8 @@ Layout make_layout(int64_t m, int64_t n, int l, int dt) {
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
   L.status = take(sizeof(DeviceStatus));
+  L.ntilecnt = (std::max(m, n) + 127) / 128 + 1;
+  L.tilecnt = take((size_t)L.ntilecnt * sizeof(int));
   // TF32 tensor cores read A only K-major (an MN-major TF32 operand gave
   // all-zero products on GB300), so the fp32-container dtypes keep a
   // transposed copy A^T (n x m, ld ldn) for T1 = A T2 and W = A Q2.
@@ -151,6 +154,14 @@ struct Ctx {
   void* at(size_t o) const { return ws + o; }
 };
 
+// clear the status word and the split-tile counters of the passes (the
+// counters return to zero after every complete pass)
+cudaError_t begin_call(const Ctx& c) {
+  cudaError_t e = cudaMemsetAsync(c.status(), 0, sizeof(DeviceStatus), c.st);
+  if (e != cudaSuccess) return e;
+  return cudaMemsetAsync(c.at(c.L.tilecnt), 0, (size_t)c.L.ntilecnt * sizeof(int), c.st);
+}
+
 #define CK(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) return SORSVD_ERR_CUDA; } while (0)
 
 // C (M x N, ldc) = op(A) B on CUDA cores, with split-K through the partial
@@ -203,7 +214,8 @@ int pass(const Ctx& c, int kcls, bool trans, int64_t M, int64_t N, int64_t K, co
         ldbop = c.L.ldb;
       }
       CK(launch_tc_gemm(trans || use_at, elt, M, N, K, Aop, ldop, Bop, ldbop, c.at(c.L.blo), (float*)C, ldc, C16,
-                        ld16, dt == SORSVD_BF16 ? 1 : 2, (float*)c.at(c.L.parts), c.status(), kcls, c.st));
+                        ld16, dt == SORSVD_BF16 ? 1 : 2, (float*)c.at(c.L.parts), (int*)c.at(c.L.tilecnt),
+                        c.L.ntilecnt, c.status(), kcls, c.st));
       return SORSVD_OK;
     }
   }
@@ -211,6 +223,57 @@ int pass(const Ctx& c, int kcls, bool trans, int64_t M, int64_t N, int64_t K, co
   if (r) return r;
   if (C16) LAUNCH(K_MISC, launch_convert_f32((const float*)C, ldc, M, N, C16, ld16, dt, nullptr, c.st));
   return SORSVD_OK;
+}
+
+// A non-blocking stream of this device for work that runs beside the
+// caller's stream (created once; nullptr when that fails)
+cudaStream_t side_stream() {
+  static cudaStream_t streams[64] = {nullptr};
+  static bool tried[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return nullptr;
+  if (!tried[dev]) {
+    tried[dev] = true;
+    // highest priority: its blocks are placed before the caller's queued ones
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (cudaStreamCreateWithPriority(&streams[dev], cudaStreamNonBlocking, hi) != cudaSuccess) streams[dev] = nullptr;
+  }
+  return streams[dev];
+}
+
+// Omega on the side stream while `work` runs on the caller's stream; the
+// caller's stream then waits for Omega (fork and join by events, which
+// stream capture also follows)
+template <typename Work>
+int gaussian_beside(const Ctx& c, void* out, int64_t rows, int cols, int64_t ld, uint64_t seed, int dtype, Work work) {
+  cudaStream_t side = side_stream();
+  cudaEvent_t fork = nullptr, join = nullptr;
+  if (!side || cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess) {
+    if (fork) cudaEventDestroy(fork);
+    int r = work();
+    if (r) return r;
+    LAUNCH(K_GAUSSIAN, launch_gaussian(out, rows, cols, ld, seed, 0, dtype, c.st));
+    return SORSVD_OK;
+  }
+  int r = SORSVD_OK;
+  if (cudaEventRecord(fork, c.st) != cudaSuccess || cudaStreamWaitEvent(side, fork, 0) != cudaSuccess) {
+    r = SORSVD_ERR_CUDA;
+  } else {
+    {
+      ProfScope ps(K_GAUSSIAN, side);
+      if (launch_gaussian(out, rows, cols, ld, seed, 0, dtype, side) != cudaSuccess) r = SORSVD_ERR_CUDA;
+    }
+    if (cudaEventRecord(join, side) != cudaSuccess) r = SORSVD_ERR_CUDA;
+    const int rw = work();
+    if (!r) r = rw;
+    if (cudaStreamWaitEvent(c.st, join, 0) != cudaSuccess && !r) r = SORSVD_ERR_CUDA;
+  }
+  cudaEventDestroy(fork);
+  cudaEventDestroy(join);
+  return r;
 }
 
 // A^T into the workspace (fp32 containers), once per call that passes over A
@@ -228,10 +291,26 @@ int prepare_at(const Ctx& c, const void* A, int64_t m, int64_t n, int64_t lda) {
 // Gram was not already within kOrthTol of the identity (decided on the
 // device; a skipped pass leaves the result in T).  out16, when non-null,
 // receives the 16-bit rounding of the result (the operand of the next
-// BF16 / F16 pass).  binary64 sketches use the CUDA-core GEMMs.
+// BF16 / F16 pass).  With `result` non-null and a single pass the
+// product stays in the tmp buffer (ld unchanged) and *result points to it:
+// no copy back.  binary64 sketches use the CUDA-core GEMMs.
 int orth(const Ctx& c, void* T, int64_t rows, int64_t ld, int l, int passes, double shift0, void* out16 = nullptr,
-         int64_t ld16 = 0) {
+         int64_t ld16 = 0, void** result = nullptr) {
   const int kind16 = out16 ? (c.dt == SORSVD_BF16 ? 1 : 2) : 0;
+  if (result) *result = T;
+  if (!c.f64 && result && passes == 1) {
+    float* parts = (float*)c.at(c.L.parts);
+    float* Y = (float*)c.at(c.L.tmp);
+    LAUNCH(K_SMALL_GEMM, launch_rb_gram((const float*)T, ld, (const float*)T, ld, rows, l, l, true, parts, nullptr,
+                                        c.st));
+    LAUNCH(K_REDUCE, launch_reduce_parts(parts, (int)rb_gram_blocks(rows, l, l, true), (int64_t)l * l, l, l, l,
+                                         (double*)c.at(c.L.G), l, c.st));
+    LAUNCH(K_CHOL, launch_chol_inv((const double*)c.at(c.L.G), l, shift0, c.at(c.L.Rinv), false, c.status(), c.st));
+    LAUNCH(K_SMALL_GEMM, launch_rb_apply((const float*)T, ld, rows, l, (const float*)c.at(c.L.Rinv), l, l, true, Y, ld,
+                                         out16, ld16, kind16, nullptr, c.st));
+    *result = Y;
+    return SORSVD_OK;
+  }
   if (!c.f64) {
     float* parts = (float*)c.at(c.L.parts);
     const int nb = (int)rb_gram_blocks(rows, l, l, true);
@@ -435,6 +514,7 @@ int sorsvd_power_pass(const void* A, int64_t m, int64_t n, int64_t lda, int dtyp
   Layout L = make_layout(m, n, l, dtype);
   if (int r = check_ws(workspace, ws_bytes, L)) return r;
   Ctx c{(char*)workspace, L, dtype, dtype == SORSVD_F64, (cudaStream_t)stream};
+  CK(begin_call(c));
   if (int r = prepare_at(c, A, m, n, lda)) return r;
   const void* xop = X;
   int64_t ldop = ldx;
@@ -457,6 +537,7 @@ int sorsvd_core(const void* A, int64_t m, int64_t n, int64_t lda, int dtype, uns
   Layout L = make_layout(m, n, l, dtype);
   if (int r = check_ws(workspace, ws_bytes, L)) return r;
   Ctx c{(char*)workspace, L, dtype, dtype == SORSVD_F64, (cudaStream_t)stream};
+  CK(begin_call(c));
   if (int r = prepare_at(c, A, m, n, lda)) return r;
   return core_impl(c, A, m, n, lda, flags, Q1, ldq1, Q2, ldq2, l, M, ldm);
 }
@@ -479,10 +560,17 @@ int sorsvd_run(const void* A, int64_t m, int64_t n, int64_t lda, int k, int p, i
   const bool h16 = dtype_is_16(dtype);
   int r;
 
-  CK(cudaMemsetAsync(c.status(), 0, sizeof(DeviceStatus), c.st));
-  r = prepare_at(c, A, m, n, lda);
-  if (r) return r;
-  LAUNCH(K_GAUSSIAN, launch_gaussian(c.at(L.t2op), n, l, L.ldn, seed, 0, dtype, c.st));
+  CK(begin_call(c));
+  if (L.has_at && tc_enabled()) {
+    // the transposed copy of A (memory-bound) and Omega (binary64 ALU-bound)
+    // are independent: Omega is drawn on a side stream meanwhile
+    r = gaussian_beside(c, c.at(L.t2op), n, l, L.ldn, seed, dtype, [&] { return prepare_at(c, A, m, n, lda); });
+    if (r) return r;
+  } else {
+    r = prepare_at(c, A, m, n, lda);
+    if (r) return r;
+    LAUNCH(K_GAUSSIAN, launch_gaussian(c.at(L.t2op), n, l, L.ldn, seed, 0, dtype, c.st));
+  }
   if (flags & SORSVD_FLAG_LITERAL_POWER) {
     // Algorithm 3 as printed: the sketches are orthonormalised only at the end
     for (int i = 1; i <= q + 1; ++i) {
@@ -507,21 +595,29 @@ int sorsvd_run(const void* A, int64_t m, int64_t n, int64_t lda, int k, int p, i
     // (CholeskyQR3) in the last iteration, which fixes Q1 and Q2.
     const int kc = dtype == SORSVD_F32 ? K_PASS_SPLIT : K_PASS;
     void* t1op = h16 ? c.at(L.t1op) : c.at(L.t1);
+    const void* x2 = c.at(L.t2op);           // operand of the next product A X (Omega first)
     for (int i = 1; i <= q + 1; ++i) {
       const bool last = (i == q + 1);
       const int np = last ? 3 : 1;
       // F32: TF32 products while the loop only steers the subspace, the
-      // fp32-accurate split products in the last iteration
-      r = pass(c, last ? kc : K_PASS, false, m, l, n, A, lda, c.at(L.t2op), L.ldn, h16 ? dtype : adt, c.at(L.t1),
-               L.ldm, nullptr, 0, last);
-      if (r) return r;
-      r = orth(c, c.at(L.t1), m, L.ldm, l, np, first_shift(dtype), h16 ? t1op : nullptr, L.ldm);
-      if (r) return r;
-      r = pass(c, last ? kc : K_PASS, true, n, l, m, A, lda, t1op, L.ldm, h16 ? dtype : adt, c.at(L.t2), L.ldn,
+      // fp32-accurate split products in the last iteration.  Inside the
+      // loop the orthonormalised sketch may stay in the tmp buffer: it is
+      // only the operand of the next product.
+      r = pass(c, last ? kc : K_PASS, false, m, l, n, A, lda, x2, L.ldn, h16 ? dtype : adt, c.at(L.t1), L.ldm,
                nullptr, 0, last);
       if (r) return r;
-      r = orth(c, c.at(L.t2), n, L.ldn, l, np, first_shift(dtype), (!last && h16) ? c.at(L.t2op) : nullptr, L.ldn);
+      void* q1 = nullptr;
+      r = orth(c, c.at(L.t1), m, L.ldm, l, np, first_shift(dtype), h16 ? t1op : nullptr, L.ldm, last ? nullptr : &q1);
       if (r) return r;
+      const void* y1 = h16 ? t1op : (q1 ? q1 : c.at(L.t1));
+      r = pass(c, last ? kc : K_PASS, true, n, l, m, A, lda, y1, L.ldm, h16 ? dtype : adt, c.at(L.t2), L.ldn,
+               nullptr, 0, last);
+      if (r) return r;
+      void* q2 = nullptr;
+      r = orth(c, c.at(L.t2), n, L.ldn, l, np, first_shift(dtype), (!last && h16) ? c.at(L.t2op) : nullptr, L.ldn,
+               last ? nullptr : &q2);
+      if (r) return r;
+      x2 = h16 ? c.at(L.t2op) : (q2 ? q2 : c.at(L.t2));
     }
   }
   r = core_impl(c, A, m, n, lda, flags, c.at(L.t1), L.ldm, c.at(L.t2), L.ldn, l, (double*)c.at(L.M), l);
