@@ -665,7 +665,10 @@ TcParams shape(int elt, int64_t M, int64_t N, int64_t K, int KA, int MT) {
   const uint32_t mult = (elt == 3 ? 2u : 1u);                             // + low parts in split mode
   P.stage_bytes = mult * P.a_bytes;
   P.bstage_bytes = mult * P.b_bytes;
-  P.bstages = 2;
+  // B ring depth (SORSVD_TC_BSTAGES overrides, 2..4)
+  const int envB = env_int("SORSVD_TC_BSTAGES", 0);
+  // a B stage larger than the A stage (16-bit operands, N > 128): one more
+  P.bstages = (envB >= 2 && envB <= 4) ? envB : ((elt < 2 && P.b_bytes > P.a_bytes) ? 3 : 2);
   const uint32_t left = kSmemBudget > P.bstages * P.bstage_bytes ? kSmemBudget - P.bstages * P.bstage_bytes : 0;
   P.stages = (int)std::min<uint32_t>(12u, left / P.stage_bytes);
   if (MT * P.Npad > 512 || cols > 512) P.stages = 0;

@@ -12,9 +12,9 @@
 //       only, written to both halves.  CTA x of the grid sums its chunks
 //       (x, x + G, ...) into partial x, in order; the partials are summed
 //       by launch_reduce_parts in a fixed order.
-//   rb_apply_kernel<TRI>: Y = X B, B small (K x N).  A CTA computes 128
-//       rows x 32 columns (4 warps, lane 4 x 8 again); its column tile of B
-//       is staged once, X streams through a 3-stage cp.async ring of 32-deep
+//   rb_apply_kernel<TRI>: Y = X B, B small (K x N).  A CTA computes 256
+//       rows x 32 columns (8 warps, lane 4 x 8 again); its column tile of B
+//       is staged once, X streams through a 2-stage cp.async ring of 32-deep
 //       K slices stored K-major (a column of X is contiguous rows, so the
 //       copies are plain 16-byte chunks).  TRI: B upper triangular, the K
 //       loop stops at the tile's last column.  Out of place; an optional
@@ -30,9 +30,10 @@ namespace {
 constexpr int kT = 32;               // output tile edge
 constexpr int kGramRows = 32;        // rows per staged chunk (Gram)
 constexpr int kGramMaxWarps = 16;
-constexpr int kApRows = 128;         // rows per CTA (apply)
+constexpr int kApRows = 256;         // rows per CTA (apply), 32 per warp
+constexpr int kApThreads = kApRows;  // 8 warps
 constexpr int kApKT = 32;            // K slice depth (apply)
-constexpr int kApStages = 3;
+constexpr int kApStages = 2;
 constexpr int kBs = kT + 4;          // row stride of B's staged tile (4-way conflicts on the one-time fill)
 
 __host__ __device__ inline int ntile(int l) { return (l + kT - 1) / kT; }
@@ -185,12 +186,12 @@ rb_gram_kernel(const float* __restrict__ X, int64_t ldx, const float* __restrict
 
 // ---------------------------------------------------------------- apply
 
-// K slice (rows r0 .. r0 + 127 of columns k0 .. k0 + 31 of X) into
-// Xt[kk * kApRows + r]: thread t copies the 16-byte row quad t % 32 of
-// columns k0 + t / 32 + 4 i, i < 8 (zero-filled past rows / K)
+// K slice (rows r0 .. r0 + 255 of columns k0 .. k0 + 31 of X) into
+// Xt[kk * kApRows + r]: thread t copies the 16-byte row quad t % 64 of
+// columns k0 + t / 64 + 4 i, i < 8 (zero-filled past rows / K)
 __device__ __forceinline__ void slice_issue(const float* __restrict__ X, int64_t ldx, int K, int rbytes, int k0,
                                             const float* xq, float* Xt) {
-  const int q4 = threadIdx.x & 31, kk0 = threadIdx.x >> 5;
+  const int q4 = threadIdx.x & 63, kk0 = threadIdx.x >> 6;
 #pragma unroll
   for (int i = 0; i < kApKT / 4; ++i) {
     const int kk = kk0 + 4 * i;
@@ -200,7 +201,7 @@ __device__ __forceinline__ void slice_issue(const float* __restrict__ X, int64_t
 }
 
 template <bool TRI>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kApThreads)
 rb_apply_kernel(const float* __restrict__ X, int64_t ldx, int64_t rows, int K, const float* __restrict__ B,
                 int64_t ldb, int N, float* __restrict__ Yo, int64_t ldy, void* __restrict__ Y16, int64_t ld16,
                 int kind16, const int* __restrict__ skip) {
@@ -214,7 +215,7 @@ rb_apply_kernel(const float* __restrict__ X, int64_t ldx, int64_t rows, int K, c
   float* Bs = sm;                                          // [nslice * 32][kBs]
   float* Xt = sm + (size_t)nslice * kApKT * kBs;           // kApStages x [32][128]
   // this thread's row quad of X (the same in every slice)
-  const int64_t rq = r0 + 4 * (threadIdx.x & 31);
+  const int64_t rq = r0 + 4 * (threadIdx.x & 63);
   const int rbytes = rq < rows ? (int)(4 * std::min<int64_t>(4, rows - rq)) : 0;
   const float* xq = X + rq;
   // prologue: the first kApStages - 1 slices in flight
@@ -226,7 +227,7 @@ rb_apply_kernel(const float* __restrict__ X, int64_t ldx, int64_t rows, int K, c
   // B's column tile, zero below the diagonal (TRI) and past K / N; a warp
   // reads one column of B (contiguous k) at a time
   const int nk = nslice * kApKT;
-  for (int jj = warp; jj < kT; jj += 4) {
+  for (int jj = warp; jj < kT; jj += kApThreads / 32) {
     const int j = kT * jt + jj;
     const float* bc = B + (int64_t)j * ldb;
     for (int k = lane; k < nk; k += 32) {
@@ -401,11 +402,11 @@ cudaError_t launch_rb_apply(const float* X, int64_t ldx, int64_t rows, int K, co
   if (tri) {
     e = cudaFuncSetAttribute(rb_apply_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    rb_apply_kernel<true><<<grid, 128, smem, st>>>(X, ldx, rows, K, B, ldb, N, Y, ldy, Y16, ld16, kind16, skip);
+    rb_apply_kernel<true><<<grid, kApThreads, smem, st>>>(X, ldx, rows, K, B, ldb, N, Y, ldy, Y16, ld16, kind16, skip);
   } else {
     e = cudaFuncSetAttribute(rb_apply_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    rb_apply_kernel<false><<<grid, 128, smem, st>>>(X, ldx, rows, K, B, ldb, N, Y, ldy, Y16, ld16, kind16, skip);
+    rb_apply_kernel<false><<<grid, kApThreads, smem, st>>>(X, ldx, rows, K, B, ldb, N, Y, ldy, Y16, ld16, kind16, skip);
   }
   return cudaGetLastError();
 }
