@@ -20,13 +20,22 @@
 // per-CTA partial buffer and a fix-up kernel sums them per tile in CTA
 // order: the result is deterministic and uses no atomics.
 //
-// Split mode (ELT 3, fp32 containers, K-major only, MT = 1): a fourth
-// warpgroup splits each staged fp32 tile x of A into hi = RN_tf32(x),
-// rewritten in place, and lo = x - hi (exact in fp32) next to it; B comes
-// split the same way from two tensors prepared by the caller; every K step
-// issues hi*hi + hi*lo + lo*hi TF32 MMAs.  The neglected lo*lo term and the
-// TF32 truncation of lo are below 2^-21 relative and of random sign, so the
-// products carry fp32-level error.
+// Split mode (ELT 3, fp32 containers, K-major only, MT = 1, KA = 1): the
+// MMAs read the staged fp32 tile x of A as hi = trunc_tf32(x) (kind::tf32
+// ignores the low 13 mantissa bits of a container), and a fourth warpgroup
+// reads x (one row per thread) and puts lo = x - hi (exact in fp32) into a
+// TMEM slot (or, for N > 112, next to the tile in shared memory).  B comes split
+// the same way from two tensors prepared by the caller and sits in the stage
+// as one 2 N-row operand [B_hi | B_lo].  Every K step issues two MMAs:
+// hi x [B_hi | B_lo] (N = 2 Npad) into [D1 | D2] of the current fill buffer
+// and lo x B_hi into D2 of the other buffer.  Back-to-back MMAs on one
+// accumulator serialise (~115 cycles each for N <= 224, measured), so one
+// wide MMA plus one on an independent accumulator keeps the tensor pipe
+// busy where three N = Npad MMAs on one accumulator left it half idle.  The
+// neglected lo*lo term and the TF32 truncation of lo are below 2^-20
+// relative and of random sign, so the products carry fp32-level error.
+// The hi*hi columns D1 drain every kDrainAtoms atoms; the correction
+// columns D2 (2^-11 of the result) drain once per tile segment.
 //
 // Warp roles (224 threads): warp 0 issues the TMA loads of A into a deep
 // ring (HBM latency), warp 6 those of B into a short ring (B is re-read
@@ -56,6 +65,9 @@ struct TcParams {
   int pair;              // 1: clusters of two CTAs share B (multicast)
   int nbuf;
   uint32_t tmem_cols;
+  int lo_tmem;           // split mode: A's low parts in TMEM slots (else next to A in shared memory)
+  int aslots;            // split mode: converted stages in flight (TMEM slots / handshakes)
+  uint32_t aslot_col;    // split mode: first TMEM column of the low-part slots
   int stages, bstages;   // ring depths: A (from HBM), B (from L2)
   uint32_t stage_bytes, a_bytes, b_atom, b_bytes, bstage_bytes;
   float* out;
@@ -73,12 +85,19 @@ namespace {
 constexpr int kThreads = 224;
 constexpr int kThreadsSplit = 352;
 // Split mode drains each accumulator fill of kDrainAtoms K atoms into a
-// running sum kept in TMEM (round-to-nearest fp32 adds in registers):
-// tensor-core accumulation truncates, which over thousands of MMA steps
-// biases long fp32 sums by ~1e-5; short fills bound that bias.  Two fills
-// and the running sum need 3 Npad <= 512 TMEM columns (l <= kAccCols).
+// running sum held in the epilogue threads' registers (round-to-nearest fp32
+// adds): tensor-core accumulation truncates, which over thousands of MMA
+// steps biases long fp32 sums by ~1e-5; short fills bound that bias (the
+// correction block D2, 2^-11 of the result, drains once per segment).  The
+// two fill buffers [D1 | D2] take 4 Npad <= 512 TMEM columns (l <= kAccCols).
 constexpr int kDrainAtoms = 4;
 constexpr int kAccCols = 128;
+// split mode: the two fill buffers [D1 | D2] take 4 Npad TMEM columns; the
+// low parts of A take 32 columns per stage above them when they fit (up to
+// kASlots stages in flight)
+constexpr uint32_t kASlotCols = 32u;
+constexpr uint32_t kASlots = 4u;
+constexpr int kLoTmemMaxNpad = 112;
 constexpr uint32_t kAtomBytes = 128u * 128u;   // 128 rows x 128 bytes
 constexpr int kMaxKA = 2;                      // K atoms per stage, at most
 
@@ -88,6 +107,10 @@ __device__ __forceinline__ float rn_tf32(float x) {
   uint32_t u = __float_as_uint(x);
   u = (u + 0xFFFu + ((u >> 13) & 1u)) & 0xFFFFE000u;
   return __uint_as_float(u);
+}
+// x - trunc_tf32(x): the part of x a TF32 MMA ignores (exact in fp32)
+__device__ __forceinline__ float tf32_rest(float x) {
+  return x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
 }
 
 __device__ __forceinline__ void fence_proxy_async() {
@@ -124,8 +147,9 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   uint64_t* tfull = bempty + P.bstages;
   uint64_t* tempty = tfull + 2;
   uint64_t* done = tempty + 2;
-  uint64_t* conv = done + 1;          // split mode: low parts written (per A stage)
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(conv + P.stages);
+  uint64_t* afull = done + 1;         // split mode: stage converted (4 converter warps)
+  uint64_t* aempty = afull + kASlots; // split mode: its low-part slot consumed by the MMAs
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(aempty + kASlots);
   volatile int* abortp = reinterpret_cast<volatile int*>(tslot + 1);
   volatile int* lastp = abortp + 1;   // split tiles this CTA finishes: bit 0 head, bit 1 tail
 
@@ -137,7 +161,6 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   constexpr uint32_t FMT = (ELT == 0) ? 1u : (ELT == 1 ? 0u : 2u);
   // accumulator fill length in stages (split mode drains every kDrainAtoms atoms)
   const int64_t CHUNK = SPLIT ? (int64_t)((kDrainAtoms + KA - 1) / KA) : ((int64_t)1 << 40);
-  // split mode: the low parts sit right after the hi tiles of each stage
   const int mrows = 128 * MT;
   const int64_t urows = PAIR ? 2 * mrows : mrows;        // rows of a unit tile
 
@@ -149,7 +172,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     for (int b = 0; b < 2; ++b) { tc::mbar_init(&tfull[b], 1); tc::mbar_init(&tempty[b], 128); }
     tc::mbar_init(done, 1);
     if (SPLIT)
-      for (int s2 = 0; s2 < P.stages; ++s2) tc::mbar_init(&conv[s2], 4);
+      for (uint32_t b = 0; b < kASlots; ++b) { tc::mbar_init(&afull[b], 4); tc::mbar_init(&aempty[b], 1); }
     *abortp = 0;
     tc::fence_barrier_init();
   }
@@ -164,6 +187,21 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   if (PAIR) tc::cluster_sync_all();
   tc::fence_after_sync();
   const uint32_t tbase = *tslot;
+  if constexpr (SPLIT) {
+    // the MMAs always accumulate: the fill buffers start at zero, and the
+    // epilogue zeroes what it drains
+    if (warp >= 2 && warp <= 5) {
+      const uint32_t tz = tbase + ((uint32_t)((warp & 3) * 32) << 16);
+      float z[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) z[i] = 0.f;
+      for (int c = 0; c < 4 * P.Npad; c += 16) tc::tmem_st16(tz + (uint32_t)c, z);
+      tc::tmem_st_wait();
+      tc::fence_before_sync();
+    }
+    __syncthreads();
+    tc::fence_after_sync();
+  }
 
   // the stream-K unit: one CTA, or (PAIR) the two CTAs of a cluster, which
   // take the two 128 MT-row halves of every unit tile and share B
@@ -237,10 +275,15 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             for (int ch = 0; ch < NCH; ++ch) {
               const size_t off = (size_t)j * P.b_atom + (size_t)ch * P.ch0 * 128;
               if (PAIR) {
-                // each CTA loads one N-chunk (both with one chunk: CTA 0)
-                // into both CTAs' stage; every CTA armed its own stage
-                if ((NCH == 2 ? ch : 0) == rank)
+                // each CTA loads one N-chunk (both with one chunk: CTA 0;
+                // split mode: CTA 0 the hi, CTA 1 the lo tensor) into both
+                // CTAs' stage; every CTA armed its own stage
+                if (SPLIT) {
+                  if (rank == 0) tc::tma_load_2d_mc(sb + off, &tmB, &bfull[stage], k, ch * P.ch0, (uint16_t)3, polB);
+                  else tc::tma_load_2d_mc(sb + P.b_bytes + off, &tmBlo, &bfull[stage], k, ch * P.ch0, (uint16_t)3, polB);
+                } else if ((NCH == 2 ? ch : 0) == rank) {
                   tc::tma_load_2d_mc(sb + off, &tmB, &bfull[stage], k, ch * P.ch0, (uint16_t)3, polB);
+                }
               } else {
                 tc::tma_load_2d_hint(sb + off, &tmB, &bfull[stage], k, ch * P.ch0, polB);
                 if (SPLIT) tc::tma_load_2d_hint(sb + P.b_bytes + off, &tmBlo, &bfull[stage], k, ch * P.ch0, polB);
@@ -264,7 +307,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     if (lane == 0) {
       const uint32_t idesc0 = tc::idesc_make(FMT, A_MN, false, 128, P.ch0);
       const uint32_t idesc1 = tc::idesc_make(FMT, A_MN, false, 128, P.Npad - P.ch0);
+      // split mode: hi x [B_hi | B_lo], N = 2 Npad
+      const uint32_t idescW = tc::idesc_make(FMT, false, false, 128, SPLIT ? 2 * P.Npad : 16);
       uint32_t stage = 0, phase = 0, bstage = 0, bphase = 0;
+      uint32_t aslot = 0, aphase = 0;  // split mode: converted-stage ring
       int chunk = 0;                 // accumulator fills (TMEM buffer alternation)
       bool ok = true;
       for (int64_t g = it0; g < it1 && ok;) {
@@ -276,15 +322,47 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           const int b = (P.nbuf == 2) ? (chunk & 1) : 0;
           const uint32_t use = (P.nbuf == 2) ? (uint32_t)(chunk >> 1) : (uint32_t)chunk;
           if (!tc::mbar_wait(&tempty[b], (use & 1u) ^ 1u, abortp)) { ok = false; break; }
+          if (SPLIT && c0 == kb0 && chunk > 0) {
+            // a new segment: the previous fill (the last of the previous
+            // segment) has had both correction blocks D2 read and zeroed
+            const int pc = chunk - 1;
+            if (!tc::mbar_wait(&tempty[pc & 1], (uint32_t)(pc >> 1) & 1u, abortp)) { ok = false; break; }
+          }
           tc::fence_after_sync();
           const uint32_t dcol = tbase + (uint32_t)(b * MT * P.Npad);
           for (int64_t kb = c0; kb < c1; ++kb) {
-            if (!tc::mbar_wait(&full[stage], phase, abortp)) { ok = false; break; }
+            if constexpr (SPLIT) {
+              if (!tc::mbar_wait(&afull[aslot], aphase, abortp)) { ok = false; break; }
+            } else {
+              if (!tc::mbar_wait(&full[stage], phase, abortp)) { ok = false; break; }
+            }
             if (!tc::mbar_wait(&bfull[bstage], bphase, abortp)) { ok = false; break; }
-            if (SPLIT && !tc::mbar_wait(&conv[stage], phase, abortp)) { ok = false; break; }
             tc::fence_after_sync();
-            const uint32_t sa = tc::smem_u32(smem + (size_t)stage * P.stage_bytes);
             const uint32_t sb = tc::smem_u32(bring + (size_t)bstage * P.bstage_bytes);
+            if constexpr (SPLIT) {
+              // hi x [B_hi | B_lo] into [D1 | D2] of buffer b (A_hi: the fp32
+              // stage itself), lo x B_hi into D2 of buffer 1 - b (A_lo from
+              // its TMEM slot, or from the stage after the tile)
+              const uint32_t sa = tc::smem_u32(smem + (size_t)stage * P.stage_bytes);
+              const uint32_t dw = tbase + (uint32_t)(b * 2 * P.Npad);
+              const uint32_t dc = tbase + (uint32_t)((1 - b) * 2 * P.Npad + P.Npad);
+              const uint32_t alo = tbase + P.aslot_col + aslot * kASlotCols;
+#pragma unroll
+              for (int ks = 0; ks < AK / KMMA; ++ks) {
+                const uint64_t ad = tc::desc_sw128(sa + ks * 32, 16, 1024);
+                const uint64_t bd = tc::desc_sw128(sb + ks * 32, 16, 1024);
+                tc::mma_tf32(dw, ad, bd, idescW, 1u);
+                if (P.lo_tmem) tc::mma_tf32_ts(dc, alo + (uint32_t)(ks * KMMA), bd, idesc0, 1u);
+                else tc::mma_tf32(dc, tc::desc_sw128(sa + P.a_bytes + ks * 32, 16, 1024), bd, idesc0, 1u);
+              }
+              tc::mma_commit(&empty[stage]);
+              tc::mma_commit(&aempty[aslot]);
+              if (PAIR) tc::mma_commit_mc(&bempty[bstage], (uint16_t)3);
+              else tc::mma_commit(&bempty[bstage]);
+              if (++stage == (uint32_t)P.stages) { stage = 0; phase ^= 1; }
+              if (++aslot == (uint32_t)P.aslots) { aslot = 0; aphase ^= 1u; }
+            } else {
+            const uint32_t sa = tc::smem_u32(smem + (size_t)stage * P.stage_bytes);
 #pragma unroll
             for (int j = 0; j < KA; ++j) {
 #pragma unroll
@@ -302,17 +380,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     const uint32_t dch = dm + (ch ? (uint32_t)P.ch0 : 0u);
                     const uint32_t bat = sb + (uint32_t)j * P.b_atom + (ch ? (uint32_t)(P.ch0 * 128) : 0u);
                     const uint64_t bd = tc::desc_sw128(bat + ks * 32, 16, 1024);
-                    if (SPLIT) {
-                      const uint64_t ad_lo = tc::desc_sw128(aat + P.a_bytes + ks * 32, 16, 1024);
-                      const uint64_t bd_lo = tc::desc_sw128(bat + P.b_bytes + ks * 32, 16, 1024);
-                      tc::mma_tf32(dch, ad, bd, id, acc);
-                      tc::mma_tf32(dch, ad, bd_lo, id, 1u);
-                      tc::mma_tf32(dch, ad_lo, bd, id, 1u);
-                    } else if (ELT == 2) {
-                      tc::mma_tf32(dch, ad, bd, id, acc);
-                    } else {
-                      tc::mma_f16(dch, ad, bd, id, acc);
-                    }
+                    if (ELT == 2) tc::mma_tf32(dch, ad, bd, id, acc);
+                    else tc::mma_f16(dch, ad, bd, id, acc);
                   }
                 }
               }
@@ -321,6 +390,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             if (PAIR) tc::mma_commit_mc(&bempty[bstage], (uint16_t)3);
             else tc::mma_commit(&bempty[bstage]);
             if (++stage == (uint32_t)P.stages) { stage = 0; phase ^= 1; }
+            }
             if (++bstage == (uint32_t)P.bstages) { bstage = 0; bphase ^= 1; }
           }
           if (!ok) break;
@@ -336,31 +406,53 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     }
   } else if (SPLIT && warp >= 7) {
     // ------------------------------------------------------------ converter
-    // hi = RN_tf32(x) rewritten in place (exactly representable, so the MMA
-    // reads it without truncation) and lo = x - hi (exact in fp32) right
-    // after the A tiles of the stage; elementwise, so the 128-byte swizzle of
-    // the copies carries over.  B arrives already split (hi and lo tensors).
-    const int ct = threadIdx.x - 224;          // 0..127
-    uint32_t stage = 0, phase = 0;
+    // thread = row r of the 128-row block = TMEM lane r (warp 7 + i covers
+    // lanes 32 ((7 + i) mod 4) ..): the row's 32 fp32 values come from the
+    // 128-byte-swizzled stage (16-byte chunk c of row r sits at chunk
+    // c ^ (r mod 8), conflict-free across 8 rows); lo goes to the row's TMEM
+    // lane in the slot (tcgen05.st) or to the same place one tile on.  B
+    // arrives already split (hi and lo tensors).
+    const int q = warp & 3;
+    const int r = q * 32 + lane;
+    const uint32_t tlane = tbase + ((uint32_t)(q * 32) << 16) + P.aslot_col;
+    uint32_t stage = 0, phase = 0, aslot = 0, aphase = 0;
     bool ok = true;
     for (int64_t g = it0; g < it1 && ok;) {
       const int64_t t = g / P.ipt;
       const int64_t gend = min(it1, (t + 1) * P.ipt);
       for (int64_t kb = g - t * P.ipt; kb < gend - t * P.ipt; ++kb) {
         if (!tc::mbar_wait(&full[stage], phase, abortp)) { ok = false; break; }
-        float4* src = reinterpret_cast<float4*>(smem + (size_t)stage * P.stage_bytes);
-        float4* dst = reinterpret_cast<float4*>(smem + (size_t)stage * P.stage_bytes + P.a_bytes);
-        for (uint32_t v = ct; v < P.a_bytes / 16; v += 128) {
-          float4 x = src[v], h, r;
-          h.x = rn_tf32(x.x); h.y = rn_tf32(x.y); h.z = rn_tf32(x.z); h.w = rn_tf32(x.w);
-          r.x = x.x - h.x; r.y = x.y - h.y; r.z = x.z - h.z; r.w = x.w - h.w;
-          src[v] = h;
-          dst[v] = r;
+        uint8_t* row = smem + (size_t)stage * P.stage_bytes + (size_t)r * 128;
+        float lo[2][16];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const float4* px = reinterpret_cast<const float4*>(row + ((c ^ (r & 7)) << 4));
+          const float4 x = *px;
+          const float4 l = make_float4(tf32_rest(x.x), tf32_rest(x.y), tf32_rest(x.z), tf32_rest(x.w));
+          if (P.lo_tmem) {
+            lo[c >> 2][(4 * c) & 15] = l.x;
+            lo[c >> 2][(4 * c + 1) & 15] = l.y;
+            lo[c >> 2][(4 * c + 2) & 15] = l.z;
+            lo[c >> 2][(4 * c + 3) & 15] = l.w;
+          } else {
+            *reinterpret_cast<float4*>(reinterpret_cast<uint8_t*>(const_cast<float4*>(px)) + P.a_bytes) = l;
+          }
         }
-        fence_proxy_async();                   // generic writes -> tensor-core reads
+        if (!P.lo_tmem) fence_proxy_async();   // generic writes -> tensor-core reads
+        // at most aslots converted stages ahead of the MMAs
+        if (!tc::mbar_wait(&aempty[aslot], aphase ^ 1u, abortp)) { ok = false; break; }
+        if (P.lo_tmem) {
+          tc::fence_after_sync();
+          const uint32_t ta = tlane + aslot * kASlotCols;
+          tc::tmem_st16(ta, lo[0]);
+          tc::tmem_st16(ta + 16, lo[1]);
+          tc::tmem_st_wait();
+          tc::fence_before_sync();
+        }
         __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&conv[stage]);
+        if (lane == 0) tc::mbar_arrive(&afull[aslot]);
         if (++stage == (uint32_t)P.stages) { stage = 0; phase ^= 1; }
+        if (++aslot == (uint32_t)P.aslots) { aslot = 0; aphase ^= 1u; }
       }
       g = gend;
     }
@@ -379,8 +471,65 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         const int slot = (t == it0 / P.ipt) ? 0 : 1;
         pdst = P.parts + ((size_t)blockIdx.x * 2 + slot) * mrows * P.Npad;
       }
-      // split mode: running sum in TMEM columns [2 Npad, 3 Npad) of this warp's lanes
-      const uint32_t tmaster = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(2 * P.Npad);
+      if constexpr (SPLIT) {
+        // MT = 1: one row per thread; the running sum of the fills lives in
+        // registers (columns past Npad stay unused)
+        const int row = q * 32 + lane;
+        const int64_t grow = t * urows + rank * mrows + row;
+        float sum[kAccCols];
+#pragma unroll
+        for (int i = 0; i < kAccCols; ++i) sum[i] = 0.f;
+        const uint32_t tq = tbase + ((uint32_t)(q * 32) << 16);
+        float z[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) z[i] = 0.f;
+        // add TMEM columns [col, col + Npad) of this row into the running
+        // sum (round-to-nearest fp32 adds) and zero them for the next fill
+        auto drain = [&](uint32_t col) {
+#pragma unroll
+          for (int cc = 0; cc < kAccCols; cc += 16) {
+            if (cc < P.Npad) {
+              float v[16];
+              tc::tmem_ld16(tq + col + cc, v);
+              tc::tmem_ld_wait();
+#pragma unroll
+              for (int i = 0; i < 16; ++i) sum[cc + i] += v[i];
+              tc::tmem_st16(tq + col + cc, z);
+            }
+          }
+        };
+        for (int64_t c0 = kb0; c0 < kb1; c0 += CHUNK) {
+          const int b = chunk & 1;
+          const uint32_t use = (uint32_t)(chunk >> 1);
+          if (!tc::mbar_wait(&tfull[b], use & 1u, abortp)) { ok = false; break; }
+          tc::fence_after_sync();
+          drain((uint32_t)(b * 2 * P.Npad));               // D1 of this fill
+          if (c0 + CHUNK >= kb1) {
+            // the segment's last fill: every MMA of the segment is complete,
+            // so both correction blocks D2 are final
+            drain((uint32_t)P.Npad);
+            drain((uint32_t)(3 * P.Npad));
+          }
+          tc::tmem_st_wait();
+          tc::fence_before_sync();
+          tc::mbar_arrive(&tempty[b]);
+          ++chunk;
+        }
+        if (ok) {
+#pragma unroll
+          for (int cb = 0; cb < kAccCols; cb += 16) {
+            if (cb < P.N) {
+#pragma unroll
+              for (int i = 0; i < 16; ++i) {
+                if (cb + i < P.N) {
+                  if (whole) { if (grow < P.M) store_out(P, grow, cb + i, sum[cb + i]); }
+                  else pdst[row + (size_t)(cb + i) * mrows] = sum[cb + i];
+                }
+              }
+            }
+          }
+        }
+      } else {
       for (int64_t c0 = kb0; c0 < kb1; c0 += CHUNK) {
         const int b = (P.nbuf == 2) ? (chunk & 1) : 0;
         const uint32_t use = (P.nbuf == 2) ? (uint32_t)(chunk >> 1) : (uint32_t)chunk;
@@ -391,34 +540,20 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
               tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * MT * P.Npad + mt * P.Npad);
           const int row = mt * 128 + q * 32 + lane;
           const int64_t grow = t * urows + rank * mrows + row;
-          if (SPLIT) {
-            // drain: round-to-nearest fp32 adds of the fill into the running sum
-            for (int cc = 0; cc < P.Npad; cc += 16) {
-              float v[16], acc[16];
-              tc::tmem_ld16(taddr + cc, v);
-              if (c0 != kb0) tc::tmem_ld16(tmaster + cc, acc);
-              tc::tmem_ld_wait();
-#pragma unroll
-              for (int i = 0; i < 16; ++i) acc[i] = (c0 != kb0) ? acc[i] + v[i] : v[i];
-              tc::tmem_st16(tmaster + cc, acc);
-            }
-            tc::tmem_st_wait();
-          } else {
-            for (int cb = 0; cb < P.N; cb += 16) {
-              float v[16];
-              tc::tmem_ld16(taddr + cb, v);
-              tc::tmem_ld_wait();
-              if (whole) {
-                if (grow < P.M) {
-#pragma unroll
-                  for (int i = 0; i < 16; ++i)
-                    if (cb + i < P.N) store_out(P, grow, cb + i, v[i]);
-                }
-              } else {
+          for (int cb = 0; cb < P.N; cb += 16) {
+            float v[16];
+            tc::tmem_ld16(taddr + cb, v);
+            tc::tmem_ld_wait();
+            if (whole) {
+              if (grow < P.M) {
 #pragma unroll
                 for (int i = 0; i < 16; ++i)
-                  if (cb + i < P.N) pdst[row + (size_t)(cb + i) * mrows] = v[i];
+                  if (cb + i < P.N) store_out(P, grow, cb + i, v[i]);
               }
+            } else {
+#pragma unroll
+              for (int i = 0; i < 16; ++i)
+                if (cb + i < P.N) pdst[row + (size_t)(cb + i) * mrows] = v[i];
             }
           }
         }
@@ -426,22 +561,6 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         tc::mbar_arrive(&tempty[b]);
         ++chunk;
       }
-      if (SPLIT && ok) {
-        // split mode runs with MT = 1
-        const int row = q * 32 + lane;
-        const int64_t grow = t * urows + rank * mrows + row;
-        for (int cb = 0; cb < P.N; cb += 16) {
-          float v[16];
-          tc::tmem_ld16(tmaster + cb, v);
-          tc::tmem_ld_wait();
-#pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            if (cb + i < P.N) {
-              if (whole) { if (grow < P.M) store_out(P, grow, cb + i, v[i]); }
-              else pdst[row + (size_t)(cb + i) * mrows] = v[i];
-            }
-          }
-        }
       }
       g = gend;
     }
@@ -631,7 +750,7 @@ cudaError_t launch_shape(const CUtensorMap& ma, const CUtensorMap& mb, const CUt
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(2 * P.G), 1, 1);
-  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.blockDim = dim3(ELT == 3 ? kThreadsSplit : kThreads, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -650,10 +769,18 @@ template <int ELT, bool A_MN>
 cudaError_t launch_typed(const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& mblo, const TcParams& P,
                          size_t smem, cudaStream_t st) {
   if constexpr (ELT == 3) {
-    if (P.MT != 1 || P.nch != 1) return cudaErrorInvalidValue;
-    return P.KA == 1 ? launch_shape<ELT, A_MN, 1, 1, 1>(ma, mb, mblo, P, smem, st)
-                     : launch_shape<ELT, A_MN, 1, 1, 2>(ma, mb, mblo, P, smem, st);
+    if (P.MT != 1 || P.nch != 1 || P.KA != 1) return cudaErrorInvalidValue;
+    return P.pair ? launch_shape<ELT, A_MN, 1, 1, 1, true>(ma, mb, mblo, P, smem, st)
+                  : launch_shape<ELT, A_MN, 1, 1, 1>(ma, mb, mblo, P, smem, st);
   } else {
+  if constexpr (ELT == 2) {
+  if (P.pair) {
+    // TF32: one N-chunk and one K atom per stage, B shared by the pair
+    if (P.nch != 1 || P.KA != 1) return cudaErrorInvalidValue;
+    return P.MT == 2 ? launch_shape<ELT, A_MN, 2, 1, 1, true>(ma, mb, mblo, P, smem, st)
+                     : launch_shape<ELT, A_MN, 1, 1, 1, true>(ma, mb, mblo, P, smem, st);
+  }
+  }
   if constexpr (ELT < 2) {
   if (P.pair) {
     // one 128-row block per CTA, B shared by the pair
@@ -709,24 +836,32 @@ TcParams shape(int elt, int64_t M, int64_t N, int64_t K, int KA, int MT, bool pa
   if (P.G < 1) P.G = 1;
   P.nbuf = (2 * MT * P.Npad <= 512) ? 2 : 1;
   uint32_t cols = 32;
-  // split mode keeps its running sum in a third block of Npad columns
-  const uint32_t need_cols = (uint32_t)(P.nbuf * MT * P.Npad + (elt == 3 ? P.Npad : 0));
+  // split mode: two fill buffers [D1 | D2] (4 Npad columns), then the
+  // low-part slots of A when they fit (Npad <= kLoTmemMaxNpad)
+  if (elt == 3) {
+    P.lo_tmem = P.Npad <= kLoTmemMaxNpad ? 1 : 0;
+    P.aslot_col = (uint32_t)(4 * P.Npad);
+    P.aslots = P.lo_tmem ? (int)std::min<uint32_t>(kASlots, (512u - P.aslot_col) / kASlotCols) : (int)kASlots;
+  }
+  const uint32_t need_cols = elt == 3 ? 512u : (uint32_t)(P.nbuf * MT * P.Npad);
   while (cols < need_cols) cols <<= 1;
   P.tmem_cols = cols;
   P.a_bytes = (uint32_t)(MT * KA) * kAtomBytes;
   P.b_atom = (uint32_t)P.nch * (uint32_t)P.ch0 * 128u;
   P.b_bytes = (uint32_t)KA * P.b_atom;
-  const uint32_t mult = (elt == 3 ? 2u : 1u);                             // + low parts in split mode
-  P.stage_bytes = mult * P.a_bytes;
-  P.bstage_bytes = mult * P.b_bytes;
+  // split mode: a B stage holds the hi and lo tensors; A's parts live in TMEM
+  P.stage_bytes = (elt == 3 && !P.lo_tmem ? 2u : 1u) * P.a_bytes;
+  P.bstage_bytes = (elt == 3 ? 2u : 1u) * P.b_bytes;
   // B ring depth (SORSVD_TC_BSTAGES overrides, 2..4)
   const int envB = env_int("SORSVD_TC_BSTAGES", 0);
   // a B stage larger than the A stage (16-bit operands, N > 128): one more
-  P.bstages = (envB >= 2 && envB <= 4) ? envB : ((elt < 2 && P.b_bytes > P.a_bytes) ? 3 : 2);
+  // (split mode: a B stage holds hi and lo, twice the A stage)
+  P.bstages = (envB >= 2 && envB <= 4) ? envB
+              : ((elt < 2 && P.b_bytes > P.a_bytes) || (elt == 3 && P.lo_tmem) ? 3 : 2);
   const uint32_t left = kSmemBudget > P.bstages * P.bstage_bytes ? kSmemBudget - P.bstages * P.bstage_bytes : 0;
   P.stages = (int)std::min<uint32_t>(12u, left / P.stage_bytes);
   if (MT * P.Npad > 512 || cols > 512) P.stages = 0;
-  if (elt == 3 && (MT != 1 || P.nbuf != 2 || need_cols > 512)) P.stages = 0;
+  if (elt == 3 && (MT != 1 || KA != 1 || P.nbuf != 2 || 4 * P.Npad > 512 || P.aslots < 2)) P.stages = 0;
   return P;
 }
 
@@ -742,12 +877,15 @@ TcParams tc_plan(int elt, int64_t M, int64_t N, int64_t K) {
   const int64_t Npad = (N + 15) / 16 * 16;
   int MT = envMT > 0 ? envMT : ((elt != 3 && 4 * Npad <= 512) ? 2 : 1);
   if (elt == 3 || MT * Npad > 512 || MT < 1 || MT > 2) MT = 1;
-  // 16-bit operands with one 128-row block per tile and a B stage larger
-  // than the A stage: two-CTA clusters halve the B reads from L2
-  // (SORSVD_TC_PAIR=0 turns this off)
-  const bool pair = elt < 2 && MT == 1 && Npad > 128 && M > 128 && env_int("SORSVD_TC_PAIR", 1) != 0;
+  // Two-CTA clusters that share (multicast) each B stage halve the B reads
+  // from L2, whose output bandwidth bounds the passes where B is large next
+  // to A: 16-bit operands with one 128-row block per tile and N > 128, and
+  // the fp32 passes (split mode reads B twice, hi and lo).  TF32 pairs take
+  // one K atom per stage.  SORSVD_TC_PAIR=0 turns pairs off.
+  const bool pair_ok = env_int("SORSVD_TC_PAIR", 1) != 0 && M > 128 * MT;
+  const bool pair = pair_ok && ((elt < 2 && MT == 1 && Npad > 128) || elt == 3 || (elt == 2 && Npad <= 256));
   TcParams best = shape(elt, M, N, K, 1, MT, pair);
-  if (envKA > kMaxKA) return best;
+  if (envKA > kMaxKA || elt >= 2) return best;     // fp32 containers: one K atom per stage
   if (envKA > 0) {
     TcParams P = shape(elt, M, N, K, envKA, MT, pair);
     return P.stages >= 2 ? P : best;
@@ -762,7 +900,7 @@ TcParams tc_plan(int elt, int64_t M, int64_t N, int64_t K) {
 bool tc_supported(int elt, const void* A, int64_t lda, const void* B, int64_t ldb, int l) {
   const int64_t esz = elt >= 2 ? 4 : 2;
   if (l < 1 || l > 512) return false;
-  if (elt == 3 && l > kAccCols) return false;       // split mode: 3 Npad TMEM columns
+  if (elt == 3 && l > kAccCols) return false;       // split mode: 4 Npad TMEM columns
   if ((reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15)) return false;
   if ((lda * esz) % 16 || (ldb * esz) % 16) return false;
   return encode_fn() != nullptr;

@@ -128,6 +128,10 @@ Layout make_layout(int64_t m, int64_t n, int l, int dt) {
     pb = std::max(pb, tc_parts_bytes(elt, m, l, n));
     pb = std::max(pb, tc_parts_bytes(elt, n, l, m));
   }
+  if (dt == SORSVD_F32) {                           // fp32-accurate split passes
+    pb = std::max(pb, tc_parts_bytes(3, m, l, n));
+    pb = std::max(pb, tc_parts_bytes(3, n, l, m));
+  }
   if (dt != SORSVD_F64) {                           // row-block Gram partials
     pb = std::max(pb, rb_gram_parts_bytes(m, l, l, true));
     pb = std::max(pb, rb_gram_parts_bytes(n, l, l, true));

@@ -102,7 +102,8 @@ def test_gaussian_leading_dimension(nat):
 
 @pytest.mark.parametrize("dt", ["f64", "f32", "tf32", "bf16", "f16"])
 @pytest.mark.parametrize("m,n,k,p", [(333, 517, 20, 7), (1025, 130, 60, 4), (129, 2049, 9, 1), (4096, 768, 100, 12),
-                                     (1000, 360, 27, 5), (2048, 4096, 256, 10), (640, 96, 32, 0)])
+                                     (1000, 360, 27, 5), (2048, 4096, 256, 10), (640, 96, 32, 0),
+                                     (1500, 700, 100, 28)])
 def test_power_pass_elementwise(nat, dt, m, n, k, p):
     l = k + p
     if dt == "f64" and l > nat.MAX_L_F64:
