@@ -65,6 +65,10 @@ typedef enum {
                                           hi+lo pair of 16-bit operands (two
                                           tensor-core passes over A, combined
                                           in binary64) */
+#define SORSVD_FLAG_HOST_IO       0x4u /* sorsvd_workspace_size: size for
+                                          sorsvd_run_host (adds the device
+                                          copies of A, U, S and V); accepted
+                                          and ignored by sorsvd_run_host */
 
 /* Largest sketch width l = k + p supported (the small l x l factorisations
  * run in one thread block with the factor in shared memory). */
@@ -90,6 +94,29 @@ int sorsvd_run(const void* A, int64_t m, int64_t n, int64_t lda,
                int k, int p, int q, uint64_t seed, int dtype, unsigned flags,
                void* U, int64_t ldu, void* S, void* V, int64_t ldv,
                void* workspace, size_t ws_bytes, void* stream);
+
+/* sorsvd_run with A, U, S and V in HOST memory.  The paper has no
+ * counterpart: the entry point serves callers whose matrix lives on the host
+ * (the end-to-end cost of the method then includes the copy of A).
+ *   A, lda, U, ldu, S, V, ldv: as in sorsvd_run, but host pointers.  For the
+ *          copies to run asynchronously and overlap the solve they must be
+ *          page-locked (cudaHostAlloc / cudaHostRegister); pageable memory
+ *          works, with copies that the CUDA runtime stages synchronously.
+ *   workspace: device memory of at least
+ *          sorsvd_workspace_size(m, n, k, p, dtype, flags | SORSVD_FLAG_HOST_IO)
+ *          bytes, 256-byte aligned; it also holds the device copies of A,
+ *          U, S and V.
+ * A crosses in column blocks of about 64 MiB on a copy stream of the
+ * library; Omega is drawn meanwhile, and for F32 / TF32 each block's part of
+ * the transposed copy of A is made as soon as the block has landed.  The
+ * solve and the copies of U, S, V back to the host are queued on `stream`
+ * after every block (results identical to sorsvd_run on the same data).
+ * Returns SORSVD_OK when the work was queued; the host outputs are valid
+ * once `stream` has been synchronised; errors as sorsvd_run. */
+int sorsvd_run_host(const void* A, int64_t m, int64_t n, int64_t lda,
+                    int k, int p, int q, uint64_t seed, int dtype, unsigned flags,
+                    void* U, int64_t ldu, void* S, void* V, int64_t ldv,
+                    void* workspace, size_t ws_bytes, void* stream);
 
 /* Maximum scratch of sorsvd_run_noalloc: 32 MiB of device memory, held by
  * every GPU that loads the library for the life of the process. */

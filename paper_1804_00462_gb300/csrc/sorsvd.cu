@@ -19,6 +19,7 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <vector>
 
 namespace sorsvd {
 namespace {
@@ -229,22 +230,24 @@ int pass(const Ctx& c, int kcls, bool trans, int64_t M, int64_t N, int64_t K, co
   return SORSVD_OK;
 }
 
-// A non-blocking stream of this device for work that runs beside the
-// caller's stream (created once; nullptr when that fails)
-cudaStream_t side_stream() {
-  static cudaStream_t streams[64] = {nullptr};
-  static bool tried[64] = {false};
+// Non-blocking streams of this device for work that runs beside the
+// caller's stream (created once per device; nullptr when that fails).
+// which = 0: Omega, highest priority (its blocks are placed before the
+// caller's queued ones); which = 1: host <-> device copies.
+cudaStream_t side_stream(int which = 0) {
+  static cudaStream_t streams[2][64] = {{nullptr}};
+  static bool tried[2][64] = {{false}};
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) return nullptr;
-  if (!tried[dev]) {
-    tried[dev] = true;
-    // highest priority: its blocks are placed before the caller's queued ones
+  if (dev < 0 || dev >= 64 || which < 0 || which > 1) return nullptr;
+  if (!tried[which][dev]) {
+    tried[which][dev] = true;
     int lo = 0, hi = 0;
     cudaDeviceGetStreamPriorityRange(&lo, &hi);
-    if (cudaStreamCreateWithPriority(&streams[dev], cudaStreamNonBlocking, hi) != cudaSuccess) streams[dev] = nullptr;
+    if (cudaStreamCreateWithPriority(&streams[which][dev], cudaStreamNonBlocking, which == 0 ? hi : lo) != cudaSuccess)
+      streams[which][dev] = nullptr;
   }
-  return streams[dev];
+  return streams[which][dev];
 }
 
 // Omega on the side stream while `work` runs on the caller's stream; the
@@ -442,6 +445,151 @@ int check_ws(void* ws, size_t ws_bytes, const Layout& L) {
 
 int max_l(int dt) { return dt == SORSVD_F64 ? SORSVD_MAX_L_F64 : SORSVD_MAX_L; }
 
+// Device copies of A, U, S, V for sorsvd_run_host, after the solve's own
+// workspace (256-byte aligned regions; leading dimensions padded so that
+// the tensor-core passes can map A).
+struct HostIo {
+  size_t a, u, s, v, total;
+  int64_t lda, ldu, ldv;
+};
+
+HostIo host_io_layout(size_t base, int64_t m, int64_t n, int k, int dt) {
+  HostIo H{};
+  const size_t op = dtype_size(dt), acc = acc_size(dt);
+  size_t off = align_up(base);
+  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
+  H.lda = pad16(m);
+  H.ldu = pad16(m);
+  H.ldv = pad16(n);
+  H.a = take((size_t)H.lda * n * op);
+  H.u = take((size_t)H.ldu * k * acc);
+  H.s = take((size_t)k * acc);
+  H.v = take((size_t)H.ldv * k * acc);
+  H.total = off;
+  return H;
+}
+
+// A (host, column-major, lda) -> its device copy Ad (ld ldd) in column
+// blocks of about 64 MiB on the copy stream.  For the fp32 containers each
+// block's part of the transposed copy A^T is made on c.st as soon as the
+// block has landed, so the transpose runs under the remaining copies; c.st
+// waits for every block before it goes on.
+int upload_a(const Ctx& c, const void* Ah, int64_t lda, int64_t m, int64_t n, void* Ad, int64_t ldd) {
+  const size_t esz = dtype_size(c.dt);
+  const bool at = c.L.has_at && tc_enabled();
+  const size_t col_bytes = std::max<size_t>(1, (size_t)m * esz);
+  int64_t cols = std::max<int64_t>(1, (int64_t)((size_t)(64u << 20) / col_bytes));
+  const int nblk = (int)std::min<int64_t>(32, (n + cols - 1) / cols);
+  cols = (n + nblk - 1) / nblk;
+  auto copy_cols = [&](int64_t j0, int64_t j1, cudaStream_t st) {
+    return cudaMemcpy2DAsync((char*)Ad + (size_t)j0 * ldd * esz, (size_t)ldd * esz,
+                             (const char*)Ah + (size_t)j0 * lda * esz, (size_t)lda * esz, (size_t)m * esz,
+                             (size_t)(j1 - j0), cudaMemcpyHostToDevice, st);
+  };
+  float* At = at ? (float*)c.at(c.L.at) : nullptr;
+  cudaStream_t cs = side_stream(1);
+  std::vector<cudaEvent_t> ev(nblk + 1, nullptr);
+  bool events = cs != nullptr;
+  for (int b = 0; b <= nblk && events; ++b)
+    events = cudaEventCreateWithFlags(&ev[b], cudaEventDisableTiming) == cudaSuccess;
+  int r = SORSVD_OK;
+  if (!events) {
+    // no copy stream: one copy, then the transposed copy, both on c.st
+    if (copy_cols(0, n, c.st) != cudaSuccess) r = SORSVD_ERR_CUDA;
+    else if (at) r = prepare_at(c, Ad, m, n, ldd);
+  } else if (cudaEventRecord(ev[nblk], c.st) != cudaSuccess || cudaStreamWaitEvent(cs, ev[nblk], 0) != cudaSuccess) {
+    r = SORSVD_ERR_CUDA;
+  } else {
+    for (int b = 0; b < nblk && !r; ++b) {
+      const int64_t j0 = b * cols, j1 = std::min<int64_t>(n, j0 + cols);
+      if (j0 >= j1) break;
+      if (copy_cols(j0, j1, cs) != cudaSuccess || cudaEventRecord(ev[b], cs) != cudaSuccess) { r = SORSVD_ERR_CUDA; break; }
+      if (at || j1 == n) {
+        if (cudaStreamWaitEvent(c.st, ev[b], 0) != cudaSuccess) { r = SORSVD_ERR_CUDA; break; }
+      }
+      if (at) {
+        ProfScope ps(K_MISC, c.st);
+        if (launch_transpose_f32((const float*)((char*)Ad + (size_t)j0 * ldd * esz), ldd, m, j1 - j0, At + j0,
+                                 c.L.ldn, c.st) != cudaSuccess)
+          r = SORSVD_ERR_CUDA;
+      }
+    }
+  }
+  for (cudaEvent_t e : ev)
+    if (e) cudaEventDestroy(e);
+  return r;
+}
+
+// Algorithm 3 after Omega (in t2op) and, for the fp32 containers, the
+// transposed copy of A are in place: the power loop, the QR step, the core,
+// its truncated SVD and the output assembly, all queued on c.st.
+int solve(const Ctx& c, const void* A, int64_t m, int64_t n, int64_t lda, int k, int l, int q, unsigned flags,
+          void* U, int64_t ldu, void* S, void* V, int64_t ldv) {
+  const Layout& L = c.L;
+  const int dtype = c.dt;
+  const int adt = c.f64 ? SORSVD_F64 : SORSVD_F32;
+  const bool h16 = dtype_is_16(dtype);
+  int r;
+  if (flags & SORSVD_FLAG_LITERAL_POWER) {
+    // Algorithm 3 as printed: the sketches are orthonormalised only at the end
+    for (int i = 1; i <= q + 1; ++i) {
+      if (i > 1 && h16)
+        LAUNCH(K_MISC, launch_convert_f32((const float*)c.at(L.t2), L.ldn, n, l, c.at(L.t2op), L.ldn, dtype, nullptr,
+                                          c.st));
+      r = power_pass_impl(c, A, m, n, lda, c.at(L.t2op), L.ldn, l, c.at(L.t1), L.ldm, c.at(L.t2), L.ldn,
+                          i == q + 1);
+      if (r) return r;
+    }
+    r = orth(c, c.at(L.t1), m, L.ldm, l, 3, first_shift(dtype));
+    if (r) return r;
+    r = orth(c, c.at(L.t2), n, L.ldn, l, 3, first_shift(dtype));
+    if (r) return r;
+  } else {
+    // Each sketch is orthonormalised as soon as it is formed: T1 before the
+    // product A^T T1 and T2 before the next A T2.  By Lemma 1 this leaves
+    // range(T1) and range(T2) - hence Q1, Q2 and the result - unchanged,
+    // while every product sees the conditioning of A instead of its square
+    // (the trailing directions of a fast-decaying spectrum survive fp32).
+    // One CholeskyQR pass while the loop only steers the subspace, three
+    // (CholeskyQR3) in the last iteration, which fixes Q1 and Q2.
+    const int kc = dtype == SORSVD_F32 ? K_PASS_SPLIT : K_PASS;
+    void* t1op = h16 ? c.at(L.t1op) : c.at(L.t1);
+    const void* x2 = c.at(L.t2op);           // operand of the next product A X (Omega first)
+    for (int i = 1; i <= q + 1; ++i) {
+      const bool last = (i == q + 1);
+      const int np = last ? 3 : 1;
+      // F32: TF32 products while the loop only steers the subspace, the
+      // fp32-accurate split products in the last iteration.  Inside the
+      // loop the orthonormalised sketch may stay in the tmp buffer: it is
+      // only the operand of the next product.
+      r = pass(c, last ? kc : K_PASS, false, m, l, n, A, lda, x2, L.ldn, h16 ? dtype : adt, c.at(L.t1), L.ldm,
+               nullptr, 0, last);
+      if (r) return r;
+      void* q1 = nullptr;
+      r = orth(c, c.at(L.t1), m, L.ldm, l, np, first_shift(dtype), h16 ? t1op : nullptr, L.ldm, last ? nullptr : &q1);
+      if (r) return r;
+      const void* y1 = h16 ? t1op : (q1 ? q1 : c.at(L.t1));
+      r = pass(c, last ? kc : K_PASS, true, n, l, m, A, lda, y1, L.ldm, h16 ? dtype : adt, c.at(L.t2), L.ldn,
+               nullptr, 0, last);
+      if (r) return r;
+      void* q2 = nullptr;
+      r = orth(c, c.at(L.t2), n, L.ldn, l, np, first_shift(dtype), (!last && h16) ? c.at(L.t2op) : nullptr, L.ldn,
+               last ? nullptr : &q2);
+      if (r) return r;
+      x2 = h16 ? c.at(L.t2op) : (q2 ? q2 : c.at(L.t2));
+    }
+  }
+  r = core_impl(c, A, m, n, lda, flags, c.at(L.t1), L.ldm, c.at(L.t2), L.ldn, l, (double*)c.at(L.M), l);
+  if (r) return r;
+  LAUNCH(K_JACOBI, launch_jacobi((const double*)c.at(L.M), l, k, c.f64, c.at(L.Ut), c.at(L.Vt), S, c.f64,
+                                  c.at(L.jwork), c.status(), c.st));
+  r = assemble(c, c.at(L.t1), L.ldm, m, l, c.at(L.Ut), k, U, ldu);
+  if (r) return r;
+  r = assemble(c, c.at(L.t2), L.ldn, n, l, c.at(L.Vt), k, V, ldv);
+  if (r) return r;
+  return SORSVD_OK;
+}
+
 }  // namespace
 
 // the status word is the first region of every workspace layout
@@ -454,11 +602,11 @@ using namespace sorsvd;
 extern "C" {
 
 size_t sorsvd_workspace_size(int64_t m, int64_t n, int k, int p, int dtype, unsigned flags) {
-  (void)flags;
   if (check_dtype(dtype) || m < 1 || n < 1 || k < 1 || p < 0) return 0;
   int l = k + p;
   if (l > std::min(m, n) || l > max_l(dtype)) return 0;
-  return make_layout(m, n, l, dtype).total;
+  const size_t base = make_layout(m, n, l, dtype).total;
+  return (flags & SORSVD_FLAG_HOST_IO) ? host_io_layout(base, m, n, k, dtype).total : base;
 }
 
 const char* sorsvd_status_string(int s) {
@@ -560,8 +708,6 @@ int sorsvd_run(const void* A, int64_t m, int64_t n, int64_t lda, int k, int p, i
   Layout L = make_layout(m, n, l, dtype);
   if (int r = check_ws(workspace, ws_bytes, L)) return r;
   Ctx c{(char*)workspace, L, dtype, dtype == SORSVD_F64, (cudaStream_t)stream};
-  const int adt = c.f64 ? SORSVD_F64 : SORSVD_F32;
-  const bool h16 = dtype_is_16(dtype);
   int r;
 
   CK(begin_call(c));
@@ -575,63 +721,43 @@ int sorsvd_run(const void* A, int64_t m, int64_t n, int64_t lda, int k, int p, i
     if (r) return r;
     LAUNCH(K_GAUSSIAN, launch_gaussian(c.at(L.t2op), n, l, L.ldn, seed, 0, dtype, c.st));
   }
-  if (flags & SORSVD_FLAG_LITERAL_POWER) {
-    // Algorithm 3 as printed: the sketches are orthonormalised only at the end
-    for (int i = 1; i <= q + 1; ++i) {
-      if (i > 1 && h16)
-        LAUNCH(K_MISC, launch_convert_f32((const float*)c.at(L.t2), L.ldn, n, l, c.at(L.t2op), L.ldn, dtype, nullptr,
-                                          c.st));
-      r = power_pass_impl(c, A, m, n, lda, c.at(L.t2op), L.ldn, l, c.at(L.t1), L.ldm, c.at(L.t2), L.ldn,
-                          i == q + 1);
-      if (r) return r;
-    }
-    r = orth(c, c.at(L.t1), m, L.ldm, l, 3, first_shift(dtype));
-    if (r) return r;
-    r = orth(c, c.at(L.t2), n, L.ldn, l, 3, first_shift(dtype));
-    if (r) return r;
-  } else {
-    // Each sketch is orthonormalised as soon as it is formed: T1 before the
-    // product A^T T1 and T2 before the next A T2.  By Lemma 1 this leaves
-    // range(T1) and range(T2) - hence Q1, Q2 and the result - unchanged,
-    // while every product sees the conditioning of A instead of its square
-    // (the trailing directions of a fast-decaying spectrum survive fp32).
-    // One CholeskyQR pass while the loop only steers the subspace, three
-    // (CholeskyQR3) in the last iteration, which fixes Q1 and Q2.
-    const int kc = dtype == SORSVD_F32 ? K_PASS_SPLIT : K_PASS;
-    void* t1op = h16 ? c.at(L.t1op) : c.at(L.t1);
-    const void* x2 = c.at(L.t2op);           // operand of the next product A X (Omega first)
-    for (int i = 1; i <= q + 1; ++i) {
-      const bool last = (i == q + 1);
-      const int np = last ? 3 : 1;
-      // F32: TF32 products while the loop only steers the subspace, the
-      // fp32-accurate split products in the last iteration.  Inside the
-      // loop the orthonormalised sketch may stay in the tmp buffer: it is
-      // only the operand of the next product.
-      r = pass(c, last ? kc : K_PASS, false, m, l, n, A, lda, x2, L.ldn, h16 ? dtype : adt, c.at(L.t1), L.ldm,
-               nullptr, 0, last);
-      if (r) return r;
-      void* q1 = nullptr;
-      r = orth(c, c.at(L.t1), m, L.ldm, l, np, first_shift(dtype), h16 ? t1op : nullptr, L.ldm, last ? nullptr : &q1);
-      if (r) return r;
-      const void* y1 = h16 ? t1op : (q1 ? q1 : c.at(L.t1));
-      r = pass(c, last ? kc : K_PASS, true, n, l, m, A, lda, y1, L.ldm, h16 ? dtype : adt, c.at(L.t2), L.ldn,
-               nullptr, 0, last);
-      if (r) return r;
-      void* q2 = nullptr;
-      r = orth(c, c.at(L.t2), n, L.ldn, l, np, first_shift(dtype), (!last && h16) ? c.at(L.t2op) : nullptr, L.ldn,
-               last ? nullptr : &q2);
-      if (r) return r;
-      x2 = h16 ? c.at(L.t2op) : (q2 ? q2 : c.at(L.t2));
-    }
-  }
-  r = core_impl(c, A, m, n, lda, flags, c.at(L.t1), L.ldm, c.at(L.t2), L.ldn, l, (double*)c.at(L.M), l);
+  return solve(c, A, m, n, lda, k, l, q, flags, U, ldu, S, V, ldv);
+}
+
+int sorsvd_run_host(const void* A, int64_t m, int64_t n, int64_t lda, int k, int p, int q, uint64_t seed, int dtype,
+                    unsigned flags, void* U, int64_t ldu, void* S, void* V, int64_t ldv, void* workspace,
+                    size_t ws_bytes, void* stream) {
+  if (check_dtype(dtype)) return SORSVD_ERR_DTYPE;
+  if (!A || !U || !S || !V) return SORSVD_ERR_ARG;
+  if (m < 1 || n < 1 || k < 1 || p < 0 || q < 0 || q > 1000 || lda < m || ldu < m || ldv < n)
+    return SORSVD_ERR_ARG;
+  if (flags & ~(SORSVD_FLAG_LITERAL_POWER | SORSVD_FLAG_REFINE | SORSVD_FLAG_HOST_IO)) return SORSVD_ERR_ARG;
+  const int l = k + p;
+  if (l > std::min(m, n)) return SORSVD_ERR_ARG;
+  if (l > max_l(dtype)) return SORSVD_ERR_UNSUPPORTED;
+  Layout L = make_layout(m, n, l, dtype);
+  const HostIo H = host_io_layout(L.total, m, n, k, dtype);
+  if (!workspace || ((uintptr_t)workspace) % kAlign || ws_bytes < H.total) return SORSVD_ERR_WORKSPACE;
+  Ctx c{(char*)workspace, L, dtype, dtype == SORSVD_F64, (cudaStream_t)stream};
+  void* Ad = c.at(H.a);
+  void* Ud = c.at(H.u);
+  void* Sd = c.at(H.s);
+  void* Vd = c.at(H.v);
+  int r;
+
+  CK(begin_call(c));
+  // Omega (no dependence on A) on the side stream while A crosses
+  r = gaussian_beside(c, c.at(L.t2op), n, l, L.ldn, seed, dtype,
+                      [&] { return upload_a(c, A, lda, m, n, Ad, H.lda); });
   if (r) return r;
-  LAUNCH(K_JACOBI, launch_jacobi((const double*)c.at(L.M), l, k, c.f64, c.at(L.Ut), c.at(L.Vt), S, c.f64,
-                                  c.at(L.jwork), c.status(), c.st));
-  r = assemble(c, c.at(L.t1), L.ldm, m, l, c.at(L.Ut), k, U, ldu);
+  r = solve(c, Ad, m, n, H.lda, k, l, q, flags & ~SORSVD_FLAG_HOST_IO, Ud, H.ldu, Sd, Vd, H.ldv);
   if (r) return r;
-  r = assemble(c, c.at(L.t2), L.ldn, n, l, c.at(L.Vt), k, V, ldv);
-  if (r) return r;
+  const size_t acc = acc_size(dtype);
+  CK(cudaMemcpy2DAsync(U, (size_t)ldu * acc, Ud, (size_t)H.ldu * acc, (size_t)m * acc, (size_t)k,
+                       cudaMemcpyDeviceToHost, c.st));
+  CK(cudaMemcpyAsync(S, Sd, (size_t)k * acc, cudaMemcpyDeviceToHost, c.st));
+  CK(cudaMemcpy2DAsync(V, (size_t)ldv * acc, Vd, (size_t)H.ldv * acc, (size_t)n * acc, (size_t)k,
+                       cudaMemcpyDeviceToHost, c.st));
   return SORSVD_OK;
 }
 

@@ -40,6 +40,9 @@ _lib.sorsvd_workspace_size.restype = _sz
 _lib.sorsvd_run.argtypes = [_vp, _i64, _i64, _i64, _int, _int, _int, _u64, _int, _uint,
                             _vp, _i64, _vp, _vp, _i64, _vp, _sz, _vp]
 _lib.sorsvd_run.restype = _int
+_lib.sorsvd_run_host.argtypes = [_vp, _i64, _i64, _i64, _int, _int, _int, _u64, _int, _uint,
+                                 _vp, _i64, _vp, _vp, _i64, _vp, _sz, _vp]
+_lib.sorsvd_run_host.restype = _int
 _lib.sorsvd_get_status.argtypes = [_vp, C.POINTER(_int), C.POINTER(_int), _vp]
 _lib.sorsvd_get_status.restype = _int
 _lib.sorsvd_status_string.argtypes = [_int]
@@ -147,6 +150,55 @@ def run(A: torch.Tensor, k: int, p: int, q: int, seed: int = 0, dtype=None, flag
     if check:
         st, info = get_status(workspace, stream)
         _check(st, "sorsvd_run (device)")
+    if trans:
+        U, V = V, U
+    return U, S, V
+
+
+FLAG_HOST_IO = 0x4
+
+
+def _colmajor_host(A: torch.Tensor):
+    """(ptr, rows, cols, ld, transposed) of a 2-D CPU tensor."""
+    if A.dim() != 2 or A.is_cuda:
+        raise ValueError("expected a 2-D host (CPU) tensor")
+    r, c = A.shape
+    s0, s1 = A.stride()
+    if s0 == 1 and (s1 >= max(r, 1) or c == 1):
+        return A.data_ptr(), r, c, max(s1, r), False
+    if s1 == 1 and (s0 >= max(c, 1) or r == 1):
+        return A.data_ptr(), c, r, max(s0, c), True
+    raise ValueError("A must be column-major or row-major with unit inner stride")
+
+
+def run_host(A: torch.Tensor, k: int, p: int, q: int, seed: int = 0, dtype=None, flags: int = 0,
+             workspace: torch.Tensor | None = None, stream=None, out=None, device=None):
+    """sorsvd_run_host: A and the outputs in host memory (pin them with
+    ``pin_memory()`` for asynchronous copies).  Returns host (U, S, V); they
+    hold the result once the stream has been synchronised."""
+    ptr, m, n, lda, trans = _colmajor_host(A)
+    code = dtype_code(dtype if dtype is not None else A.dtype)
+    if _TORCH_OF[code] != A.dtype:
+        raise ValueError(f"dtype code {code} does not match tensor dtype {A.dtype}")
+    od = out_dtype(code)
+    if out is None:
+        pin = A.is_pinned()
+        U = torch.empty(k, m, dtype=od, pin_memory=pin).T
+        S = torch.empty(k, dtype=od, pin_memory=pin)
+        V = torch.empty(k, n, dtype=od, pin_memory=pin).T
+    else:
+        U, S, V = out
+        if trans:
+            U, V = V, U
+    if workspace is None:
+        workspace = alloc_workspace(m, n, k, p, code, flags | FLAG_HOST_IO, device)
+    uptr, um, uk, ldu, ut = _colmajor_host(U)
+    vptr, vn, vk, ldv, vt = _colmajor_host(V)
+    if ut or vt or um != m or vn != n or uk != k or vk != k or S.is_cuda or S.numel() != k:
+        raise ValueError("outputs must be column-major host tensors U m x k, S k, V n x k")
+    _check(_lib.sorsvd_run_host(ptr, m, n, lda, k, p, q, seed & 0xFFFFFFFFFFFFFFFF, code, flags,
+                                uptr, ldu, S.data_ptr(), vptr, ldv,
+                                workspace.data_ptr(), workspace.numel(), _stream(stream)), "sorsvd_run_host")
     if trans:
         U, V = V, U
     return U, S, V
