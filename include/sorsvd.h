@@ -191,6 +191,19 @@ int sorsvd_core(const void* A, int64_t m, int64_t n, int64_t lda, int dtype, uns
  * 1 <= l <= SORSVD_MAX_L (SORSVD_MAX_L_F64 for F64). */
 int sorsvd_chol_inv(const double* G, int l, double shift_rel, int dtype, void* Rinv, void* status, void* stream);
 
+/* Polar factor used by the second CholeskyQR3 pass of sorsvd_run (fp32
+ * dtypes; Sec. III QR step): for a Gram G close to I, with D = diag(G) and
+ * I + E = D^{-1/2} G D^{-1/2}, X = D^{-1/2} (I + E)^{-1/2} by the binomial
+ * series to E^3, so that X^T G X = I and T X is an orthonormal basis of
+ * range(T) when G = T^T T.  *ok (device int) = 1 when ||E||_F <= 0.02 (the
+ * series then meets fp32 accuracy), else 0 and X must not be used (the
+ * solve then factorises with Cholesky).
+ * G: l x l binary64, column-major, ld = l.  X: l x l fp32, ld = l (full,
+ * symmetric up to the left scaling).  scratch: device memory of at least
+ * 8 l^2 + 8 (l + 31) / 32 * l + 4 l bytes.  1 <= l <= SORSVD_MAX_L. */
+int sorsvd_polar_inv(const double* G, int l, float* X, int* ok, void* scratch, size_t scratch_bytes,
+                     void* stream);
+
 /* ---- batched SOR-SVD -------------------------------------------------------
  * Many independent problems of uneven shape (m, n, k, p, q may all differ)
  * in one sequence of grouped launches: each launch runs one stage of

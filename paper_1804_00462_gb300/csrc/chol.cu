@@ -50,7 +50,9 @@ __device__ __forceinline__ int pidx(int i, int c) { return i * (i + 1) / 2 + c; 
 template <typename F>
 __global__ void __launch_bounds__(CT)
 chol_inv_kernel(const double* __restrict__ G, int l, double shift_rel, F* __restrict__ Rinv,
-                DeviceStatus* status) {
+                DeviceStatus* status, const int* done_in) {
+  // an earlier kernel has already written R^{-1}
+  if (done_in && *done_in) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   F* P = reinterpret_cast<F*>(smem_raw);
   F* dg = P + (l * (l + 1) / 2);                                  // diagonal of L
@@ -229,7 +231,10 @@ __device__ __forceinline__ F inv_col_warp(const F* D, int c, int lane, const F* 
 template <typename F>
 __device__ __forceinline__ void chol_inv_blocked_body(const double* __restrict__ G, int l, double shift_rel,
                                                       F* __restrict__ Rinv, DeviceStatus* status,
-                                                      const int* skip_in, int* conv_out, float conv_tol) {
+                                                      const int* skip_in, int* conv_out, float conv_tol,
+                                                      const int* done_in) {
+  // an earlier kernel has already written R^{-1} (and the convergence flag)
+  if (done_in && *done_in) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nb = (l + TB - 1) / TB;
   const int ntile = nb * (nb + 1) / 2;
@@ -523,15 +528,16 @@ __device__ __forceinline__ void chol_inv_blocked_body(const double* __restrict__
 template <typename F>
 __global__ void __launch_bounds__(BT)
 chol_inv_blocked_kernel(const double* __restrict__ G, int l, double shift_rel, F* __restrict__ Rinv,
-                        DeviceStatus* status, const int* skip_in, int* conv_out, float conv_tol) {
-  chol_inv_blocked_body<F>(G, l, shift_rel, Rinv, status, skip_in, conv_out, conv_tol);
+                        DeviceStatus* status, const int* skip_in, int* conv_out, float conv_tol,
+                        const int* done_in) {
+  chol_inv_blocked_body<F>(G, l, shift_rel, Rinv, status, skip_in, conv_out, conv_tol, done_in);
 }
 
 // one problem per block
 template <typename F>
 __global__ void __launch_bounds__(BT) chol_batched_kernel(const CholJob* __restrict__ jobs) {
   const CholJob& j = jobs[blockIdx.x];
-  chol_inv_blocked_body<F>(j.G, j.l, j.shift, (F*)j.Rinv, j.status, nullptr, nullptr, 0.f);
+  chol_inv_blocked_body<F>(j.G, j.l, j.shift, (F*)j.Rinv, j.status, nullptr, nullptr, 0.f, nullptr);
 }
 
 template <typename F>
@@ -554,7 +560,7 @@ size_t chol_smem(int l) {
 
 cudaError_t launch_chol_inv(const double* G, int l, double shift_rel, void* Rinv, bool f64,
                             DeviceStatus* status, cudaStream_t st, const int* skip_in, int* conv_out,
-                            float conv_tol) {
+                            float conv_tol, const int* done_in) {
   if (f64) {
     size_t sb = chol_blocked_smem<double>(l);
     if (sb <= kCholSmemMax) {
@@ -562,7 +568,7 @@ cudaError_t launch_chol_inv(const double* G, int l, double shift_rel, void* Rinv
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
       if (e != cudaSuccess) return e;
       chol_inv_blocked_kernel<double><<<1, BT, sb, st>>>(G, l, shift_rel, (double*)Rinv, status, skip_in, conv_out,
-                                                         conv_tol);
+                                                         conv_tol, done_in);
       return cudaGetLastError();
     }
     // the packed kernel always factorises and reports no convergence (the
@@ -571,7 +577,7 @@ cudaError_t launch_chol_inv(const double* G, int l, double shift_rel, void* Rinv
     size_t sm = chol_smem<double>(l);
     cudaError_t e = cudaFuncSetAttribute(chol_inv_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    chol_inv_kernel<double><<<1, CT, sm, st>>>(G, l, shift_rel, (double*)Rinv, status);
+    chol_inv_kernel<double><<<1, CT, sm, st>>>(G, l, shift_rel, (double*)Rinv, status, done_in);
   } else {
     size_t sb = chol_blocked_smem<float>(l);
     if (sb <= kCholSmemMax) {
@@ -579,14 +585,14 @@ cudaError_t launch_chol_inv(const double* G, int l, double shift_rel, void* Rinv
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
       if (e != cudaSuccess) return e;
       chol_inv_blocked_kernel<float><<<1, BT, sb, st>>>(G, l, shift_rel, (float*)Rinv, status, skip_in, conv_out,
-                                                        conv_tol);
+                                                        conv_tol, done_in);
       return cudaGetLastError();
     }
     if (conv_out && cudaMemsetAsync(conv_out, 0, sizeof(int), st) != cudaSuccess) return cudaErrorUnknown;
     size_t sm = chol_smem<float>(l);
     cudaError_t e = cudaFuncSetAttribute(chol_inv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    chol_inv_kernel<float><<<1, CT, sm, st>>>(G, l, shift_rel, (float*)Rinv, status);
+    chol_inv_kernel<float><<<1, CT, sm, st>>>(G, l, shift_rel, (float*)Rinv, status, done_in);
   }
   return cudaGetLastError();
 }

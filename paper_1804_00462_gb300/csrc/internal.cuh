@@ -17,7 +17,8 @@ namespace sorsvd {
 struct DeviceStatus {
   int code;        // first non-OK sorsvd_status raised on the device
   int info;        // bit 0: shifted Cholesky retry; bits 8..15: Jacobi sweeps
-  int pad[14];      // pad[0]: CholeskyQR3's second pass found Q orthonormal (the third is skipped)
+  int pad[14];      // pad[0]: CholeskyQR3's second pass found Q orthonormal (the third is skipped);
+                   // pad[1]: the second pass took the polar factor (its Cholesky kernel returned)
 };
 
 __device__ __forceinline__ void raise_status(DeviceStatus* st, int code) {
@@ -157,7 +158,17 @@ cudaError_t launch_jacobi_batched(const JacobiJob* jobs, int njobs, int max_l, b
 // are orthonormal to that level) and no shifted retry was needed, else 0.
 cudaError_t launch_chol_inv(const double* G, int l, double shift_rel, void* Rinv, bool f64,
                             DeviceStatus* status, cudaStream_t st, const int* skip_in = nullptr,
-                            int* conv_out = nullptr, float conv_tol = 0.f);
+                            int* conv_out = nullptr, float conv_tol = 0.f, const int* done_in = nullptr);
+
+// polar.cu: X = D^{-1/2} (I + E)^{-1/2} (binomial series to E^3) for a Gram
+// G close to I (I + E = D^{-1/2} G D^{-1/2}, D = diag G) into Rinv (fp32,
+// l x l, ld l), so that X^T G X = I.  *ok = 1 when ||E||_F <= 0.02 (the
+// series then reaches fp32 accuracy), else 0 (Rinv is not usable; the
+// Cholesky kernel given done_in = ok then factorises).  *conv (optional) =
+// *ok and max |E_ij| <= conv_tol.  scratch: polar_scratch_bytes(l), device.
+size_t polar_scratch_bytes(int l);
+cudaError_t launch_polar_inv(const double* G, int l, float* Rinv, float* scratch, int* ok, int* conv,
+                             float conv_tol, cudaStream_t st);
 
 // jacobi.cu: SVD of the l x l matrix M (binary64 input): one-sided Jacobi
 // sweeps in binary64 (f64) or fp32, binary64 finish.  Writes sigma

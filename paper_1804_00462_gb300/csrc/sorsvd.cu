@@ -31,6 +31,9 @@ int env_flag(const char* name, int dflt) {
   return v ? std::atoi(v) : dflt;
 }
 bool tc_enabled() { static const int v = env_flag("SORSVD_TC", 1); return v != 0; }
+// SORSVD_POLAR=0: the second CholeskyQR3 pass factorises (Cholesky) instead
+// of taking the polar factor of its near-identity Gram
+bool polar_enabled() { static const int v = env_flag("SORSVD_POLAR", 1); return v != 0; }
 
 constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
@@ -144,7 +147,9 @@ Layout make_layout(int64_t m, int64_t n, int l, int dt) {
   L.M = take((size_t)l * l * 8);
   L.Ut = take((size_t)l * l * acc);
   L.Vt = take((size_t)l * l * acc);
-  L.jwork = take(jacobi_work_bytes(l));
+  // the Jacobi work area doubles as the scratch of the polar second
+  // CholeskyQR pass (the two are never live at the same time)
+  L.jwork = take(std::max(jacobi_work_bytes(l), polar_scratch_bytes(l)));
   L.total = off;
   return L;
 }
@@ -322,16 +327,25 @@ int orth(const Ctx& c, void* T, int64_t rows, int64_t ld, int l, int passes, dou
     float* parts = (float*)c.at(c.L.parts);
     const int nb = (int)rb_gram_blocks(rows, l, l, true);
     int* conv = c.status()->pad;
+    int* pol_ok = c.status()->pad + 1;
     float* X = (float*)T;
     float* Y = (float*)c.at(c.L.tmp);
     for (int p = 0; p < passes; ++p) {
       const int* skip = p == 2 ? conv : nullptr;
+      // second pass: the Gram is close to I; its polar factor (series) when
+      // it converges, the Cholesky factorisation otherwise (decided on the
+      // device); the polar factor is a full matrix
+      const bool polar = p == 1 && polar_enabled();
       LAUNCH(K_SMALL_GEMM, launch_rb_gram(X, ld, X, ld, rows, l, l, true, parts, skip, c.st));
       LAUNCH(K_REDUCE, launch_reduce_parts(parts, nb, (int64_t)l * l, l, l, l, (double*)c.at(c.L.G), l, c.st));
+      if (polar)
+        LAUNCH(K_CHOL, launch_polar_inv((const double*)c.at(c.L.G), l, (float*)c.at(c.L.Rinv),
+                                        (float*)c.at(c.L.jwork), pol_ok, conv, kOrthTol, c.st));
       LAUNCH(K_CHOL, launch_chol_inv((const double*)c.at(c.L.G), l, p == 0 ? shift0 : 0.0, c.at(c.L.Rinv), false,
-                                     c.status(), c.st, skip, p == 1 ? conv : nullptr, kOrthTol));
-      LAUNCH(K_SMALL_GEMM, launch_rb_apply(X, ld, rows, l, (const float*)c.at(c.L.Rinv), l, l, true, Y, ld, nullptr,
-                                           0, 0, skip, c.st));
+                                     c.status(), c.st, skip, p == 1 ? conv : nullptr, kOrthTol,
+                                     polar ? pol_ok : nullptr));
+      LAUNCH(K_SMALL_GEMM, launch_rb_apply(X, ld, rows, l, (const float*)c.at(c.L.Rinv), l, l, !polar, Y, ld,
+                                           nullptr, 0, 0, skip, c.st));
       std::swap(X, Y);
     }
     if (X != (float*)T || kind16)
@@ -653,6 +667,17 @@ int sorsvd_chol_inv(const double* G, int l, double shift_rel, int dtype, void* R
   CK(cudaMemsetAsync(status, 0, sizeof(DeviceStatus), st));
   ProfScope ps(K_CHOL, st);
   CK(launch_chol_inv(G, l, shift_rel, Rinv, dtype == SORSVD_F64, (DeviceStatus*)status, st));
+  return SORSVD_OK;
+}
+
+int sorsvd_polar_inv(const double* G, int l, float* X, int* ok, void* scratch, size_t scratch_bytes,
+                     void* stream) {
+  if (!G || !X || !ok || !scratch || l < 1) return SORSVD_ERR_ARG;
+  if (l > SORSVD_MAX_L) return SORSVD_ERR_UNSUPPORTED;
+  if (scratch_bytes < polar_scratch_bytes(l) || ((uintptr_t)scratch) % 16) return SORSVD_ERR_WORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
+  ProfScope ps(K_CHOL, st);
+  CK(launch_polar_inv(G, l, X, (float*)scratch, ok, nullptr, 0.f, st));
   return SORSVD_OK;
 }
 

@@ -58,6 +58,8 @@ _lib.sorsvd_core.restype = _int
 
 _lib.sorsvd_chol_inv.argtypes = [_vp, _int, C.c_double, _int, _vp, _vp, _vp]
 _lib.sorsvd_chol_inv.restype = _int
+_lib.sorsvd_polar_inv.argtypes = [_vp, _int, _vp, _vp, _vp, _sz, _vp]
+_lib.sorsvd_polar_inv.restype = _int
 
 lib = _lib
 
@@ -275,6 +277,22 @@ def chol_inv(G: torch.Tensor, shift_rel: float, dtype=F32, stream=None):
            "sorsvd_chol_inv")
     s, info = get_status(st, stream)
     return R, s, info
+
+
+def polar_inv(G: torch.Tensor, stream=None):
+    """Polar factor X = D^{-1/2} (I + E)^{-1/2} of a near-identity binary64
+    Gram G (l x l CUDA tensor), fp32.  Returns (X, ok)."""
+    if G.dtype != torch.float64 or G.dim() != 2 or G.shape[0] != G.shape[1]:
+        raise ValueError("G must be a square binary64 CUDA tensor")
+    l = G.shape[0]
+    Gc = G.T.contiguous().T if G.stride(0) != 1 else G
+    X = colmajor_empty(l, l, torch.float32, G.device)
+    ok = torch.full((1,), -1, dtype=torch.int32, device=G.device)
+    nb = 8 * l * l + 8 * ((l + 31) // 32) * l + 4 * l
+    scratch = torch.empty(nb, dtype=torch.uint8, device=G.device)
+    _check(_lib.sorsvd_polar_inv(Gc.data_ptr(), l, X.data_ptr(), ok.data_ptr(), scratch.data_ptr(), nb,
+                                 _stream(stream)), "sorsvd_polar_inv")
+    return X, int(ok.item())
 
 
 # ---- batched SOR-SVD ----------------------------------------------------------

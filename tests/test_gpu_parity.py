@@ -313,6 +313,36 @@ def test_chol_inv_retry_and_breakdown(nat):
     assert np.array_equal(R.cpu().numpy(), np.eye(20, dtype=np.float32))
 
 
+@pytest.mark.parametrize("l,scale", [(1, 0.0), (17, 1e-3), (64, 1e-6), (110, 1e-4), (266, 2e-5), (320, 1e-5)])
+def test_polar_inv_near_identity(nat, l, scale):
+    # G = D^{1/2} (I + E) D^{1/2}, E symmetric with zero diagonal and
+    # ||E||_F <= 0.02: X must equal D^{-1/2} (I + E)^{-1/2}, taken here from
+    # an eigendecomposition (independent of the kernel's series), and
+    # satisfy X^T G X = I to fp32 level
+    g = np.random.default_rng(l)
+    E = g.standard_normal((l, l)) * scale
+    E = (E + E.T) / 2
+    np.fill_diagonal(E, 0.0)
+    assert np.linalg.norm(E) <= 0.02
+    d = np.exp(g.uniform(-1.0, 1.0, l))
+    G = d[:, None] * (np.eye(l) + E) * d[None, :]
+    X, ok = nat.polar_inv(torch.from_numpy(G).cuda())
+    assert ok == 1
+    X = to_np(X)
+    w, Qe = np.linalg.eigh(np.eye(l) + E)
+    P = (Qe * w ** -0.5) @ Qe.T
+    assert np.max(np.abs(X * d[:, None] - P)) <= 1e-6
+    assert np.max(np.abs(X.T @ G @ X - np.eye(l))) <= 1e-5
+
+
+def test_polar_inv_declines_far_from_identity(nat):
+    g = np.random.default_rng(3)
+    T = g.standard_normal((400, 60))
+    T[:, 1] += 0.5 * T[:, 0]                        # columns far from orthonormal
+    X, ok = nat.polar_inv(torch.from_numpy(T.T @ T).cuda())
+    assert ok == 0
+
+
 @pytest.mark.parametrize("dt,l", [("f32", 129), ("f32", 200), ("bf16", 266), ("tf32", 288), ("f32", 320)])
 def test_run_large_sketch(nat, dt, l):
     """l beyond one SM's shared memory for the Jacobi sweep (cooperative grid
