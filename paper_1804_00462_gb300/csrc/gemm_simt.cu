@@ -234,6 +234,62 @@ transpose32_kernel(const float* __restrict__ A, int64_t lda, int64_t rows, int64
   }
 }
 
+// The same transpose in 64 x 64 tiles with 8-byte accesses: a lane moves
+// two consecutive rows (loads) or columns (stores), so each thread keeps 8
+// loads of 8 bytes in flight (the 32 x 32 kernel: 4 of 4 bytes), enough to
+// cover HBM latency at full bandwidth.  Needs lda, ldt even and 8-byte
+// aligned A, At; ragged edges fall back to scalar accesses.
+__global__ void __launch_bounds__(256)
+transpose64_kernel(const float* __restrict__ A, int64_t lda, int64_t rows, int64_t cols, float* __restrict__ At,
+                   int64_t ldt) {
+  __shared__ float tile[64][65];                  // tile[c][r]
+  const int64_t r0 = (int64_t)blockIdx.x * 64, c0 = (int64_t)blockIdx.y * 64;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+  const bool full = r0 + 64 <= rows && c0 + 64 <= cols;
+  if (full) {
+    float2 v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      v[k] = *reinterpret_cast<const float2*>(A + (r0 + 2 * tx) + (c0 + ty + 8 * k) * lda);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      tile[ty + 8 * k][2 * tx] = v[k].x;
+      tile[ty + 8 * k][2 * tx + 1] = v[k].y;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int64_t c = c0 + ty + 8 * k;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int64_t r = r0 + 2 * tx + h;
+        tile[ty + 8 * k][2 * tx + h] = (r < rows && c < cols) ? A[r + c * lda] : 0.f;
+      }
+    }
+  }
+  __syncthreads();
+  if (full) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int rr = ty + 8 * k;
+      float2 w;
+      w.x = tile[2 * tx][rr];
+      w.y = tile[2 * tx + 1][rr];
+      *reinterpret_cast<float2*>(At + (c0 + 2 * tx) + (r0 + rr) * ldt) = w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int64_t r = r0 + ty + 8 * k;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int64_t c = c0 + 2 * tx + h;
+        if (c < cols && r < rows) At[c + r * ldt] = tile[2 * tx + h][ty + 8 * k];
+      }
+    }
+  }
+}
+
 inline int grid_for(int64_t total) {
   int64_t b = (total + 255) / 256;
   int64_t cap = (int64_t)num_sms() * 16;
@@ -293,6 +349,13 @@ cudaError_t launch_convert_f32(const float* x, int64_t ldx, int64_t rows, int64_
 cudaError_t launch_transpose_f32(const float* A, int64_t lda, int64_t rows, int64_t cols, float* At, int64_t ldt,
                                  cudaStream_t st) {
   if (rows <= 0 || cols <= 0) return cudaSuccess;
+  const bool pairs = !(lda & 1) && !(ldt & 1) && !(reinterpret_cast<uintptr_t>(A) & 7) &&
+                     !(reinterpret_cast<uintptr_t>(At) & 7);
+  if (pairs && (cols + 63) / 64 <= 65535) {
+    dim3 grid((unsigned)((rows + 63) / 64), (unsigned)((cols + 63) / 64));
+    transpose64_kernel<<<grid, 256, 0, st>>>(A, lda, rows, cols, At, ldt);
+    return cudaGetLastError();
+  }
   dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((cols + 31) / 32));
   if (grid.y > 65535) return cudaErrorInvalidValue;
   transpose32_kernel<<<grid, 256, 0, st>>>(A, lda, rows, cols, At, ldt);

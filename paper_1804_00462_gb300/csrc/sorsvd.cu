@@ -494,7 +494,7 @@ int upload_a(const Ctx& c, const void* Ah, int64_t lda, int64_t m, int64_t n, vo
   const size_t col_bytes = std::max<size_t>(1, (size_t)m * esz);
   int64_t cols = std::max<int64_t>(1, (int64_t)((size_t)(64u << 20) / col_bytes));
   const int nblk = (int)std::min<int64_t>(32, (n + cols - 1) / cols);
-  cols = (n + nblk - 1) / nblk;
+  cols = ((n + nblk - 1) / nblk + 63) / 64 * 64;   // whole 64-column tiles of the transpose
   auto copy_cols = [&](int64_t j0, int64_t j1, cudaStream_t st) {
     return cudaMemcpy2DAsync((char*)Ad + (size_t)j0 * ldd * esz, (size_t)ldd * esz,
                              (const char*)Ah + (size_t)j0 * lda * esz, (size_t)lda * esz, (size_t)m * esz,
