@@ -310,24 +310,27 @@ __global__ void rb_copy_kernel(const float* __restrict__ src, float* __restrict_
 }
 
 // out[i + j ldo] = sum_s parts[s * stride + i + j ldp] (binary64) for an
-// rows x cols result.  Four threads per element: thread u sums the
-// partials u, u + 4, ... in index order with Neumaier's compensation in
-// fp32 (error ~ 2 eps |sum| plus second-order terms), then the four
-// (sum + compensation) values are added in binary64 in a fixed xor order:
-// deterministic.  Neighbouring elements sit in neighbouring thread groups,
-// so every partial is read in coalesced runs.
+// rows x cols result.  kRedLanes threads per element: thread u sums the
+// partials u, u + kRedLanes, ... in index order with Neumaier's
+// compensation in fp32 (error ~ 2 eps |sum| plus second-order terms), then
+// the (sum + compensation) values are added in binary64 in a fixed xor
+// order: deterministic.  More lanes per element mean more independent
+// chains and loads in flight (the sum is latency-bound: a few MB from L2).
+// Neighbouring elements sit in neighbouring thread groups, so every partial
+// is read in runs of neighbouring addresses.
+constexpr int kRedLanes = 8;
 __global__ void reduce_parts_kernel(const float* __restrict__ parts, int nparts, int64_t stride, int rows,
                                     int cols, int ldp, double* __restrict__ out, int ldo) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t e = g >> 2;
-  const int u = (int)(g & 3);
+  const int64_t e = g / kRedLanes;
+  const int u = (int)(g % kRedLanes);
   const bool ok = e < (int64_t)rows * cols;
   float s = 0.f, c = 0.f;
   if (ok) {
     const int j = (int)(e / rows), i = (int)(e - (int64_t)j * rows);
     const float* p = parts + i + (int64_t)j * ldp;
 #pragma unroll 4
-    for (int q = u; q < nparts; q += 4) {
+    for (int q = u; q < nparts; q += kRedLanes) {
       const float x = p[(int64_t)q * stride];
       const float t = __fadd_rn(s, x);
       c = __fadd_rn(c, fabsf(s) >= fabsf(x) ? __fadd_rn(__fsub_rn(s, t), x) : __fadd_rn(__fsub_rn(x, t), s));
@@ -335,8 +338,8 @@ __global__ void reduce_parts_kernel(const float* __restrict__ parts, int nparts,
     }
   }
   double v = (double)s + (double)c;
-  v += __shfl_xor_sync(0xffffffffu, v, 1);
-  v += __shfl_xor_sync(0xffffffffu, v, 2);
+#pragma unroll
+  for (int o = 1; o < kRedLanes; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   if (ok && u == 0) {
     const int j = (int)(e / rows), i = (int)(e - (int64_t)j * rows);
     out[i + (int64_t)j * ldo] = v;
@@ -422,7 +425,7 @@ cudaError_t launch_rb_copy(const float* src, float* dst, int64_t ld, int64_t row
 
 cudaError_t launch_reduce_parts(const float* parts, int nparts, int64_t stride, int rows, int cols, int ldp,
                                      double* out, int ldo, cudaStream_t st) {
-  const int64_t threads = (int64_t)rows * cols * 4;
+  const int64_t threads = (int64_t)rows * cols * kRedLanes;
   if (threads <= 0) return cudaSuccess;
   reduce_parts_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(parts, nparts, stride, rows, cols, ldp, out,
                                                                      ldo);
