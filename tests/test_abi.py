@@ -82,6 +82,57 @@ def test_run_rejects_bad_arguments_before_any_device_work():
     assert call(ws=0x1000, wsb=16) == 7             # too small
 
 
+def test_run_host_sizes_and_rejects_bad_arguments_before_any_device_work():
+    lib = _lib()
+    ws = lib.sorsvd_workspace_size
+    ws.argtypes = [C.c_int64, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_uint]
+    ws.restype = C.c_size_t
+    host_io = 0x4
+    for m, n, k, p, dt, esz in ((20000, 10000, 100, 10, 1, 4), (1000, 700, 20, 5, 3, 2), (300, 200, 10, 4, 0, 8)):
+        base, host = ws(m, n, k, p, dt, 0), ws(m, n, k, p, dt, host_io)
+        acc = 8 if dt == 0 else 4
+        # the device copies of A, U, S, V come on top of the solve's workspace
+        assert host >= base + m * n * esz + (m * k + k + n * k) * acc
+        assert host % 256 == 0
+    assert ws(10, 1000, 20, 5, 1, host_io) == 0     # l > min(m, n)
+    f = lib.sorsvd_run_host
+    f.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_int,
+                  C.c_uint, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_size_t,
+                  C.c_void_p]
+    fake = 0x1000
+    ok = dict(A=fake, m=100, n=80, lda=100, k=5, p=5, q=1, seed=0, dt=1, fl=0, U=fake, ldu=100, S=fake,
+              V=fake, ldv=80, ws=None, wsb=0, st=None)
+
+    def call(**kw):
+        a = dict(ok, **kw)
+        return f(a["A"], a["m"], a["n"], a["lda"], a["k"], a["p"], a["q"], a["seed"], a["dt"], a["fl"],
+                 a["U"], a["ldu"], a["S"], a["V"], a["ldv"], a["ws"], a["wsb"], a["st"])
+    assert call(A=None) == 1
+    assert call(S=None) == 1
+    assert call(lda=99) == 1
+    assert call(k=80, p=1) == 1
+    assert call(fl=0x80) == 1
+    assert call(dt=7) == 2
+    assert call() == 7                              # no workspace
+    assert call(fl=host_io) == 7                    # the flag is accepted; still no workspace
+    # a workspace that fits sorsvd_run but not the device copies of A and the factors
+    base = ws(100, 80, 5, 5, 1, 0)
+    assert call(ws=0x100000, wsb=base) == 7
+    assert call(ws=0x100010, wsb=1 << 30) == 7      # misaligned
+
+
+def test_polar_inv_rejects_bad_arguments_before_any_device_work():
+    lib = _lib()
+    f = lib.sorsvd_polar_inv
+    f.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
+    fake = 0x1000
+    assert f(None, 10, fake, fake, fake, 1 << 20, None) == 1
+    assert f(fake, 0, fake, fake, fake, 1 << 20, None) == 1
+    assert f(fake, 321, fake, fake, fake, 1 << 30, None) == 8    # beyond SORSVD_MAX_L
+    assert f(fake, 110, fake, fake, fake, 16, None) == 7         # scratch too small
+    assert f(fake, 110, fake, fake, fake + 4, 1 << 20, None) == 7  # scratch misaligned
+
+
 def test_rpca_rejects_bad_arguments_before_any_device_work():
     from paper_1804_00462_gb300 import native as nat
     lib = nat.lib
