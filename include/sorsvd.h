@@ -154,8 +154,10 @@ const char* sorsvd_status_string(int status);
 /* Gaussian test matrix Omega (Sec. III, "standard Gaussian matrix"):
  * out[i + j*ld] for i < rows, j < cols is the N(0,1) value of linear element
  * e = i + rows*j drawn from Philox4x64-10 with key (seed, 0) and counter
- * (e / 4, stream_id, 0, 0), Box-Muller on word pairs, rounded to `dtype`
- * (binary64 -> fp32 RNE -> 16-bit RNE).  Bit-identical to the CPU oracle. */
+ * (e / 4, stream_id, 0, 0), Box-Muller on word pairs with the transform
+ * in binary32 (series in correctly rounded operations); the binary32 value
+ * is stored as is (F64: exactly; F32 / TF32) or rounded to the 16-bit type
+ * (RNE).  Bit-identical to the CPU oracle. */
 int sorsvd_gaussian(void* out, int64_t rows, int64_t cols, int64_t ld,
                     uint64_t seed, uint64_t stream_id, int dtype, void* stream);
 

@@ -15,23 +15,27 @@ and on the GPU:
   0x9E3779B97F4A7C15 / 0xBB67AE8584CAA73B.
 * key = (seed, 0); counter = (g, stream, 0, 0) where g = e // 4 is the group of
   four column-major elements e = i + rows * j of Omega and stream = 0 for Omega.
-* each 64-bit word x gives u = ((x >> 12) + 1/2) * 2^-52, strictly inside (0, 1).
+* each 64-bit word x gives u = ((x >> 41) + 1/2) * 2^-23, a binary32 value
+  strictly inside (0, 1) (both steps exact in binary32).
 * Box-Muller on the word pairs (w0, w1) -> elements 4g, 4g+1 and
   (w2, w3) -> elements 4g+2, 4g+3: z_even = r cos(2 pi u_b), z_odd = r sin(2 pi u_b),
   r = sqrt(-2 ln u_a).
-* ln and sin/cos are evaluated from series written out below using only
-  correctly rounded +, -, *, / and sqrt (no fused multiply-add, no libm), so
-  every step has exactly one IEEE-754 binary64 rounding:
+* the transform runs in IEEE-754 binary32 (the GPU's binary64 rate is a
+  small fraction of its binary32 rate), from series written out below using
+  only correctly rounded +, -, *, / and sqrt (no fused multiply-add, no
+  libm), so every step has exactly one binary32 rounding:
     ln u: u = f 2^e with f in [sqrt(1/2), sqrt(2)); s = (f-1)/(f+1);
-          ln f = 2 s (1 + s^2/3 + s^4/5 + ... + s^24/25)  (atanh series);
+          ln f = 2 s (1 + s^2/3 + s^4/5 + ... + s^10/11)  (atanh series;
+          |s| <= 0.172, so the next term is below 2^-24 relative);
           ln u = e*ln2 + ln f.
     sin/cos(2 pi u): t = 4u, q = rint(t), r = t - q in [-1/2, 1/2] (exact),
-          theta = r * (pi/2); Taylor series of sin and cos to theta^19 and
-          theta^18 with coefficients 1/n! (n! exact in binary64 for n <= 22);
-          the quadrant q mod 4 selects +-sin / +-cos.
-* reduced-precision Omega (fp32, bf16, fp16, tf32-in-fp32) is the binary64
-  value rounded to fp32 with round-to-nearest-even, then (bf16 / fp16) rounded
-  again to the 16-bit format with round-to-nearest-even.
+          theta = r * (pi/2); Taylor series of sin and cos to theta^11 and
+          theta^12 with coefficients 1/n! rounded to binary32; the quadrant
+          q mod 4 selects +-sin / +-cos.
+  The binary32 constants (ln 2, pi/2, sqrt(1/2) and the coefficients) are
+  the nearest binary32 values of the exact numbers.
+* Omega is the binary32 value (exact in binary64 for F64); bf16 / fp16
+  round it to the 16-bit format with round-to-nearest-even.
 """
 from __future__ import annotations
 
@@ -46,16 +50,20 @@ _W1 = np.uint64(0xBB67AE8584CAA73B)
 _LO32 = np.uint64(0xFFFFFFFF)
 _S32 = np.uint64(32)
 
-# ln 2 and pi/2 as the nearest binary64 values.
-_LN2 = 0.6931471805599453
-_HALF_PI = 1.5707963267948966
-_SQRT_HALF = 0.7071067811865476
+_F32 = np.float32
+# ln 2, pi/2 and sqrt(1/2) as the nearest binary32 values (0x3F317218,
+# 0x3FC90FDB, 0x3F3504F3).
+_LN2 = _F32(0.6931471805599453)
+_HALF_PI = _F32(1.5707963267948966)
+_SQRT_HALF = _F32(0.7071067811865476)
 
-# atanh-series coefficients 1/(2i+1), i = 0..12, each one correctly rounded division.
-_LOG_C = [1.0 / float(2 * i + 1) for i in range(13)]
-# sin: (-1)^i / (2i+1)!, i = 1..9 ; cos: (-1)^i / (2i)!, i = 1..9.
-_SIN_C = [(-1.0) ** i * (1.0 / float(math.factorial(2 * i + 1))) for i in range(1, 10)]
-_COS_C = [(-1.0) ** i * (1.0 / float(math.factorial(2 * i))) for i in range(1, 10)]
+# atanh-series coefficients 1/(2i+1), i = 0..5; sin: (-1)^i / (2i+1)!,
+# i = 1..5; cos: (-1)^i / (2i)!, i = 1..6; each the nearest binary32 value
+# (the binary64 quotient rounded once more to binary32 lands on it for all
+# of these: pinned against exact rationals in the tests).
+_LOG_C = [_F32(1.0 / float(2 * i + 1)) for i in range(6)]
+_SIN_C = [_F32((-1.0) ** i * (1.0 / float(math.factorial(2 * i + 1)))) for i in range(1, 6)]
+_COS_C = [_F32((-1.0) ** i * (1.0 / float(math.factorial(2 * i)))) for i in range(1, 7)]
 
 
 def _mulhilo(a: np.ndarray, b: np.uint64):
@@ -91,29 +99,35 @@ def philox4x64_10(ctr: np.ndarray, key) -> np.ndarray:
 
 
 def uniform_from_u64(x: np.ndarray) -> np.ndarray:
-    """Map 64-bit words to doubles strictly inside (0, 1) exactly."""
-    return ((x >> np.uint64(12)).astype(np.float64) + 0.5) * (2.0 ** -52)
+    """Map 64-bit words to binary32 values strictly inside (0, 1) exactly:
+    ((x >> 41) + 1/2) * 2^-23 (23-bit integer plus one half: 24 bits)."""
+    k = (np.asarray(x, dtype=np.uint64) >> np.uint64(41)).astype(np.float32)
+    return (k + _F32(0.5)) * _F32(2.0 ** -23)
 
 
 def ln_series(u: np.ndarray) -> np.ndarray:
-    """Natural log of u in (0, 1] from the atanh series (see module doc)."""
+    """Natural log of binary32 u in (0, 1] from the atanh series, every
+    operation one binary32 rounding (see module doc)."""
+    u = np.asarray(u, dtype=np.float32)
     fr, ex = np.frexp(u)                     # u = fr * 2^ex, fr in [0.5, 1)
     small = fr < _SQRT_HALF
-    f = np.where(small, fr * 2.0, fr)
-    e = np.where(small, ex - 1, ex).astype(np.float64)
-    s = (f - 1.0) / (f + 1.0)
+    f = np.where(small, fr * _F32(2.0), fr).astype(np.float32)
+    e = np.where(small, ex - 1, ex).astype(np.float32)
+    s = (f - _F32(1.0)) / (f + _F32(1.0))
     s2 = s * s
     p = np.full_like(s, _LOG_C[-1])
     for c in reversed(_LOG_C[:-1]):
         p = p * s2
         p = p + c
-    lnf = (2.0 * s) * p
+    lnf = (_F32(2.0) * s) * p
     return e * _LN2 + lnf
 
 
 def sincos_2pi(u: np.ndarray):
-    """(sin(2 pi u), cos(2 pi u)) for u in (0, 1) (see module doc)."""
-    t = 4.0 * u
+    """(sin(2 pi u), cos(2 pi u)) in binary32 for binary32 u in (0, 1) (see
+    module doc)."""
+    u = np.asarray(u, dtype=np.float32)
+    t = _F32(4.0) * u
     q = np.rint(t)
     r = t - q
     th = r * _HALF_PI
@@ -127,15 +141,16 @@ def sincos_2pi(u: np.ndarray):
     for c in reversed(_COS_C[:-1]):
         pc = pc * x2
         pc = pc + c
-    c_ = 1.0 + x2 * pc
+    c_ = _F32(1.0) + x2 * pc
     quad = q.astype(np.int64) & 3
     sin_v = np.select([quad == 0, quad == 1, quad == 2], [s, c_, -s], -c_)
     cos_v = np.select([quad == 0, quad == 1, quad == 2], [c_, -s, -c_], s)
-    return sin_v, cos_v
+    return sin_v.astype(np.float32), cos_v.astype(np.float32)
 
 
 def gaussian_elements(e: np.ndarray, seed: int, stream: int = 0) -> np.ndarray:
-    """Standard normal values of the linear element indices ``e`` (binary64)."""
+    """Standard normal values of the linear element indices ``e`` (binary32
+    values, returned as binary64)."""
     e = np.asarray(e, dtype=np.uint64)
     g = e >> np.uint64(2)
     ctr = np.zeros((e.size, 4), dtype=np.uint64)
@@ -148,9 +163,10 @@ def gaussian_elements(e: np.ndarray, seed: int, stream: int = 0) -> np.ndarray:
     wb = np.where(hi_pair, w[:, 3], w[:, 1])
     ua = uniform_from_u64(wa)
     ub = uniform_from_u64(wb)
-    r = np.sqrt(-2.0 * ln_series(ua))
+    r = np.sqrt(_F32(-2.0) * ln_series(ua))
     sn, cs = sincos_2pi(ub)
-    return np.where((lane & 1) == 0, r * cs, r * sn)
+    z = np.where((lane & 1) == 0, r * cs, r * sn).astype(np.float32)
+    return z.astype(np.float64)             # binary32 values, exact in binary64
 
 
 def round_fp32(x: np.ndarray) -> np.ndarray:

@@ -4,18 +4,21 @@
 // Generator (published definitions, implemented here from scratch):
 //   Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): key (seed, 0),
 //   counter (e / 4, stream_id, 0, 0) for column-major element e of Omega.
-//   Each word x -> u = ((x >> 12) + 1/2) 2^-52 in (0, 1).
+//   Each word x -> u = ((x >> 41) + 1/2) 2^-23, a binary32 value in (0, 1).
 //   Box-Muller on (w0, w1) -> elements 4g, 4g+1 and (w2, w3) -> 4g+2, 4g+3:
 //   z = sqrt(-2 ln u_a) * {cos, sin}(2 pi u_b).
-// ln and sin/cos are series evaluated with one explicitly rounded IEEE
-// operation per step (__dadd_rn / __dmul_rn / __ddiv_rn / __dsqrt_rn, which
-// the compiler may not fuse), so the result depends only on IEEE-754 and is
-// identical on any conforming implementation:
+// The transform runs in binary32 (GB300's binary64 rate is 1/64 of its
+// binary32 rate): ln and sin/cos are series evaluated with one explicitly
+// rounded IEEE operation per step (__fadd_rn / __fmul_rn / __fdiv_rn /
+// __fsqrt_rn, which the compiler may not fuse), so the result depends only
+// on IEEE-754 and is identical on any conforming implementation:
 //   ln u : u = f 2^e, f in [sqrt(1/2), sqrt(2)); s = (f-1)/(f+1);
-//          ln f = 2 s sum_{i=0}^{12} s^{2i}/(2i+1)  (atanh series, Horner in s^2)
+//          ln f = 2 s sum_{i=0}^{5} s^{2i}/(2i+1)  (atanh series, Horner in s^2)
 //   2 pi u: t = 4u, q = rint(t), r = t - q, theta = r * pi/2;
-//          sin, cos by Taylor series to theta^19 / theta^18 (Horner in theta^2),
+//          sin, cos by Taylor series to theta^11 / theta^12 (Horner in theta^2),
 //          then rotated by the quadrant q mod 4.
+// Constants: the nearest binary32 values of ln 2, pi/2, sqrt(1/2) and of the
+// series coefficients.
 #include "internal.cuh"
 
 #include <algorithm>
@@ -36,58 +39,56 @@ __device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64
   }
 }
 
-__device__ __forceinline__ double unit_open(uint64_t x) {
-  double v = __ull2double_rn(x >> 12);           // exact: < 2^52
-  return __dmul_rn(__dadd_rn(v, 0.5), 0x1p-52);   // both exact
+// ((x >> 41) + 1/2) 2^-23: both steps exact in binary32
+__device__ __forceinline__ float unit_open(uint64_t x) {
+  const float k = (float)(uint32_t)(x >> 41);       // < 2^23: exact
+  return __fmul_rn(__fadd_rn(k, 0.5f), 0x1p-23f);
 }
 
-// 1/(2i+1), i = 0..12 (each a correctly rounded quotient of exact integers)
-__constant__ double kLogC[13] = {1.0 / 1.0, 1.0 / 3.0, 1.0 / 5.0, 1.0 / 7.0, 1.0 / 9.0,
-                                 1.0 / 11.0, 1.0 / 13.0, 1.0 / 15.0, 1.0 / 17.0, 1.0 / 19.0,
-                                 1.0 / 21.0, 1.0 / 23.0, 1.0 / 25.0};
-// (-1)^i / (2i+1)!, i = 1..9
-__constant__ double kSinC[9] = {-(1.0 / 6.0), 1.0 / 120.0, -(1.0 / 5040.0), 1.0 / 362880.0,
-                                -(1.0 / 39916800.0), 1.0 / 6227020800.0, -(1.0 / 1307674368000.0),
-                                1.0 / 355687428096000.0, -(1.0 / 121645100408832000.0)};
-// (-1)^i / (2i)!, i = 1..9
-__constant__ double kCosC[9] = {-(1.0 / 2.0), 1.0 / 24.0, -(1.0 / 720.0), 1.0 / 40320.0,
-                                -(1.0 / 3628800.0), 1.0 / 479001600.0, -(1.0 / 87178291200.0),
-                                1.0 / 20922789888000.0, -(1.0 / 6402373705728000.0)};
+// 1/(2i+1), i = 0..5
+__constant__ float kLogC[6] = {0x1p+0f, 0x1.555556p-2f, 0x1.99999ap-3f, 0x1.24924ap-3f, 0x1.c71c72p-4f,
+                               0x1.745d18p-4f};
+// (-1)^i / (2i+1)!, i = 1..5
+__constant__ float kSinC[5] = {-0x1.555556p-3f, 0x1.111112p-7f, -0x1.a01a02p-13f, 0x1.71de3ap-19f,
+                               -0x1.ae6456p-26f};
+// (-1)^i / (2i)!, i = 1..6
+__constant__ float kCosC[6] = {-0x1p-1f, 0x1.555556p-5f, -0x1.6c16c2p-10f, 0x1.a01a02p-16f, -0x1.27e4fcp-22f,
+                               0x1.1eed8ep-29f};
 
-__device__ __forceinline__ double ln_series(double u) {
-  const double LN2 = 0.6931471805599453, SQRT_HALF = 0.7071067811865476;
-  long long b = __double_as_longlong(u);
-  int ex = (int)((b >> 52) & 0x7FF) - 1022;                       // u normal
-  double fr = __longlong_as_double((b & 0x800FFFFFFFFFFFFFll) | (1022ll << 52));  // [0.5, 1)
-  double f = fr;
+__device__ __forceinline__ float ln_series(float u) {
+  const float LN2 = 0x1.62e430p-1f, SQRT_HALF = 0x1.6a09e6p-1f;
+  const uint32_t b = __float_as_uint(u);
+  const int ex = (int)((b >> 23) & 0xFF) - 126;                     // u normal: u = fr 2^ex
+  const float fr = __uint_as_float((b & 0x807FFFFFu) | (126u << 23));   // [0.5, 1)
+  float f = fr;
   int e = ex;
-  if (fr < SQRT_HALF) { f = __dmul_rn(fr, 2.0); e = ex - 1; }
-  double s = __ddiv_rn(__dsub_rn(f, 1.0), __dadd_rn(f, 1.0));
-  double s2 = __dmul_rn(s, s);
-  double p = kLogC[12];
+  if (fr < SQRT_HALF) { f = __fmul_rn(fr, 2.0f); e = ex - 1; }
+  const float s = __fdiv_rn(__fsub_rn(f, 1.0f), __fadd_rn(f, 1.0f));
+  const float s2 = __fmul_rn(s, s);
+  float p = kLogC[5];
 #pragma unroll
-  for (int i = 11; i >= 0; --i) p = __dadd_rn(__dmul_rn(p, s2), kLogC[i]);
-  double lnf = __dmul_rn(__dmul_rn(2.0, s), p);
-  return __dadd_rn(__dmul_rn((double)e, LN2), lnf);
+  for (int i = 4; i >= 0; --i) p = __fadd_rn(__fmul_rn(p, s2), kLogC[i]);
+  const float lnf = __fmul_rn(__fmul_rn(2.0f, s), p);
+  return __fadd_rn(__fmul_rn((float)e, LN2), lnf);
 }
 
-__device__ __forceinline__ void sincos_2pi(double u, double* sn, double* cs) {
-  const double HALF_PI = 1.5707963267948966;
-  double t = __dmul_rn(4.0, u);
-  double q = rint(t);
-  double r = __dsub_rn(t, q);
-  double th = __dmul_rn(r, HALF_PI);
-  double x2 = __dmul_rn(th, th);
-  double ps = kSinC[8];
+__device__ __forceinline__ void sincos_2pi(float u, float* sn, float* cs) {
+  const float HALF_PI = 0x1.921fb6p+0f;
+  const float t = __fmul_rn(4.0f, u);
+  const float q = rintf(t);
+  const float r = __fsub_rn(t, q);
+  const float th = __fmul_rn(r, HALF_PI);
+  const float x2 = __fmul_rn(th, th);
+  float ps = kSinC[4];
 #pragma unroll
-  for (int i = 7; i >= 0; --i) ps = __dadd_rn(__dmul_rn(ps, x2), kSinC[i]);
-  double s = __dadd_rn(th, __dmul_rn(__dmul_rn(th, x2), ps));
-  double pc = kCosC[8];
+  for (int i = 3; i >= 0; --i) ps = __fadd_rn(__fmul_rn(ps, x2), kSinC[i]);
+  const float s = __fadd_rn(th, __fmul_rn(__fmul_rn(th, x2), ps));
+  float pc = kCosC[5];
 #pragma unroll
-  for (int i = 7; i >= 0; --i) pc = __dadd_rn(__dmul_rn(pc, x2), kCosC[i]);
-  double c = __dadd_rn(1.0, __dmul_rn(x2, pc));
-  int quad = ((int)q) & 3;
-  double sv, cv;
+  for (int i = 4; i >= 0; --i) pc = __fadd_rn(__fmul_rn(pc, x2), kCosC[i]);
+  const float c = __fadd_rn(1.0f, __fmul_rn(x2, pc));
+  const int quad = ((int)q) & 3;
+  float sv, cv;
   if (quad == 0) { sv = s; cv = c; }
   else if (quad == 1) { sv = c; cv = -s; }
   else if (quad == 2) { sv = -s; cv = -c; }
@@ -105,22 +106,22 @@ __device__ __forceinline__ void gaussian_body(T* __restrict__ out, int64_t rows,
        g += (int64_t)gridDim.x * blockDim.x) {
     uint64_t c[4] = {(uint64_t)g, stream_id, 0ull, 0ull};
     philox4x64_10(c, seed, 0ull);
-    double z[4];
+    float z[4];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      double ua = unit_open(c[2 * h]), ub = unit_open(c[2 * h + 1]);
-      double r = __dsqrt_rn(__dmul_rn(-2.0, ln_series(ua)));
-      double sn, cs;
+      const float ua = unit_open(c[2 * h]), ub = unit_open(c[2 * h + 1]);
+      const float r = __fsqrt_rn(__fmul_rn(-2.0f, ln_series(ua)));
+      float sn, cs;
       sincos_2pi(ub, &sn, &cs);
-      z[2 * h] = __dmul_rn(r, cs);
-      z[2 * h + 1] = __dmul_rn(r, sn);
+      z[2 * h] = __fmul_rn(r, cs);
+      z[2 * h + 1] = __fmul_rn(r, sn);
     }
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
       int64_t e = 4 * g + h;
       if (e < total) {
         int64_t j = e / rows, i = e - j * rows;
-        out[i + j * ld] = from_f64<T>(z[h]);
+        out[i + j * ld] = from_f32<T>(z[h]);
       }
     }
   }
@@ -147,8 +148,9 @@ cudaError_t launch_gaussian(void* out, int64_t rows, int64_t cols, int64_t ld, u
   int64_t groups = (rows * cols + 3) / 4;
   int threads = 256;
   int64_t blocks = (groups + threads - 1) / threads;
-  // binary64-ALU bound: two blocks per SM keep the FP64 pipes busy and
-  // leave the SMs' other thread slots to a memory-bound kernel beside it
+  // ALU bound (Philox's 64-bit products, the binary32 series): two blocks
+  // per SM leave the SMs' other thread slots to a memory-bound kernel that
+  // may run beside it (the transposed copy of A)
   int cap = num_sms() * 2;
   if (blocks > cap) blocks = cap;
   switch (dtype) {
