@@ -11,14 +11,18 @@
 // column of a column-major A per stage (KA x 128 bytes); MT = 2 halves the
 // re-reads of B from L2.
 //
-// Work decomposition: a persistent grid of G <= #SM CTAs splits the
+// Work decomposition: a persistent grid of G <= #SM units splits the
 // tiles x K-stages iteration space into G contiguous ranges ("stream-K"),
-// so every SM streams the same share of A whatever the tile count.  A CTA
-// walks its range as segments (one per output tile it touches).  A segment
-// that covers a whole tile is written straight to the output; the at most
-// two partial segments of a CTA (head and tail of its range) go to a
-// per-CTA partial buffer and a fix-up kernel sums them per tile in CTA
-// order: the result is deterministic and uses no atomics.
+// so every SM streams the same share of A whatever the tile count.  A unit
+// is one CTA, or (PAIR) a cluster of two CTAs that take the two 128 MT-row
+// halves of each unit tile and share every B stage (each CTA loads part of
+// it by TMA multicast into both).  A unit walks its range as segments (one
+// per output tile it touches).  A segment that covers a whole tile is
+// written straight to the output; the at most two partial segments of a CTA
+// (head and tail of its range) go to a per-CTA partial buffer, and the CTA
+// that finishes a split tile last (a per-tile counter) sums its shares in
+// CTA order and writes the tile: deterministic, no atomics on the data.
+// Without counters a separate fix-up kernel does the same sum.
 //
 // Split mode (ELT 3, fp32 containers, K-major only, MT = 1, KA = 1): the
 // MMAs read the staged fp32 tile x of A as hi = trunc_tf32(x) (kind::tf32
