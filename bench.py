@@ -10,8 +10,11 @@ resident in HBM.  Default workload: fp32 A 20000 x 10000 = U diag(1/i) V^T
 ``value`` is whole-job TFLOP/s with the operation count of the paper's eq.
 (C_SOR-SVD+PM) (2q+3) l C_mult + 2 l (m+n)(l+k) + 2 l^2 (m+l), C_mult = 2mn.
 ``e2e`` is the same metric through the public API with the matrix in pinned
-host memory: host-to-device copy of A and device-to-host copy of U, S, V are
-inside the timed region.  Multi-GPU runs (torchrun) solve one independent
+host memory (``sorsvd_run_host``): the host-to-device copy of A and the
+device-to-host copy of U, S, V are inside the timed region.  The timed
+region records CUDA events around the passes over A only (the roofline's
+kernel); the per-class times come from a few extra untimed steps with events
+around every launch.  Multi-GPU runs (torchrun) solve one independent
 replica per rank (the path has no exchange step): scaling is weak.
 
 ``--impl reference`` times the binary64 CPU oracle on the host cores instead
