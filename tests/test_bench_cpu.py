@@ -1,0 +1,50 @@
+"""bench.py's reference arm (the oracle on the host cores) keeps the JSON
+contract of the benchmark line; it needs no GPU."""
+import json
+import os
+import subprocess
+import sys
+
+from conftest import ROOT
+
+
+def _bench(*args, env=None):
+    e = dict(os.environ)
+    e.update(env or {})
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *args], capture_output=True, text=True,
+                       timeout=600, env=e, cwd=ROOT)
+    return r
+
+
+def test_reference_arm_prints_one_contract_line():
+    r = _bench("--impl", "reference", "--steps", "1", "--warmup", "3", "--cpu-rows", "400")
+    assert r.returncode == 0, r.stderr
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["unit"] == "TFLOP/s" and d["value"] > 0
+    assert d["steps"] == 1 and d["warmup"] == 3 and d["higher_is_better"] is True
+    assert d["config"]["workload"].startswith("cfg2") and d["config"]["sample_rows"] == 400
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_reference_arm_warmup_floor_and_unavailable_workloads():
+    r = _bench("--impl", "reference", "--steps", "1", "--warmup", "1", "--cpu-rows", "300")
+    assert r.returncode == 0, r.stderr
+    assert json.loads(r.stdout.strip().splitlines()[-1])["warmup"] == 3     # at least 3 warm-up steps
+    r = _bench("--impl", "reference", "--workload", "cfg4")
+    assert r.returncode == 0
+    d = json.loads(r.stdout.strip())
+    assert d["impl"] == "reference" and "unavailable" in d
+
+
+def test_reference_arm_prints_on_rank_zero_only():
+    r = _bench("--impl", "reference", "--steps", "1", "--warmup", "3", "--cpu-rows", "300",
+               env={"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == ""
