@@ -164,6 +164,23 @@ def traffic_from_profiles(kernel_key: str):
     return ent["bytes_per_launch"] if h == ent.get("source_sha256_16") else None
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest x over all ranks (a job's step time is its slowest
+    rank's); x itself on a single rank."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_tflops(flops_per_rank: float, world: int, ms: float) -> float:
+    """Whole-job throughput: the work of every rank over the job's step time."""
+    return flops_per_rank * world / (ms * 1e-3) / 1e12
+
+
 def run_ours(args, w, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -224,12 +241,9 @@ def run_ours(args, w, rank, world, local_rank):
     all_prof = native.profile_end()
     barrier()
     clocks = clk.summary()
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     F = flops(m, n, k, p, q)
-    value = F * world / (ms * 1e-3) / 1e12
+    value = job_tflops(F, world, ms)
 
     # --- end to end through the public API: A in pinned host memory, U S V
     # back to pinned host memory; sorsvd_run_host copies A in column blocks
@@ -253,11 +267,7 @@ def run_ours(args, w, rank, world, local_rank):
         e2e_step(2000 + i)
     ev1.record(stream)
     barrier()
-    e_ms = ev0.elapsed_time(ev1) / e_steps
-    if world > 1:
-        t = torch.tensor([e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e_ms = float(t.item())
+    e_ms = max_over_ranks(ev0.elapsed_time(ev1) / e_steps, world, dev)
     h2d = m * n * esz
     d2h = (m * k + k + n * k) * torch.empty(0, dtype=od).element_size()
 
@@ -297,7 +307,7 @@ def run_ours(args, w, rank, world, local_rank):
            "config": {"workload": f"{args.workload}: {w['desc']}", "m": m, "n": n, "k": k, "p": p, "q": q,
                       "flops_per_step": F, "l2": "inputs larger than L2 (A is %d MB)" % (m * n * esz // 2**20),
                       "parallelism": f"replicas x{world}"},
-           "e2e": {"value": F * world / (e_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": e_ms,
+           "e2e": {"value": job_tflops(F, world, e_ms), "unit": "TFLOP/s", "ms_per_step": e_ms,
                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
            "gpu_launches": launches, "roofline": roofline, "clocks": clocks,
            "kernel_ms_per_step": {c: round(v[0] / prof_steps, 4) for c, v in all_prof.items()},
@@ -369,11 +379,7 @@ def _timed(args, world, fn, stream):
             fn(1000 + i)
         ev1.record(stream)
         torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, "cuda")
     return ms, clk.summary()
 
 
@@ -397,7 +403,7 @@ def run_batched(args, w, rank, world, local_rank):
     if any(st):
         raise RuntimeError(f"device status: {[native.status_string(c) for c in st if c][:3]}")
     F = sum(flops(m, n, k, w["p"], w["q"]) for m, n, k in sizes)
-    value = F * world / (ms * 1e-3) / 1e12
+    value = job_tflops(F, world, ms)
     # end to end: pinned host matrices -> device, solve, U S V -> host
     hostA = [a.T.contiguous().cpu().pin_memory() for a in As]
     hU = [torch.empty(u.shape[1], u.shape[0], pin_memory=True) for u in plan.U]
@@ -427,7 +433,7 @@ def run_batched(args, w, rank, world, local_rank):
             "config": {"workload": f"{args.workload}: {w['desc']}", "batch": len(sizes), "flops_per_step": F,
                        "a_bytes": total_bytes, "l2": "inputs larger than L2 (%d MB of A)" % (total_bytes // 2**20),
                        "parallelism": f"replicas x{world}"},
-            "e2e": {"value": F * world / (e_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": e_ms,
+            "e2e": {"value": job_tflops(F, world, e_ms), "unit": "TFLOP/s", "ms_per_step": e_ms,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches), "clocks": clocks,
             "roofline": {"bound": "hbm", "kernel": "whole batch (all stages)",

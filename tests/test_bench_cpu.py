@@ -1,5 +1,6 @@
-"""bench.py's reference arm (the oracle on the host cores) keeps the JSON
-contract of the benchmark line; it needs no GPU."""
+"""bench.py on the CPU: the reference arm (the oracle on the host cores)
+keeps the JSON contract of the benchmark line, and the multi-rank timing
+(max over ranks, work summed over ranks) holds on two gloo ranks."""
 import json
 import os
 import subprocess
@@ -48,3 +49,41 @@ def test_reference_arm_prints_on_rank_zero_only():
                env={"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def _replica_rank(rank, world, port, root, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    sys.path.insert(0, root)
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        ms = bench.max_over_ranks(1.0 + rank, world, "cpu")     # rank r took 1 + r ms
+        q.put((rank, ms, bench.job_tflops(3e9, world, ms)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_replicas_take_the_slowest_rank_and_sum_the_work():
+    # the N > 1 path: one independent problem per rank, no data-path
+    # collective; the step time is the slowest rank's, the work is summed
+    import socket
+    import torch.multiprocessing as mp
+    with socket.socket() as sck:
+        sck.bind(("127.0.0.1", 0))
+        port = sck.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    world = 2
+    procs = [ctx.Process(target=_replica_rank, args=(r, world, port, ROOT, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    got = sorted(q.get(timeout=120) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [g[0] for g in got] == [0, 1]
+    for _, ms, tf in got:
+        assert ms == 2.0                                        # max over ranks
+        assert abs(tf - 3e9 * world / 2e-3 / 1e12) < 1e-12       # both ranks' work / slowest time
