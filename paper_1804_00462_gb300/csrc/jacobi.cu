@@ -32,7 +32,6 @@
 namespace sorsvd {
 namespace {
 
-constexpr int JT = 1024;
 constexpr int kMaxSweeps = 30;
 
 __device__ __forceinline__ int rr_player(int pos, int round, int N) {
