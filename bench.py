@@ -4,8 +4,13 @@
 A step is one whole SOR-SVD solve (Algorithm 3: Omega, q+1 power passes with
 re-orthonormalisation, CholeskyQR of both sketches, core product Q1^T A Q2,
 Jacobi SVD of the core, output assembly) on a synthetic matrix already
-resident in HBM.  Default workload: fp32 A 20000 x 10000 = U diag(1/i) V^T
-(Haar U, V of width 500) + 1e-3 N(0,1) noise, k = 100, p = 10, q = 1.
+resident in HBM.  Default workload: bf16 A 65536 x 16384 = U diag(exp(-i/64))
+V^T (i <= 1024, Haar U and V), k = 256, p = 10, q = 2, with the precision
+comparison of the metric beside it: the same stored matrix solved as BF16,
+BF16 + REFINE and FP32 (fp32-accurate split-TF32 tensor-core products),
+each timed and scored by ||A - U S V^T||_F / sigma_{k+1}.  ``--workload
+cfg2`` runs the fp32 20000 x 10000 matrix U diag(1/i) V^T (Haar U, V of
+width 500) + 1e-3 N(0,1), k = 100, p = 10, q = 1.
 
 ``value`` is whole-job TFLOP/s with the operation count of the paper's eq.
 (C_SOR-SVD+PM) (2q+3) l C_mult + 2 l (m+n)(l+k) + 2 l^2 (m+l), C_mult = 2mn.
@@ -18,7 +23,8 @@ around every launch.  Multi-GPU runs (torchrun) solve one independent
 replica per rank (the path has no exchange step): scaling is weak.
 
 ``--impl reference`` times the binary64 CPU oracle on the host cores instead
-(rank 0 only), on a row-sample of the same workload.
+(rank 0 only), on a row-sample of the same workload (sized so that a step
+takes a few seconds of CPU time).
 """
 from __future__ import annotations
 
@@ -54,6 +60,15 @@ WORKLOADS = {
                       "L rank 5 (Gaussian factors), S 5% support, |S| uniform [1, 10]; k=5, p=5, q=1; "
                       "tol 1e-7, <= 50 iterations, fp32 SOR-SVD with a binary64 finish"),
 }
+
+
+# (rows, columns) of the oracle's sample of a workload: the cpu_baseline leg
+# (one solve, ~10-30 s) and the reference arm (one solve per step, W + K
+# steps within a few minutes).  The oracle's Householder QR of an n x 266
+# sketch costs ~10 s at n = 16384, so the 65536 x 16384 workload is sampled
+# in both dimensions.
+CPU_SAMPLE = {"cfg2": (20000, 10000), "cfg3": (8192, 4096), ("cfg3", "reference"): (3072, 2048),
+              "cfg1": (1000, 1000)}
 
 
 def flops(m, n, k, p, q):
@@ -315,8 +330,8 @@ def run_ours(args, w, rank, world, local_rank):
            "jacobi_sweeps": (info >> 8) & 0xFF,
            "wall_s_timed": t_wall}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(w, args.cpu_rows)
-    if args.compare_precisions and dt in ("bf16", "f16"):
+        out["cpu_baseline"] = cpu_baseline(w, args.cpu_rows, args.cpu_cols)
+    if not args.no_compare_precisions and dt in ("bf16", "f16"):
         out["precision_comparison"] = compare_precisions(w, A, At, k, p, q, max(3, min(args.steps, 5)))
     return out
 
@@ -357,6 +372,11 @@ def compare_precisions(w, A, At, k, p, q, steps):
         del ws
     res["speedup_bf16_vs_f32"] = res["f32"]["ms"] / res["bf16"]["ms"]
     res["speedup_bf16_refine_vs_f32"] = res["f32"]["ms"] / res["bf16_refine"]["ms"]
+    # "equal relative error": the two errors within 1 % of each other
+    ef = res["f32"]["err_over_sigma_k1"]
+    for name in ("bf16", "bf16_refine"):
+        res[name]["err_rel_to_f32"] = res[name]["err_over_sigma_k1"] / ef - 1.0
+        res[name]["equal_error_within_1pct"] = abs(res[name]["err_over_sigma_k1"] / ef - 1.0) <= 0.01
     res["note"] = ("same stored matrix; err = ||A - U S V^T||_F / sigma_{k+1}; the Eckart-Young floor "
                    "is ||sigma_{k+1:}||_2 / sigma_{k+1}")
     res["eckart_young_floor"] = float((sig[k:] ** 2).sum() ** 0.5 / s_k1)
@@ -481,23 +501,30 @@ def run_rpca(args, w, rank, world, local_rank):
             "gpu_launches": int(launches), "clocks": clocks, "roofline": None}
 
 
-def cpu_baseline(w, rows):
-    """The binary64 oracle timed on the host on a row-sample of the workload."""
+def oracle_sample(w, rows, cols):
+    """The workload's recipe at rows x cols (the same spectrum, cut to the
+    sample's rank), stored in the workload's dtype and widened exactly."""
     import numpy as np
-    import oracle
     from paper_1804_00462_gb300 import inputs
-    m_s = min(rows, w["m"])
-    A64, _, _, _ = inputs.noisy_poly(m_s, w["n"], min(w["width"], m_s, w["n"]), w["noise"], seed=0) \
-        if w["spectrum"] == "poly1" else inputs.spectral(m_s, w["n"], sigma_of(w)[:min(m_s, w["n"], w["width"])], 0)
+    m_s, n_s = min(rows, w["m"]), min(cols or w["n"], w["n"])
+    r = min(w["width"], m_s, n_s)
+    A64, _, _, _ = inputs.noisy_poly(m_s, n_s, r, w["noise"], seed=0) if w["spectrum"] == "poly1" \
+        else inputs.spectral(m_s, n_s, sigma_of(w)[:r], 0)
     _, exact = inputs.to_storage(A64, w["dtype"])
-    exact = np.ascontiguousarray(exact)
+    return np.ascontiguousarray(exact), m_s, n_s
+
+
+def cpu_baseline(w, rows, cols):
+    """The binary64 oracle timed on the host on a sample of the workload."""
+    import oracle
+    exact, m_s, n_s = oracle_sample(w, rows, cols)
     t = time.perf_counter()
     oracle.sorsvd(exact, w["k"], w["p"], w["q"], 0, omega_dtype=w["dtype"])
     t = time.perf_counter() - t
-    F = flops(m_s, w["n"], w["k"], w["p"], w["q"])
+    F = flops(m_s, n_s, w["k"], w["p"], w["q"])
     return {"value": F / t / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"one solve of the same recipe with {m_s} of {w['m']} rows "
-                      f"({m_s}x{w['n']}, k={w['k']}, p={w['p']}, q={w['q']}), numpy BLAS threads",
+            "sample": f"one solve of the same recipe at {m_s}x{n_s} (of {w['m']}x{w['n']}), "
+                      f"k={w['k']}, p={w['p']}, q={w['q']}; numpy BLAS threads",
             "seconds": t}
 
 
@@ -505,29 +532,23 @@ def run_reference(args, w, rank, world):
     """The oracle (binary64, host cores) as the reference arm."""
     if rank != 0:
         return None
-    import numpy as np
     import oracle
-    from paper_1804_00462_gb300 import inputs
-    m_s = min(args.cpu_rows, w["m"])
-    A64, _, _, _ = inputs.noisy_poly(m_s, w["n"], min(w["width"], m_s, w["n"]), w["noise"], seed=0) \
-        if w["spectrum"] == "poly1" else inputs.spectral(m_s, w["n"], sigma_of(w)[:min(m_s, w["n"], w["width"])], 0)
-    _, exact = inputs.to_storage(A64, w["dtype"])
-    exact = np.ascontiguousarray(exact)
+    exact, m_s, n_s = oracle_sample(w, args.cpu_rows, args.cpu_cols)
     for i in range(args.warmup):
         oracle.sorsvd(exact, w["k"], w["p"], w["q"], i, omega_dtype=w["dtype"])
     t = time.perf_counter()
     for i in range(args.steps):
         oracle.sorsvd(exact, w["k"], w["p"], w["q"], 1000 + i, omega_dtype=w["dtype"])
     t = (time.perf_counter() - t) / args.steps
-    F = flops(m_s, w["n"], w["k"], w["p"], w["q"])
+    F = flops(m_s, n_s, w["k"], w["p"], w["q"])
     v = F / t / 1e12
-    sample = (f"each step one oracle solve of the same recipe with {m_s} of {w['m']} rows "
-              f"({m_s}x{w['n']}, k={w['k']}, p={w['p']}, q={w['q']})")
+    sample = (f"each step one oracle solve of the same recipe at {m_s}x{n_s} (of {w['m']}x{w['n']}), "
+              f"k={w['k']}, p={w['p']}, q={w['q']}")
     return {"metric": METRIC, "value": v, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded, built on the host)",
             "config": {"workload": f"{args.workload}: {w['desc']}", "m": w["m"], "n": w["n"], "k": w["k"],
-                       "p": w["p"], "q": w["q"], "sample_rows": m_s},
+                       "p": w["p"], "q": w["q"], "sample_rows": m_s, "sample_cols": n_s},
             "impl": "reference",
             "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
                              "sample": sample},
@@ -540,12 +561,19 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=tuple(WORKLOADS), default="cfg2")
-    ap.add_argument("--cpu-rows", type=int, default=20000)
+    ap.add_argument("--workload", choices=tuple(WORKLOADS), default="cfg3")
+    ap.add_argument("--cpu-rows", type=int, default=None,
+                    help="rows of the oracle's sample (default: per workload, a few seconds of CPU work)")
+    ap.add_argument("--cpu-cols", type=int, default=None, help="columns of the oracle's sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--compare-precisions", action="store_true",
-                    help="16-bit workloads: also time the fp32 and REFINE paths on the same matrix")
+    ap.add_argument("--no-compare-precisions", action="store_true",
+                    help="16-bit workloads: skip the BF16 / BF16+REFINE / FP32 comparison on the same matrix")
     args = ap.parse_args()
+    samp = CPU_SAMPLE.get((args.workload, args.impl), CPU_SAMPLE.get(args.workload, (20000, None)))
+    if args.cpu_rows is None:
+        args.cpu_rows = samp[0]
+    if args.cpu_cols is None:
+        args.cpu_cols = samp[1]
     if args.warmup < 3:
         args.warmup = 3
     rank = int(os.environ.get("RANK", "0"))

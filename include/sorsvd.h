@@ -135,11 +135,19 @@ int sorsvd_run_host(const void* A, int64_t m, int64_t n, int64_t lda,
  * any stream capture.  Nothing is allocated or freed.  Every call shares the
  * array and leaves its contents behind: calls that may overlap on the GPU
  * (different streams or host threads) race and must be serialised by the
- * caller.  Device-side status: sorsvd_get_status is not available for this
- * entry point (the workspace is internal); check the outputs. */
+ * caller.  The cached address belongs to the primary context: do not call
+ * it after a cudaDeviceReset or from another context.  Device-side status
+ * (the workspace is internal): sorsvd_noalloc_get_status. */
 int sorsvd_run_noalloc(const void* A, int64_t m, int64_t n, int64_t lda,
                        int k, int p, int q, uint64_t seed, int dtype, unsigned flags,
                        void* U, int64_t ldu, void* S, void* V, int64_t ldv, void* stream);
+
+/* Device status word of the last sorsvd_run_noalloc call on the current
+ * device, as sorsvd_get_status gives it for a caller workspace (synchronous
+ * on `stream`; same meaning of *device_status and *info; either pointer may
+ * be NULL).  The paper has no counterpart.  Returns SORSVD_ERR_CUDA when the
+ * scratch array cannot be looked up. */
+int sorsvd_noalloc_get_status(int* device_status, int* info, void* stream);
 
 /* Copies the device status word of a workspace to the host (synchronous on
  * `stream`).  *device_status receives a sorsvd_status code (SORSVD_OK when

@@ -3,26 +3,25 @@
 TEST INFRASTRUCTURE: only tests, ``__graft_entry__.smoke()`` and the CPU
 baseline leg of ``bench.py`` may import this package.
 
-Follows Algorithm 3 (SOR-SVD with power method, Sec. III) step by step; q = 0
-is Algorithm "first" (basic SOR-SVD, eqs. T1 = A Omega, T2 = A^T T1,
-M = Q1^T A Q2):
+Follows Algorithm 3 (SOR-SVD with power method, Sec. III).  The method
+draws a standard Gaussian test matrix Omega (n x l, l = k + p) and builds two
+sketches alternately, T1 = A T2 and then T2 = A^T T1 (eqs. T1 and AT1),
+starting from T2 = Omega and going round q + 1 times (q = 0 is the basic
+method of Sec. III).  QR factorisations of the final sketches give orthonormal
+bases Q1 (m x l) and Q2 (n x l); the l x l core is M = Q1^T A Q2 (eq. M).  The
+SVD of M, cut to its k largest singular values, gives U~_k, S~_k, V~_k, and
+the rank-k factors are U = Q1 U~_k, S = S~_k, V = Q2 V~_k (A_hat = U S V^T;
+the paper prints the last factor without its transpose).
 
-  1. T2 <- Omega (n x l standard Gaussian, l = k + p; Sec. III).
-  2. for i = 1 .. q+1:  T1 <- A T2 ;  T2 <- A^T T1.
-  3. T1 = Q1 R1, T2 = Q2 R2 (QR decompositions).
-  4. M <- Q1^T A Q2 (core, eq. M).
-  5. rank-k truncated SVD  M_k = U~_k S~_k V~_k^T.
-  6. U = Q1 U~_k, S = S~_k, V = Q2 V~_k  (A_hat = U S V^T).
-
-``mode="literal"`` runs step 2 exactly as printed.  ``mode="stabilised"``
+``mode="literal"`` runs the alternating products exactly as printed.  ``mode="stabilised"``
 replaces T2 by the Q factor of its QR decomposition before every pass i > 1.
 By Gu's lemma (Sec. IV, Lemma 1: QR projectors are invariant under right
 multiplication by a nonsingular matrix) this changes neither Q1 Q1^T nor
 Q2 Q2^T in exact arithmetic, so A_hat is unchanged; it only keeps the
 columns of T2 from collapsing onto the leading singular direction.
 
-``core="two_pass"`` replaces step 4 by the paper's M_approx =
-Q1^T T1 (Q2^T T2_prev)^+ (Algorithm 3, step 7 second option), where T2_prev
+``core="two_pass"`` replaces the core product by the paper's M_approx =
+Q1^T T1 (Q2^T T2_prev)^+ (the second core option of Algorithm 3), where T2_prev
 is the T2 that entered the last pass (the "non-updated" T2, Sec. III).
 
 The GEMMs are numpy matmul calls (a library primitive); QR and SVD are the

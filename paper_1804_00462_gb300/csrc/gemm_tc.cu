@@ -14,10 +14,8 @@
 // Work decomposition: a persistent grid of G <= #SM units splits the
 // tiles x K-stages iteration space into G contiguous ranges ("stream-K"),
 // so every SM streams the same share of A whatever the tile count.  A unit
-// is one CTA, or (PAIR) a cluster of two CTAs that take the two 128 MT-row
-// halves of each unit tile and share every B stage (each CTA loads part of
-// it by TMA multicast into both).  A unit walks its range as segments (one
-// per output tile it touches).  A segment that covers a whole tile is
+// is one CTA; it walks its range as segments (one per output tile it
+// touches).  A segment that covers a whole tile is
 // written straight to the output; the at most two partial segments of a CTA
 // (head and tail of its range) go to a per-CTA partial buffer, and the CTA
 // that finishes a split tile last (a per-tile counter) sums its shares in
@@ -65,8 +63,7 @@ struct TcParams {
   int N, Npad, nch, ch0; // output columns, padded, N-chunks of ch0 rows
   int KA, MT;            // K atoms per stage, 128-row blocks per tile
   int64_t tiles, ipt, total;
-  int G;                 // stream-K units (CTAs, or CTA pairs when pair)
-  int pair;              // 1: clusters of two CTAs share B (multicast)
+  int G;                 // stream-K units (CTAs)
   int nbuf;
   uint32_t tmem_cols;
   int lo_tmem;           // split mode: A's low parts in TMEM slots (else next to A in shared memory)
@@ -137,7 +134,7 @@ __device__ __forceinline__ void store_out(const TcParams& P, int64_t grow, int c
 // N-chunks and K atoms per stage, fixed at compile time so that the MMA
 // issue loop is straight-line code (issued from a rolled loop, the same
 // tcgen05.mma sequence ran 2-4x slower, measured).
-template <int ELT, bool A_MN, int MT, int NCH, int KA, bool PAIR>
+template <int ELT, bool A_MN, int MT, int NCH, int KA>
 __global__ void __launch_bounds__((ELT == 3 ? kThreadsSplit : kThreads), 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const __grid_constant__ CUtensorMap tmBlo, const TcParams P) {
@@ -166,13 +163,12 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   // accumulator fill length in stages (split mode drains every kDrainAtoms atoms)
   const int64_t CHUNK = SPLIT ? (int64_t)((kDrainAtoms + KA - 1) / KA) : ((int64_t)1 << 40);
   const int mrows = 128 * MT;
-  const int64_t urows = PAIR ? 2 * mrows : mrows;        // rows of a unit tile
+  const int64_t urows = mrows;                           // rows of a unit tile
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < P.stages; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
-    // PAIR: a B stage is free once both CTAs of the pair have consumed it
-    for (int s = 0; s < P.bstages; ++s) { tc::mbar_init(&bfull[s], 1); tc::mbar_init(&bempty[s], PAIR ? 2 : 1); }
+    for (int s = 0; s < P.bstages; ++s) { tc::mbar_init(&bfull[s], 1); tc::mbar_init(&bempty[s], 1); }
     for (int b = 0; b < 2; ++b) { tc::mbar_init(&tfull[b], 1); tc::mbar_init(&tempty[b], 128); }
     tc::mbar_init(done, 1);
     if (SPLIT)
@@ -187,8 +183,6 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   if (warp == 0 && lane == 0) tc::prefetch_tmap(&tmA);
   if (warp == 6 && lane == 0) { tc::prefetch_tmap(&tmB); if (SPLIT) tc::prefetch_tmap(&tmBlo); }
   __syncthreads();
-  // PAIR: the partner's barriers are initialised before any multicast
-  if (PAIR) tc::cluster_sync_all();
   tc::fence_after_sync();
   const uint32_t tbase = *tslot;
   if constexpr (SPLIT) {
@@ -207,10 +201,9 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     tc::fence_after_sync();
   }
 
-  // the stream-K unit: one CTA, or (PAIR) the two CTAs of a cluster, which
-  // take the two 128 MT-row halves of every unit tile and share B
-  const int rank = PAIR ? (int)(blockIdx.x & 1) : 0;
-  const int64_t cta = PAIR ? (int64_t)(blockIdx.x >> 1) : (int64_t)blockIdx.x;
+  // the stream-K unit of this CTA
+  const int rank = 0;
+  const int64_t cta = (int64_t)blockIdx.x;
   const int64_t it0 = cta * P.total / P.G, it1 = (cta + 1) * P.total / P.G;
 
   if (warp == 0) {
@@ -278,20 +271,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             const int k = (int)((kb * KA + j) * AK);
             for (int ch = 0; ch < NCH; ++ch) {
               const size_t off = (size_t)j * P.b_atom + (size_t)ch * P.ch0 * 128;
-              if (PAIR) {
-                // each CTA loads one N-chunk (both with one chunk: CTA 0;
-                // split mode: CTA 0 the hi, CTA 1 the lo tensor) into both
-                // CTAs' stage; every CTA armed its own stage
-                if (SPLIT) {
-                  if (rank == 0) tc::tma_load_2d_mc(sb + off, &tmB, &bfull[stage], k, ch * P.ch0, (uint16_t)3, polB);
-                  else tc::tma_load_2d_mc(sb + P.b_bytes + off, &tmBlo, &bfull[stage], k, ch * P.ch0, (uint16_t)3, polB);
-                } else if ((NCH == 2 ? ch : 0) == rank) {
-                  tc::tma_load_2d_mc(sb + off, &tmB, &bfull[stage], k, ch * P.ch0, (uint16_t)3, polB);
-                }
-              } else {
-                tc::tma_load_2d_hint(sb + off, &tmB, &bfull[stage], k, ch * P.ch0, polB);
-                if (SPLIT) tc::tma_load_2d_hint(sb + P.b_bytes + off, &tmBlo, &bfull[stage], k, ch * P.ch0, polB);
-              }
+              tc::tma_load_2d_hint(sb + off, &tmB, &bfull[stage], k, ch * P.ch0, polB);
+              if (SPLIT) tc::tma_load_2d_hint(sb + P.b_bytes + off, &tmBlo, &bfull[stage], k, ch * P.ch0, polB);
             }
           }
           if (++stage == (uint32_t)P.bstages) { stage = 0; phase ^= 1; }
@@ -361,8 +342,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
               }
               tc::mma_commit(&empty[stage]);
               tc::mma_commit(&aempty[aslot]);
-              if (PAIR) tc::mma_commit_mc(&bempty[bstage], (uint16_t)3);
-              else tc::mma_commit(&bempty[bstage]);
+              tc::mma_commit(&bempty[bstage]);
               if (++stage == (uint32_t)P.stages) { stage = 0; phase ^= 1; }
               if (++aslot == (uint32_t)P.aslots) { aslot = 0; aphase ^= 1u; }
             } else {
@@ -391,8 +371,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
               }
             }
             tc::mma_commit(&empty[stage]);
-            if (PAIR) tc::mma_commit_mc(&bempty[bstage], (uint16_t)3);
-            else tc::mma_commit(&bempty[bstage]);
+            tc::mma_commit(&bempty[bstage]);
             if (++stage == (uint32_t)P.stages) { stage = 0; phase ^= 1; }
             }
             if (++bstage == (uint32_t)P.bstages) { bstage = 0; bphase ^= 1; }
@@ -579,7 +558,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   }
   // Split tiles: the CTA that writes the last share of a tile sums the
   // shares in CTA order (as the separate fix-up kernel does) and writes the
-  // tile; no CTA waits for another.  PAIR: each half tile (rank) on its own.
+  // tile; no CTA waits for another.
   if (P.tilecnt && !*abortp) {
     const int64_t th = it0 / P.ipt, tt = (it1 - 1) / P.ipt;
     const bool head_split = (it0 % P.ipt != 0) || (it1 < (th + 1) * P.ipt);
@@ -592,7 +571,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         if (!split) continue;
         const int64_t t = h ? tt : th;
         const int64_t c0 = cta_of(t * P.ipt, P.total, P.G), c1 = cta_of(t * P.ipt + P.ipt - 1, P.total, P.G);
-        if (atomicAdd(&P.tilecnt[PAIR ? 2 * t + rank : t], 1) == (int)(c1 - c0)) bits |= 1 << h;
+        if (atomicAdd(&P.tilecnt[t], 1) == (int)(c1 - c0)) bits |= 1 << h;
       }
       *lastp = bits;
     }
@@ -608,9 +587,9 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         const int64_t t = h ? tt : th;
         const int64_t c0 = cta_of(t * P.ipt, P.total, P.G), c1 = cta_of(t * P.ipt + P.ipt - 1, P.total, P.G);
         const int slot0 = (c0 * P.total / P.G < t * P.ipt) ? 1 : 0;
-        // the share of unit cc comes from CTA cc (PAIR: 2 cc + rank)
+        // the share of unit cc comes from CTA cc
         auto share = [&](int64_t cc, int slot) {
-          return reinterpret_cast<const float4*>(P.parts + ((size_t)(PAIR ? 2 * cc + rank : cc) * 2 + slot) * seg);
+          return reinterpret_cast<const float4*>(P.parts + ((size_t)cc * 2 + slot) * seg);
         };
         // 4 consecutive rows per float4, 4 float4 per thread in flight
         const int q4 = mrows / 4, nv = per / 4;
@@ -649,12 +628,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
               if (grow + u < P.M) store_out(P, grow + u, col, v[u]);
           }
         }
-        if (threadIdx.x == 0) P.tilecnt[PAIR ? 2 * t + rank : t] = 0;     // ready for the next launch
+        if (threadIdx.x == 0) P.tilecnt[t] = 0;     // ready for the next launch
       }
     }
   }
-  // PAIR: neither CTA leaves while the other may still multicast into it
-  if (PAIR) tc::cluster_sync_all();
 }
 
 // Sum the partial segments of every tile touched by more than one CTA, in
@@ -742,29 +719,14 @@ bool make_map(CUtensorMap* map, const void* ptr, int elt, int64_t rows, int64_t 
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int ELT, bool A_MN, int MT, int NCH, int KA, bool PAIR = false>
+template <int ELT, bool A_MN, int MT, int NCH, int KA>
 cudaError_t launch_shape(const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& mblo, const TcParams& P,
                          size_t smem, cudaStream_t st) {
-  auto kern = tc_gemm_kernel<ELT, A_MN, MT, NCH, KA, PAIR>;
+  auto kern = tc_gemm_kernel<ELT, A_MN, MT, NCH, KA>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  if (!PAIR) {
-    kern<<<P.G, ELT == 3 ? kThreadsSplit : kThreads, smem, st>>>(ma, mb, mblo, P);
-    return cudaGetLastError();
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(2 * P.G), 1, 1);
-  cfg.blockDim = dim3(ELT == 3 ? kThreadsSplit : kThreads, 1, 1);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = 2;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, ma, mb, mblo, P);
+  kern<<<P.G, ELT == 3 ? kThreadsSplit : kThreads, smem, st>>>(ma, mb, mblo, P);
+  return cudaGetLastError();
 }
 
 // the instantiation for the plan's (MT, nch, KA); split mode has MT = 1 and
@@ -774,31 +736,8 @@ cudaError_t launch_typed(const CUtensorMap& ma, const CUtensorMap& mb, const CUt
                          size_t smem, cudaStream_t st) {
   if constexpr (ELT == 3) {
     if (P.MT != 1 || P.nch != 1 || P.KA != 1) return cudaErrorInvalidValue;
-    return P.pair ? launch_shape<ELT, A_MN, 1, 1, 1, true>(ma, mb, mblo, P, smem, st)
-                  : launch_shape<ELT, A_MN, 1, 1, 1>(ma, mb, mblo, P, smem, st);
+    return launch_shape<ELT, A_MN, 1, 1, 1>(ma, mb, mblo, P, smem, st);
   } else {
-  if constexpr (ELT == 2) {
-  if (P.pair) {
-    // TF32: one N-chunk and one K atom per stage, B shared by the pair
-    if (P.nch != 1 || P.KA != 1) return cudaErrorInvalidValue;
-    return P.MT == 2 ? launch_shape<ELT, A_MN, 2, 1, 1, true>(ma, mb, mblo, P, smem, st)
-                     : launch_shape<ELT, A_MN, 1, 1, 1, true>(ma, mb, mblo, P, smem, st);
-  }
-  }
-  if constexpr (ELT < 2) {
-  if (P.pair) {
-    // one 128-row block per CTA, B shared by the pair
-    if (P.MT != 1) return cudaErrorInvalidValue;
-    const int pc = (P.nch - 1) * 2 + (P.KA - 1);
-    switch (pc) {
-      case 0: return launch_shape<ELT, A_MN, 1, 1, 1, true>(ma, mb, mblo, P, smem, st);
-      case 1: return launch_shape<ELT, A_MN, 1, 1, 2, true>(ma, mb, mblo, P, smem, st);
-      case 2: return launch_shape<ELT, A_MN, 1, 2, 1, true>(ma, mb, mblo, P, smem, st);
-      case 3: return launch_shape<ELT, A_MN, 1, 2, 2, true>(ma, mb, mblo, P, smem, st);
-      default: return cudaErrorInvalidValue;
-    }
-  }
-  }
   const int code = (P.MT - 1) * 4 + (P.nch - 1) * 2 + (P.KA - 1);
   switch (code) {
     case 0: return launch_shape<ELT, A_MN, 1, 1, 1>(ma, mb, mblo, P, smem, st);
@@ -822,21 +761,19 @@ int env_int(const char* name, int dflt) {
 constexpr uint32_t kSmemBudget = 220u * 1024u;
 
 // Shape of a launch for a given (KA, MT); stages = 0 when it does not fit.
-// pair: units of two 128 MT-row blocks on a two-CTA cluster.
-TcParams shape(int elt, int64_t M, int64_t N, int64_t K, int KA, int MT, bool pair = false) {
+TcParams shape(int elt, int64_t M, int64_t N, int64_t K, int KA, int MT) {
   TcParams P{};
-  P.pair = pair ? 1 : 0;
   P.M = M; P.K = K; P.N = (int)N;
   P.Npad = (int)((N + 15) / 16 * 16);
   if (P.Npad <= 256) { P.nch = 1; P.ch0 = P.Npad; }
   else { P.nch = 2; P.ch0 = (P.Npad / 2 + 15) / 16 * 16; }
   P.KA = KA; P.MT = MT;
   const int AK = elt >= 2 ? 32 : 64;
-  const int64_t urows = (pair ? 2 : 1) * 128 * MT;
+  const int64_t urows = 128 * MT;
   P.tiles = (M + urows - 1) / urows;
   P.ipt = (K + (int64_t)AK * KA - 1) / ((int64_t)AK * KA);
   P.total = P.tiles * P.ipt;
-  P.G = (int)std::min<int64_t>(num_sms() / (pair ? 2 : 1), P.total);
+  P.G = (int)std::min<int64_t>(num_sms(), P.total);
   if (P.G < 1) P.G = 1;
   P.nbuf = (2 * MT * P.Npad <= 512) ? 2 : 1;
   uint32_t cols = 32;
@@ -881,21 +818,14 @@ TcParams tc_plan(int elt, int64_t M, int64_t N, int64_t K) {
   const int64_t Npad = (N + 15) / 16 * 16;
   int MT = envMT > 0 ? envMT : ((elt != 3 && 4 * Npad <= 512) ? 2 : 1);
   if (elt == 3 || MT * Npad > 512 || MT < 1 || MT > 2) MT = 1;
-  // Two-CTA clusters that share (multicast) each B stage halve the B reads
-  // from L2, whose output bandwidth bounds the passes where B is large next
-  // to A: 16-bit operands with one 128-row block per tile and N > 128, and
-  // the fp32 passes (split mode reads B twice, hi and lo).  TF32 pairs take
-  // one K atom per stage.  SORSVD_TC_PAIR=0 turns pairs off.
-  const bool pair_ok = env_int("SORSVD_TC_PAIR", 1) != 0 && M > 128 * MT;
-  const bool pair = pair_ok && ((elt < 2 && MT == 1 && Npad > 128) || elt == 3 || (elt == 2 && Npad <= 256));
-  TcParams best = shape(elt, M, N, K, 1, MT, pair);
+  TcParams best = shape(elt, M, N, K, 1, MT);
   if (envKA > kMaxKA || elt >= 2) return best;     // fp32 containers: one K atom per stage
   if (envKA > 0) {
-    TcParams P = shape(elt, M, N, K, envKA, MT, pair);
+    TcParams P = shape(elt, M, N, K, envKA, MT);
     return P.stages >= 2 ? P : best;
   }
   for (int KA = 2; KA <= kMaxKA; ++KA) {
-    TcParams P = shape(elt, M, N, K, KA, MT, pair);
+    TcParams P = shape(elt, M, N, K, KA, MT);
     if (P.stages >= 4) best = P;
   }
   return best;
@@ -912,7 +842,7 @@ bool tc_supported(int elt, const void* A, int64_t lda, const void* B, int64_t ld
 
 size_t tc_parts_bytes(int elt, int64_t M, int64_t N, int64_t K) {
   TcParams P = tc_plan(elt, M, N, K);
-  return (size_t)(P.pair ? 2 : 1) * P.G * 2 * 128 * P.MT * P.Npad * sizeof(float);
+  return (size_t)P.G * 2 * 128 * P.MT * P.Npad * sizeof(float);
 }
 
 cudaError_t launch_tc_gemm(bool trans_a, int elt, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
@@ -928,8 +858,7 @@ cudaError_t launch_tc_gemm(bool trans_a, int elt, int64_t M, int64_t N, int64_t 
   if (P.stages < 2) return cudaErrorInvalidValue;
   P.out = out; P.ldo = ldo; P.out16 = out16; P.ld16 = ld16; P.out16_kind = out16 ? out16_kind : 0;
   P.parts = parts; P.status = status;
-  P.tilecnt = (tilecnt && (P.pair ? 2 : 1) * P.tiles <= ntilecnt) ? tilecnt : nullptr;
-  if (P.pair && !P.tilecnt) return cudaErrorInvalidValue;   // the fix-up kernel sums single-CTA units
+  P.tilecnt = (tilecnt && P.tiles <= ntilecnt) ? tilecnt : nullptr;
   const int AK = elt >= 2 ? 32 : 64, AMN = elt >= 2 ? 32 : 64;
   const int map_elt = elt == 3 ? 2 : elt;
   CUtensorMap ma, mb;
@@ -954,7 +883,7 @@ cudaError_t launch_tc_gemm(bool trans_a, int elt, int64_t M, int64_t N, int64_t 
   if (e != cudaSuccess) return e;
   // fix-up of the tiles split across CTAs (when no counters were given):
   // one block row per CTA boundary, about 4 elements of the tile per thread
-  if (P.G < 2 || P.tilecnt || P.pair) return cudaSuccess;
+  if (P.G < 2 || P.tilecnt) return cudaSuccess;
   const int64_t per = (int64_t)128 * P.MT * P.N;
   const int64_t gy = std::max<int64_t>(1, std::min<int64_t>((per + 1023) / 1024, 65535));
   ProfScope ps2(K_REDUCE, st);

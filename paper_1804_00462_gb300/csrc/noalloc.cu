@@ -13,7 +13,13 @@
 // should come before any stream capture.  All calls share the one array and
 // it keeps the last call's contents: sorsvd_run clears the status word it
 // starts from and writes every other buffer before reading it, and calls
-// that overlap on the GPU race on the array.
+// that overlap on the GPU race on the array.  The cached address belongs to
+// the device's primary context: do not use this entry point after a
+// cudaDeviceReset or from another context in the same process.
+//
+// sorsvd_noalloc_get_status reads the device status word at the start of
+// the array (Cholesky breakdown, Jacobi not converged, bounded-wait
+// timeout), the counterpart of sorsvd_get_status for a caller workspace.
 #include "internal.cuh"
 
 #include <mutex>
@@ -62,4 +68,10 @@ extern "C" int sorsvd_run_noalloc(const void* A, int64_t m, int64_t n, int64_t l
   if (int r = sorsvd::noalloc_scratch(&ws)) return r;
   return sorsvd_run(A, m, n, lda, k, p, q, seed, dtype, flags, U, ldu, S, V, ldv, ws, sorsvd::kNoallocBytes,
                     stream);
+}
+
+extern "C" int sorsvd_noalloc_get_status(int* device_status, int* info, void* stream) {
+  void* ws = nullptr;
+  if (int r = sorsvd::noalloc_scratch(&ws)) return r;
+  return sorsvd_get_status(ws, device_status, info, stream);
 }

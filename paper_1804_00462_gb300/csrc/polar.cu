@@ -1,4 +1,4 @@
-// Second CholeskyQR pass of the QR step (Alg. 3 step 6) in polar form.
+// Second CholeskyQR pass of the QR step of Algorithm 3 (T1 = Q1 R1, T2 = Q2 R2) in polar form.
 //
 // After one CholeskyQR pass the Gram G = T^T T of the sketch is close to the
 // identity.  Any l x l matrix X with X^T G X = I makes Q = T X an

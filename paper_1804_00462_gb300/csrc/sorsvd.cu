@@ -56,6 +56,9 @@ int splits_for(int64_t M, int64_t N, int64_t K, int cap) {
   return (int)std::max<int64_t>(s, 1);
 }
 constexpr int kCapBig = 16, kCapSmall = 256;
+// split tensor-core products: widest skinny operand of one launch (the
+// low parts of A then fit in TMEM beside the two accumulator fills)
+constexpr int64_t kSplitMaxCols = 128, kSplitChunkCols = 112;
 
 inline int64_t pad16(int64_t x) { return (x + 15) / 16 * 16; }
 
@@ -213,7 +216,14 @@ int pass(const Ctx& c, int kcls, bool trans, int64_t M, int64_t N, int64_t K, co
     const bool use_at = (elt >= 2 && !trans);
     const void* Aop = use_at ? c.at(c.L.at) : A;
     const int64_t ldop = use_at ? c.L.ldn : lda;
-    if ((!use_at || c.L.has_at) && tc_supported(elt, Aop, ldop, B, ldb, (int)N)) {
+    // split mode keeps two [D1 | D2] accumulator fills of <= kSplitMaxCols
+    // columns in TMEM: wider skinny operands run as column chunks, one
+    // launch each (every chunk re-reads A; at these widths the split
+    // products are bound by their MMAs, not by the reads of A)
+    const int nchunk = (elt == 3 && N > kSplitMaxCols) ? (int)((N + kSplitChunkCols - 1) / kSplitChunkCols) : 1;
+    const int64_t wchunk = nchunk > 1 ? (N + nchunk - 1) / nchunk : N;
+    const int64_t wpad = nchunk > 1 ? (wchunk + 15) / 16 * 16 : N;
+    if ((!use_at || c.L.has_at) && tc_supported(elt, Aop, ldop, B, ldb, (int)wpad)) {
       const void* Bop = B;
       int64_t ldbop = ldb;
       if (elt == 3) {
@@ -223,9 +233,16 @@ int pass(const Ctx& c, int kcls, bool trans, int64_t M, int64_t N, int64_t K, co
         Bop = c.at(c.L.bhi);
         ldbop = c.L.ldb;
       }
-      CK(launch_tc_gemm(trans || use_at, elt, M, N, K, Aop, ldop, Bop, ldbop, c.at(c.L.blo), (float*)C, ldc, C16,
-                        ld16, dt == SORSVD_BF16 ? 1 : 2, (float*)c.at(c.L.parts), (int*)c.at(c.L.tilecnt),
-                        c.L.ntilecnt, c.status(), kcls, c.st));
+      for (int64_t c0 = 0; c0 < N; c0 += wpad) {
+        const int64_t w = std::min<int64_t>(wpad, N - c0);
+        const size_t eb = elt >= 2 ? 4 : 2;
+        const void* Bc = (const char*)Bop + (size_t)c0 * ldbop * eb;
+        const void* Blo = (const char*)c.at(c.L.blo) + (size_t)c0 * c.L.ldb * 4;
+        void* C16c = C16 ? (void*)((char*)C16 + (size_t)c0 * ld16 * 2) : nullptr;
+        CK(launch_tc_gemm(trans || use_at, elt, M, w, K, Aop, ldop, Bc, ldbop, Blo, (float*)C + c0 * ldc, ldc,
+                          C16c, ld16, dt == SORSVD_BF16 ? 1 : 2, (float*)c.at(c.L.parts), (int*)c.at(c.L.tilecnt),
+                          c.L.ntilecnt, c.status(), kcls, c.st));
+      }
       return SORSVD_OK;
     }
   }

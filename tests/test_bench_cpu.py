@@ -18,7 +18,7 @@ def _bench(*args, env=None):
 
 
 def test_reference_arm_prints_one_contract_line():
-    r = _bench("--impl", "reference", "--steps", "1", "--warmup", "3", "--cpu-rows", "400")
+    r = _bench("--impl", "reference", "--workload", "cfg2", "--steps", "1", "--warmup", "3", "--cpu-rows", "400")
     assert r.returncode == 0, r.stderr
     lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
     assert len(lines) == 1
@@ -35,9 +35,13 @@ def test_reference_arm_prints_one_contract_line():
 
 
 def test_reference_arm_warmup_floor_and_unavailable_workloads():
-    r = _bench("--impl", "reference", "--steps", "1", "--warmup", "1", "--cpu-rows", "300")
+    # the default workload is the bf16 65536 x 16384 matrix (row-sampled here)
+    r = _bench("--impl", "reference", "--steps", "1", "--warmup", "1", "--cpu-rows", "300", "--cpu-cols", "300")
     assert r.returncode == 0, r.stderr
-    assert json.loads(r.stdout.strip().splitlines()[-1])["warmup"] == 3     # at least 3 warm-up steps
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    assert d["warmup"] == 3                                                 # at least 3 warm-up steps
+    assert d["config"]["workload"].startswith("cfg3")
+    assert d["config"]["sample_rows"] == 300 and d["config"]["sample_cols"] == 300
     r = _bench("--impl", "reference", "--workload", "cfg4")
     assert r.returncode == 0
     d = json.loads(r.stdout.strip())
@@ -45,7 +49,7 @@ def test_reference_arm_warmup_floor_and_unavailable_workloads():
 
 
 def test_reference_arm_prints_on_rank_zero_only():
-    r = _bench("--impl", "reference", "--steps", "1", "--warmup", "3", "--cpu-rows", "300",
+    r = _bench("--impl", "reference", "--workload", "cfg2", "--steps", "1", "--warmup", "3", "--cpu-rows", "300",
                env={"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""

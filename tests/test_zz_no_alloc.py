@@ -2,7 +2,8 @@
 device memory when they call (it takes its scratch from a library-owned
 device array).  Checked through the C ABI against sorsvd_run with a caller
 workspace, on two calls in a row (the shared scratch keeps the first call's
-contents when the second starts)."""
+contents when the second starts), with the device status word of each call
+read back through sorsvd_noalloc_get_status."""
 import ctypes as C
 
 import numpy as np
@@ -24,7 +25,17 @@ def nat():
     f.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_int,
                   C.c_uint, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]
     f.restype = C.c_int
+    g = native.lib.sorsvd_noalloc_get_status
+    g.argtypes = [C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_void_p]
+    g.restype = C.c_int
     return native
+
+
+def _noalloc_status(nat):
+    st, info = C.c_int(-1), C.c_int(-1)
+    rc = nat.lib.sorsvd_noalloc_get_status(C.byref(st), C.byref(info), torch.cuda.current_stream().cuda_stream)
+    assert rc == 0, nat.status_string(rc)
+    return st.value, info.value
 
 
 def _noalloc(nat, A, k, p, q, seed, code):
@@ -57,6 +68,10 @@ def test_noalloc_matches_workspace_entry_point_twice(nat):
         A = torch.from_numpy(np.ascontiguousarray(store.T)).cuda().T
         Ur, Sr, Vr = nat.run(A, k, p, q, seed=seed, dtype=dt, check=True)
         Un, Sn, Vn = _noalloc(nat, A, k, p, q, seed, code)
+        # the device status word of the call (kept in the library's array)
+        st, info = _noalloc_status(nat)
+        assert st == 0, nat.status_string(st)
+        assert (info >> 8) & 0xFF > 0                # Jacobi sweeps of the call
         tol = 1e-10 if dt == "f64" else 1e-5
         assert abs(_rel(exact, Un, Sn, Vn) - _rel(exact, Ur, Sr, Vr)) <= tol
         assert float((Sn.double() - Sr.double()).abs().max() / Sr.double()[0]) <= tol
