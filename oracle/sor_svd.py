@@ -48,7 +48,7 @@ def sorsvd(A: np.ndarray, k: int, p: int, q: int, seed: int, *,
     Returns (U m x k, S k, V n x k) or, with ``return_intermediates``,
     (U, S, V, info dict).
     """
-    A = np.asarray(A, dtype=np.float64)
+    A = np.asanyarray(A, dtype=np.float64)
     m, n = A.shape
     l = k + p
     if not (1 <= k <= l <= min(m, n)):

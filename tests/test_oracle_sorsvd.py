@@ -164,6 +164,82 @@ def test_flop_count_matches_paper_example_terms():
     assert orc.flop_count(1000, 1000, 20, 5, 1) - f == 2 * 25 * 2 * 1000 * 1000
 
 
+class _Counting(np.ndarray):
+    """ndarray view that adds 2 r c k to a counter for every r x k by k x c
+    matrix product it takes part in (the usual multiply-add count)."""
+    flops = [0]
+
+    def __array_ufunc__(self, ufunc, method, *args, **kw):
+        plain = [np.asarray(a) if isinstance(a, _Counting) else a for a in args]
+        if ufunc is np.matmul and method == "__call__":
+            a, b = plain
+            _Counting.flops[0] += 2 * a.shape[0] * a.shape[1] * (b.shape[1] if b.ndim == 2 else 1)
+        out = getattr(ufunc, method)(*plain, **kw)
+        return out.view(_Counting) if isinstance(out, np.ndarray) else out
+
+
+@pytest.mark.parametrize("m,n,k,p,q", [(60, 40, 3, 2, 0), (50, 70, 4, 3, 1), (80, 30, 5, 5, 2)])
+def test_flop_count_equals_the_operations_the_oracle_performs(monkeypatch, m, n, k, p, q):
+    # Sec. IV-C prices a QR factorisation or an SVD of an r x c matrix at
+    # 2 r c^2 flops and a product with A at C_mult = 2mn per vector.  Run the
+    # printed algorithm (literal power loop) with every matrix product, QR
+    # and SVD counted at those prices: the total must be eq.
+    # (C_SOR-SVD+PM) exactly, so a dropped pass, QR, core or assembly term
+    # in flop_count fails here.
+    real_qr, real_svd = orc.householder_qr, orc.jacobi_svd
+
+    def qr(T):
+        r, c = T.shape
+        _Counting.flops[0] += 2 * r * c * c
+        Q, R = real_qr(np.asarray(T))
+        return Q.view(_Counting), R
+
+    def svd(M):
+        r, c = M.shape
+        _Counting.flops[0] += 2 * r * c * c
+        return real_svd(np.asarray(M))
+    monkeypatch.setattr(orc, "householder_qr", qr)
+    monkeypatch.setattr(orc, "jacobi_svd", svd)
+    A = np.random.default_rng(m).standard_normal((m, n)).view(_Counting)
+    _Counting.flops[0] = 0
+    orc.sorsvd(A, k, p, q, seed=1, mode="literal")
+    assert _Counting.flops[0] == orc.flop_count(m, n, k, p, q)
+
+
+def test_bounds_at_hand_computed_values():
+    # A = diag(2, 1, 1/2, 1/4) (V = I), k = 1, p = 2, l = 3 and
+    # Omega = [[2,0,0],[0,1,0],[0,0,1],[0,0,0]]: Omega1 = V1^T Omega = (2 0 0)
+    # has sigma_min 2 and Omega2 = V2^T Omega has spectral norm 1, so
+    # x = ||Omega2||^2 ||Omega1^+||^2 = 1/4.  sigma_{l-p+1} = sigma_2 = 1.
+    s = np.array([2.0, 1.0, 0.5, 0.25])
+    V = np.eye(4)
+    om = np.array([[2.0, 0, 0], [0, 1, 0], [0, 0, 1], [0, 0, 0]])
+    r3, r17, r65, r257, r1025 = (np.sqrt(v) for v in (3.0, 17.0, 65.0, 257.0, 1025.0))
+    # Theorem 4: sigma_1 / sqrt(1 + x (sigma_2/sigma_1)^(4q+4))
+    #   q = 0: 2 / sqrt(1 + 1/64) = 16/sqrt(65);  q = 1: 2 / sqrt(1 + 1/1024) = 64/sqrt(1025)
+    assert np.isclose(bounds.thm4_lower(s, V, om, 1, 0)[0], 16 / r65, rtol=1e-14, atol=0)
+    assert np.isclose(bounds.thm4_lower(s, V, om, 1, 1)[0], 64 / r1025, rtol=1e-14, atol=0)
+    # Theorem 5 (sigma_k = sigma_1 = 2, sigma_{k+1} = 1):
+    #   q = 0: alpha = 1/2, beta = 1/4, eta = 1, tau = 1/2
+    #     sqrt(alpha^2 x / (1 + beta^2 x)) = 2/sqrt(65), sqrt(eta^2 x / (1 + tau^2 x)) = 2/sqrt(17)
+    #   q = 1: (sigma_2/sigma_1)^2 = 1/4 scales alpha, beta, eta, tau:
+    #     2/sqrt(1025) and 2/sqrt(257)
+    #   ||A0||_2 = 1, ||A0||_F = sqrt(1 + 1/4 + 1/16) = sqrt(21)/4
+    a0f = np.sqrt(21.0) / 4
+    assert np.isclose(bounds.thm5_upper(s, V, om, 1, 0, "2"), 1 + 2 / r65 + 2 / r17, rtol=1e-14, atol=0)
+    assert np.isclose(bounds.thm5_upper(s, V, om, 1, 0, "fro"), a0f + 2 / r65 + 2 / r17, rtol=1e-14, atol=0)
+    assert np.isclose(bounds.thm5_upper(s, V, om, 1, 1, "2"), 1 + 2 / r1025 + 2 / r257, rtol=1e-14, atol=0)
+    # Theorems 6 and 7: nu = nu1 nu2, nu1 = sqrt(n - l + p) + sqrt(l) + 7 = 7 + 2 sqrt(3),
+    # nu2 = 4 e sqrt(l) / (p + 1) = 4 e sqrt(3) / 3; gamma_1 = sigma_2 / sigma_1 = 1/2
+    nu = (7 + 2 * r3) * 4 * np.e * r3 / 3
+    assert np.isclose(bounds.thm6_expected_lower(s, 4, 1, 2, 0)[0], 2 / np.sqrt(1 + nu ** 2 / 16), rtol=1e-14)
+    assert np.isclose(bounds.thm6_expected_lower(s, 4, 1, 2, 1)[0], 2 / np.sqrt(1 + nu ** 2 / 256), rtol=1e-14)
+    # (1 + gamma_k) sqrt(k) nu sigma_{k+1} gamma_k^(2q) = 1.5 nu (q = 0), 0.375 nu (q = 1)
+    assert np.isclose(bounds.thm7_expected_upper(s, 4, 1, 2, 0, "2"), 1 + 1.5 * nu, rtol=1e-14)
+    assert np.isclose(bounds.thm7_expected_upper(s, 4, 1, 2, 1, "2"), 1 + 0.375 * nu, rtol=1e-14)
+    assert np.isclose(bounds.thm7_expected_upper(s, 4, 1, 2, 1, "fro"), a0f + 0.375 * nu, rtol=1e-14)
+
+
 # -- planted mistakes: each plausible slip in the oracle must trip a pin above --
 
 def test_planted_dropped_qr_column_is_caught(monkeypatch):
