@@ -69,6 +69,15 @@ typedef enum {
                                           sorsvd_run_host (adds the device
                                           copies of A, U, S and V); accepted
                                           and ignored by sorsvd_run_host */
+#define SORSVD_FLAG_TWO_PASS      0x8u /* the two-pass core of Sec. III
+                                          (second core option of Algorithm 3):
+                                          M_approx = Q1^T T1 (Q2^T T2_prev)^+
+                                          with T2_prev the operand of the last
+                                          product T1 = A T2_prev; no core pass
+                                          over A (2q + 2 passes instead of
+                                          2q + 3).  REFINE is then ignored.
+                                          Needs the same flag in
+                                          sorsvd_workspace_size. */
 
 /* Largest sketch width l = k + p supported (the small l x l factorisations
  * run in one thread block with the factor in shared memory). */
@@ -155,6 +164,20 @@ int sorsvd_noalloc_get_status(int* device_status, int* info, void* stream);
  * (bit 0: a Cholesky needed a shifted retry; bits 8..15: Jacobi sweeps of
  * the last call).  Either pointer may be NULL. */
 int sorsvd_get_status(const void* workspace, int* device_status, int* info, void* stream);
+
+/* Limits of the device-side failure paths, for tests of those paths (the
+ * paper has no counterpart).  wait_cycles: how long (SM clock cycles) a
+ * tensor-core pass waits for its pipeline to make progress before it
+ * records SORSVD_ERR_TIMEOUT, stops, lets its copies and MMAs in flight
+ * land, frees its tensor memory and returns; <= 0 restores the built-in
+ * 4e9 cycles (about 2 s), larger values are clamped to it.  max_sweeps:
+ * Jacobi sweeps before SORSVD_ERR_NOT_CONVERGED (1..30); <= 0 restores 30.
+ * Applies to calls made afterwards by any thread of the process; the sweep
+ * cap is set on the current device (synchronous copy: not during stream
+ * capture).  Results of a call that hit either limit are not meaningful;
+ * later calls with the defaults restored are unaffected.  Returns SORSVD_OK
+ * or SORSVD_ERR_CUDA. */
+int sorsvd_set_limits(long long wait_cycles, int max_sweeps);
 
 /* Human-readable name of a status code (static string). */
 const char* sorsvd_status_string(int status);

@@ -79,6 +79,8 @@ struct TcParams {
   float* parts;          // G x 2 x (128 MT) x Npad fp32
   int* tilecnt;          // per tile: shares written so far (zero between launches), or null
   DeviceStatus* status;
+  long long wait_cycles; // limit of the waits for pipeline progress (the waits for
+                         // copies and MMAs in flight after an abort keep tc::kWaitCycles)
 };
 
 namespace {
@@ -127,6 +129,53 @@ __device__ __forceinline__ void store_out(const TcParams& P, int64_t grow, int c
   P.out[grow + (int64_t)col * P.ldo] = v;
   if (P.out16_kind == 1) reinterpret_cast<bf16*>(P.out16)[grow + (int64_t)col * P.ld16] = __float2bfloat16_rn(v);
   else if (P.out16_kind == 2) reinterpret_cast<f16*>(P.out16)[grow + (int64_t)col * P.ld16] = __float2half_rn(v);
+}
+
+// Sum of the shares of split tile t (rows row0.., mrows x N), CTA c0's share
+// from slot slot0 and the others' from slot 0, in CTA order (fp32); 4
+// consecutive rows per float4, 4 float4 per thread in flight.
+__device__ void sum_split_tile(const TcParams& P, int64_t row0, int mrows, int64_t c0, int64_t c1, int slot0) {
+  const int per = mrows * P.N;
+  const size_t seg = (size_t)mrows * P.Npad;
+  auto share = [&](int64_t cc, int slot) {
+    return reinterpret_cast<const float4*>(P.parts + ((size_t)cc * 2 + slot) * seg);
+  };
+  const int q4 = mrows / 4, nv = per / 4;
+  const float4* first = share(c0, slot0);
+  for (int f0 = threadIdx.x; f0 < nv; f0 += 4 * blockDim.x) {
+    float acc[4][4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int f = f0 + b * blockDim.x;
+      if (f < nv) {
+        const int col = f / q4, r4 = f - col * q4;
+        const float4 x = first[(size_t)r4 + (size_t)col * q4];
+        acc[b][0] = x.x; acc[b][1] = x.y; acc[b][2] = x.z; acc[b][3] = x.w;
+      }
+    }
+    for (int64_t cc = c0 + 1; cc <= c1; ++cc) {
+      const float4* pc = share(cc, 0);
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int f = f0 + b * blockDim.x;
+        if (f < nv) {
+          const int col = f / q4, r4 = f - col * q4;
+          const float4 x = pc[(size_t)r4 + (size_t)col * q4];
+          acc[b][0] += x.x; acc[b][1] += x.y; acc[b][2] += x.z; acc[b][3] += x.w;
+        }
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int f = f0 + b * blockDim.x;
+      if (f >= nv) continue;
+      const int col = f / q4, r4 = f - col * q4;
+      const int64_t grow = row0 + 4 * r4;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (grow + u < P.M) store_out(P, grow + u, col, acc[b][u]);
+    }
+  }
 }
 
 // ELT: 0 bf16, 1 fp16, 2 tf32, 3 tf32 split (3 MMAs).  A_MN: A operand
@@ -218,7 +267,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         const int64_t t = g / P.ipt;
         const int64_t gend = min(it1, (t + 1) * P.ipt);
         for (int64_t kb = g - t * P.ipt; kb < gend - t * P.ipt; ++kb) {
-          if (!tc::mbar_wait(&empty[stage], phase ^ 1, abortp)) { ok = false; break; }
+          if (!tc::mbar_wait(&empty[stage], phase ^ 1, abortp, P.wait_cycles)) { ok = false; break; }
           tc::mbar_arrive_expect_tx(&full[stage], P.a_bytes);
           armed |= 1u << stage;
           armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
@@ -262,7 +311,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         const int64_t t = g / P.ipt;
         const int64_t gend = min(it1, (t + 1) * P.ipt);
         for (int64_t kb = g - t * P.ipt; kb < gend - t * P.ipt; ++kb) {
-          if (!tc::mbar_wait(&bempty[stage], phase ^ 1, abortp)) { ok = false; break; }
+          if (!tc::mbar_wait(&bempty[stage], phase ^ 1, abortp, P.wait_cycles)) { ok = false; break; }
           tc::mbar_arrive_expect_tx(&bfull[stage], (SPLIT ? 2u : 1u) * P.b_bytes);
           armed |= 1u << stage;
           armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
@@ -306,22 +355,22 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           const int64_t c1 = min(kb1, c0 + CHUNK);
           const int b = (P.nbuf == 2) ? (chunk & 1) : 0;
           const uint32_t use = (P.nbuf == 2) ? (uint32_t)(chunk >> 1) : (uint32_t)chunk;
-          if (!tc::mbar_wait(&tempty[b], (use & 1u) ^ 1u, abortp)) { ok = false; break; }
+          if (!tc::mbar_wait(&tempty[b], (use & 1u) ^ 1u, abortp, P.wait_cycles)) { ok = false; break; }
           if (SPLIT && c0 == kb0 && chunk > 0) {
             // a new segment: the previous fill (the last of the previous
             // segment) has had both correction blocks D2 read and zeroed
             const int pc = chunk - 1;
-            if (!tc::mbar_wait(&tempty[pc & 1], (uint32_t)(pc >> 1) & 1u, abortp)) { ok = false; break; }
+            if (!tc::mbar_wait(&tempty[pc & 1], (uint32_t)(pc >> 1) & 1u, abortp, P.wait_cycles)) { ok = false; break; }
           }
           tc::fence_after_sync();
           const uint32_t dcol = tbase + (uint32_t)(b * MT * P.Npad);
           for (int64_t kb = c0; kb < c1; ++kb) {
             if constexpr (SPLIT) {
-              if (!tc::mbar_wait(&afull[aslot], aphase, abortp)) { ok = false; break; }
+              if (!tc::mbar_wait(&afull[aslot], aphase, abortp, P.wait_cycles)) { ok = false; break; }
             } else {
-              if (!tc::mbar_wait(&full[stage], phase, abortp)) { ok = false; break; }
+              if (!tc::mbar_wait(&full[stage], phase, abortp, P.wait_cycles)) { ok = false; break; }
             }
-            if (!tc::mbar_wait(&bfull[bstage], bphase, abortp)) { ok = false; break; }
+            if (!tc::mbar_wait(&bfull[bstage], bphase, abortp, P.wait_cycles)) { ok = false; break; }
             tc::fence_after_sync();
             const uint32_t sb = tc::smem_u32(bring + (size_t)bstage * P.bstage_bytes);
             if constexpr (SPLIT) {
@@ -404,7 +453,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       const int64_t t = g / P.ipt;
       const int64_t gend = min(it1, (t + 1) * P.ipt);
       for (int64_t kb = g - t * P.ipt; kb < gend - t * P.ipt; ++kb) {
-        if (!tc::mbar_wait(&full[stage], phase, abortp)) { ok = false; break; }
+        // warp-uniform: the tcgen05.st below is a warp-collective
+        if (!__all_sync(0xffffffffu, tc::mbar_wait(&full[stage], phase, abortp, P.wait_cycles))) { ok = false; break; }
         uint8_t* row = smem + (size_t)stage * P.stage_bytes + (size_t)r * 128;
         float lo[2][16];
 #pragma unroll
@@ -423,7 +473,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         }
         if (!P.lo_tmem) fence_proxy_async();   // generic writes -> tensor-core reads
         // at most aslots converted stages ahead of the MMAs
-        if (!tc::mbar_wait(&aempty[aslot], aphase ^ 1u, abortp)) { ok = false; break; }
+        if (!__all_sync(0xffffffffu, tc::mbar_wait(&aempty[aslot], aphase ^ 1u, abortp, P.wait_cycles))) {
+          ok = false;
+          break;
+        }
         if (P.lo_tmem) {
           tc::fence_after_sync();
           const uint32_t ta = tlane + aslot * kASlotCols;
@@ -484,7 +537,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         for (int64_t c0 = kb0; c0 < kb1; c0 += CHUNK) {
           const int b = chunk & 1;
           const uint32_t use = (uint32_t)(chunk >> 1);
-          if (!tc::mbar_wait(&tfull[b], use & 1u, abortp)) { ok = false; break; }
+          // warp-uniform: tcgen05.ld / st are warp-collectives
+          if (!__all_sync(0xffffffffu, tc::mbar_wait(&tfull[b], use & 1u, abortp, P.wait_cycles))) {
+            ok = false;
+            break;
+          }
           tc::fence_after_sync();
           drain((uint32_t)(b * 2 * P.Npad));               // D1 of this fill
           if (c0 + CHUNK >= kb1) {
@@ -516,7 +573,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       for (int64_t c0 = kb0; c0 < kb1; c0 += CHUNK) {
         const int b = (P.nbuf == 2) ? (chunk & 1) : 0;
         const uint32_t use = (P.nbuf == 2) ? (uint32_t)(chunk >> 1) : (uint32_t)chunk;
-        if (!tc::mbar_wait(&tfull[b], use & 1u, abortp)) { ok = false; break; }
+        if (!__all_sync(0xffffffffu, tc::mbar_wait(&tfull[b], use & 1u, abortp, P.wait_cycles))) {
+          ok = false;
+          break;
+        }
         tc::fence_after_sync();
         for (int mt = 0; mt < MT; ++mt) {
           const uint32_t taddr =
@@ -579,55 +639,13 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     const int bits = *lastp;
     if (bits) {
       __threadfence();
-      const int per = mrows * P.N;
-      const size_t seg = (size_t)mrows * P.Npad;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         if (!((bits >> h) & 1)) continue;
         const int64_t t = h ? tt : th;
         const int64_t c0 = cta_of(t * P.ipt, P.total, P.G), c1 = cta_of(t * P.ipt + P.ipt - 1, P.total, P.G);
         const int slot0 = (c0 * P.total / P.G < t * P.ipt) ? 1 : 0;
-        // the share of unit cc comes from CTA cc
-        auto share = [&](int64_t cc, int slot) {
-          return reinterpret_cast<const float4*>(P.parts + ((size_t)cc * 2 + slot) * seg);
-        };
-        // 4 consecutive rows per float4, 4 float4 per thread in flight
-        const int q4 = mrows / 4, nv = per / 4;
-        const float4* first = share(c0, slot0);
-        for (int f0 = threadIdx.x; f0 < nv; f0 += 4 * blockDim.x) {
-          float4 acc[4];
-#pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            const int f = f0 + b * blockDim.x;
-            if (f < nv) {
-              const int col = f / q4, r4 = f - col * q4;
-              acc[b] = first[(size_t)r4 + (size_t)col * q4];
-            }
-          }
-          for (int64_t cc = c0 + 1; cc <= c1; ++cc) {
-            const float4* pc = share(cc, 0);
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-              const int f = f0 + b * blockDim.x;
-              if (f < nv) {
-                const int col = f / q4, r4 = f - col * q4;
-                const float4 x = pc[(size_t)r4 + (size_t)col * q4];
-                acc[b].x += x.x; acc[b].y += x.y; acc[b].z += x.z; acc[b].w += x.w;
-              }
-            }
-          }
-#pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            const int f = f0 + b * blockDim.x;
-            if (f >= nv) continue;
-            const int col = f / q4, r4 = f - col * q4;
-            const int64_t grow = t * urows + rank * mrows + 4 * r4;
-            const float v[4] = {acc[b].x, acc[b].y, acc[b].z, acc[b].w};
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-              if (grow + u < P.M) store_out(P, grow + u, col, v[u]);
-          }
-        }
+        sum_split_tile(P, t * urows + rank * mrows, mrows, c0, c1, slot0);
         if (threadIdx.x == 0) P.tilecnt[t] = 0;     // ready for the next launch
       }
     }
@@ -642,6 +660,22 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 // tile's elements.  The CTAs that cover tile t are c0..c1 (consecutive);
 // tile t is the head segment (slot 0) of each of them except c0 when c0's
 // range starts inside an earlier tile (then it is c0's tail, slot 1).
+// sum of the shares c0..c1 of one tile element (fp32; four independent
+// chains for loads in flight, combined in a fixed order)
+__device__ __forceinline__ float sum_shares(const TcParams& P, int64_t c0, int64_t c1, int slot0, size_t off,
+                                            size_t seg) {
+  float a0 = P.parts[((size_t)c0 * 2 + slot0) * seg + off], a1 = 0.f, a2 = 0.f, a3 = 0.f;
+  int64_t c = c0 + 1;
+  for (; c + 3 <= c1; c += 4) {
+    a0 += P.parts[(size_t)c * 2 * seg + off];
+    a1 += P.parts[(size_t)(c + 1) * 2 * seg + off];
+    a2 += P.parts[(size_t)(c + 2) * 2 * seg + off];
+    a3 += P.parts[(size_t)(c + 3) * 2 * seg + off];
+  }
+  for (; c <= c1; ++c) a0 += P.parts[(size_t)c * 2 * seg + off];
+  return (a0 + a1) + (a2 + a3);
+}
+
 __global__ void tc_fixup_kernel(const TcParams P) {
   const int mrows = 128 * P.MT;
   const int per = mrows * P.N;
@@ -660,10 +694,7 @@ __global__ void tc_fixup_kernel(const TcParams P) {
       if (grow >= P.M) continue;
       const size_t off = (size_t)row + (size_t)col * mrows;
       const size_t seg = (size_t)mrows * P.Npad;
-      // a handful of fp32 partials: fp32 sums (binary64 adds are slow here)
-      float s = P.parts[((size_t)c0 * 2 + slot0) * seg + off];
-      for (int64_t c = c0 + 1; c <= c1; ++c) s += P.parts[(size_t)c * 2 * seg + off];
-      store_out(P, grow, col, s);
+      store_out(P, grow, col, sum_shares(P, c0, c1, slot0, off, seg));
     }
   }
 }
@@ -752,6 +783,9 @@ cudaError_t launch_typed(const CUtensorMap& ma, const CUtensorMap& mb, const CUt
   }
   }
 }
+
+// limit of the progress waits of the next launches (0: tc::kWaitCycles)
+long long g_wait_cycles = 0;
 
 int env_int(const char* name, int dflt) {
   const char* v = std::getenv(name);
@@ -858,6 +892,8 @@ cudaError_t launch_tc_gemm(bool trans_a, int elt, int64_t M, int64_t N, int64_t 
   if (P.stages < 2) return cudaErrorInvalidValue;
   P.out = out; P.ldo = ldo; P.out16 = out16; P.ld16 = ld16; P.out16_kind = out16 ? out16_kind : 0;
   P.parts = parts; P.status = status;
+  P.wait_cycles = (g_wait_cycles > 0 && g_wait_cycles < tc::kWaitCycles) ? g_wait_cycles : tc::kWaitCycles;
+
   P.tilecnt = (tilecnt && P.tiles <= ntilecnt) ? tilecnt : nullptr;
   const int AK = elt >= 2 ? 32 : 64, AMN = elt >= 2 ? 32 : 64;
   const int map_elt = elt == 3 ? 2 : elt;
@@ -885,11 +921,13 @@ cudaError_t launch_tc_gemm(bool trans_a, int elt, int64_t M, int64_t N, int64_t 
   // one block row per CTA boundary, about 4 elements of the tile per thread
   if (P.G < 2 || P.tilecnt) return cudaSuccess;
   const int64_t per = (int64_t)128 * P.MT * P.N;
-  const int64_t gy = std::max<int64_t>(1, std::min<int64_t>((per + 1023) / 1024, 65535));
+  const int64_t gy = std::max<int64_t>(1, std::min<int64_t>((per + 255) / 256, 65535));
   ProfScope ps2(K_REDUCE, st);
   tc_fixup_kernel<<<dim3((unsigned)(P.G - 1), (unsigned)gy), 256, 0, st>>>(P);
   return cudaGetLastError();
 }
+
+void set_tc_wait_cycles(long long cycles) { g_wait_cycles = cycles > 0 ? cycles : 0; }
 
 cudaError_t launch_split_tf32(const float* X, int64_t ldx, int64_t rows, int64_t cols, float* hi, float* lo,
                               int64_t ldh, cudaStream_t st) {

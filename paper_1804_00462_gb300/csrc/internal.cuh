@@ -178,6 +178,12 @@ cudaError_t launch_polar_inv(const double* G, int l, float* Rinv, float* scratch
 cudaError_t launch_jacobi(const double* M, int l, int k, bool f64, void* Ut, void* Vt,
                           void* S, bool S_f64, void* work, DeviceStatus* status, cudaStream_t st);
 size_t jacobi_work_bytes(int l);
+// Sweep cap of the Jacobi kernels launched next on the current device
+// (<= 0 or above the built-in cap of 30: 30).
+cudaError_t set_jacobi_sweep_cap(int cap);
+// Limit (SM cycles) of the tensor-core passes' waits for pipeline progress
+// in the launches that follow (<= 0: the built-in ~2 s).
+void set_tc_wait_cycles(long long cycles);
 
 // rowblock.cu: fp32 row-block products (l <= SORSVD_MAX_L columns).
 // launch_rb_gram: rb_gram_blocks(rows, lx, ly, sym) partials (lx x ly, ld lx,
@@ -200,6 +206,14 @@ cudaError_t launch_rb_copy(const float* src, float* dst, int64_t ld, int64_t row
 // partials (ld ldp, stride between partials), one thread per element
 cudaError_t launch_reduce_parts(const float* parts, int nparts, int64_t stride, int rows, int cols, int ldp,
                                      double* out, int ldo, cudaStream_t st);
+
+// twopass.cu: C (l x l) = op(A) op(B) in binary64 (op: transpose when the
+// flag is set); exact widening of a column-major matrix: 16-bit (BF16/F16)
+// to fp32, or fp32 to binary64 (y_f64).
+cudaError_t launch_small_gemm64(const double* A, bool ta, const double* B, bool tb, double* C, int l,
+                                cudaStream_t st);
+cudaError_t launch_widen(const void* x, int in_dtype, int64_t ldx, int64_t rows, int64_t cols, void* y, bool y_f64,
+                         int64_t ldy, cudaStream_t st);
 
 // sorsvd.cu: the device status word of a sorsvd_run workspace
 DeviceStatus* workspace_status(void* ws);

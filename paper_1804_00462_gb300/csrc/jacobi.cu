@@ -33,6 +33,10 @@ namespace sorsvd {
 namespace {
 
 constexpr int kMaxSweeps = 30;
+// sweep cap of the next launches on this device (1..kMaxSweeps; a test
+// lowers it to make SORSVD_ERR_NOT_CONVERGED happen)
+__device__ int g_sweep_cap = kMaxSweeps;
+__device__ __forceinline__ int sweep_cap() { return min(max(g_sweep_cap, 1), kMaxSweeps); }
 
 __device__ __forceinline__ int rr_player(int pos, int round, int N) {
   // position 0 is fixed; positions 1..N-1 rotate by one place per round
@@ -102,7 +106,8 @@ __device__ __forceinline__ void jacobi_sweep_body(const double* __restrict__ Min
 
   const int N = (l + 1) & ~1;
   int sweep;
-  for (sweep = 1; sweep <= kMaxSweeps; ++sweep) {
+  const int cap = sweep_cap();
+  for (sweep = 1; sweep <= cap; ++sweep) {
     if (t == 0) { s_rot = 0; s_big = 0; }
     __syncthreads();
     int rot_local = 0, big_local = 0;
@@ -152,12 +157,12 @@ __device__ __forceinline__ void jacobi_sweep_body(const double* __restrict__ Min
     const int rot = s_rot, bg = s_big;
     __syncthreads();
     if (!rot) break;
-    if (sweep == kMaxSweeps) {
+    if (sweep == cap) {
       if (bg && t == 0) raise_status(status, SORSVD_ERR_NOT_CONVERGED);
       break;
     }
   }
-  if (t == 0) atomicOr(&status->info, (min(sweep, kMaxSweeps)) << 8);
+  if (t == 0) atomicOr(&status->info, (min(sweep, cap)) << 8);
   for (int e = t; e < l * l; e += blockDim.x) Vout[e] = V[e];
 }
 
@@ -193,7 +198,8 @@ __device__ __forceinline__ void jacobi_sweep_body_f2(const double* __restrict__ 
 
   const int N = (l + 1) & ~1;
   int sweep;
-  for (sweep = 1; sweep <= kMaxSweeps; ++sweep) {
+  const int cap = sweep_cap();
+  for (sweep = 1; sweep <= cap; ++sweep) {
     if (t == 0) { s_rot = 0; s_big = 0; }
     __syncthreads();
     int rot_local = 0, big_local = 0;
@@ -242,12 +248,12 @@ __device__ __forceinline__ void jacobi_sweep_body_f2(const double* __restrict__ 
     const int rot = s_rot, bg = s_big;
     __syncthreads();
     if (!rot) break;
-    if (sweep == kMaxSweeps) {
+    if (sweep == cap) {
       if (bg && t == 0) raise_status(status, SORSVD_ERR_NOT_CONVERGED);
       break;
     }
   }
-  if (t == 0) atomicOr(&status->info, (min(sweep, kMaxSweeps)) << 8);
+  if (t == 0) atomicOr(&status->info, (min(sweep, cap)) << 8);
   for (int e = t; e < l * l; e += blockDim.x) {
     const int c = e / l, i = e - c * l;
     Vout[e] = V[i + (size_t)c * ldw];
@@ -291,7 +297,8 @@ __device__ __forceinline__ void jacobi_sweep_body_g(const double* __restrict__ M
   __syncthreads();
 
   int sweep;
-  for (sweep = 1; sweep <= kMaxSweeps; ++sweep) {
+  const int cap = sweep_cap();
+  for (sweep = 1; sweep <= cap; ++sweep) {
     if (t == 0) { s_rot = 0; s_big = 0; }
     __syncthreads();
     int rot_local = 0, big_local = 0;
@@ -346,12 +353,12 @@ __device__ __forceinline__ void jacobi_sweep_body_g(const double* __restrict__ M
     const int rot = s_rot, bg = s_big;
     __syncthreads();
     if (!rot) break;
-    if (sweep == kMaxSweeps) {
+    if (sweep == cap) {
       if (bg && t == 0) raise_status(status, SORSVD_ERR_NOT_CONVERGED);
       break;
     }
   }
-  if (t == 0) atomicOr(&status->info, (min(sweep, kMaxSweeps)) << 8);
+  if (t == 0) atomicOr(&status->info, (min(sweep, cap)) << 8);
   for (int e = t; e < l * l; e += blockDim.x) {
     const int c = e / l, i = e - c * l;
     Vout[e] = V[i + (size_t)c * ldw];
@@ -395,7 +402,8 @@ jacobi_sweep_coop_kernel(const double* __restrict__ Min, int l, int ldw, float* 
   const int N = (l + 1) & ~1;
   const int pr_base = blockIdx.x * kCoopPairsPerCta + grp;
   int sweep;
-  for (sweep = 1; sweep <= kMaxSweeps; ++sweep) {
+  const int cap = sweep_cap();
+  for (sweep = 1; sweep <= cap; ++sweep) {
     int rot_local = 0, big_local = 0;
     for (int r = 0; r < N - 1; ++r) {
       for (int pr = pr_base; pr < N / 2; pr += gridDim.x * kCoopPairsPerCta) {
@@ -446,12 +454,12 @@ jacobi_sweep_coop_kernel(const double* __restrict__ Min, int l, int ldw, float* 
     grid.sync();
     const int rot = *((volatile int*)&flags[2 * sweep]), bg = *((volatile int*)&flags[2 * sweep + 1]);
     if (!rot) break;
-    if (sweep == kMaxSweeps) {
+    if (sweep == cap) {
       if (bg && gt == 0) raise_status(status, SORSVD_ERR_NOT_CONVERGED);
       break;
     }
   }
-  if (gt == 0) atomicOr(&status->info, (min(sweep, kMaxSweeps)) << 8);
+  if (gt == 0) atomicOr(&status->info, (min(sweep, cap)) << 8);
   for (int64_t e = gt; e < (int64_t)l * l; e += gn) {
     const int c = (int)(e / l), i = (int)(e - (int64_t)c * l);
     Vout[e] = V[i + (size_t)c * ldw];
@@ -606,7 +614,8 @@ jacobi_sweep_cluster_kernel(const double* __restrict__ Min, int l, int gpc, floa
     dcta[h] = g2 / gpc;
   }
   int buf = 0, sweep;
-  for (sweep = 1; sweep <= kMaxSweeps; ++sweep) {
+  const int cap = sweep_cap();
+  for (sweep = 1; sweep <= cap; ++sweep) {
     const int par = sweep & 1;
     int rot_local = 0, big_local = 0;
     // players at the group's positions: rr_player(p, r, N) = 1 + (p - 1 - r) mod (N - 1), stepped down per round
@@ -717,12 +726,12 @@ jacobi_sweep_cluster_kernel(const double* __restrict__ Min, int l, int gpc, floa
     // this parity's flags are next used two sweeps on, after two more barriers
     if (rank == 0 && t == 0) { s_flag[par] = 0; s_big[par] = 0; }
     if (!rot) break;
-    if (sweep == kMaxSweeps) {
+    if (sweep == cap) {
       if (bg && rank == 0 && t == 0) raise_status(status, SORSVD_ERR_NOT_CONVERGED);
       break;
     }
   }
-  if (rank == 0 && t == 0) atomicOr(&status->info, (min(sweep, kMaxSweeps)) << 8);
+  if (rank == 0 && t == 0) atomicOr(&status->info, (min(sweep, cap)) << 8);
   // a sweep ends where it began: position p holds column p
   for (int e = t; e < 2 * gpc * LDW; e += blockDim.x) {
     const int sl = e / LDW, i = e - sl * LDW;
@@ -1145,6 +1154,11 @@ cudaError_t run_all(const double* M, int l, int k, void* Ut, void* Vt, void* S, 
 }
 
 }  // namespace
+
+cudaError_t set_jacobi_sweep_cap(int cap) {
+  const int v = (cap > 0 && cap < kMaxSweeps) ? cap : kMaxSweeps;
+  return cudaMemcpyToSymbol(g_sweep_cap, &v, sizeof(int));
+}
 
 size_t jacobi_work_bytes(int l) {
   return ((jacobi_base_bytes(l) + 255) & ~(size_t)255) + sweep_coop_work_bytes(l);

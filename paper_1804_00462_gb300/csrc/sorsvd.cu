@@ -35,6 +35,7 @@ bool tc_enabled() { static const int v = env_flag("SORSVD_TC", 1); return v != 0
 // of taking the polar factor of its near-identity Gram
 bool polar_enabled() { static const int v = env_flag("SORSVD_POLAR", 1); return v != 0; }
 
+
 constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
@@ -76,12 +77,13 @@ inline int elt_of(int dt) {
 struct Layout {
   int64_t ldm, ldn;      // leading dimensions of the m x l / n x l sketches
   size_t status, tilecnt, at, t2op, t2, t1, t1op, q2op, tmp, bhi, blo, parts, G, Rinv, M, Ut, Vt, jwork, total;
+  size_t t1s, t2s, tp;   // two-pass core: T1 before its QR, T2_prev, five l x l binary64 matrices
   int64_t ntilecnt;      // counters of the split tiles of a tensor-core pass
   int64_t ldb;           // leading dimension of bhi / blo
   bool has_at;           // fp32 containers: A^T kept for the products A X
 };
 
-Layout make_layout(int64_t m, int64_t n, int l, int dt) {
+Layout make_layout(int64_t m, int64_t n, int l, int dt, unsigned flags = 0) {
   Layout L{};
   const size_t acc = acc_size(dt), op = dtype_size(dt);
   const bool h16 = dtype_is_16(dt);
@@ -153,6 +155,11 @@ Layout make_layout(int64_t m, int64_t n, int l, int dt) {
   // the Jacobi work area doubles as the scratch of the polar second
   // CholeskyQR pass (the two are never live at the same time)
   L.jwork = take(std::max(jacobi_work_bytes(l), polar_scratch_bytes(l)));
+  if (flags & SORSVD_FLAG_TWO_PASS) {
+    L.t1s = take((size_t)L.ldm * l * acc);
+    L.t2s = take((size_t)L.ldn * l * acc);
+    L.tp = take((size_t)5 * l * l * 8);
+  }
   L.total = off;
   return L;
 }
@@ -551,6 +558,43 @@ int upload_a(const Ctx& c, const void* Ah, int64_t lda, int64_t m, int64_t n, vo
   return r;
 }
 
+// Keep the operand X (n x l, ldx; the pass element type) of the last
+// product T1 = A X as T2_prev for the two-pass core: fp32 (binary64 for
+// F64), the 16-bit operand widened exactly.
+int save_t2prev(const Ctx& c, const void* X, int64_t ldx, int64_t n, int l) {
+  if (dtype_is_16(c.dt)) {
+    LAUNCH(K_MISC, launch_widen(X, c.dt, ldx, n, l, c.at(c.L.t2s), false, c.L.ldn, c.st));
+  } else {
+    LAUNCH(K_MISC, launch_copy2d(X, ldx, c.at(c.L.t2s), c.L.ldn, n, l, acc_size(c.dt), c.st));
+  }
+  return SORSVD_OK;
+}
+
+// The two-pass core (Sec. III): M (l x l, binary64) = C B^+ with
+// C = Q1^T T1 and B = Q2^T T2_prev, B^+ = B^T (B B^T)^{-1} and
+// (B B^T)^{-1} = R^{-1} R^{-T} from the Cholesky-inverse kernel (binary64
+// factor for l <= SORSVD_MAX_L_F64, fp32 above: then the error grows with
+// cond(B)^2, which stays near 1 once the power loop has converged).
+int core_two_pass(const Ctx& c, int64_t m, int64_t n, int l, double* M) {
+  const Layout& L = c.L;
+  double* tp = (double*)c.at(L.tp);
+  const size_t ll = (size_t)l * l;
+  double *Cm = tp, *Bm = tp + ll, *R = tp + 2 * ll, *W = tp + 3 * ll, *V = tp + 4 * ll;
+  double* G = (double*)c.at(L.G);
+  int r = cross_gram(c, c.at(L.t1), L.ldm, c.at(L.t1s), L.ldm, m, l, Cm, l);
+  if (r) return r;
+  r = cross_gram(c, c.at(L.t2), L.ldn, c.at(L.t2s), L.ldn, n, l, Bm, l);
+  if (r) return r;
+  LAUNCH(K_SMALL_GEMM, launch_small_gemm64(Bm, false, Bm, true, G, l, c.st));         // B B^T
+  const bool r64 = l <= SORSVD_MAX_L_F64;
+  LAUNCH(K_CHOL, launch_chol_inv(G, l, 0.0, r64 ? (void*)R : c.at(L.Rinv), r64, c.status(), c.st));
+  if (!r64) LAUNCH(K_MISC, launch_widen(c.at(L.Rinv), SORSVD_F32, l, l, l, R, true, l, c.st));
+  LAUNCH(K_SMALL_GEMM, launch_small_gemm64(Cm, false, Bm, true, W, l, c.st));          // C B^T
+  LAUNCH(K_SMALL_GEMM, launch_small_gemm64(W, false, R, false, V, l, c.st));           // . R^{-1}
+  LAUNCH(K_SMALL_GEMM, launch_small_gemm64(V, false, R, true, M, l, c.st));            // . R^{-T}
+  return SORSVD_OK;
+}
+
 // Algorithm 3 after Omega (in t2op) and, for the fp32 containers, the
 // transposed copy of A are in place: the power loop, the QR step, the core,
 // its truncated SVD and the output assembly, all queued on c.st.
@@ -560,6 +604,13 @@ int solve(const Ctx& c, const void* A, int64_t m, int64_t n, int64_t lda, int k,
   const int dtype = c.dt;
   const int adt = c.f64 ? SORSVD_F64 : SORSVD_F32;
   const bool h16 = dtype_is_16(dtype);
+  const bool two = (flags & SORSVD_FLAG_TWO_PASS) != 0;
+  auto orth1 = [&](int np, void* o16, void** res) {
+    return orth(c, c.at(L.t1), m, L.ldm, l, np, first_shift(dtype), o16, L.ldm, res);
+  };
+  auto orth2 = [&](int np, void* o16, void** res) {
+    return orth(c, c.at(L.t2), n, L.ldn, l, np, first_shift(dtype), o16, L.ldn, res);
+  };
   int r;
   if (flags & SORSVD_FLAG_LITERAL_POWER) {
     // Algorithm 3 as printed: the sketches are orthonormalised only at the end
@@ -567,13 +618,18 @@ int solve(const Ctx& c, const void* A, int64_t m, int64_t n, int64_t lda, int k,
       if (i > 1 && h16)
         LAUNCH(K_MISC, launch_convert_f32((const float*)c.at(L.t2), L.ldn, n, l, c.at(L.t2op), L.ldn, dtype, nullptr,
                                           c.st));
+      if (i == q + 1 && two) {
+        r = save_t2prev(c, c.at(L.t2op), L.ldn, n, l);
+        if (r) return r;
+      }
       r = power_pass_impl(c, A, m, n, lda, c.at(L.t2op), L.ldn, l, c.at(L.t1), L.ldm, c.at(L.t2), L.ldn,
                           i == q + 1);
       if (r) return r;
     }
-    r = orth(c, c.at(L.t1), m, L.ldm, l, 3, first_shift(dtype));
+    if (two) LAUNCH(K_MISC, launch_copy2d(c.at(L.t1), L.ldm, c.at(L.t1s), L.ldm, m, l, acc_size(dtype), c.st));
+    r = orth1(3, nullptr, nullptr);
     if (r) return r;
-    r = orth(c, c.at(L.t2), n, L.ldn, l, 3, first_shift(dtype));
+    r = orth2(3, nullptr, nullptr);
     if (r) return r;
   } else {
     // Each sketch is orthonormalised as soon as it is formed: T1 before the
@@ -593,24 +649,30 @@ int solve(const Ctx& c, const void* A, int64_t m, int64_t n, int64_t lda, int k,
       // fp32-accurate split products in the last iteration.  Inside the
       // loop the orthonormalised sketch may stay in the tmp buffer: it is
       // only the operand of the next product.
+      if (last && two) {
+        r = save_t2prev(c, x2, L.ldn, n, l);
+        if (r) return r;
+      }
       r = pass(c, last ? kc : K_PASS, false, m, l, n, A, lda, x2, L.ldn, h16 ? dtype : adt, c.at(L.t1), L.ldm,
                nullptr, 0, last);
       if (r) return r;
+      if (last && two)
+        LAUNCH(K_MISC, launch_copy2d(c.at(L.t1), L.ldm, c.at(L.t1s), L.ldm, m, l, acc_size(dtype), c.st));
       void* q1 = nullptr;
-      r = orth(c, c.at(L.t1), m, L.ldm, l, np, first_shift(dtype), h16 ? t1op : nullptr, L.ldm, last ? nullptr : &q1);
+      r = orth1(np, h16 ? t1op : nullptr, last ? nullptr : &q1);
       if (r) return r;
       const void* y1 = h16 ? t1op : (q1 ? q1 : c.at(L.t1));
       r = pass(c, last ? kc : K_PASS, true, n, l, m, A, lda, y1, L.ldm, h16 ? dtype : adt, c.at(L.t2), L.ldn,
                nullptr, 0, last);
       if (r) return r;
       void* q2 = nullptr;
-      r = orth(c, c.at(L.t2), n, L.ldn, l, np, first_shift(dtype), (!last && h16) ? c.at(L.t2op) : nullptr, L.ldn,
-               last ? nullptr : &q2);
+      r = orth2(np, (!last && h16) ? c.at(L.t2op) : nullptr, last ? nullptr : &q2);
       if (r) return r;
       x2 = h16 ? c.at(L.t2op) : (q2 ? q2 : c.at(L.t2));
     }
   }
-  r = core_impl(c, A, m, n, lda, flags, c.at(L.t1), L.ldm, c.at(L.t2), L.ldn, l, (double*)c.at(L.M), l);
+  r = two ? core_two_pass(c, m, n, l, (double*)c.at(L.M))
+          : core_impl(c, A, m, n, lda, flags, c.at(L.t1), L.ldm, c.at(L.t2), L.ldn, l, (double*)c.at(L.M), l);
   if (r) return r;
   LAUNCH(K_JACOBI, launch_jacobi((const double*)c.at(L.M), l, k, c.f64, c.at(L.Ut), c.at(L.Vt), S, c.f64,
                                   c.at(L.jwork), c.status(), c.st));
@@ -636,7 +698,7 @@ size_t sorsvd_workspace_size(int64_t m, int64_t n, int k, int p, int dtype, unsi
   if (check_dtype(dtype) || m < 1 || n < 1 || k < 1 || p < 0) return 0;
   int l = k + p;
   if (l > std::min(m, n) || l > max_l(dtype)) return 0;
-  const size_t base = make_layout(m, n, l, dtype).total;
+  const size_t base = make_layout(m, n, l, dtype, flags).total;
   return (flags & SORSVD_FLAG_HOST_IO) ? host_io_layout(base, m, n, k, dtype).total : base;
 }
 
@@ -653,6 +715,11 @@ const char* sorsvd_status_string(int s) {
     case SORSVD_ERR_UNSUPPORTED: return "size beyond a documented limit";
     default: return "unknown status";
   }
+}
+
+int sorsvd_set_limits(long long wait_cycles, int max_sweeps) {
+  set_tc_wait_cycles(wait_cycles);
+  return set_jacobi_sweep_cap(max_sweeps) == cudaSuccess ? SORSVD_OK : SORSVD_ERR_CUDA;
 }
 
 int sorsvd_get_status(const void* workspace, int* device_status, int* info, void* stream) {
@@ -743,11 +810,11 @@ int sorsvd_run(const void* A, int64_t m, int64_t n, int64_t lda, int k, int p, i
   if (!A || !U || !S || !V) return SORSVD_ERR_ARG;
   if (m < 1 || n < 1 || k < 1 || p < 0 || q < 0 || q > 1000 || lda < m || ldu < m || ldv < n)
     return SORSVD_ERR_ARG;
-  if (flags & ~(SORSVD_FLAG_LITERAL_POWER | SORSVD_FLAG_REFINE)) return SORSVD_ERR_ARG;
+  if (flags & ~(SORSVD_FLAG_LITERAL_POWER | SORSVD_FLAG_REFINE | SORSVD_FLAG_TWO_PASS)) return SORSVD_ERR_ARG;
   const int l = k + p;
   if (l > std::min(m, n)) return SORSVD_ERR_ARG;
   if (l > max_l(dtype)) return SORSVD_ERR_UNSUPPORTED;
-  Layout L = make_layout(m, n, l, dtype);
+  Layout L = make_layout(m, n, l, dtype, flags);
   if (int r = check_ws(workspace, ws_bytes, L)) return r;
   Ctx c{(char*)workspace, L, dtype, dtype == SORSVD_F64, (cudaStream_t)stream};
   int r;
@@ -773,11 +840,12 @@ int sorsvd_run_host(const void* A, int64_t m, int64_t n, int64_t lda, int k, int
   if (!A || !U || !S || !V) return SORSVD_ERR_ARG;
   if (m < 1 || n < 1 || k < 1 || p < 0 || q < 0 || q > 1000 || lda < m || ldu < m || ldv < n)
     return SORSVD_ERR_ARG;
-  if (flags & ~(SORSVD_FLAG_LITERAL_POWER | SORSVD_FLAG_REFINE | SORSVD_FLAG_HOST_IO)) return SORSVD_ERR_ARG;
+  if (flags & ~(SORSVD_FLAG_LITERAL_POWER | SORSVD_FLAG_REFINE | SORSVD_FLAG_HOST_IO | SORSVD_FLAG_TWO_PASS))
+    return SORSVD_ERR_ARG;
   const int l = k + p;
   if (l > std::min(m, n)) return SORSVD_ERR_ARG;
   if (l > max_l(dtype)) return SORSVD_ERR_UNSUPPORTED;
-  Layout L = make_layout(m, n, l, dtype);
+  Layout L = make_layout(m, n, l, dtype, flags & ~SORSVD_FLAG_HOST_IO);
   const HostIo H = host_io_layout(L.total, m, n, k, dtype);
   if (!workspace || ((uintptr_t)workspace) % kAlign || ws_bytes < H.total) return SORSVD_ERR_WORKSPACE;
   Ctx c{(char*)workspace, L, dtype, dtype == SORSVD_F64, (cudaStream_t)stream};

@@ -23,6 +23,7 @@ from ._build import LIB
 F64, F32, TF32, BF16, F16 = 0, 1, 2, 3, 4
 FLAG_LITERAL_POWER = 0x1
 FLAG_REFINE = 0x2
+FLAG_TWO_PASS = 0x8
 MAX_L, MAX_L_F64 = 320, 224
 
 _TORCH_OF = {F64: torch.float64, F32: torch.float32, TF32: torch.float32, BF16: torch.bfloat16,
@@ -45,6 +46,8 @@ _lib.sorsvd_run_host.argtypes = [_vp, _i64, _i64, _i64, _int, _int, _int, _u64, 
 _lib.sorsvd_run_host.restype = _int
 _lib.sorsvd_get_status.argtypes = [_vp, C.POINTER(_int), C.POINTER(_int), _vp]
 _lib.sorsvd_get_status.restype = _int
+_lib.sorsvd_set_limits.argtypes = [C.c_longlong, _int]
+_lib.sorsvd_set_limits.restype = _int
 _lib.sorsvd_status_string.argtypes = [_int]
 _lib.sorsvd_status_string.restype = C.c_char_p
 _lib.sorsvd_gaussian.argtypes = [_vp, _i64, _i64, _i64, _u64, _u64, _int, _vp]
@@ -211,6 +214,11 @@ def get_status(workspace: torch.Tensor, stream=None):
     _check(_lib.sorsvd_get_status(workspace.data_ptr(), C.byref(st), C.byref(info), _stream(stream)),
            "sorsvd_get_status")
     return st.value, info.value
+
+
+def set_limits(wait_cycles: int = 0, max_sweeps: int = 0):
+    """Failure-path limits of later calls (0 restores the defaults)."""
+    _check(_lib.sorsvd_set_limits(int(wait_cycles), int(max_sweeps)), "sorsvd_set_limits")
 
 
 def gaussian(rows: int, cols: int, seed: int, stream_id: int = 0, dtype=F64, device="cuda", stream=None):

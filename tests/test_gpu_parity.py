@@ -62,6 +62,39 @@ def gates(exact, got, ref):
     return r_gpu, r_orc, ds
 
 
+def subspace_sin(Y, X, C, j):
+    """sin of the largest principal angle between the spans of the first j
+    columns of Y and of the orthonormal basis X (C = X^T Y): the spectral
+    norm of the residual Y_j - X_j X_j^T Y_j, formed explicitly (the form
+    sqrt(1 - sigma_min(C_j)^2) cannot resolve angles below ~1e-8)."""
+    R = Y[:, :j] - X[:, :j] @ C[:j, :j]
+    return float(np.sqrt(max(0.0, float(np.linalg.eigvalsh(R.T @ R)[-1]))))
+
+
+def leading_gaps(sigma_core, k, tol):
+    """Leading j <= k whose relative gap (sigma_j - sigma_{j+1}) / sigma_1 in
+    the oracle's core spectrum exceeds 100 tol: there U_j, V_j are
+    determined to about tol / gap."""
+    s = np.asarray(sigma_core)
+    return [(j, (s[j - 1] - s[j]) / s[0]) for j in range(1, k + 1) if (s[j - 1] - s[j]) / s[0] > 100 * tol]
+
+
+def check_subspaces(got, ref, info, k, tol, factor=10.0, every=1):
+    """Davis-Kahan-Wedin form: sin Theta_j <= factor tol / gap_j for the
+    leading j with a gap (every `every`-th of them, and the last); returns
+    the largest sin Theta seen."""
+    U, S, V = (to_np(t) for t in got)
+    Uo, So, Vo = ref
+    Cu, Cv = Uo.T @ U, Vo.T @ V
+    worst = 0.0
+    gaps = leading_gaps(info["sigma_core"], k, tol)
+    for j, gap in gaps[::every] + gaps[-1:]:
+        su, sv = subspace_sin(U, Uo, Cu, j), subspace_sin(V, Vo, Cv, j)
+        assert su <= factor * tol / gap and sv <= factor * tol / gap, (j, gap, su, sv)
+        worst = max(worst, su, sv)
+    return worst
+
+
 def run_both(nat, A64, k, p, q, seed, dt, flags=0, mode="stabilised"):
     store, exact = inputs.to_storage(A64, dt)
     A = cuda_colmajor(store, dt)
@@ -199,12 +232,20 @@ def test_core_elementwise(nat, dt, flags, tol):
     tq2 = torch.from_numpy(np.ascontiguousarray(Q2.T)).to(qd).cuda().T
     M = nat.core(cuda_colmajor(store, dt), tq1, tq2, k, p, dtype=dt, flags=flags)
     torch.cuda.synchronize()
-    if dt == "tf32" and TC_ON:
-        Mo = to_np(tq1).T @ (trunc_tf32(exact) @ trunc_tf32(to_np(tq2)))
-    else:
-        Mo = to_np(tq1).T @ exact @ to_np(tq2)
+    tc = TC_ON and dt != "f64"
+    Aop = trunc_tf32(exact) if dt == "tf32" and tc else exact
+    Q2op = trunc_tf32(to_np(tq2)) if dt == "tf32" and tc else to_np(tq2)
+    Mo = to_np(tq1).T @ (Aop @ Q2op)
     err = np.linalg.norm(to_np(M) - Mo) / np.linalg.norm(Mo)
     assert err <= tol, err
+    # element by element: |M - Mo| <= t (|Q1|^T |A| |Q2|) with t the bound of
+    # the pass W = A Q2 (K = n), the fp32 Gram Q1^T W (K = m) and the 16-bit
+    # rounding of Q2 (REFINE: of what hi + lo leaves, 2^-(2p+2))
+    rnd = {"bf16": (2.0 ** -9, 2.0 ** -17), "f16": (2.0 ** -11, 2.0 ** -22)}.get(dt, (0.0, 0.0))[flags == 2]
+    t = rnd + (2 if flags == 2 else 1) * elem_tol(dt if dt != "f64" else "f64", n, tc) + \
+        (2 * m * 2.0 ** -53 if dt == "f64" else 2 * m * 2.0 ** -24)
+    bound = np.abs(to_np(tq1)).T @ (np.abs(Aop) @ np.abs(Q2op))
+    assert float(np.max(np.abs(to_np(M) - Mo) / bound)) <= t
 
 
 # ---------------------------------------------------------------------------
@@ -214,10 +255,24 @@ def test_core_elementwise(nat, dt, flags, tol):
 @pytest.mark.parametrize("q", [0, 1])
 def test_run_cfg1_f64(nat, q):
     A64, s, _, _ = inputs.cfg1(seed=0)
-    exact, got, ref = run_both(nat, A64, 20, 5, q, 0, "f64")
+    store, exact = inputs.to_storage(A64, "f64")
+    got = nat.run(cuda_colmajor(store, "f64"), 20, 5, q, seed=0, dtype="f64", check=True)
+    torch.cuda.synchronize()
+    Uo, So, Vo, info = oracle.sorsvd(exact, 20, 5, q, 0, omega_dtype="f64", return_intermediates=True)
+    ref = (Uo, So, Vo)
     r_gpu, r_orc, ds = gates(exact, got, ref)
     assert abs(r_gpu - r_orc) <= TOL["f64"] and ds <= TOL["f64"], (r_gpu, r_orc, ds)
     assert r_orc >= oracle.eckart_young(s, 20)[1] / np.linalg.norm(exact) * (1 - 1e-12)
+    # the truncation point is well separated (sigma_20 = 1, sigma_21 = 0.79):
+    # A_hat = U S V^T is determined, element by element
+    U, S, V = (to_np(t) for t in got)
+    Ahat, Ahat_o = (U * S) @ V.T, (Uo * So) @ Vo.T
+    assert np.max(np.abs(Ahat - Ahat_o)) <= TOL["f64"] * np.max(np.abs(Ahat_o))
+    # the leading singular subspaces wherever the core spectrum has a gap
+    # (sigma_j = 1 for j <= 20 in A; the sketch's core separates them by
+    # 1e-8 .. 0.2): binary64 agreement
+    assert len(leading_gaps(info["sigma_core"], 20, TOL["f64"])) >= 1
+    assert check_subspaces(got, ref, info, 20, TOL["f64"]) <= 1e-6
 
 
 def test_run_literal_power_f64(nat):
@@ -302,9 +357,55 @@ def test_workspace_errors(nat):
 
 def test_run_cfg2_full_size(nat):
     A64, s, _, _ = inputs.cfg2(seed=0)
-    exact, got, ref = run_both(nat, A64, 100, 10, 1, 0, "f32")
+    store, exact = inputs.to_storage(A64, "f32")
+    del A64
+    got = nat.run(cuda_colmajor(store, "f32"), 100, 10, 1, seed=0, dtype="f32", check=True)
+    torch.cuda.synchronize()
+    Uo, So, Vo, info = oracle.sorsvd(exact, 100, 10, 1, 0, omega_dtype="f32", return_intermediates=True)
+    ref = (Uo, So, Vo)
     r_gpu, r_orc, ds = gates(exact, got, ref)
     assert abs(r_gpu - r_orc) <= 1e-5 and ds <= 1e-5, (r_gpu, r_orc, ds)
+    # the noise bulk (1e-3 N(0,1): singular values ~0.04-0.24) leaves the
+    # truncation at k = 100 without a gap, so A_hat is not determined there;
+    # the leading singular vectors of the signal (sigma_i = 1/i > 0.24) are
+    check_subspaces(got, ref, info, 100, 1e-5)
+
+
+# ---------------------------------------------------------------------------
+# full size: the bf16 65536 x 16384 workload of the bench line (k = 256,
+# p = 10, q = 2), plain BF16 and BF16 + REFINE against one binary64 oracle
+# solve of the stored matrix
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def cfg3_case():
+    A64, s, _, _ = inputs.cfg3(seed=0)
+    store, exact = inputs.to_storage(A64, "bf16")
+    del A64
+    Uo, So, Vo, info = oracle.sorsvd(exact, 256, 10, 2, 0, omega_dtype="bf16", return_intermediates=True)
+    return store, exact, (Uo, So, Vo), info
+
+
+def test_run_cfg3_full_size(nat, cfg3_case):
+    store, exact, ref, info = cfg3_case
+    A = cuda_colmajor(store, "bf16")
+    res = {}
+    for refine in (False, True):
+        got = nat.run(A, 256, 10, 2, seed=0, dtype="bf16", flags=nat.FLAG_REFINE if refine else 0, check=True)
+        torch.cuda.synchronize()
+        r_gpu, r_orc, ds = gates(exact, got, ref)
+        # the 16-bit class bound on the reconstruction error and the
+        # singular values, and on the leading subspaces where they are
+        # determined to it
+        assert abs(r_gpu - r_orc) <= TOL["bf16"] and ds <= TOL["bf16"], (refine, r_gpu, r_orc, ds)
+        check_subspaces(got, ref, info, 256, TOL["bf16"])
+        res[refine] = (abs(r_gpu - r_orc), ds)
+    del A
+    # REFINE (Q2 as a hi + lo bf16 pair in the core, ~16 bits) meets the
+    # fp32-class bound 1e-5 on the reconstruction error, and improves on
+    # plain BF16 in both the error and the singular values
+    assert res[True][0] <= 1e-5, res
+    assert res[True][0] < res[False][0] and res[True][1] < res[False][1], res
 
 
 # ---- CholeskyQR building block ---------------------------------------------
@@ -395,3 +496,46 @@ def test_run_large_sketch(nat, dt, l):
     # orthonormal to fp32 level, and U~, V~ come from the binary64 finish
     assert np.abs(U.T @ U - np.eye(k)).max() <= 1e-4
     assert np.abs(V.T @ V - np.eye(k)).max() <= 1e-4
+
+
+@pytest.mark.parametrize("dt,m,n,k,p,q", [("f32", 4096, 2304, 190, 10, 1), ("bf16", 4096, 2304, 256, 10, 1),
+                                          ("tf32", 2048, 4096, 40, 8, 2), ("f16", 3072, 2048, 100, 12, 1),
+                                          ("f32", 2560, 2176, 16, 4, 0)])
+def test_run_mid_size_wide_sketches(nat, dt, m, n, k, p, q):
+    """Sketches of 2048-4096 rows and l up to 266: the split-TF32 passes run
+    as column chunks for l > 128, the CholeskyQR factors take their tiled
+    form, every pass and product over full tiles and ragged edges."""
+    A64, s, _, _ = inputs.spectral(m, n, inputs.sigma_exp(min(m, n), 48.0), seed=m + k)
+    exact, got, ref = run_both(nat, A64, k, p, q, 6, dt)
+    r_gpu, r_orc, ds = gates(exact, got, ref)
+    tol = TOL[dt]
+    assert abs(r_gpu - r_orc) <= tol and ds <= tol, (r_gpu, r_orc, ds)
+    U, S, V = (to_np(t) for t in got)
+    assert np.abs(U.T @ U - np.eye(k)).max() <= 1e-4
+    assert np.abs(V.T @ V - np.eye(k)).max() <= 1e-4
+
+
+@pytest.mark.parametrize("dt,m,n,k,p,q,mode", [("f64", 1000, 600, 20, 5, 0, "stabilised"),
+                                               ("f64", 1000, 600, 20, 5, 1, "stabilised"),
+                                               ("f64", 700, 500, 15, 5, 1, "literal"),
+                                               ("f32", 3000, 1500, 40, 10, 1, "stabilised"),
+                                               ("f32", 2560, 2304, 230, 10, 2, "stabilised"),
+                                               ("bf16", 2048, 1024, 32, 8, 2, "stabilised"),
+                                               ("tf32", 4096, 2048, 100, 12, 1, "stabilised")])
+def test_run_two_pass_core(nat, dt, m, n, k, p, q, mode):
+    """The two-pass core of Sec. III (M_approx = Q1^T T1 (Q2^T T2_prev)^+, no
+    core pass over A) against the oracle's two-pass core on the same loop;
+    l = 240 takes the fp32 Cholesky of B B^T (beyond the binary64 limit)."""
+    A64, s, _, _ = inputs.spectral(m, n, inputs.sigma_exp(min(m, n), 30.0), seed=m + q)
+    flags = nat.FLAG_TWO_PASS | (nat.FLAG_LITERAL_POWER if mode == "literal" else 0)
+    store, exact = inputs.to_storage(A64, dt)
+    got = nat.run(cuda_colmajor(store, dt), k, p, q, seed=9, dtype=dt, flags=flags, check=True)
+    torch.cuda.synchronize()
+    ref = oracle.sorsvd(exact, k, p, q, 9, omega_dtype=dt, mode=mode, core="two_pass")
+    r_gpu, r_orc, ds = gates(exact, got, ref)
+    tol = TOL[dt]
+    assert abs(r_gpu - r_orc) <= tol and ds <= tol, (r_gpu, r_orc, ds)
+    # the two-pass core approximates the three-pass one: never better than
+    # Eckart-Young, and within a few percent of it on this decay
+    ey = oracle.eckart_young(s, k)[1] / np.linalg.norm(exact)
+    assert ey * (1 - 1e-6) <= r_gpu <= 1.5 * ey
