@@ -171,9 +171,13 @@ def traffic_from_profiles(kernel_key: str):
     ent = d.get(kernel_key)
     if not ent:
         return None
-    src = os.path.join(ROOT, ent["source"])
+    # every source file that defines the kernel, hashed in the listed order
+    srcs = ent.get("sources") or [ent["source"]]
     try:
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        hh = hashlib.sha256()
+        for src in srcs:
+            hh.update(open(os.path.join(ROOT, src), "rb").read())
+        h = hh.hexdigest()[:16]
     except Exception:
         return None
     return ent["bytes_per_launch"] if h == ent.get("source_sha256_16") else None
@@ -565,6 +569,9 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=None,
                     help="rows of the oracle's sample (default: per workload, a few seconds of CPU work)")
     ap.add_argument("--cpu-cols", type=int, default=None, help="columns of the oracle's sample")
+    ap.add_argument("--shrink", type=int, default=1,
+                    help="single-matrix workloads: divide m and n by this factor (a smaller case of the same "
+                         "recipe for profiler captures; not a bench line of the workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare-precisions", action="store_true",
                     help="16-bit workloads: skip the BF16 / BF16+REFINE / FP32 comparison on the same matrix")
@@ -579,7 +586,11 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    if args.shrink > 1 and "m" in w and args.workload not in ("cfg4", "cfg5"):
+        w["m"] //= args.shrink
+        w["n"] //= args.shrink
+        w["desc"] = f"{w['desc']} [rows and columns divided by {args.shrink}: {w['m']}x{w['n']}]"
     if args.impl == "reference" and args.workload in ("cfg4", "cfg5"):
         if rank == 0:
             print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the oracle on the "

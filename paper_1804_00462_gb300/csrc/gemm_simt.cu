@@ -7,8 +7,11 @@
 //   T2 = A^T T1, G = T^T T, M = Q1^T W                    (op(A) = A^T)
 // The kernel below covers both with a 128 x 64 output tile, 16-deep K
 // slices staged in shared memory and 8 x 4 register blocking per thread.
-// K may be split across blockIdx.z; partial tiles are combined by
-// reduce_splits in a fixed order (no atomics, deterministic results).
+// Binary64 products with at most 32 columns use a 64 x 32 tile (4 x 2 per
+// thread): GB300 runs binary64 FMAs at 1/64 of the fp32 rate, so padding a
+// narrow product to 64 columns wastes most of a scarce unit.  K may be
+// split across blockIdx.z; partial tiles are combined by reduce_splits in a
+// fixed order (no atomics, deterministic results).
 #include "internal.cuh"
 
 #include <algorithm>
@@ -30,15 +33,24 @@ int num_sms() {
 
 namespace {
 
-constexpr int BM = 128, BN = 64, BK = 16, TM = 8, TN = 4, NT = 256;
+template <int BM_, int BN_, int BK_, int TM_, int TN_>
+struct TileCfg {
+  static constexpr int BM = BM_, BN = BN_, BK = BK_, TM = TM_, TN = TN_;
+  static constexpr int NT = (BM / TM) * (BN / TN);
+};
+using BigTile = TileCfg<128, 64, 16, 8, 4>;      // 256 threads
+using SkinnyTile = TileCfg<64, 32, 16, 4, 2>;    // 256 threads
+constexpr int NT = 256;
+static_assert(BigTile::NT == NT && SkinnyTile::NT == NT, "tile configurations use 256 threads");
 
 template <typename Acc, typename T> __device__ __forceinline__ Acc ld_as(const T* p) { return to_acc<Acc, T>(*p); }
 
 // One BM x BN tile of C = op(A) B over the K range [kbeg, kend).
-template <typename TA, typename TB, typename Acc, bool TRANS>
+template <class Cfg, typename TA, typename TB, typename Acc, bool TRANS>
 __device__ __forceinline__ void gemm_tile(int64_t M, int64_t N, const TA* __restrict__ A, int64_t lda,
                                           const TB* __restrict__ B, int64_t ldb, Acc* __restrict__ C,
                                           int64_t ldc, int64_t row0, int64_t col0, int64_t kbeg, int64_t kend) {
+  constexpr int BM = Cfg::BM, BN = Cfg::BN, BK = Cfg::BK, TM = Cfg::TM, TN = Cfg::TN;
   __shared__ Acc As[BK][BM];
   __shared__ Acc Bs[BK][BN];
   const int t = threadIdx.x;
@@ -97,14 +109,15 @@ __device__ __forceinline__ void gemm_tile(int64_t M, int64_t N, const TA* __rest
   }
 }
 
-template <typename TA, typename TB, typename Acc, bool TRANS>
+template <class Cfg, typename TA, typename TB, typename Acc, bool TRANS>
 __global__ void __launch_bounds__(NT)
 gemm_kernel(int64_t M, int64_t N, int64_t K, const TA* __restrict__ A, int64_t lda,
             const TB* __restrict__ B, int64_t ldb, Acc* __restrict__ C, int64_t ldc,
             int64_t k_chunk, int64_t split_stride) {
   const int64_t kbeg = (int64_t)blockIdx.z * k_chunk;
-  gemm_tile<TA, TB, Acc, TRANS>(M, N, A, lda, B, ldb, C + (int64_t)blockIdx.z * split_stride, ldc,
-                                (int64_t)blockIdx.x * BM, (int64_t)blockIdx.y * BN, kbeg, min(K, kbeg + k_chunk));
+  gemm_tile<Cfg, TA, TB, Acc, TRANS>(M, N, A, lda, B, ldb, C + (int64_t)blockIdx.z * split_stride, ldc,
+                                     (int64_t)blockIdx.x * Cfg::BM, (int64_t)blockIdx.y * Cfg::BN, kbeg,
+                                     min(K, kbeg + k_chunk));
 }
 
 // Grouped form: block b computes unit units[b] = (job, m-tile, n-tile,
@@ -115,28 +128,39 @@ gemm_batched_kernel(const GemmJob* __restrict__ jobs, const int4* __restrict__ u
   const int4 u = units[blockIdx.x];
   const GemmJob& j = jobs[u.x];
   const int64_t kbeg = (int64_t)u.w * j.k_chunk;
-  gemm_tile<Acc, Acc, Acc, TRANS>(j.M, j.N, (const Acc*)j.A, j.lda, (const Acc*)j.B, j.ldb,
-                                  (Acc*)j.C + (int64_t)u.w * j.split_stride, j.ldc, (int64_t)u.y * BM,
-                                  (int64_t)u.z * BN, kbeg, min(j.K, kbeg + j.k_chunk));
+  gemm_tile<BigTile, Acc, Acc, Acc, TRANS>(j.M, j.N, (const Acc*)j.A, j.lda, (const Acc*)j.B, j.ldb,
+                                           (Acc*)j.C + (int64_t)u.w * j.split_stride, j.ldc,
+                                           (int64_t)u.y * BigTile::BM, (int64_t)u.z * BigTile::BN, kbeg,
+                                           min(j.K, kbeg + j.k_chunk));
+}
+
+template <class Cfg, typename TA, typename TB, typename Acc>
+cudaError_t gemm_dispatch_cfg(bool trans, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
+                              const void* B, int64_t ldb, void* C, int64_t ldc, int splits,
+                              int64_t split_stride, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (splits < 1) splits = 1;
+  int64_t k_chunk = (K + splits - 1) / splits;
+  k_chunk = ((k_chunk + Cfg::BK - 1) / Cfg::BK) * Cfg::BK;
+  if (k_chunk < Cfg::BK) k_chunk = Cfg::BK;
+  dim3 grid((unsigned)((M + Cfg::BM - 1) / Cfg::BM), (unsigned)((N + Cfg::BN - 1) / Cfg::BN), (unsigned)splits);
+  if (trans)
+    gemm_kernel<Cfg, TA, TB, Acc, true><<<grid, NT, 0, st>>>(M, N, K, (const TA*)A, lda, (const TB*)B, ldb,
+                                                             (Acc*)C, ldc, k_chunk, split_stride);
+  else
+    gemm_kernel<Cfg, TA, TB, Acc, false><<<grid, NT, 0, st>>>(M, N, K, (const TA*)A, lda, (const TB*)B, ldb,
+                                                              (Acc*)C, ldc, k_chunk, split_stride);
+  return cudaGetLastError();
 }
 
 template <typename TA, typename TB, typename Acc>
 cudaError_t gemm_dispatch(bool trans, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
                           const void* B, int64_t ldb, void* C, int64_t ldc, int splits,
                           int64_t split_stride, cudaStream_t st) {
-  if (M <= 0 || N <= 0) return cudaSuccess;
-  if (splits < 1) splits = 1;
-  int64_t k_chunk = (K + splits - 1) / splits;
-  k_chunk = ((k_chunk + BK - 1) / BK) * BK;
-  if (k_chunk < BK) k_chunk = BK;
-  dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN), (unsigned)splits);
-  if (trans)
-    gemm_kernel<TA, TB, Acc, true><<<grid, NT, 0, st>>>(M, N, K, (const TA*)A, lda, (const TB*)B, ldb,
-                                                        (Acc*)C, ldc, k_chunk, split_stride);
-  else
-    gemm_kernel<TA, TB, Acc, false><<<grid, NT, 0, st>>>(M, N, K, (const TA*)A, lda, (const TB*)B, ldb,
-                                                         (Acc*)C, ldc, k_chunk, split_stride);
-  return cudaGetLastError();
+  if (sizeof(Acc) == 8 && N <= SkinnyTile::BN)
+    return gemm_dispatch_cfg<SkinnyTile, TA, TB, Acc>(trans, M, N, K, A, lda, B, ldb, C, ldc, splits, split_stride,
+                                                      st);
+  return gemm_dispatch_cfg<BigTile, TA, TB, Acc>(trans, M, N, K, A, lda, B, ldb, C, ldc, splits, split_stride, st);
 }
 
 // Fixed-order sum of split partials.  fp32 partials are summed with
@@ -397,7 +421,7 @@ cudaError_t launch_reduce_batched(bool parts_f64, const ReduceJob* jobs, int njo
 }
 
 // the tile shape of the grouped kernel (units are counted in these tiles)
-void gemm_tile_shape(int* bm, int* bn, int* bk) { *bm = BM; *bn = BN; *bk = BK; }
+void gemm_tile_shape(int* bm, int* bn, int* bk) { *bm = BigTile::BM; *bn = BigTile::BN; *bk = BigTile::BK; }
 
 namespace {
 __global__ void add_f64_kernel(const double* __restrict__ x, int64_t ldx, double* __restrict__ y, int64_t ldy,

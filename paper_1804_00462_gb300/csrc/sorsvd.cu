@@ -46,12 +46,16 @@ inline double first_shift(int dt) { return dt == SORSVD_F64 ? 1e-13 : 1e-5; }
 // working precision (its error grows with cond(Q)^2 <= (1 + l tol) / (1 - l tol))
 constexpr float kOrthTol = 1e-4f;
 
-// K splits of a product with an M x N output and reduction length K
-int splits_for(int64_t M, int64_t N, int64_t K, int cap) {
-  int64_t tiles = ((M + 127) / 128) * ((N + 63) / 64);
+// K splits of a product with an M x N output and reduction length K, for
+// the CUDA-core tiles: 128 x 64 with at least 256 K per split, or for
+// binary64 products of <= 32 columns 64 x 32 with at least 16 K per split
+// (binary64 FMAs are scarce: the product is spread over every SM)
+int splits_for(int64_t M, int64_t N, int64_t K, int cap, bool f64 = false) {
+  const bool skinny = f64 && N <= 32;
+  int64_t tiles = skinny ? ((M + 63) / 64) * ((N + 31) / 32) : ((M + 127) / 128) * ((N + 63) / 64);
   int64_t want = 2 * (int64_t)num_sms();
   int64_t s = (want + tiles - 1) / tiles;
-  int64_t by_k = (K + 255) / 256;
+  int64_t by_k = skinny ? (K + 15) / 16 : (K + 255) / 256;
   s = std::min<int64_t>(s, by_k);
   s = std::min<int64_t>(s, cap);
   return (int)std::max<int64_t>(s, 1);
@@ -119,7 +123,7 @@ Layout make_layout(int64_t m, int64_t n, int l, int dt, unsigned flags = 0) {
   // a reduction.
   size_t pb = 0;
   auto need = [&](int64_t M, int64_t N, int64_t K, int cap, bool always) {
-    int s = splits_for(M, N, K, cap);
+    int s = splits_for(M, N, K, cap, dt == SORSVD_F64);
     if (s > 1 || always) pb = std::max(pb, (size_t)s * M * N * acc);
   };
   need(m, l, n, kCapBig, false);     // T1 = A T2, W = A Q2
@@ -189,7 +193,7 @@ cudaError_t begin_call(const Ctx& c) {
 int gemm(const Ctx& c, int kcls, bool trans, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
          int adt, const void* B, int64_t ldb, int bdt, void* C, int64_t ldc, bool c_f64, int cap) {
   const bool accf = c.f64;
-  int s = splits_for(M, N, K, cap);
+  int s = splits_for(M, N, K, cap, accf);
   if (s == 1 && (c_f64 == accf)) {
     ProfScope ps(kcls, c.st);
     CK(launch_gemm(trans, M, N, K, A, lda, adt, B, ldb, bdt, C, ldc, accf, 1, 0, c.st));

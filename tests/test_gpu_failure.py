@@ -1,6 +1,6 @@
 """Device-side failure paths, made to happen without faulting or hanging a
 GPU: a Jacobi sweep cap of one sweep gives SORSVD_ERR_NOT_CONVERGED, and a
-wait limit of a few hundred cycles in the tensor-core passes gives
+wait limit of 64 cycles in the tensor-core passes gives
 SORSVD_ERR_TIMEOUT.  Each call returns cleanly and the next call with the
 default limits is clean and matches the oracle (the aborted passes let
 their copies and MMAs land and freed their tensor memory, or the next pass
@@ -81,7 +81,7 @@ def test_pass_wait_limit_times_out_cleanly(nat, dt):
     A, exact = _problem(m, n, dt, seed=7)
     before, st, _ = _call(nat, A, k, p, 1, dt)
     assert st == 0 and _matches_oracle(before, exact, k, p, 1, dt, 1e-5 if dt == "f32" else 1e-2)
-    nat.set_limits(300, 0)
+    nat.set_limits(64, 0)
     try:
         _, st, _ = _call(nat, A, k, p, 1, dt)
     finally:
