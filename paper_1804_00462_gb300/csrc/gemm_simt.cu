@@ -113,7 +113,8 @@ template <class Cfg, typename TA, typename TB, typename Acc, bool TRANS>
 __global__ void __launch_bounds__(NT)
 gemm_kernel(int64_t M, int64_t N, int64_t K, const TA* __restrict__ A, int64_t lda,
             const TB* __restrict__ B, int64_t ldb, Acc* __restrict__ C, int64_t ldc,
-            int64_t k_chunk, int64_t split_stride) {
+            int64_t k_chunk, int64_t split_stride, const int* __restrict__ skip) {
+  if (skip && *skip) return;                       // a device-side decision skipped this product
   const int64_t kbeg = (int64_t)blockIdx.z * k_chunk;
   gemm_tile<Cfg, TA, TB, Acc, TRANS>(M, N, A, lda, B, ldb, C + (int64_t)blockIdx.z * split_stride, ldc,
                                      (int64_t)blockIdx.x * Cfg::BM, (int64_t)blockIdx.y * Cfg::BN, kbeg,
@@ -137,7 +138,7 @@ gemm_batched_kernel(const GemmJob* __restrict__ jobs, const int4* __restrict__ u
 template <class Cfg, typename TA, typename TB, typename Acc>
 cudaError_t gemm_dispatch_cfg(bool trans, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
                               const void* B, int64_t ldb, void* C, int64_t ldc, int splits,
-                              int64_t split_stride, cudaStream_t st) {
+                              int64_t split_stride, cudaStream_t st, const int* skip) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   if (splits < 1) splits = 1;
   int64_t k_chunk = (K + splits - 1) / splits;
@@ -146,21 +147,22 @@ cudaError_t gemm_dispatch_cfg(bool trans, int64_t M, int64_t N, int64_t K, const
   dim3 grid((unsigned)((M + Cfg::BM - 1) / Cfg::BM), (unsigned)((N + Cfg::BN - 1) / Cfg::BN), (unsigned)splits);
   if (trans)
     gemm_kernel<Cfg, TA, TB, Acc, true><<<grid, NT, 0, st>>>(M, N, K, (const TA*)A, lda, (const TB*)B, ldb,
-                                                             (Acc*)C, ldc, k_chunk, split_stride);
+                                                             (Acc*)C, ldc, k_chunk, split_stride, skip);
   else
     gemm_kernel<Cfg, TA, TB, Acc, false><<<grid, NT, 0, st>>>(M, N, K, (const TA*)A, lda, (const TB*)B, ldb,
-                                                              (Acc*)C, ldc, k_chunk, split_stride);
+                                                              (Acc*)C, ldc, k_chunk, split_stride, skip);
   return cudaGetLastError();
 }
 
 template <typename TA, typename TB, typename Acc>
 cudaError_t gemm_dispatch(bool trans, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
                           const void* B, int64_t ldb, void* C, int64_t ldc, int splits,
-                          int64_t split_stride, cudaStream_t st) {
+                          int64_t split_stride, cudaStream_t st, const int* skip = nullptr) {
   if (sizeof(Acc) == 8 && N <= SkinnyTile::BN)
     return gemm_dispatch_cfg<SkinnyTile, TA, TB, Acc>(trans, M, N, K, A, lda, B, ldb, C, ldc, splits, split_stride,
-                                                      st);
-  return gemm_dispatch_cfg<BigTile, TA, TB, Acc>(trans, M, N, K, A, lda, B, ldb, C, ldc, splits, split_stride, st);
+                                                      st, skip);
+  return gemm_dispatch_cfg<BigTile, TA, TB, Acc>(trans, M, N, K, A, lda, B, ldb, C, ldc, splits, split_stride, st,
+                                                 skip);
 }
 
 // Fixed-order sum of split partials.  fp32 partials are summed with
@@ -186,7 +188,9 @@ __device__ __forceinline__ double sum_parts(const double* __restrict__ p, int sp
 
 template <typename TP, typename TO>
 __global__ void reduce_kernel(const TP* __restrict__ parts, int splits, int64_t stride, int64_t rows,
-                              int64_t cols, int64_t ldp, TO* __restrict__ out, int64_t ldo) {
+                              int64_t cols, int64_t ldp, TO* __restrict__ out, int64_t ldo,
+                              const int* __restrict__ skip) {
+  if (skip && *skip) return;
   const int64_t total = rows * cols;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -227,7 +231,8 @@ __global__ void convert_kernel(const float* __restrict__ x, int64_t ldx, int64_t
 
 template <typename T>
 __global__ void copy2d_kernel(const T* __restrict__ x, int64_t ldx, T* __restrict__ y, int64_t ldy,
-                              int64_t rows, int64_t cols) {
+                              int64_t rows, int64_t cols, const int* __restrict__ skip) {
+  if (skip && *skip) return;
   const int64_t total = rows * cols;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -326,10 +331,11 @@ inline int grid_for(int64_t total) {
 
 cudaError_t launch_gemm(bool trans_a, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda, int a_dt,
                         const void* B, int64_t ldb, int b_dt, void* C, int64_t ldc, bool acc_f64,
-                        int splits, int64_t split_stride, cudaStream_t st) {
+                        int splits, int64_t split_stride, cudaStream_t st, const int* skip) {
   if (acc_f64) {
     if (a_dt == SORSVD_F64 && b_dt == SORSVD_F64)
-      return gemm_dispatch<double, double, double>(trans_a, M, N, K, A, lda, B, ldb, C, ldc, splits, split_stride, st);
+      return gemm_dispatch<double, double, double>(trans_a, M, N, K, A, lda, B, ldb, C, ldc, splits, split_stride, st,
+                                                   skip);
     return cudaErrorInvalidValue;
   }
   bool a32 = (a_dt == SORSVD_F32 || a_dt == SORSVD_TF32), b32 = (b_dt == SORSVD_F32 || b_dt == SORSVD_TF32);
@@ -343,17 +349,17 @@ cudaError_t launch_gemm(bool trans_a, int64_t M, int64_t N, int64_t K, const voi
 
 cudaError_t launch_reduce_splits(const void* parts, bool parts_f64, int splits, int64_t split_stride,
                                  int64_t rows, int64_t cols, int64_t ld_part, void* out, bool out_f64,
-                                 int64_t ld_out, cudaStream_t st) {
+                                 int64_t ld_out, cudaStream_t st, const int* skip) {
   if (rows <= 0 || cols <= 0) return cudaSuccess;
   int g = grid_for(rows * cols);
   if (parts_f64 && out_f64)
-    reduce_kernel<double, double><<<g, 256, 0, st>>>((const double*)parts, splits, split_stride, rows, cols, ld_part, (double*)out, ld_out);
+    reduce_kernel<double, double><<<g, 256, 0, st>>>((const double*)parts, splits, split_stride, rows, cols, ld_part, (double*)out, ld_out, skip);
   else if (parts_f64)
-    reduce_kernel<double, float><<<g, 256, 0, st>>>((const double*)parts, splits, split_stride, rows, cols, ld_part, (float*)out, ld_out);
+    reduce_kernel<double, float><<<g, 256, 0, st>>>((const double*)parts, splits, split_stride, rows, cols, ld_part, (float*)out, ld_out, skip);
   else if (out_f64)
-    reduce_kernel<float, double><<<g, 256, 0, st>>>((const float*)parts, splits, split_stride, rows, cols, ld_part, (double*)out, ld_out);
+    reduce_kernel<float, double><<<g, 256, 0, st>>>((const float*)parts, splits, split_stride, rows, cols, ld_part, (double*)out, ld_out, skip);
   else
-    reduce_kernel<float, float><<<g, 256, 0, st>>>((const float*)parts, splits, split_stride, rows, cols, ld_part, (float*)out, ld_out);
+    reduce_kernel<float, float><<<g, 256, 0, st>>>((const float*)parts, splits, split_stride, rows, cols, ld_part, (float*)out, ld_out, skip);
   return cudaGetLastError();
 }
 
@@ -387,12 +393,12 @@ cudaError_t launch_transpose_f32(const float* A, int64_t lda, int64_t rows, int6
 }
 
 cudaError_t launch_copy2d(const void* x, int64_t ldx, void* y, int64_t ldy, int64_t rows, int64_t cols,
-                          size_t elem, cudaStream_t st) {
+                          size_t elem, cudaStream_t st, const int* skip) {
   if (rows <= 0 || cols <= 0) return cudaSuccess;
   int g = grid_for(rows * cols);
-  if (elem == 8) copy2d_kernel<double><<<g, 256, 0, st>>>((const double*)x, ldx, (double*)y, ldy, rows, cols);
-  else if (elem == 4) copy2d_kernel<float><<<g, 256, 0, st>>>((const float*)x, ldx, (float*)y, ldy, rows, cols);
-  else if (elem == 2) copy2d_kernel<uint16_t><<<g, 256, 0, st>>>((const uint16_t*)x, ldx, (uint16_t*)y, ldy, rows, cols);
+  if (elem == 8) copy2d_kernel<double><<<g, 256, 0, st>>>((const double*)x, ldx, (double*)y, ldy, rows, cols, skip);
+  else if (elem == 4) copy2d_kernel<float><<<g, 256, 0, st>>>((const float*)x, ldx, (float*)y, ldy, rows, cols, skip);
+  else if (elem == 2) copy2d_kernel<uint16_t><<<g, 256, 0, st>>>((const uint16_t*)x, ldx, (uint16_t*)y, ldy, rows, cols, skip);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }

@@ -80,15 +80,18 @@ cudaError_t launch_gaussian(void* out, int64_t rows, int64_t cols, int64_t ld, u
 // partial product to C + s * split_stride; reduce_splits combines them.
 // a_dt / b_dt: element types (sorsvd_dtype); c is fp32 for acc_f64 = false,
 // binary64 otherwise.
+// (skip: a device flag that, when an earlier kernel set it, makes the
+// launch do nothing; for the products of a skipped CholeskyQR pass)
 cudaError_t launch_gemm(bool trans_a, int64_t M, int64_t N, int64_t K,
                         const void* A, int64_t lda, int a_dt,
                         const void* B, int64_t ldb, int b_dt,
                         void* C, int64_t ldc, bool acc_f64,
-                        int splits, int64_t split_stride, cudaStream_t st);
+                        int splits, int64_t split_stride, cudaStream_t st, const int* skip = nullptr);
 // out = sum_s parts[s] (fixed order, binary64 sums); parts are fp32 or f64.
 cudaError_t launch_reduce_splits(const void* parts, bool parts_f64, int splits, int64_t split_stride,
                                  int64_t rows, int64_t cols, int64_t ld_part,
-                                 void* out, bool out_f64, int64_t ld_out, cudaStream_t st);
+                                 void* out, bool out_f64, int64_t ld_out, cudaStream_t st,
+                                 const int* skip = nullptr);
 // y (16-bit) = round(x) elementwise; x fp32 (rows x cols, ldx) -> y (ldy).
 // When `lo` is non-null it also receives round(x - float(y)) (hi/lo split).
 cudaError_t launch_convert_f32(const float* x, int64_t ldx, int64_t rows, int64_t cols,
@@ -101,7 +104,7 @@ cudaError_t launch_add_f64(const double* x, int64_t ldx, double* y, int64_t ldy,
                            cudaStream_t st);
 // copy with leading dimensions (same element size)
 cudaError_t launch_copy2d(const void* x, int64_t ldx, void* y, int64_t ldy,
-                          int64_t rows, int64_t cols, size_t elem, cudaStream_t st);
+                          int64_t rows, int64_t cols, size_t elem, cudaStream_t st, const int* skip = nullptr);
 
 // ---------------------------------------------------------------------------
 // grouped ("batched") launches: one launch runs one stage of many problems,

@@ -10,6 +10,9 @@
 //     kernel).  Rotations are applied while a pair's cosine exceeds l * eps
 //     of the sweep precision.  The sweep count is capped; hitting the cap
 //     with a cosine above 32 l eps raises SORSVD_ERR_NOT_CONVERGED.
+//     fp32 sweeps of l >= 48 run block-cyclic on a 16-CTA cluster; binary64
+//     sweeps are preceded by fp32 sweeps and polish their result
+//     (jacobi_f64_mixed).
 //  2. finish (one block per column), binary64: v_j normalised (fp32
 //     rotations keep its norm only to a few ulps each), z = M v_j,
 //     sigma_j = ||z||, u_j = z / sigma_j.  V stays orthonormal to the sweep precision whatever
@@ -493,22 +496,15 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 }
 
 // ---------------------------------------------------------------- cluster
-// Sweeps on a thread-block cluster of kClusterCtas CTAs (one per SM).  The
-// N/2 pairs of a round are spread over the CTAs, gpc per CTA, one 16-lane
-// group each with the arithmetic of the one-block 16-lane sweep.  A group's
-// two slots hold the W and V columns of the round-robin positions g and
-// N - 1 - g; after the rotation each column is written to the slot of its
-// next position, in the other of two slot buffers (in another CTA's shared
-// memory when that position belongs to it, by asynchronous stores that the
-// receiving CTA's mbarrier counts).  A round ends with a CTA barrier and a
-// wait for the neighbours' columns, no cluster-wide barrier: shared memory
-// bandwidth and the per-round latency scale with the CTAs instead of
-// queueing on one SM, and no round trip goes through L2.  Only neighbouring
-// CTAs exchange columns, and a CTA can run at most one round ahead of a
-// neighbour (it needs that neighbour's columns), so with two slot buffers
-// no column is overwritten before it has been read.  The
-// convergence flags of a sweep are OR-ed into CTA 0 and read back by all
-// CTAs before any of them decides, so every CTA runs the same barriers.
+// Sweeps on a thread-block cluster of kClusterCtas CTAs (one per SM): the
+// columns move between the CTAs' shared memory by asynchronous stores that
+// the receiving CTA's mbarrier counts, with no cluster-wide barrier per
+// exchange.  A CTA can run at most one exchange ahead of a neighbour (it
+// needs that neighbour's columns), so with two buffers no column is
+// overwritten before it has been read.  The convergence flags of a sweep
+// are OR-ed into CTA 0 and read back by all CTAs before any of them
+// decides, so every CTA runs the same barriers.  The ordering (blocks of
+// columns, local rounds between exchanges) is described at the kernel.
 constexpr int kClusterCtas = 16;
 constexpr int kClusterMinL = 48;                 // below: the one-block sweeps
 
@@ -550,37 +546,107 @@ __device__ __forceinline__ bool cl_mbar_try_wait(uint64_t* bar, uint32_t parity)
 }
 constexpr long long kClusterWaitCycles = 4000000000ll;   // about 2 s
 
+// Block-cyclic sweeps on the 16-CTA cluster.  The l columns (padded with
+// zero columns) form NB = 32 blocks of b = ceil(l / 32); CTA c holds the
+// blocks at positions c (slot 0) and NB - 1 - c (slot 1).  A sweep is
+// NB - 1 block rounds of the round-robin over blocks (position 0 fixed,
+// the others move one place per round).  In a block round a CTA rotates
+// every pair (x of slot 0, y of slot 1) in b local rounds of b disjoint pairs
+// (x_i, y_{(i + s) mod b}), and in the first block round of a sweep also the
+// pairs inside each of its two blocks (round-robin, b' - 1 local rounds of
+// b' / 2 pairs per block, b' = b rounded up to even): every pair of columns
+// once per sweep.  Local rounds touch only this CTA's shared memory (one
+// __syncthreads each); the blocks then move to their next positions,
+// neighbouring CTAs by st.async counted by the receiver's mbarrier - one
+// exchange per b^2 pairs, where the column-cyclic kernel exchanges after
+// every pair.  Convergence flags per sweep as in that kernel.
+constexpr int kBlockNb = 2 * kClusterCtas;
+
+__device__ __forceinline__ void cl_st_async4(uint32_t addr, float4 v, uint32_t mbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(addr),
+               "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(mbar)
+               : "memory");
+}
+
+// One Jacobi rotation of columns (x, y) of W and (u, v) of V (V at column +
+// LDW), 16 lanes, in place.  Returns the lanes' flags: bit 0 rotated, bit 1
+// a large rotation (cosine above 32 tol).
 template <int EP>
-__global__ void __launch_bounds__(512)
-jacobi_sweep_cluster_kernel(const double* __restrict__ Min, int l, int gpc, float* __restrict__ Vout,
+__device__ __forceinline__ int rotate_pair16(float* cx, float* cy, int gl, unsigned gmask, float tol2, float big2) {
+  constexpr int LDW = 32 * EP;
+  float2* wx = reinterpret_cast<float2*>(cx);
+  float2* wy = reinterpret_cast<float2*>(cy);
+  float2* vx = reinterpret_cast<float2*>(cx + LDW);
+  float2* vy = reinterpret_cast<float2*>(cy + LDW);
+  float2 x[EP], y[EP], u[EP], v[EP];
+  float2 al2 = make_float2(0.f, 0.f), be2 = al2, ga2 = al2;
+#pragma unroll
+  for (int e = 0; e < EP; ++e) {
+    x[e] = wx[gl + 16 * e];
+    y[e] = wy[gl + 16 * e];
+    al2 = __ffma2_rn(x[e], x[e], al2);
+    be2 = __ffma2_rn(y[e], y[e], be2);
+    ga2 = __ffma2_rn(x[e], y[e], ga2);
+  }
+  float al = al2.x + al2.y, be = be2.x + be2.y, ga = ga2.x + ga2.y;
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) {
+    al += __shfl_xor_sync(gmask, al, o);
+    be += __shfl_xor_sync(gmask, be, o);
+    ga += __shfl_xor_sync(gmask, ga, o);
+  }
+  if (!(ga * ga > tol2 * al * be)) return 0;
+  const int flags = (ga * ga > big2 * al * be) ? 3 : 1;
+  float cs, sn;
+  rotation(al, be, ga, &cs, &sn);
+  const float2 c2 = make_float2(cs, cs), s2 = make_float2(sn, sn), ns2 = make_float2(-sn, -sn);
+#pragma unroll
+  for (int e = 0; e < EP; ++e) {
+    u[e] = vx[gl + 16 * e];
+    v[e] = vy[gl + 16 * e];
+  }
+#pragma unroll
+  for (int e = 0; e < EP; ++e) {
+    wx[gl + 16 * e] = __ffma2_rn(c2, x[e], __fmul2_rn(ns2, y[e]));
+    wy[gl + 16 * e] = __ffma2_rn(s2, x[e], __fmul2_rn(c2, y[e]));
+    vx[gl + 16 * e] = __ffma2_rn(c2, u[e], __fmul2_rn(ns2, v[e]));
+    vy[gl + 16 * e] = __ffma2_rn(s2, u[e], __fmul2_rn(c2, v[e]));
+  }
+  return flags;
+}
+
+template <int EP>
+__global__ void __launch_bounds__(352)
+jacobi_block_cluster_kernel(const double* __restrict__ Min, int l, int b, float* __restrict__ Vout,
                             DeviceStatus* status) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
+  constexpr int LDW = 32 * EP;                       // floats per column (W or V)
+  constexpr int NB = kBlockNb, C = kClusterCtas;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int LDW = 32 * EP;                       // floats per column slot
-  float* S = reinterpret_cast<float*>(smem_raw);     // [buffer 2][slot 2 gpc][W, V][LDW]
+  float* S = reinterpret_cast<float*>(smem_raw);     // [buffer 2][slot 2][column b][W, V][LDW]
   __shared__ int s_flag[2], s_big[2];                // used in CTA 0, by sweep parity
-  __shared__ __align__(8) uint64_t s_mbar[2];        // incoming remote columns, by buffer
-  const int N = (l + 1) & ~1, G = N / 2;
+  __shared__ __align__(8) uint64_t s_mbar[2];        // incoming remote blocks, by buffer
   const int t = threadIdx.x, lane = t & 31;
-  const int lg = t >> 4, gl = t & 15;
-  const int gg = rank * gpc + lg;
-  const bool act = gg < G;
+  const int grp = t >> 4, gl = t & 15;
   const unsigned gmask = 0xFFFFu << ((lane >> 4) * 16);
+  const int bp = b + (b & 1);
   const float eps = 1.1920928955078125e-07f;
   const float tol = (float)l * eps, tol2 = tol * tol;
   const float big = 32.f * tol, big2 = big * big;
-  auto slot = [&](int b, int sl) { return S + ((size_t)(b * 2 * gpc + sl) * 2) * LDW; };
+  const int colf = 2 * LDW;                          // floats per column slot (W and V)
+  auto col = [&](int bf, int sl, int j) { return S + ((size_t)(bf * 2 + sl) * b + j) * colf; };
+  const int pos[2] = {rank, NB - 1 - rank};          // the positions of this CTA's two slots
 
-  // round 0: position p holds column p (zero columns past l)
-  for (int e = t; e < 2 * gpc * LDW; e += blockDim.x) {
-    const int sl = e / LDW, i = e - sl * LDW;
-    const int g = rank * gpc + (sl >> 1);
-    const int j = g < G ? ((sl & 1) ? N - 1 - g : g) : N;
-    float* w = slot(0, sl);
-    w[i] = (i < l && j < l) ? (float)Min[i + (size_t)j * l] : 0.f;
-    w[LDW + i] = (i == j && j < l) ? 1.f : 0.f;
+  // sweep start: position p holds block p; zero columns past l
+  for (int e = t; e < 2 * b * LDW; e += blockDim.x) {
+    const int sj = e / LDW, i = e - sj * LDW;
+    const int sl = sj / b, j = sj - sl * b;
+    const int g = pos[sl] * b + j;
+    float* w = col(0, sl, j);
+    w[i] = (i < l && g < l) ? (float)Min[i + (size_t)g * l] : 0.f;
+    w[LDW + i] = (i == g && g < l) ? 1.f : 0.f;
   }
   if (rank == 0 && t == 0) { s_flag[0] = s_flag[1] = 0; s_big[0] = s_big[1] = 0; }
   if (t == 0) {
@@ -588,111 +654,67 @@ jacobi_sweep_cluster_kernel(const double* __restrict__ Min, int l, int gpc, floa
     cl_mbar_init(&s_mbar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // bytes this CTA receives from other CTAs per round: its slots whose
-  // previous position belongs to another CTA
-  int rem_cols = 0;
-  for (int sl = 0; sl < 2 * gpc; ++sl) {
-    const int g = rank * gpc + (sl >> 1);
-    if (g >= G) continue;
-    const int p = prev_pos((sl & 1) ? N - 1 - g : g, N);
-    const int gs = p < G ? p : N - 1 - p;
-    if (gs / gpc != rank) ++rem_cols;
-  }
-  uint32_t rem_bytes = (uint32_t)rem_cols * 2u * LDW * (uint32_t)sizeof(float);
-  uint32_t mpar0 = 0u, mpar1 = 0u;                 // phase parity of s_mbar[0], s_mbar[1]
-  cluster.sync();
-
-  // the next positions of a group's slots do not change from round to
-  // round: their slots (and whether they are local) are fixed per group
-  const int pa = gg, pb = N - 1 - gg;
-  int dsl[2], dcta[2];
+  // where each slot's block goes (next position), and the bytes this CTA
+  // receives from other CTAs per block round
+  int dcta[2], dslot[2], rem_blocks = 0;
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
-    const int q = next_pos(h ? pb : pa, N);
-    const int g2 = q < G ? q : N - 1 - q;
-    dsl[h] = 2 * (g2 % gpc) + (q < G ? 0 : 1);
-    dcta[h] = g2 / gpc;
+    const int q = next_pos(pos[h], NB);
+    dcta[h] = q < C ? q : NB - 1 - q;
+    dslot[h] = q < C ? 0 : 1;
+    const int pp = prev_pos(pos[h], NB);
+    if ((pp < C ? pp : NB - 1 - pp) != rank) ++rem_blocks;
   }
+  uint32_t rem_bytes = (uint32_t)rem_blocks * (uint32_t)b * (uint32_t)colf * 4u;
+  uint32_t mpar0 = 0u, mpar1 = 0u;
+  cluster.sync();
+
   int buf = 0, sweep;
   const int cap = sweep_cap();
   for (sweep = 1; sweep <= cap; ++sweep) {
     const int par = sweep & 1;
-    int rot_local = 0, big_local = 0;
-    // players at the group's positions: rr_player(p, r, N) = 1 + (p - 1 - r) mod (N - 1), stepped down per round
-    int ia = pa == 0 ? 0 : pa, ib = pb;
-    for (int r = 0; r < N - 1; ++r) {
-      // the columns written this round land in buffer buf ^ 1
+    int fl = 0;                                      // bit 0 rotated, bit 1 large rotation
+    for (int r = 0; r < NB - 1; ++r) {
       if (t == 0 && rem_bytes) cl_mbar_arm(&s_mbar[buf ^ 1], rem_bytes);
-      if (act) {
-        const bool sw = ia > ib;                     // x: the smaller column index
-        float* sx = slot(buf, 2 * lg + (sw ? 1 : 0));
-        float* sy = slot(buf, 2 * lg + (sw ? 0 : 1));
-        const float2* wx = reinterpret_cast<const float2*>(sx);
-        const float2* wy = reinterpret_cast<const float2*>(sy);
-        const float2* vx = reinterpret_cast<const float2*>(sx + LDW);
-        const float2* vy = reinterpret_cast<const float2*>(sy + LDW);
-        float2 x[EP], y[EP], u[EP], v[EP];
-        float2 al2 = make_float2(0.f, 0.f), be2 = al2, ga2 = al2;
-#pragma unroll
-        for (int e = 0; e < EP; ++e) {
-          x[e] = wx[gl + 16 * e];
-          y[e] = wy[gl + 16 * e];
-          u[e] = vx[gl + 16 * e];
-          v[e] = vy[gl + 16 * e];
-          al2 = __ffma2_rn(x[e], x[e], al2);
-          be2 = __ffma2_rn(y[e], y[e], be2);
-          ga2 = __ffma2_rn(x[e], y[e], ga2);
-        }
-        float al = al2.x + al2.y, be = be2.x + be2.y, ga = ga2.x + ga2.y;
-#pragma unroll
-        for (int o = 8; o > 0; o >>= 1) {
-          al += __shfl_xor_sync(gmask, al, o);
-          be += __shfl_xor_sync(gmask, be, o);
-          ga += __shfl_xor_sync(gmask, ga, o);
-        }
-        if (ga * ga > tol2 * al * be) {
-          if (ga * ga > big2 * al * be) big_local = 1;
-          float cs, sn;
-          rotation(al, be, ga, &cs, &sn);
-          const float2 c2 = make_float2(cs, cs), s2 = make_float2(sn, sn), ns2 = make_float2(-sn, -sn);
-#pragma unroll
-          for (int e = 0; e < EP; ++e) {
-            const float2 xn = __ffma2_rn(c2, x[e], __fmul2_rn(ns2, y[e]));
-            const float2 yn = __ffma2_rn(s2, x[e], __fmul2_rn(c2, y[e]));
-            const float2 un = __ffma2_rn(c2, u[e], __fmul2_rn(ns2, v[e]));
-            const float2 vn = __ffma2_rn(s2, u[e], __fmul2_rn(c2, v[e]));
-            x[e] = xn; y[e] = yn; u[e] = un; v[e] = vn;
+      if (r == 0) {
+        // the pairs inside each block: round-robin on bp players
+        for (int s = 0; s < bp - 1; ++s) {
+          if (grp < bp) {
+            const int sl = grp / (bp / 2), pr = grp - sl * (bp / 2);
+            const int i = rr_player(pr, s, bp), j = rr_player(bp - 1 - pr, s, bp);
+            if (i < b && j < b)
+              fl |= rotate_pair16<EP>(col(buf, sl, min(i, j)), col(buf, sl, max(i, j)), gl, gmask, tol2, big2);
           }
-          rot_local = 1;
-        }
-        // each column to the slot of its next position (buffer buf ^ 1)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          float* dst = slot(buf ^ 1, dsl[h]);
-          const bool is_x = (h == 0) != sw;          // the slot at pa holds x unless swapped
-          if (dcta[h] == rank) {
-            float2* dw = reinterpret_cast<float2*>(dst);
-            float2* dv = reinterpret_cast<float2*>(dst + LDW);
-#pragma unroll
-            for (int e = 0; e < EP; ++e) {
-              dw[gl + 16 * e] = is_x ? x[e] : y[e];
-              dv[gl + 16 * e] = is_x ? u[e] : v[e];
-            }
-          } else {
-            // a neighbouring CTA's slot: asynchronous stores counted by its mbarrier
-            const uint32_t rd = cl_mapa(cl_smem_u32(dst), dcta[h]);
-            const uint32_t rb = cl_mapa(cl_smem_u32(&s_mbar[buf ^ 1]), dcta[h]);
-#pragma unroll
-            for (int e = 0; e < EP; ++e) {
-              cl_st_async(rd + 8u * (gl + 16 * e), is_x ? x[e] : y[e], rb);
-              cl_st_async(rd + 4u * LDW + 8u * (gl + 16 * e), is_x ? u[e] : v[e], rb);
-            }
-          }
+          __syncthreads();
         }
       }
-      __syncthreads();                               // this CTA's own column moves
+      // the pairs across the two blocks
+      for (int s = 0; s < b; ++s) {
+        if (grp < b) {
+          int j = grp + s;
+          if (j >= b) j -= b;
+          fl |= rotate_pair16<EP>(col(buf, 0, grp), col(buf, 1, j), gl, gmask, tol2, big2);
+        }
+        __syncthreads();
+      }
+      // every block to its next position (buffer buf ^ 1): 16-byte pieces
+      const int per = b * colf / 4;                  // float4 per block
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float4* src = reinterpret_cast<const float4*>(col(buf, h, 0));
+        float* dst = col(buf ^ 1, dslot[h], 0);
+        if (dcta[h] == rank) {
+          float4* d4 = reinterpret_cast<float4*>(dst);
+          for (int e = t; e < per; e += blockDim.x) d4[e] = src[e];
+        } else {
+          const uint32_t rd = cl_mapa(cl_smem_u32(dst), dcta[h]);
+          const uint32_t rb = cl_mapa(cl_smem_u32(&s_mbar[buf ^ 1]), dcta[h]);
+          for (int e = t; e < per; e += blockDim.x) cl_st_async4(rd + 16u * (uint32_t)e, src[e], rb);
+        }
+      }
+      __syncthreads();                               // this CTA's own block moves
       if (rem_bytes) {
-        // the neighbours' columns (bounded wait: on a timeout the status
+        // the neighbours' blocks (bounded wait: on a timeout the status
         // records it and the sweeps run on without waiting, so every CTA
         // still meets every cluster barrier)
         const uint32_t ph = (buf ^ 1) ? mpar1 : mpar0;
@@ -710,11 +732,9 @@ jacobi_sweep_cluster_kernel(const double* __restrict__ Min, int l, int gpc, floa
         else mpar0 ^= 1u;
       }
       buf ^= 1;
-      if (pa != 0) ia = ia == 1 ? N - 1 : ia - 1;
-      ib = ib == 1 ? N - 1 : ib - 1;
     }
-    rot_local = __syncthreads_or(rot_local);
-    big_local = __syncthreads_or(big_local);
+    const int rot_local = __syncthreads_or(fl & 1);
+    const int big_local = __syncthreads_or(fl & 2);
     if (t == 0) {
       if (rot_local) atomicOr(cluster.map_shared_rank(&s_flag[par], 0), 1);
       if (big_local) atomicOr(cluster.map_shared_rank(&s_big[par], 0), 1);
@@ -732,13 +752,12 @@ jacobi_sweep_cluster_kernel(const double* __restrict__ Min, int l, int gpc, floa
     }
   }
   if (rank == 0 && t == 0) atomicOr(&status->info, (min(sweep, cap)) << 8);
-  // a sweep ends where it began: position p holds column p
-  for (int e = t; e < 2 * gpc * LDW; e += blockDim.x) {
-    const int sl = e / LDW, i = e - sl * LDW;
-    const int g = rank * gpc + (sl >> 1);
-    if (g >= G || i >= l) continue;
-    const int j = (sl & 1) ? N - 1 - g : g;
-    if (j < l) Vout[i + (size_t)j * l] = slot(buf, sl)[LDW + i];
+  // a sweep ends where it began: slot h holds block pos[h]
+  for (int e = t; e < 2 * b * LDW; e += blockDim.x) {
+    const int sj = e / LDW, i = e - sj * LDW;
+    const int sl = sj / b, j = sj - sl * b;
+    const int g = pos[sl] * b + j;
+    if (g < l && i < l) Vout[i + (size_t)g * l] = col(buf, sl, j)[LDW + i];
   }
 }
 
@@ -1016,26 +1035,27 @@ cudaError_t launch_sweep_coop(const double* M, int l, float* vout, void* work, D
 #undef COOP
 }
 
-// cluster sweep: 16 lanes x gpc pairs per CTA, kClusterCtas CTAs
+// cluster sweep: 16 lanes per pair, columns of 32 EP floats
 inline int sweep_cluster_ep(int l) {
   const int need = (l + 31) / 32;
   return need <= 10 ? need : 0;
 }
-inline int sweep_cluster_gpc(int l) {
-  const int G = (l + 1) / 2;
-  return (G + kClusterCtas - 1) / kClusterCtas;
-}
-inline size_t sweep_cluster_smem(int l) {
-  return (size_t)2 * 2 * sweep_cluster_gpc(l) * 2 * 32 * std::max(1, sweep_cluster_ep(l)) * sizeof(float);
+
+// block-cyclic cluster sweep: b = ceil(l / 32) columns per block, 16 lanes
+// per pair, (b rounded up to even) pairs per CTA at once
+inline int block_cluster_b(int l) { return (l + kBlockNb - 1) / kBlockNb; }
+inline size_t block_cluster_smem(int l) {
+  return (size_t)2 * 2 * block_cluster_b(l) * 2 * 32 * std::max(1, sweep_cluster_ep(l)) * sizeof(float);
 }
 
-cudaError_t launch_sweep_cluster(const double* M, int l, float* vout, DeviceStatus* status, cudaStream_t st) {
-  const int ep = sweep_cluster_ep(l), gpc = sweep_cluster_gpc(l);
-  const size_t smem = sweep_cluster_smem(l);
-  if (!ep || gpc * 16 > 512 || smem > kSweepSmemMax) return cudaErrorInvalidValue;
+cudaError_t launch_block_cluster(const double* M, int l, float* vout, DeviceStatus* status, cudaStream_t st) {
+  const int ep = sweep_cluster_ep(l), b = block_cluster_b(l);
+  const size_t smem = block_cluster_smem(l);
+  const int nt = 16 * (b + (b & 1));
+  if (!ep || nt > 352 || smem > kSweepSmemMax) return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(kClusterCtas, 1, 1);
-  cfg.blockDim = dim3(gpc * 16, 1, 1);
+  cfg.blockDim = dim3(nt, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -1045,29 +1065,29 @@ cudaError_t launch_sweep_cluster(const double* M, int l, float* vout, DeviceStat
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-#define CLSWEEP(E)                                                                                  \
+#define BLSWEEP(E)                                                                                  \
   {                                                                                                 \
-    auto kern = jacobi_sweep_cluster_kernel<E>;                                                     \
+    auto kern = jacobi_block_cluster_kernel<E>;                                                     \
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);  \
     if (e == cudaSuccess)                                                                           \
       e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);       \
     if (e != cudaSuccess) return e;                                                                 \
-    return cudaLaunchKernelEx(&cfg, kern, M, l, gpc, vout, status);                                 \
+    return cudaLaunchKernelEx(&cfg, kern, M, l, b, vout, status);                                   \
   }
   switch (ep) {
-    case 1: CLSWEEP(1)
-    case 2: CLSWEEP(2)
-    case 3: CLSWEEP(3)
-    case 4: CLSWEEP(4)
-    case 5: CLSWEEP(5)
-    case 6: CLSWEEP(6)
-    case 7: CLSWEEP(7)
-    case 8: CLSWEEP(8)
-    case 9: CLSWEEP(9)
-    case 10: CLSWEEP(10)
+    case 1: BLSWEEP(1)
+    case 2: BLSWEEP(2)
+    case 3: BLSWEEP(3)
+    case 4: BLSWEEP(4)
+    case 5: BLSWEEP(5)
+    case 6: BLSWEEP(6)
+    case 7: BLSWEEP(7)
+    case 8: BLSWEEP(8)
+    case 9: BLSWEEP(9)
+    case 10: BLSWEEP(10)
     default: return cudaErrorInvalidValue;
   }
-#undef CLSWEEP
+#undef BLSWEEP
 }
 
 cudaError_t launch_sweep_g(const double* M, int l, float* vout, DeviceStatus* status, cudaStream_t st) {
@@ -1121,6 +1141,62 @@ cudaError_t launch_sweep_f2(const double* M, int l, float* vout, DeviceStatus* s
 #undef F2SWEEP
 }
 
+// binary64 Jacobi work beyond the common areas: the fp32 rotations (l^2
+// fp32), six l x l binary64 matrices and a scratch status word
+inline size_t jacobi_mixed_bytes(int l) {
+  return (((size_t)l * l * 4 + 255) & ~(size_t)255) + 6 * (size_t)l * l * 8 + 256;
+}
+
+// fp32 sweeps of M (one block, or the cluster for l >= kClusterMinL); false
+// when neither form takes l
+bool launch_sweep32(const double* M, int l, float* vout, DeviceStatus* status, cudaStream_t st, cudaError_t* e) {
+  if (l >= kClusterMinL && sweep_cluster_ep(l) && block_cluster_smem(l) <= kSweepSmemMax) {
+    *e = launch_block_cluster(M, l, vout, status, st);
+    return true;
+  }
+  if (sweep_g_smem(l) <= kSweepSmemMax) {
+    *e = launch_sweep_g(M, l, vout, status, st);
+    return true;
+  }
+  return false;
+}
+
+// The binary64 SVD of M by fp32 sweeps polished in binary64: fp32 sweeps
+// give rotations V32 (orthogonal to fp32 level); V = V32 R^{-1} with
+// R^T R = V32^T V32 (binary64 Cholesky) is orthonormal to binary64 level;
+// binary64 sweeps of W = M V (columns already orthogonal to fp32 level, so
+// one or two sweeps reach the binary64 tolerance: Jacobi converges
+// quadratically) give V'; the right vectors are V V'.  The binary64 sweeps
+// are the expensive part on this GPU (binary64 runs at 1/64 of the fp32
+// rate, one block), so most of the rotation work moves to fp32.  The fp32
+// sweeps only precondition: they report into a scratch status word, since
+// on a core with an exact null space (columns at 1e-17 of sigma_1, below
+// fp32 rounding) they cannot meet their own tolerance - the binary64 sweeps
+// decide convergence.
+// Returns false (nothing launched) when the fp32 sweeps do not take l.
+bool jacobi_f64_mixed(const double* M, int l, double* vout, char* mixed, double* gwork, DeviceStatus* status,
+                      cudaStream_t st, cudaError_t* e) {
+  if (l < 2 || l > SORSVD_MAX_L_F64) return false;
+  float* v32 = reinterpret_cast<float*>(mixed);
+  double* d = reinterpret_cast<double*>(mixed + (((size_t)l * l * 4 + 255) & ~(size_t)255));
+  const size_t ll = (size_t)l * l;
+  double *V64 = d, *G = d + ll, *R = d + 2 * ll, *V = d + 3 * ll, *W = d + 4 * ll, *Vp = d + 5 * ll;
+  DeviceStatus* scratch = reinterpret_cast<DeviceStatus*>(d + 6 * ll);
+  if (!launch_sweep32(M, l, v32, scratch, st, e)) return false;
+  if (*e != cudaSuccess) return true;
+  if ((*e = launch_widen(v32, SORSVD_F32, l, l, l, V64, true, l, st)) != cudaSuccess) return true;
+  if ((*e = launch_small_gemm64(V64, true, V64, false, G, l, st)) != cudaSuccess) return true;      // V32^T V32
+  if ((*e = launch_chol_inv(G, l, 0.0, R, true, status, st)) != cudaSuccess) return true;
+  if ((*e = launch_small_gemm64(V64, false, R, false, V, l, st)) != cudaSuccess) return true;      // V32 R^{-1}
+  if ((*e = launch_small_gemm64(M, false, V, false, W, l, st)) != cudaSuccess) return true;        // W = M V
+  const size_t need = 2 * ll * sizeof(double);
+  *e = (need <= kSweepSmemMax) ? launch_sweep<double, true>(W, l, Vp, gwork, need, status, st)
+                               : launch_sweep<double, false>(W, l, Vp, gwork, 0, status, st);
+  if (*e != cudaSuccess) return true;
+  *e = launch_small_gemm64(V, false, Vp, false, vout, l, st);                                      // V V'
+  return true;
+}
+
 template <typename J, typename TS>
 cudaError_t run_all(const double* M, int l, int k, void* Ut, void* Vt, void* S, void* work, DeviceStatus* status,
                     cudaStream_t st) {
@@ -1134,9 +1210,13 @@ cudaError_t run_all(const double* M, int l, int k, void* Ut, void* Vt, void* S, 
   const size_t need = 2 * (size_t)l * l * sizeof(J);
   cudaError_t e;
   static const int lanes = [] { const char* v = std::getenv("SORSVD_JACOBI_LANES"); return v ? std::atoi(v) : 16; }();
-  if (sizeof(J) == 4 && lanes == 16 && l >= kClusterMinL && sweep_cluster_ep(l) &&
-      sweep_cluster_smem(l) <= kSweepSmemMax)
-    e = launch_sweep_cluster(M, l, reinterpret_cast<float*>(vout), status, st);
+  char* mixed = w + ((jacobi_base_bytes(l) + 255) & ~(size_t)255) + sweep_coop_work_bytes(l);
+  if (sizeof(J) == 8 && jacobi_f64_mixed(M, l, reinterpret_cast<double*>(vout), mixed,
+                                          reinterpret_cast<double*>(gwork), status, st, &e)) {
+    // binary64: fp32 sweeps polished in binary64
+  } else if (sizeof(J) == 4 && lanes == 16 && l >= kClusterMinL && sweep_cluster_ep(l) &&
+      block_cluster_smem(l) <= kSweepSmemMax)
+    e = launch_block_cluster(M, l, reinterpret_cast<float*>(vout), status, st);
   else if (sizeof(J) == 4 && lanes == 16 && sweep_g_smem(l) <= kSweepSmemMax)
     e = launch_sweep_g(M, l, reinterpret_cast<float*>(vout), status, st);
   else if (sizeof(J) == 4 && sweep_coop_ep(l) && sweep_f2_smem(l) > kSweepSmemMax)
@@ -1161,7 +1241,7 @@ cudaError_t set_jacobi_sweep_cap(int cap) {
 }
 
 size_t jacobi_work_bytes(int l) {
-  return ((jacobi_base_bytes(l) + 255) & ~(size_t)255) + sweep_coop_work_bytes(l);
+  return ((jacobi_base_bytes(l) + 255) & ~(size_t)255) + sweep_coop_work_bytes(l) + jacobi_mixed_bytes(l);
 }
 
 cudaError_t launch_jacobi(const double* M, int l, int k, bool f64, void* Ut, void* Vt, void* S, bool S_f64,

@@ -191,21 +191,22 @@ cudaError_t begin_call(const Ctx& c) {
 // C (M x N, ldc) = op(A) B on CUDA cores, with split-K through the partial
 // buffer when useful.
 int gemm(const Ctx& c, int kcls, bool trans, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
-         int adt, const void* B, int64_t ldb, int bdt, void* C, int64_t ldc, bool c_f64, int cap) {
+         int adt, const void* B, int64_t ldb, int bdt, void* C, int64_t ldc, bool c_f64, int cap,
+         const int* skip = nullptr) {
   const bool accf = c.f64;
   int s = splits_for(M, N, K, cap, accf);
   if (s == 1 && (c_f64 == accf)) {
     ProfScope ps(kcls, c.st);
-    CK(launch_gemm(trans, M, N, K, A, lda, adt, B, ldb, bdt, C, ldc, accf, 1, 0, c.st));
+    CK(launch_gemm(trans, M, N, K, A, lda, adt, B, ldb, bdt, C, ldc, accf, 1, 0, c.st, skip));
     return SORSVD_OK;
   }
   int64_t stride = M * N;
   {
     ProfScope ps(kcls, c.st);
-    CK(launch_gemm(trans, M, N, K, A, lda, adt, B, ldb, bdt, c.at(c.L.parts), M, accf, s, stride, c.st));
+    CK(launch_gemm(trans, M, N, K, A, lda, adt, B, ldb, bdt, c.at(c.L.parts), M, accf, s, stride, c.st, skip));
   }
   ProfScope ps(K_REDUCE, c.st);
-  CK(launch_reduce_splits(c.at(c.L.parts), accf, s, stride, M, N, M, C, c_f64, ldc, c.st));
+  CK(launch_reduce_splits(c.at(c.L.parts), accf, s, stride, M, N, M, C, c_f64, ldc, c.st, skip));
   return SORSVD_OK;
 }
 
@@ -381,16 +382,21 @@ int orth(const Ctx& c, void* T, int64_t rows, int64_t ld, int l, int passes, dou
                                     (passes == 3 && X != (float*)T) ? conv : nullptr, c.st));
     return SORSVD_OK;
   }
+  // binary64: the same device-side skip of the third pass as above (the
+  // second pass's input within kOrthTol of orthonormal leaves T
+  // orthonormal to working precision)
   const int adt = SORSVD_F64;
+  int* conv = c.status()->pad;
   for (int p = 0; p < passes; ++p) {
-    int r = gemm(c, K_SMALL_GEMM, true, l, l, rows, T, ld, adt, T, ld, adt, c.at(c.L.G), l, true, kCapSmall);
+    const int* skip = p == 2 ? conv : nullptr;
+    int r = gemm(c, K_SMALL_GEMM, true, l, l, rows, T, ld, adt, T, ld, adt, c.at(c.L.G), l, true, kCapSmall, skip);
     if (r) return r;
     LAUNCH(K_CHOL, launch_chol_inv((const double*)c.at(c.L.G), l, p == 0 ? shift0 : 0.0, c.at(c.L.Rinv), c.f64,
-                                   c.status(), c.st));
+                                   c.status(), c.st, skip, p == 1 ? conv : nullptr, kOrthTol));
     r = gemm(c, K_SMALL_GEMM, false, rows, l, l, T, ld, adt, c.at(c.L.Rinv), l, adt, c.at(c.L.tmp), ld, c.f64,
-             kCapBig);
+             kCapBig, skip);
     if (r) return r;
-    LAUNCH(K_MISC, launch_copy2d(c.at(c.L.tmp), ld, T, ld, rows, l, acc_size(c.dt), c.st));
+    LAUNCH(K_MISC, launch_copy2d(c.at(c.L.tmp), ld, T, ld, rows, l, acc_size(c.dt), c.st, skip));
   }
   return SORSVD_OK;
 }
