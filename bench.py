@@ -52,9 +52,9 @@ WORKLOADS = {
                  desc="bf16 A 65536x16384 = U diag(exp(-i/64))_{i<=1024} V^T (Haar); k=256, p=10, q=2"),
     "cfg1": dict(m=1000, n=1000, k=20, p=5, q=1, dtype="f64", width=1000, noise=0.0, spectrum="cfg1",
                  desc="fp64 A 1000x1000, sigma_i = 1 (i<=20), 10^{-(i-20)/10}; k=20, p=5, q=1"),
-    "cfg4": dict(batch=512, p=8, q=1, dtype="tf32", width=256,
+    "cfg4": dict(batch=512, p=8, q=1, dtype="tf32",
                  desc="512 fp32 matrices, m log-uniform [256, 4096], n log-uniform [128, 2048], k uniform 8..64, "
-                      "p=8, q=1, sigma_i = i^-2 (i <= 256, Haar factors); batched plan replayed as a CUDA graph"),
+                      "p=8, q=1, sigma_i = i^-2 over min(m, n) (Haar factors); batched plan replayed as a CUDA graph"),
     "cfg5": dict(batch=8, m=25344, n=400, rank=5, k=5, p=5, q=1, dtype="f32",
                  desc="RPCA (inexact ALM, SOR-SVD low-rank step) of 8 problems X = L + S, 25344x400 fp32, "
                       "L rank 5 (Gaussian factors), S 5% support, |S| uniform [1, 10]; k=5, p=5, q=1; "
@@ -414,7 +414,7 @@ def run_batched(args, w, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     sizes = inputs.batched_sizes(w["batch"], seed=0)
-    As = [inputs.batched_matrix_torch(m, n, seed=1000 * (rank + 1) + b, width=w["width"], device=dev,
+    As = [inputs.batched_matrix_torch(m, n, seed=1000 * (rank + 1) + b, device=dev,
                                       dtype=torch.float32) for b, (m, n, k) in enumerate(sizes)]
     ks = [k for _, _, k in sizes]
     plan = native.BatchedPlan(As, ks, w["p"], w["q"], seeds=list(range(len(sizes))), dtype=w["dtype"],
@@ -454,7 +454,8 @@ def run_batched(args, w, rank, world, local_rank):
     return {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded, built on the GPU)",
-            "config": {"workload": f"{args.workload}: {w['desc']}", "batch": len(sizes), "flops_per_step": F,
+            "config": {"workload": f"{args.workload}: {w['desc']}", "batch": len(sizes),
+                       "autotuned_tiles": plan.tiles, "flops_per_step": F,
                        "a_bytes": total_bytes, "l2": "inputs larger than L2 (%d MB of A)" % (total_bytes // 2**20),
                        "parallelism": f"replicas x{world}"},
             "e2e": {"value": job_tflops(F, world, e_ms), "unit": "TFLOP/s", "ms_per_step": e_ms,

@@ -78,6 +78,9 @@ typedef enum {
                                           2q + 3).  REFINE is then ignored.
                                           Needs the same flag in
                                           sorsvd_workspace_size. */
+#define SORSVD_FLAG_FIXED_TILES   0x10u /* batched plans: no autotuning, every
+                                          grouped product on the 128 x 64
+                                          tile shape */
 
 /* Largest sketch width l = k + p supported (the small l x l factorisations
  * run in one thread block with the factor in shared memory). */
@@ -279,6 +282,15 @@ int sorsvd_batched_plan_launch(sorsvd_batch_plan* plan, void* stream);
 int sorsvd_batched_plan_status(const sorsvd_batch_plan* plan, int* codes, void* stream);
 /* Kernel launches per run (for accounting). */
 int sorsvd_batched_plan_launches(const sorsvd_batch_plan* plan);
+/* The tile shape the plan's autotuner picked for each grouped product
+ * stage, in stage order (0: 128 x 64, 1: 64 x 64, 2: 64 x 32 outputs per
+ * block).  sorsvd_batched_plan_create times every shape of every stage on
+ * the plan's own jobs (CUDA events, cached per stage shape for the process;
+ * SORSVD_FLAG_FIXED_TILES keeps shape 0); the results do not depend on the
+ * choice.  Writes up to max_tiles entries and returns the
+ * number of product stages.  The paper has no counterpart (its method is
+ * single-problem). */
+int sorsvd_batched_plan_tiles(const sorsvd_batch_plan* plan, int* tiles, int max_tiles);
 void sorsvd_batched_plan_destroy(sorsvd_batch_plan* plan);
 /* One-shot: plan (no graph), launch, destroy.  Asynchronous except for the
  * descriptor upload. */

@@ -25,7 +25,12 @@
 #include "profile.cuh"
 
 #include <algorithm>
+#include <cmath>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -35,8 +40,13 @@ struct BatchStage {
   StageKind kind;
   size_t jobs_off;       // byte offset of the job array in the header's job area
   int njobs;
-  size_t units_off;      // gemm: byte offset of the int4 unit list
-  int nunits;
+  // gemm: one int4 unit list per tile shape (byte offset, count), and the
+  // shape the autotuner picked
+  size_t units_off[sorsvd::kBatchedTiles];
+  int nunits[sorsvd::kBatchedTiles];
+  int tile;
+  double work;           // gemm: sum of 2 M N K over the jobs (the autotuner's key)
+  int max_n;
   int64_t max_elems;     // gauss / reduce: largest element count of a job
   int max_l;             // chol / jacobi
 };
@@ -127,23 +137,30 @@ struct Builder {
   }
   void gemm(bool trans, const std::vector<GemmJob>& jobs) {
     if (jobs.empty()) return;
-    int bm, bn, bk;
-    gemm_tile_shape(&bm, &bn, &bk);
-    std::vector<int4> units;
-    for (size_t j = 0; j < jobs.size(); ++j) {
-      const GemmJob& g = jobs[j];
-      const int mt = (int)((g.M + bm - 1) / bm), nt = (int)((g.N + bn - 1) / bn);
-      const int ks = (int)((g.K + g.k_chunk - 1) / g.k_chunk);
-      for (int z = 0; z < ks; ++z)
-        for (int y = 0; y < nt; ++y)
-          for (int x = 0; x < mt; ++x) units.push_back(make_int4((int)j, x, y, z));
-    }
     BatchStage s{};
     s.kind = trans ? ST_GEMM_T : ST_GEMM_N;
     s.jobs_off = put(jobs);
     s.njobs = (int)jobs.size();
-    s.units_off = put(units);
-    s.nunits = (int)units.size();
+    for (const GemmJob& g : jobs) {
+      s.work += 2.0 * (double)g.M * (double)g.N * (double)g.K;
+      s.max_n = std::max(s.max_n, (int)g.N);
+    }
+    for (int tile = 0; tile < kBatchedTiles; ++tile) {
+      int bm, bn, bk;
+      gemm_tile_shape(tile, &bm, &bn, &bk);
+      std::vector<int4> units;
+      for (size_t j = 0; j < jobs.size(); ++j) {
+        const GemmJob& g = jobs[j];
+        const int mt = (int)((g.M + bm - 1) / bm), nt = (int)((g.N + bn - 1) / bn);
+        const int ks = (int)((g.K + g.k_chunk - 1) / g.k_chunk);
+        for (int z = 0; z < ks; ++z)
+          for (int y = 0; y < nt; ++y)
+            for (int x = 0; x < mt; ++x) units.push_back(make_int4((int)j, x, y, z));
+      }
+      s.units_off[tile] = put(units);
+      s.nunits[tile] = (int)units.size();
+    }
+    s.tile = 0;
     stages.push_back(s);
   }
   void reduce(const std::vector<ReduceJob>& jobs) {
@@ -176,7 +193,7 @@ GemmJob gjob(const void* A, int64_t lda, const void* B, int64_t ldb, void* C, in
   g.lda = lda; g.ldb = ldb; g.ldc = ldc;
   g.M = M; g.N = N; g.K = K;
   int bm, bn, bk;
-  gemm_tile_shape(&bm, &bn, &bk);
+  gemm_tile_shape(0, &bm, &bn, &bk);
   g.k_chunk = std::max<int64_t>(bk, (K + bk - 1) / bk * bk);
   g.split_stride = 0;
   return g;
@@ -203,7 +220,7 @@ void orth_pass(Builder& B, std::vector<ProbState>& ps, const std::vector<std::pa
   std::vector<GemmJob> apply;
   int max_l = 1;
   int bm, bn, bk;
-  gemm_tile_shape(&bm, &bn, &bk);
+  gemm_tile_shape(0, &bm, &bn, &bk);
   for (const auto& it : items) {
     const int b = it.first, which = it.second, set = which - 1;
     ProbState& s = ps[b];
@@ -336,7 +353,7 @@ int build_plan(sorsvd_batch_plan* plan, const sorsvd_problem* probs, int batch, 
     std::vector<GemmJob> w, mm;
     std::vector<ReduceJob> red;
     int bm, bn, bk;
-    gemm_tile_shape(&bm, &bn, &bk);
+    gemm_tile_shape(0, &bm, &bn, &bk);
     for (int b = 0; b < batch; ++b) {
       ProbState& s = ps[b];
       const sorsvd_problem& P = probs[b];
@@ -412,8 +429,8 @@ int enqueue(const sorsvd_batch_plan* plan, cudaStream_t st, bool count) {
         break;
       case ST_GEMM_N:
       case ST_GEMM_T:
-        e = launch_gemm_batched(s.kind == ST_GEMM_T, f64, (const GemmJob*)(hdr + s.jobs_off),
-                                (const int4*)(hdr + s.units_off), s.nunits, st);
+        e = launch_gemm_batched(s.kind == ST_GEMM_T, f64, s.tile, (const GemmJob*)(hdr + s.jobs_off),
+                                (const int4*)(hdr + s.units_off[s.tile]), s.nunits[s.tile], st);
         break;
       case ST_REDUCE:
         e = launch_reduce_batched(f64, (const ReduceJob*)(hdr + s.jobs_off), s.njobs, s.max_elems, st);
@@ -431,6 +448,73 @@ int enqueue(const sorsvd_batch_plan* plan, cudaStream_t st, bool count) {
   return SORSVD_OK;
 }
 
+// ------------------------------------------------------------ autotuner
+// The tile shape of every grouped GEMM stage is picked by timing: each
+// shape's launch of the stage, on the plan's own jobs and workspace (the
+// plan's first run overwrites whatever the trials wrote), is timed with
+// CUDA events (one untimed launch, then kTuneReps) and the fastest is kept.
+// The choice is cached per (kind, precision, job count, work to a quarter
+// octave, widest output), so plans of the same shape reuse it.  The per-
+// element K order of the grouped kernel does not depend on the shape, so
+// the results are the same bit for bit whatever the choice.
+// SORSVD_FLAG_FIXED_TILES keeps the 128 x 64 shape.
+constexpr int kTuneReps = 3;
+
+struct TuneKey {
+  int kind, f64, njobs, work_q, max_n;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(kind, f64, njobs, work_q, max_n) < std::tie(o.kind, o.f64, o.njobs, o.work_q, o.max_n);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune_cache;
+
+int autotune(sorsvd_batch_plan* plan, cudaStream_t st) {
+  const bool f64 = plan->dtype == SORSVD_F64;
+  char* hdr = plan->ws + align_up(sizeof(DeviceStatus) * (size_t)plan->batch);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return SORSVD_ERR_CUDA;
+  }
+  int r = SORSVD_OK;
+  for (BatchStage& s : plan->stages) {
+    if (s.kind != ST_GEMM_N && s.kind != ST_GEMM_T) continue;
+    const TuneKey key{(int)s.kind, f64 ? 1 : 0, s.njobs, (int)std::lround(4.0 * std::log2(std::max(1.0, s.work))),
+                      s.max_n};
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune_cache.find(key);
+      if (it != g_tune_cache.end()) { s.tile = it->second; continue; }
+    }
+    float best_ms = 0.f;
+    int best = 0;
+    for (int tile = 0; tile < kBatchedTiles && !r; ++tile) {
+      auto launch = [&] {
+        return launch_gemm_batched(s.kind == ST_GEMM_T, f64, tile, (const GemmJob*)(hdr + s.jobs_off),
+                                   (const int4*)(hdr + s.units_off[tile]), s.nunits[tile], st);
+      };
+      if (launch() != cudaSuccess || cudaEventRecord(e0, st) != cudaSuccess) { r = SORSVD_ERR_CUDA; break; }
+      for (int i = 0; i < kTuneReps; ++i)
+        if (launch() != cudaSuccess) r = SORSVD_ERR_CUDA;
+      float ms = 0.f;
+      if (r || cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        r = SORSVD_ERR_CUDA;
+        break;
+      }
+      if (tile == 0 || ms < best_ms) { best_ms = ms; best = tile; }
+    }
+    if (r) break;
+    s.tile = best;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = best;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return r;
+}
+
 int launches_of(const std::vector<BatchStage>& st) {
   int n = 0;
   for (const BatchStage& s : st) n += (s.kind == ST_JACOBI) ? 3 : 1;
@@ -440,7 +524,7 @@ int launches_of(const std::vector<BatchStage>& st) {
 int validate(const sorsvd_problem* probs, int batch, int dtype, unsigned flags) {
   if (!batched_dtype(dtype)) return SORSVD_ERR_DTYPE;
   if (!probs || batch < 1) return SORSVD_ERR_ARG;
-  if (flags & ~SORSVD_FLAG_LITERAL_POWER) return SORSVD_ERR_ARG;
+  if (flags & ~(SORSVD_FLAG_LITERAL_POWER | SORSVD_FLAG_FIXED_TILES)) return SORSVD_ERR_ARG;
   for (int b = 0; b < batch; ++b)
     if (int r = check_problem(probs[b], dtype)) return r;
   return SORSVD_OK;
@@ -499,6 +583,10 @@ extern "C" int sorsvd_batched_plan_create(sorsvd_batch_plan** out, const sorsvd_
     sorsvd_batched_plan_destroy(plan);
     return SORSVD_ERR_CUDA;
   }
+  if (int r = (flags & SORSVD_FLAG_FIXED_TILES) ? SORSVD_OK : autotune(plan, st)) {
+    sorsvd_batched_plan_destroy(plan);
+    return r;
+  }
   if (use_graph) {
     // capture on a private stream (the caller's may be the legacy stream)
     cudaStream_t cs;
@@ -548,6 +636,17 @@ extern "C" int sorsvd_batched_plan_status(const sorsvd_batch_plan* plan, int* co
 }
 
 extern "C" int sorsvd_batched_plan_launches(const sorsvd_batch_plan* plan) { return plan ? plan->launches : 0; }
+
+extern "C" int sorsvd_batched_plan_tiles(const sorsvd_batch_plan* plan, int* tiles, int max_tiles) {
+  if (!plan) return 0;
+  int n = 0;
+  for (const BatchStage& s : plan->stages) {
+    if (s.kind != ST_GEMM_N && s.kind != ST_GEMM_T) continue;
+    if (tiles && n < max_tiles) tiles[n] = s.tile;
+    ++n;
+  }
+  return n;
+}
 
 extern "C" void sorsvd_batched_plan_destroy(sorsvd_batch_plan* plan) {
   if (!plan) return;

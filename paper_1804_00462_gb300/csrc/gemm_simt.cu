@@ -39,9 +39,11 @@ struct TileCfg {
   static constexpr int NT = (BM / TM) * (BN / TN);
 };
 using BigTile = TileCfg<128, 64, 16, 8, 4>;      // 256 threads
+using MidTile = TileCfg<64, 64, 16, 4, 4>;       // 256 threads
 using SkinnyTile = TileCfg<64, 32, 16, 4, 2>;    // 256 threads
 constexpr int NT = 256;
-static_assert(BigTile::NT == NT && SkinnyTile::NT == NT, "tile configurations use 256 threads");
+static_assert(BigTile::NT == NT && MidTile::NT == NT && SkinnyTile::NT == NT,
+              "tile configurations use 256 threads");
 
 template <typename Acc, typename T> __device__ __forceinline__ Acc ld_as(const T* p) { return to_acc<Acc, T>(*p); }
 
@@ -123,16 +125,15 @@ gemm_kernel(int64_t M, int64_t N, int64_t K, const TA* __restrict__ A, int64_t l
 
 // Grouped form: block b computes unit units[b] = (job, m-tile, n-tile,
 // k-split) of jobs[job]; one launch covers a stage of every problem.
-template <typename Acc, bool TRANS>
+template <class Cfg, typename Acc, bool TRANS>
 __global__ void __launch_bounds__(NT)
 gemm_batched_kernel(const GemmJob* __restrict__ jobs, const int4* __restrict__ units) {
   const int4 u = units[blockIdx.x];
   const GemmJob& j = jobs[u.x];
   const int64_t kbeg = (int64_t)u.w * j.k_chunk;
-  gemm_tile<BigTile, Acc, Acc, Acc, TRANS>(j.M, j.N, (const Acc*)j.A, j.lda, (const Acc*)j.B, j.ldb,
-                                           (Acc*)j.C + (int64_t)u.w * j.split_stride, j.ldc,
-                                           (int64_t)u.y * BigTile::BM, (int64_t)u.z * BigTile::BN, kbeg,
-                                           min(j.K, kbeg + j.k_chunk));
+  gemm_tile<Cfg, Acc, Acc, Acc, TRANS>(j.M, j.N, (const Acc*)j.A, j.lda, (const Acc*)j.B, j.ldb,
+                                       (Acc*)j.C + (int64_t)u.w * j.split_stride, j.ldc, (int64_t)u.y * Cfg::BM,
+                                       (int64_t)u.z * Cfg::BN, kbeg, min(j.K, kbeg + j.k_chunk));
 }
 
 template <class Cfg, typename TA, typename TB, typename Acc>
@@ -403,17 +404,28 @@ cudaError_t launch_copy2d(const void* x, int64_t ldx, void* y, int64_t ldy, int6
   return cudaGetLastError();
 }
 
-cudaError_t launch_gemm_batched(bool trans_a, bool f64, const GemmJob* jobs, const int4* units, int nunits,
-                                cudaStream_t st) {
-  if (nunits <= 0) return cudaSuccess;
+template <class Cfg>
+cudaError_t launch_gemm_batched_cfg(bool trans_a, bool f64, const GemmJob* jobs, const int4* units, int nunits,
+                                    cudaStream_t st) {
   if (f64) {
-    if (trans_a) gemm_batched_kernel<double, true><<<nunits, NT, 0, st>>>(jobs, units);
-    else gemm_batched_kernel<double, false><<<nunits, NT, 0, st>>>(jobs, units);
+    if (trans_a) gemm_batched_kernel<Cfg, double, true><<<nunits, NT, 0, st>>>(jobs, units);
+    else gemm_batched_kernel<Cfg, double, false><<<nunits, NT, 0, st>>>(jobs, units);
   } else {
-    if (trans_a) gemm_batched_kernel<float, true><<<nunits, NT, 0, st>>>(jobs, units);
-    else gemm_batched_kernel<float, false><<<nunits, NT, 0, st>>>(jobs, units);
+    if (trans_a) gemm_batched_kernel<Cfg, float, true><<<nunits, NT, 0, st>>>(jobs, units);
+    else gemm_batched_kernel<Cfg, float, false><<<nunits, NT, 0, st>>>(jobs, units);
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_batched(bool trans_a, bool f64, int tile, const GemmJob* jobs, const int4* units, int nunits,
+                                cudaStream_t st) {
+  if (nunits <= 0) return cudaSuccess;
+  switch (tile) {
+    case 0: return launch_gemm_batched_cfg<BigTile>(trans_a, f64, jobs, units, nunits, st);
+    case 1: return launch_gemm_batched_cfg<MidTile>(trans_a, f64, jobs, units, nunits, st);
+    case 2: return launch_gemm_batched_cfg<SkinnyTile>(trans_a, f64, jobs, units, nunits, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_reduce_batched(bool parts_f64, const ReduceJob* jobs, int njobs, int64_t max_elems,
@@ -426,8 +438,16 @@ cudaError_t launch_reduce_batched(bool parts_f64, const ReduceJob* jobs, int njo
   return cudaGetLastError();
 }
 
-// the tile shape of the grouped kernel (units are counted in these tiles)
-void gemm_tile_shape(int* bm, int* bn, int* bk) { *bm = BigTile::BM; *bn = BigTile::BN; *bk = BigTile::BK; }
+// the tile shapes of the grouped kernel (units are counted in these tiles;
+// every shape takes 16-deep K slices, so a job's K chunks do not depend on
+// the shape)
+void gemm_tile_shape(int tile, int* bm, int* bn, int* bk) {
+  switch (tile) {
+    case 1: *bm = MidTile::BM; *bn = MidTile::BN; *bk = MidTile::BK; return;
+    case 2: *bm = SkinnyTile::BM; *bn = SkinnyTile::BN; *bk = SkinnyTile::BK; return;
+    default: *bm = BigTile::BM; *bn = BigTile::BN; *bk = BigTile::BK; return;
+  }
+}
 
 namespace {
 __global__ void add_f64_kernel(const double* __restrict__ x, int64_t ldx, double* __restrict__ y, int64_t ldy,

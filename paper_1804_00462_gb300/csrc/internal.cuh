@@ -137,9 +137,11 @@ struct JacobiJob {
   const double* M; void* Ut; void* Vt; void* S; void* work; DeviceStatus* status; int l, k;
 };
 // units: int4 (job, m-tile, n-tile, k-split) in tiles of gemm_tile_shape()
-cudaError_t launch_gemm_batched(bool trans_a, bool f64, const GemmJob* jobs, const int4* units, int nunits,
+// grouped tile shapes: 0 128 x 64, 1 64 x 64, 2 64 x 32 (kBatchedTiles)
+constexpr int kBatchedTiles = 3;
+cudaError_t launch_gemm_batched(bool trans_a, bool f64, int tile, const GemmJob* jobs, const int4* units, int nunits,
                                 cudaStream_t st);
-void gemm_tile_shape(int* bm, int* bn, int* bk);
+void gemm_tile_shape(int tile, int* bm, int* bn, int* bk);
 cudaError_t launch_reduce_batched(bool parts_f64, const ReduceJob* jobs, int njobs, int64_t max_elems,
                                   cudaStream_t st);
 cudaError_t launch_gaussian_batched(const GaussJob* jobs, int njobs, int64_t max_elems, int dtype,

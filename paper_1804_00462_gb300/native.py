@@ -24,6 +24,7 @@ F64, F32, TF32, BF16, F16 = 0, 1, 2, 3, 4
 FLAG_LITERAL_POWER = 0x1
 FLAG_REFINE = 0x2
 FLAG_TWO_PASS = 0x8
+FLAG_FIXED_TILES = 0x10
 MAX_L, MAX_L_F64 = 320, 224
 
 _TORCH_OF = {F64: torch.float64, F32: torch.float32, TF32: torch.float32, BF16: torch.bfloat16,
@@ -321,6 +322,8 @@ _lib.sorsvd_batched_plan_status.argtypes = [_vp, C.POINTER(_int), _vp]
 _lib.sorsvd_batched_plan_status.restype = _int
 _lib.sorsvd_batched_plan_launches.argtypes = [_vp]
 _lib.sorsvd_batched_plan_launches.restype = _int
+_lib.sorsvd_batched_plan_tiles.argtypes = [_vp, C.POINTER(_int), _int]
+_lib.sorsvd_batched_plan_tiles.restype = _int
 _lib.sorsvd_batched_plan_destroy.argtypes = [_vp]
 _lib.sorsvd_batched_plan_destroy.restype = None
 _lib.sorsvd_run_batched.argtypes = [C.POINTER(Problem), _int, _int, _uint, _vp, _sz, _vp]
@@ -378,6 +381,15 @@ class BatchedPlan:
     @property
     def launches(self) -> int:
         return int(_lib.sorsvd_batched_plan_launches(self._h))
+
+    @property
+    def tiles(self):
+        """The tile shape picked for each grouped product stage (0: 128 x 64,
+        1: 64 x 64, 2: 64 x 32)."""
+        n = int(_lib.sorsvd_batched_plan_tiles(self._h, None, 0))
+        out = (_int * max(n, 1))()
+        _lib.sorsvd_batched_plan_tiles(self._h, out, n)
+        return list(out)[:n]
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

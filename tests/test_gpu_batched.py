@@ -168,3 +168,24 @@ def test_batched_512_problem_workload(nat):
         assert np.abs(U.T @ U - np.eye(k)).max() <= 1e-4
         assert np.abs(V.T @ V - np.eye(k)).max() <= 1e-4
     plan.close()
+
+
+def test_autotuned_tiles_give_the_same_bits(nat):
+    # the plan's autotuner times every tile shape of every grouped product
+    # stage and keeps the fastest; the per-element K order of the grouped
+    # kernel does not depend on the shape, so a tuned plan and a plan fixed
+    # on the 128 x 64 shape return the same bits
+    sizes = inputs.batched_sizes(48, seed=5)
+    As = [inputs.batched_matrix_torch(m, n, seed=700 + b, dtype=torch.float32) for b, (m, n, k) in enumerate(sizes)]
+    ks = [k for _, _, k in sizes]
+    tuned = nat.BatchedPlan(As, ks, 8, 1, seeds=list(range(len(As))), dtype="f32")
+    fixed = nat.BatchedPlan(As, ks, 8, 1, seeds=list(range(len(As))), dtype="f32", flags=nat.FLAG_FIXED_TILES)
+    tuned.launch()
+    fixed.launch()
+    torch.cuda.synchronize()
+    assert tuned.status() == [0] * len(As) and fixed.status() == [0] * len(As)
+    tt, tf = tuned.tiles, fixed.tiles
+    assert len(tt) == len(tf) > 0 and set(tf) == {0} and set(tt) <= {0, 1, 2}
+    for b in range(len(As)):
+        assert torch.equal(tuned.U[b], fixed.U[b]) and torch.equal(tuned.S[b], fixed.S[b])
+        assert torch.equal(tuned.V[b], fixed.V[b])
