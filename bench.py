@@ -450,12 +450,13 @@ def run_batched(args, w, rank, world, local_rank):
     h2d = sum(a.numel() * 4 for a in As)
     d2h = sum(u.numel() * 4 + v.numel() * 4 + s_.numel() * 4 for u, v, s_ in zip(plan.U, plan.V, plan.S))
     total_bytes = sum(m * n * 4 for m, n, _ in sizes)
+    tiles = plan.tiles
     plan.close()
     return {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded, built on the GPU)",
             "config": {"workload": f"{args.workload}: {w['desc']}", "batch": len(sizes),
-                       "autotuned_tiles": plan.tiles, "flops_per_step": F,
+                       "autotuned_tiles": tiles, "flops_per_step": F,
                        "a_bytes": total_bytes, "l2": "inputs larger than L2 (%d MB of A)" % (total_bytes // 2**20),
                        "parallelism": f"replicas x{world}"},
             "e2e": {"value": job_tflops(F, world, e_ms), "unit": "TFLOP/s", "ms_per_step": e_ms,

@@ -734,7 +734,7 @@ EncodeTiledFn encode_fn() {
 
 // 2-D map of a column-major matrix (inner = rows, outer = cols, ld in elements)
 bool make_map(CUtensorMap* map, const void* ptr, int elt, int64_t rows, int64_t cols, int64_t ld,
-              uint32_t box_inner, uint32_t box_outer) {
+              uint32_t box_inner, uint32_t box_outer, bool swizzle = true) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   const CUtensorMapDataType dt = elt == 0 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
@@ -746,7 +746,7 @@ bool make_map(CUtensorMap* map, const void* ptr, int elt, int64_t rows, int64_t 
   cuuint32_t box[2] = {box_inner, box_outer};
   cuuint32_t estr[2] = {1, 1};
   return fn(map, dt, 2, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -928,6 +928,15 @@ cudaError_t launch_tc_gemm(bool trans_a, int elt, int64_t M, int64_t N, int64_t 
 }
 
 void set_tc_wait_cycles(long long cycles) { g_wait_cycles = cycles > 0 ? cycles : 0; }
+
+long long tc_wait_cycles() {
+  return (g_wait_cycles > 0 && g_wait_cycles < tc::kWaitCycles) ? g_wait_cycles : tc::kWaitCycles;
+}
+
+bool tc_map_2d(CUtensorMap* map, const void* ptr, int elt, int64_t rows, int64_t cols, int64_t ld, uint32_t box_inner,
+               uint32_t box_outer, bool swizzle128) {
+  return make_map(map, ptr, elt, rows, cols, ld, box_inner, box_outer, swizzle128);
+}
 
 cudaError_t launch_split_tf32(const float* X, int64_t ldx, int64_t rows, int64_t cols, float* hi, float* lo,
                               int64_t ldh, cudaStream_t st) {

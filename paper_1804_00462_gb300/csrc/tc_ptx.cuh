@@ -191,4 +191,13 @@ __host__ __device__ constexpr uint32_t idesc_make(uint32_t fmt, bool a_mn, bool 
 }
 
 }  // namespace tc
+
+// host side (gemm_tc.cu): 2-D TMA map of a column-major matrix (inner = rows,
+// outer = cols, ld in elements; elt 0 bf16, 1 fp16, 2 fp32), 128-byte
+// swizzle or none; false when the driver entry point or the encoding fails
+bool tc_map_2d(CUtensorMap* map, const void* ptr, int elt, int64_t rows, int64_t cols, int64_t ld, uint32_t box_inner,
+               uint32_t box_outer, bool swizzle128);
+// the limit of the progress waits of the next tensor-core launches
+long long tc_wait_cycles();
+
 }  // namespace sorsvd
