@@ -240,6 +240,32 @@ int sorsvd_chol_inv(const double* G, int l, double shift_rel, int dtype, void* R
 int sorsvd_polar_inv(const double* G, int l, float* X, int* ok, void* scratch, size_t scratch_bytes,
                      void* stream);
 
+/* Tall-skinny fp32 products of the QR step (CholeskyQR of a sketch T:
+ * G = T^T T, then Q = T R^{-1}; Sec. III) and of the output assembly
+ * (U = Q1 U~_k, V = Q2 V~_k; Algorithm 3), computed as sorsvd_run computes
+ * them for the binary32 and 16-bit dtypes: for l <= 288 (Gram) or
+ * K <= 288, N <= 320 (product) on the tensor cores, each operand split into
+ * a TF32 hi and an fp32 lo part and each product formed as
+ * hi*hi + hi*lo + lo*hi (fp32 accuracy; SORSVD_TSK=0 in the environment
+ * selects the CUDA-core kernels instead), else on CUDA cores.
+ *   sorsvd_gram:  G = X^T X, l x l binary64 (ldg >= l), for X rows x l; the
+ *                 per-CTA fp32 partials are summed in binary64 in a fixed
+ *                 order (bitwise repeatable).
+ *   sorsvd_apply: Y = X B, rows x N fp32 (ldy >= rows), for X rows x K and
+ *                 B K x N (ldb >= K); upper_tri != 0 declares B upper
+ *                 triangular (its entries below the diagonal must be zero).
+ * X: fp32, 16-byte aligned, ldx >= rows and a multiple of 4.  l, K, N in
+ * [1, SORSVD_MAX_L].  workspace: at least
+ * sorsvd_products_workspace_size(rows, l) bytes (l = max(K, N) for
+ * sorsvd_apply), 256-byte aligned; it starts with the device status word
+ * (sorsvd_get_status), where a bounded wait that gave up records
+ * SORSVD_ERR_TIMEOUT. */
+size_t sorsvd_products_workspace_size(int64_t rows, int l);
+int sorsvd_gram(const float* X, int64_t rows, int l, int64_t ldx, double* G, int64_t ldg,
+                void* workspace, size_t ws_bytes, void* stream);
+int sorsvd_apply(const float* X, int64_t rows, int K, int64_t ldx, const float* B, int64_t ldb, int N,
+                 int upper_tri, float* Y, int64_t ldy, void* workspace, size_t ws_bytes, void* stream);
+
 /* ---- batched SOR-SVD -------------------------------------------------------
  * Many independent problems of uneven shape (m, n, k, p, q may all differ)
  * in one sequence of grouped launches: each launch runs one stage of

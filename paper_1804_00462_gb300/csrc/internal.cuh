@@ -208,9 +208,33 @@ cudaError_t launch_rb_apply(const float* X, int64_t ldx, int64_t rows, int K, co
 cudaError_t launch_rb_copy(const float* src, float* dst, int64_t ld, int64_t rows, int l, void* Y16, int64_t ld16,
                            int kind16, const int* skip, cudaStream_t st);
 // out (binary64, rows x cols, ldo) = fixed-order sum of nparts fp32
-// partials (ld ldp, stride between partials), one thread per element
+// partials (ld ldp, stride between partials), kRedLanes threads per
+// element.  sym_split >= 0 (symmetric rows x rows result): the partials hold
+// the lower triangle, except that entries (i, j) with i >= sym_split > j
+// sit at (j, i); both halves of out are written.
 cudaError_t launch_reduce_parts(const float* parts, int nparts, int64_t stride, int rows, int cols, int ldp,
-                                     double* out, int ldo, cudaStream_t st);
+                                double* out, int ldo, cudaStream_t st, int sym_split = -1);
+
+// tsk_tc.cu: the tall-skinny fp32 products on the tensor cores (split TF32,
+// fp32 accuracy), l <= kTskMaxL columns.  launch_tsk_gram: tsk_gram_parts()
+// partials (l x l, ld l, stride l*l) of X^T X over the rows, to be summed by
+// launch_reduce_parts(..., sym_split) with the split it returns.
+// launch_tsk_apply: Y = X B (X rows x K, 16-byte aligned, ldx % 4 == 0;
+// B K x N given as hi / lo parts by launch_split_tf32, ldb % 4 == 0; tri: B
+// upper triangular), out of place, with an optional 16-bit rounding.  Both
+// return at once when *skip is set, and are unavailable (false from the
+// *_supported checks) with SORSVD_TSK=0.
+constexpr int kTskMaxL = 288;
+constexpr int kTskMaxN = 320;
+bool tsk_enabled();
+bool tsk_gram_supported(const float* X, int64_t ldx, int l);
+int tsk_gram_parts(int64_t rows);
+cudaError_t launch_tsk_gram(const float* X, int64_t ldx, int64_t rows, int l, float* parts, int* nparts,
+                            int* sym_split, const int* skip, DeviceStatus* status, cudaStream_t st);
+bool tsk_apply_supported(const float* X, int64_t ldx, int K, int N);
+cudaError_t launch_tsk_apply(const float* X, int64_t ldx, int64_t rows, int K, const float* Bhi, const float* Blo,
+                             int64_t ldb, int N, bool tri, float* Y, int64_t ldy, void* Y16, int64_t ld16,
+                             int kind16, const int* skip, DeviceStatus* status, cudaStream_t st);
 
 // twopass.cu: C (l x l) = op(A) op(B) in binary64 (op: transpose when the
 // flag is set); exact widening of a column-major matrix: 16-bit (BF16/F16)

@@ -320,14 +320,22 @@ __global__ void rb_copy_kernel(const float* __restrict__ src, float* __restrict_
 // is read in runs of neighbouring addresses.
 constexpr int kRedLanes = 8;
 __global__ void reduce_parts_kernel(const float* __restrict__ parts, int nparts, int64_t stride, int rows,
-                                    int cols, int ldp, double* __restrict__ out, int ldo) {
+                                    int cols, int ldp, double* __restrict__ out, int ldo, int sym_split) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t e = g / kRedLanes;
   const int u = (int)(g % kRedLanes);
-  const bool ok = e < (int64_t)rows * cols;
+  bool ok = e < (int64_t)rows * cols;
   float s = 0.f, c = 0.f;
+  int oi = 0, oj = 0;
   if (ok) {
-    const int j = (int)(e / rows), i = (int)(e - (int64_t)j * rows);
+    oj = (int)(e / rows);
+    oi = (int)(e - (int64_t)oj * rows);
+    // symmetric: the lower-triangle element writes both halves
+    if (sym_split >= 0 && oi < oj) ok = false;
+  }
+  if (ok) {
+    int i = oi, j = oj;
+    if (sym_split >= 0 && i >= sym_split && j < sym_split) { i = oj; j = oi; }
     const float* p = parts + i + (int64_t)j * ldp;
 #pragma unroll 4
     for (int q = u; q < nparts; q += kRedLanes) {
@@ -341,8 +349,8 @@ __global__ void reduce_parts_kernel(const float* __restrict__ parts, int nparts,
 #pragma unroll
   for (int o = 1; o < kRedLanes; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   if (ok && u == 0) {
-    const int j = (int)(e / rows), i = (int)(e - (int64_t)j * rows);
-    out[i + (int64_t)j * ldo] = v;
+    out[oi + (int64_t)oj * ldo] = v;
+    if (sym_split >= 0 && oi != oj) out[oj + (int64_t)oi * ldo] = v;
   }
 }
 
@@ -424,11 +432,12 @@ cudaError_t launch_rb_copy(const float* src, float* dst, int64_t ld, int64_t row
 }
 
 cudaError_t launch_reduce_parts(const float* parts, int nparts, int64_t stride, int rows, int cols, int ldp,
-                                     double* out, int ldo, cudaStream_t st) {
+                                double* out, int ldo, cudaStream_t st, int sym_split) {
   const int64_t threads = (int64_t)rows * cols * kRedLanes;
   if (threads <= 0) return cudaSuccess;
+  if (sym_split >= 0 && rows != cols) return cudaErrorInvalidValue;
   reduce_parts_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(parts, nparts, stride, rows, cols, ldp, out,
-                                                                     ldo);
+                                                                     ldo, sym_split);
   return cudaGetLastError();
 }
 

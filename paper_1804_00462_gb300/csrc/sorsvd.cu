@@ -82,8 +82,10 @@ struct Layout {
   int64_t ldm, ldn;      // leading dimensions of the m x l / n x l sketches
   size_t status, tilecnt, at, t2op, t2, t1, t1op, q2op, tmp, bhi, blo, parts, G, Rinv, M, Ut, Vt, jwork, total;
   size_t t1s, t2s, tp;   // two-pass core: T1 before its QR, T2_prev, five l x l binary64 matrices
+  size_t bsplit;         // hi / lo parts of the small factor of a tall-skinny tensor-core product
   int64_t ntilecnt;      // counters of the split tiles of a tensor-core pass
   int64_t ldb;           // leading dimension of bhi / blo
+  int64_t ldk;           // leading dimension of the parts in bsplit (l rounded up to 32)
   bool has_at;           // fp32 containers: A^T kept for the products A X
 };
 
@@ -149,6 +151,10 @@ Layout make_layout(int64_t m, int64_t n, int l, int dt, unsigned flags = 0) {
     pb = std::max(pb, rb_gram_parts_bytes(m, l, l, true));
     pb = std::max(pb, rb_gram_parts_bytes(n, l, l, true));
     pb = std::max(pb, rb_gram_parts_bytes(m, l, l, false));
+    if (l <= kTskMaxL) {                            // tensor-core Gram partials
+      pb = std::max(pb, (size_t)tsk_gram_parts(m) * l * l * sizeof(float));
+      pb = std::max(pb, (size_t)tsk_gram_parts(n) * l * l * sizeof(float));
+    }
   }
   L.parts = take(pb);
   L.G = take((size_t)l * l * 8);
@@ -159,6 +165,8 @@ Layout make_layout(int64_t m, int64_t n, int l, int dt, unsigned flags = 0) {
   // the Jacobi work area doubles as the scratch of the polar second
   // CholeskyQR pass (the two are never live at the same time)
   L.jwork = take(std::max(jacobi_work_bytes(l), polar_scratch_bytes(l)));
+  L.ldk = (l + 31) / 32 * 32;
+  L.bsplit = dt != SORSVD_F64 ? take((size_t)2 * L.ldk * L.ldk * sizeof(float)) : 0;
   if (flags & SORSVD_FLAG_TWO_PASS) {
     L.t1s = take((size_t)L.ldm * l * acc);
     L.t2s = take((size_t)L.ldn * l * acc);
@@ -335,26 +343,59 @@ int prepare_at(const Ctx& c, const void* A, int64_t m, int64_t n, int64_t lda) {
 // BF16 / F16 pass).  With `result` non-null and a single pass the
 // product stays in the tmp buffer (ld unchanged) and *result points to it:
 // no copy back.  binary64 sketches use the CUDA-core GEMMs.
+// G (binary64, l x l) = T^T T of an fp32 rows x l matrix: tensor cores
+// (split TF32) when they apply, else the row-block kernel; the partials are
+// summed in a fixed order
+int gram_sym(const Ctx& c, const float* T, int64_t ld, int64_t rows, int l, const int* skip, double* G = nullptr,
+             int64_t ldg = 0) {
+  float* parts = (float*)c.at(c.L.parts);
+  if (!G) { G = (double*)c.at(c.L.G); ldg = l; }
+  if (tsk_gram_supported(T, ld, l)) {
+    int np = 0, split = -1;
+    LAUNCH(K_SMALL_GEMM, launch_tsk_gram(T, ld, rows, l, parts, &np, &split, skip, c.status(), c.st));
+    LAUNCH(K_REDUCE, launch_reduce_parts(parts, np, (int64_t)l * l, l, l, l, G, (int)ldg, c.st, split));
+    return SORSVD_OK;
+  }
+  LAUNCH(K_SMALL_GEMM, launch_rb_gram(T, ld, T, ld, rows, l, l, true, parts, skip, c.st));
+  LAUNCH(K_REDUCE, launch_reduce_parts(parts, (int)rb_gram_blocks(rows, l, l, true), (int64_t)l * l, l, l, l, G,
+                                       (int)ldg, c.st));
+  return SORSVD_OK;
+}
+
+// Y (rows x N, ldy) = T B for fp32 T (rows x K) and B (K x N, ldb), out of
+// place, with an optional 16-bit rounding: tensor cores (B split into TF32
+// hi / lo first) when they apply, else the row-block kernel
+int apply(const Ctx& c, const float* T, int64_t ld, int64_t rows, int K, const float* B, int64_t ldb, int N,
+          bool tri, float* Y, int64_t ldy, void* Y16, int64_t ld16, int kind16, const int* skip) {
+  // bsplit holds 2 ldk x ldk floats' worth: K <= ldk rows, N <= ldk columns each
+  if (c.L.bsplit && K <= c.L.ldk && N <= c.L.ldk && tsk_apply_supported(T, ld, K, N)) {
+    float* hi = (float*)c.at(c.L.bsplit);
+    float* lo = hi + (size_t)c.L.ldk * N;
+    LAUNCH(K_SMALL_GEMM, launch_split_tf32(B, ldb, K, N, hi, lo, c.L.ldk, c.st));
+    LAUNCH(K_SMALL_GEMM, launch_tsk_apply(T, ld, rows, K, hi, lo, c.L.ldk, N, tri, Y, ldy, Y16, ld16, kind16, skip,
+                                          c.status(), c.st));
+    return SORSVD_OK;
+  }
+  LAUNCH(K_SMALL_GEMM, launch_rb_apply(T, ld, rows, K, B, ldb, N, tri, Y, ldy, Y16, ld16, kind16, skip, c.st));
+  return SORSVD_OK;
+}
+
 int orth(const Ctx& c, void* T, int64_t rows, int64_t ld, int l, int passes, double shift0, void* out16 = nullptr,
          int64_t ld16 = 0, void** result = nullptr) {
   const int kind16 = out16 ? (c.dt == SORSVD_BF16 ? 1 : 2) : 0;
   if (result) *result = T;
   if (!c.f64 && result && passes == 1) {
-    float* parts = (float*)c.at(c.L.parts);
     float* Y = (float*)c.at(c.L.tmp);
-    LAUNCH(K_SMALL_GEMM, launch_rb_gram((const float*)T, ld, (const float*)T, ld, rows, l, l, true, parts, nullptr,
-                                        c.st));
-    LAUNCH(K_REDUCE, launch_reduce_parts(parts, (int)rb_gram_blocks(rows, l, l, true), (int64_t)l * l, l, l, l,
-                                         (double*)c.at(c.L.G), l, c.st));
+    int r = gram_sym(c, (const float*)T, ld, rows, l, nullptr);
+    if (r) return r;
     LAUNCH(K_CHOL, launch_chol_inv((const double*)c.at(c.L.G), l, shift0, c.at(c.L.Rinv), false, c.status(), c.st));
-    LAUNCH(K_SMALL_GEMM, launch_rb_apply((const float*)T, ld, rows, l, (const float*)c.at(c.L.Rinv), l, l, true, Y, ld,
-                                         out16, ld16, kind16, nullptr, c.st));
+    r = apply(c, (const float*)T, ld, rows, l, (const float*)c.at(c.L.Rinv), l, l, true, Y, ld, out16, ld16, kind16,
+              nullptr);
+    if (r) return r;
     *result = Y;
     return SORSVD_OK;
   }
   if (!c.f64) {
-    float* parts = (float*)c.at(c.L.parts);
-    const int nb = (int)rb_gram_blocks(rows, l, l, true);
     int* conv = c.status()->pad;
     int* pol_ok = c.status()->pad + 1;
     float* X = (float*)T;
@@ -365,16 +406,16 @@ int orth(const Ctx& c, void* T, int64_t rows, int64_t ld, int l, int passes, dou
       // it converges, the Cholesky factorisation otherwise (decided on the
       // device); the polar factor is a full matrix
       const bool polar = p == 1 && polar_enabled();
-      LAUNCH(K_SMALL_GEMM, launch_rb_gram(X, ld, X, ld, rows, l, l, true, parts, skip, c.st));
-      LAUNCH(K_REDUCE, launch_reduce_parts(parts, nb, (int64_t)l * l, l, l, l, (double*)c.at(c.L.G), l, c.st));
+      int r = gram_sym(c, X, ld, rows, l, skip);
+      if (r) return r;
       if (polar)
         LAUNCH(K_CHOL, launch_polar_inv((const double*)c.at(c.L.G), l, (float*)c.at(c.L.Rinv),
                                         (float*)c.at(c.L.jwork), pol_ok, conv, kOrthTol, c.st));
       LAUNCH(K_CHOL, launch_chol_inv((const double*)c.at(c.L.G), l, p == 0 ? shift0 : 0.0, c.at(c.L.Rinv), false,
                                      c.status(), c.st, skip, p == 1 ? conv : nullptr, kOrthTol,
                                      polar ? pol_ok : nullptr));
-      LAUNCH(K_SMALL_GEMM, launch_rb_apply(X, ld, rows, l, (const float*)c.at(c.L.Rinv), l, l, !polar, Y, ld,
-                                           nullptr, 0, 0, skip, c.st));
+      r = apply(c, X, ld, rows, l, (const float*)c.at(c.L.Rinv), l, l, !polar, Y, ld, nullptr, 0, 0, skip);
+      if (r) return r;
       std::swap(X, Y);
     }
     if (X != (float*)T || kind16)
@@ -423,9 +464,7 @@ int assemble(const Ctx& c, const void* Q, int64_t ldq, int64_t rows, int l, cons
   if (c.f64 || (reinterpret_cast<uintptr_t>(Q) & 15) || (ldq & 3))
     return gemm(c, K_SMALL_GEMM, false, rows, k, l, Q, ldq, c.f64 ? SORSVD_F64 : SORSVD_F32, B, l,
                 c.f64 ? SORSVD_F64 : SORSVD_F32, C, ldc, c.f64, kCapBig);
-  LAUNCH(K_SMALL_GEMM, launch_rb_apply((const float*)Q, ldq, rows, l, (const float*)B, l, k, false, (float*)C, ldc,
-                                       nullptr, 0, 0, nullptr, c.st));
-  return SORSVD_OK;
+  return apply(c, (const float*)Q, ldq, rows, l, (const float*)B, l, k, false, (float*)C, ldc, nullptr, 0, 0, nullptr);
 }
 
 // T1 = A X (X: the operand buffer of the pass type), then T2 = A^T T1 (the
@@ -773,6 +812,52 @@ int sorsvd_polar_inv(const double* G, int l, float* X, int* ok, void* scratch, s
   ProfScope ps(K_CHOL, st);
   CK(launch_polar_inv(G, l, X, (float*)scratch, ok, nullptr, 0.f, st));
   return SORSVD_OK;
+}
+
+// workspace of sorsvd_gram / sorsvd_apply: the status word, the Gram
+// partials (tensor-core or row-block form, whichever is larger) and the
+// TF32 hi / lo parts of the small factor
+static Layout products_layout(int64_t rows, int l) {
+  Layout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
+  L.status = take(sizeof(DeviceStatus));
+  size_t pb = rb_gram_parts_bytes(rows, l, l, true);
+  if (l <= kTskMaxL) pb = std::max(pb, (size_t)tsk_gram_parts(rows) * l * l * sizeof(float));
+  L.parts = take(pb);
+  L.ldk = (l + 31) / 32 * 32;
+  L.bsplit = take((size_t)2 * L.ldk * L.ldk * sizeof(float));
+  L.total = off;
+  return L;
+}
+
+size_t sorsvd_products_workspace_size(int64_t rows, int l) {
+  if (rows < 1 || l < 1 || l > SORSVD_MAX_L) return 0;
+  return products_layout(rows, l).total;
+}
+
+int sorsvd_gram(const float* X, int64_t rows, int l, int64_t ldx, double* G, int64_t ldg, void* workspace,
+                size_t ws_bytes, void* stream) {
+  if (!X || !G || rows < 1 || l < 1 || ldx < rows || ldg < l || ldg > INT32_MAX) return SORSVD_ERR_ARG;
+  if (l > SORSVD_MAX_L) return SORSVD_ERR_UNSUPPORTED;
+  if ((reinterpret_cast<uintptr_t>(X) & 15) || (ldx & 3)) return SORSVD_ERR_ARG;
+  const Layout L = products_layout(rows, l);
+  if (int r = check_ws(workspace, ws_bytes, L)) return r;
+  Ctx c{(char*)workspace, L, SORSVD_F32, false, (cudaStream_t)stream};
+  CK(cudaMemsetAsync(c.status(), 0, sizeof(DeviceStatus), c.st));
+  return gram_sym(c, X, ldx, rows, l, nullptr, G, ldg);
+}
+
+int sorsvd_apply(const float* X, int64_t rows, int K, int64_t ldx, const float* B, int64_t ldb, int N, int upper_tri,
+                 float* Y, int64_t ldy, void* workspace, size_t ws_bytes, void* stream) {
+  if (!X || !B || !Y || rows < 1 || K < 1 || N < 1 || ldx < rows || ldb < K || ldy < rows) return SORSVD_ERR_ARG;
+  if (K > SORSVD_MAX_L || N > SORSVD_MAX_L) return SORSVD_ERR_UNSUPPORTED;
+  if ((reinterpret_cast<uintptr_t>(X) & 15) || (ldx & 3)) return SORSVD_ERR_ARG;
+  const Layout L = products_layout(rows, std::max(K, N));
+  if (int r = check_ws(workspace, ws_bytes, L)) return r;
+  Ctx c{(char*)workspace, L, SORSVD_F32, false, (cudaStream_t)stream};
+  CK(cudaMemsetAsync(c.status(), 0, sizeof(DeviceStatus), c.st));
+  return apply(c, X, ldx, rows, K, B, ldb, N, upper_tri != 0, Y, ldy, nullptr, 0, 0, nullptr);
 }
 
 int sorsvd_power_pass(const void* A, int64_t m, int64_t n, int64_t lda, int dtype, const void* X, int64_t ldx,

@@ -1,0 +1,626 @@
+// Tall-skinny products of the QR step of Algorithm 3 (CholeskyQR:
+// G = T^T T, Q = T R^{-1}), of the polar pass (Q = T X) and of the output
+// assembly (U = Q1 U~_k, V = Q2 V~_k) on the tensor cores, at fp32 accuracy.
+// T is rows x l, column-major (rows = m or n, up to the matrix size),
+// l <= kTskMaxL.
+//
+// fp32 accuracy from TF32 MMAs (kind::tf32 reads the top 19 bits of an fp32
+// container): every operand x is taken as hi + lo with hi = x truncated to
+// TF32 (what the MMA reads from the container itself) and lo = x - hi
+// (exact in fp32), and each product as hi*hi + hi*lo + lo*hi; the dropped
+// lo*lo term and the TF32 truncation of lo are below 2^-20 relative.
+//
+// tsk_gram_kernel: partial sums of G = T^T T over row ranges.  Both MMA
+// operands are K-major straight from T's column-major storage (a column of
+// T is a run of rows = K), so a staged K atom is 32 rows of every column of
+// T, 128 bytes per column, 128-byte swizzled by TMA.  A CTA keeps the lower
+// triangle of G in TMEM as blocks of 128 MMA rows:
+//   L16 <= 128:         rows 0..127 x columns 0..L16
+//   L16 <= 256:         + rows 128..255 x columns 0..L16
+//   L16 in {272, 288}:  rows 0..127 x 0..127, rows 128..255 x 0..255, and
+//                       columns 256..L16 of every row (three 16- or 32-wide
+//                       blocks; the third takes MMA rows L16-128.. and keeps
+//                       rows >= 256), which fit in 512 TMEM columns where a
+//                       third 128-row block of full width would not.
+// A converter warpgroup writes lo of each staged atom next to it in shared
+// memory; the MMA thread issues the three products per block and K step.
+// Partials are written column-major (l x l, the entries each block owns)
+// and summed in a fixed order by the reduction kernel, which mirrors the
+// lower triangle (deterministic).
+//
+// tsk_apply_kernel: Y = T B with B small (K x N, K = l).  Here T's
+// contiguous dimension (rows) is an M dimension of the product, and a TF32
+// operand must be K-major, so the 128-row tile of T goes to TMEM as the A
+// operand: a converter thread per row (= TMEM lane) reads its row's 32
+// values of a staged K atom (stored column by column, conflict-free) and
+// writes hi and lo to a TMEM slot.  B comes split into hi (rounded to TF32)
+// and lo by the caller, K-major (B is column-major: a column is a run of K),
+// streamed from L2 per K atom.  One accumulator of N <= 320 columns per row
+// tile (two MMA column chunks when N > 256); an epilogue warpgroup drains it
+// while the converter prepares the next tile.  For an upper-triangular B
+// the K atoms below a chunk's last column are skipped.
+//
+// Every mbarrier wait is bounded (the library's tensor-core wait limit); a
+// timeout records SORSVD_ERR_TIMEOUT, stops every role, waits for the
+// copies and MMAs already issued, frees TMEM and returns.
+#include "internal.cuh"
+#include "profile.cuh"
+#include "tc_ptx.cuh"
+
+#include <algorithm>
+#include <cstdlib>
+
+namespace sorsvd {
+namespace {
+
+constexpr int kAtomK = 32;                 // fp32 elements per 128-byte swizzle row
+constexpr int kMaxGramBlocks = 5;
+constexpr int kGramThreads = 192;          // warp 0 TMA, warp 1 MMA, warps 2-5 low parts + epilogue
+constexpr int kApplyThreads = 320;         // warp 0 TMA, warp 1 MMA, warps 2-5 convert, warps 6-9 epilogue
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kApplySlotCol = 320;    // first TMEM column of the apply's A slots (hi 32 + lo 32 each)
+constexpr int kApplySlots = 2;
+constexpr int kApplyStages = 2;
+constexpr uint32_t kSmemBudget = 220u * 1024u;
+
+struct GramBlock {
+  int a0, b0, n, tcol, row_lo;   // MMA rows = T columns a0.., MMA columns = T columns b0..b0+n; kept rows >= row_lo
+};
+
+struct GramParams {
+  int64_t rows, natoms;
+  int l, L16, nbox, boxc, nblk, stages;
+  uint32_t tile_bytes;           // TR x 128 bytes: one K atom of the TR >= L16 columns the MMAs read
+  GramBlock blk[kMaxGramBlocks];
+  float* parts;
+  int64_t pstride;
+  const int* skip;
+  DeviceStatus* status;
+  long long wait_cycles;
+};
+
+struct ApplyParams {
+  int64_t rows, ntiles;
+  int K, N, NP, nch, ch0, katoms, tri;
+  uint32_t x_bytes, b_bytes, stage_bytes;   // b_bytes: one of B_hi / B_lo (2 ch0 rows x 128 bytes)
+  float* Y;
+  int64_t ldy;
+  void* Y16;
+  int64_t ld16;
+  int kind16;
+  const int* skip;
+  DeviceStatus* status;
+  long long wait_cycles;
+};
+
+// x - trunc_tf32(x): the part of x a TF32 MMA ignores (exact in fp32)
+__device__ __forceinline__ float tf32_rest(float x) {
+  return x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
+  return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~(uintptr_t)1023);
+}
+
+// bounded wait for the copies a producer armed and never saw consumed
+__device__ __forceinline__ void drain_armed(uint64_t* full, int stages, uint32_t armed, uint32_t armed_par) {
+  for (int s = 0; s < stages; ++s)
+    if (armed & (1u << s)) {
+      const long long t0 = clock64();
+      while (!tc::mbar_try_wait(&full[s], (armed_par >> s) & 1u) && clock64() - t0 < tc::kWaitCycles) {}
+    }
+}
+
+template <int NBLK>
+__global__ void __launch_bounds__(kGramThreads, 1)
+tsk_gram_kernel(const __grid_constant__ CUtensorMap tmX, const GramParams P) {
+  if (P.skip && *P.skip) return;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = align1024(smem_raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)P.stages * 2 * P.tile_bytes);
+  uint64_t* lofull = full + P.stages;
+  uint64_t* empty = lofull + P.stages;
+  uint64_t* dfull = empty + P.stages;
+  uint64_t* done = dfull + 1;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abortp = reinterpret_cast<volatile int*>(tslot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < P.stages; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&lofull[s], 4);
+      tc::mbar_init(&empty[s], 1);
+    }
+    tc::mbar_init(dfull, 1);
+    tc::mbar_init(done, 1);
+    *abortp = 0;
+    tc::fence_barrier_init();
+  }
+  if (warp == 1) {
+    tc::tmem_alloc(tslot, kTmemCols);
+    tc::tmem_relinquish();
+  }
+  if (warp == 0 && lane == 0) tc::prefetch_tmap(&tmX);
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *tslot;
+  const int64_t a0 = (int64_t)blockIdx.x * P.natoms / gridDim.x;
+  const int64_t a1 = (int64_t)(blockIdx.x + 1) * P.natoms / gridDim.x;
+  const long long wc = P.wait_cycles;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      uint32_t armed = 0, armed_par = 0;
+      int stage = 0;
+      uint32_t phase = 0;
+      for (int64_t a = a0; a < a1; ++a) {
+        if (!tc::mbar_wait(&empty[stage], phase ^ 1u, abortp, wc)) break;
+        tc::mbar_arrive_expect_tx(&full[stage], P.tile_bytes);
+        armed |= 1u << stage;
+        armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
+        uint8_t* dst = smem + (size_t)stage * 2 * P.tile_bytes;
+        for (int b = 0; b < P.nbox; ++b)
+          tc::tma_load_2d(dst + (size_t)b * P.boxc * 128, &tmX, &full[stage], (int)(a * kAtomK), b * P.boxc);
+        if (++stage == P.stages) { stage = 0; phase ^= 1u; }
+      }
+      if (*abortp) drain_armed(full, P.stages, armed, armed_par);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      uint32_t idesc[NBLK];
+#pragma unroll
+      for (int b = 0; b < NBLK; ++b) idesc[b] = tc::idesc_make(2u, false, false, 128, P.blk[b].n);
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int64_t a = a0; a < a1 && ok; ++a) {
+        if (!tc::mbar_wait(&lofull[stage], phase, abortp, wc) || !tc::mbar_wait(&full[stage], phase, abortp, wc)) {
+          ok = false;
+          break;
+        }
+        tc::fence_after_sync();
+        const uint32_t sraw = tc::smem_u32(smem + (size_t)stage * 2 * P.tile_bytes);
+        const uint32_t slo = sraw + P.tile_bytes;
+#pragma unroll
+        for (int ks = 0; ks < kAtomK / 8; ++ks) {
+          const uint32_t acc0 = (a > a0 || ks > 0) ? 1u : 0u;
+#pragma unroll
+          for (int b = 0; b < NBLK; ++b) {
+            const GramBlock& g = P.blk[b];
+            const uint32_t d = tbase + (uint32_t)g.tcol;
+            const uint64_t ahi = tc::desc_sw128(sraw + (uint32_t)g.a0 * 128u + ks * 32, 16, 1024);
+            const uint64_t bhi = tc::desc_sw128(sraw + (uint32_t)g.b0 * 128u + ks * 32, 16, 1024);
+            const uint64_t alo = tc::desc_sw128(slo + (uint32_t)g.a0 * 128u + ks * 32, 16, 1024);
+            const uint64_t blo = tc::desc_sw128(slo + (uint32_t)g.b0 * 128u + ks * 32, 16, 1024);
+            tc::mma_tf32(d, ahi, bhi, idesc[b], acc0);
+            tc::mma_tf32(d, ahi, blo, idesc[b], 1u);
+            tc::mma_tf32(d, alo, bhi, idesc[b], 1u);
+          }
+        }
+        tc::mma_commit(&empty[stage]);
+        if (++stage == P.stages) { stage = 0; phase ^= 1u; }
+      }
+      if (ok) tc::mma_commit(dfull);
+      // every MMA issued by this thread has completed once `done` flips
+      tc::mma_commit(done);
+      const long long t0 = clock64();
+      while (!tc::mbar_try_wait(done, 0) && clock64() - t0 < tc::kWaitCycles) {}
+    }
+  } else {
+    // ------------------------------------------------------------ low parts, then the epilogue
+    const int ct = threadIdx.x - 64;            // 0..127
+    int stage = 0;
+    uint32_t phase = 0;
+    bool ok = true;
+    const int n4 = (int)(P.tile_bytes / 16);
+    for (int64_t a = a0; a < a1; ++a) {
+      if (!__all_sync(0xffffffffu, tc::mbar_wait(&full[stage], phase, abortp, wc))) { ok = false; break; }
+      const float4* src = reinterpret_cast<const float4*>(smem + (size_t)stage * 2 * P.tile_bytes);
+      float4* dst = reinterpret_cast<float4*>(smem + (size_t)stage * 2 * P.tile_bytes + P.tile_bytes);
+      for (int e = ct; e < n4; e += 128) {
+        const float4 x = src[e];
+        dst[e] = make_float4(tf32_rest(x.x), tf32_rest(x.y), tf32_rest(x.z), tf32_rest(x.w));
+      }
+      fence_proxy_async();                      // the MMAs read the low parts through the async proxy
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&lofull[stage]);
+      if (++stage == P.stages) { stage = 0; phase ^= 1u; }
+    }
+    // drain: thread = TMEM lane q*32 + lane = MMA row of each block
+    if (ok && __all_sync(0xffffffffu, tc::mbar_wait(dfull, 0, abortp, wc))) {
+      tc::fence_after_sync();
+      const int q = warp & 3;
+      const int r = q * 32 + lane;
+      float* out = P.parts + (size_t)blockIdx.x * P.pstride;
+#pragma unroll
+      for (int b = 0; b < NBLK; ++b) {
+        const GramBlock& g = P.blk[b];
+        const int i = g.a0 + r;
+        const bool keep = i >= g.row_lo && i < P.l;
+        for (int c = 0; c < g.n; c += 16) {
+          float v[16];
+          tc::tmem_ld16(tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(g.tcol + c), v);
+          tc::tmem_ld_wait();
+          if (keep) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+              const int j = g.b0 + c + u;
+              if (j < P.l) out[i + (size_t)j * P.l] = v[u];
+            }
+          }
+        }
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (threadIdx.x == 0 && *abortp) raise_status(P.status, SORSVD_ERR_TIMEOUT);
+  if (warp == 1) tc::tmem_dealloc(tbase, kTmemCols);
+}
+
+template <int NCH>
+__global__ void __launch_bounds__(kApplyThreads, 1)
+tsk_apply_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmBhi,
+                 const __grid_constant__ CUtensorMap tmBlo, const ApplyParams P) {
+  if (P.skip && *P.skip) return;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = align1024(smem_raw);
+  // stage s: B_hi (2 ch0 rows x 128 B), B_lo (same), then the K atom of T (32 columns x 128 rows)
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)kApplyStages * P.stage_bytes);
+  uint64_t* empty = full + kApplyStages;
+  uint64_t* afull = empty + kApplyStages;      // a TMEM slot written (4 converter warps)
+  uint64_t* aempty = afull + kApplySlots;      // a slot read by its MMAs
+  uint64_t* dfull = aempty + kApplySlots;      // the tile's accumulator complete
+  uint64_t* dempty = dfull + 1;                // the accumulator drained (4 epilogue warps)
+  uint64_t* done = dempty + 1;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abortp = reinterpret_cast<volatile int*>(tslot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kApplyStages; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
+    for (int s = 0; s < kApplySlots; ++s) { tc::mbar_init(&afull[s], 4); tc::mbar_init(&aempty[s], 1); }
+    tc::mbar_init(dfull, 1);
+    tc::mbar_init(dempty, 4);
+    tc::mbar_init(done, 1);
+    *abortp = 0;
+    tc::fence_barrier_init();
+  }
+  if (warp == 1) {
+    tc::tmem_alloc(tslot, kTmemCols);
+    tc::tmem_relinquish();
+  }
+  if (warp == 0 && lane == 0) {
+    tc::prefetch_tmap(&tmX);
+    tc::prefetch_tmap(&tmBhi);
+    tc::prefetch_tmap(&tmBlo);
+  }
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *tslot;
+  const long long wc = P.wait_cycles;
+  const int ch1 = P.NP - P.ch0;
+  // K atoms a chunk needs: all, or (upper-triangular B) those starting at or
+  // before the chunk's last column
+  auto atoms_of = [&](int ch) {
+    if (!P.tri) return P.katoms;
+    const int c1 = ch == 0 ? min(P.ch0, P.N) : P.N;
+    return min(P.katoms, (c1 + kAtomK - 1) / kAtomK);
+  };
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      uint32_t armed = 0, armed_par = 0;
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
+        for (int a = 0; a < P.katoms; ++a) {
+          if (!tc::mbar_wait(&empty[stage], phase ^ 1u, abortp, wc)) { ok = false; break; }
+          tc::mbar_arrive_expect_tx(&full[stage], P.stage_bytes);
+          armed |= 1u << stage;
+          armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
+          uint8_t* sb = smem + (size_t)stage * P.stage_bytes;
+#pragma unroll
+          for (int ch = 0; ch < NCH; ++ch) {
+            tc::tma_load_2d(sb + (size_t)ch * P.ch0 * 128, &tmBhi, &full[stage], a * kAtomK, ch * P.ch0);
+            tc::tma_load_2d(sb + P.b_bytes + (size_t)ch * P.ch0 * 128, &tmBlo, &full[stage], a * kAtomK,
+                            ch * P.ch0);
+          }
+          tc::tma_load_2d(sb + 2 * P.b_bytes, &tmX, &full[stage], (int)(t * 128), a * kAtomK);
+          if (++stage == kApplyStages) { stage = 0; phase ^= 1u; }
+        }
+      }
+      if (*abortp) drain_armed(full, kApplyStages, armed, armed_par);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t id0 = tc::idesc_make(2u, false, false, 128, P.ch0);
+      const uint32_t id1 = tc::idesc_make(2u, false, false, 128, NCH > 1 ? ch1 : 16);
+      int na[NCH];
+#pragma unroll
+      for (int ch = 0; ch < NCH; ++ch) na[ch] = atoms_of(ch);
+      int stage = 0, slot = 0;
+      uint32_t phase = 0, sphase = 0;
+      bool ok = true;
+      int tcount = 0;
+      for (int64_t t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x, ++tcount) {
+        // the previous tile's accumulator has been drained
+        if (tcount > 0 && !tc::mbar_wait(dempty, (uint32_t)(tcount - 1) & 1u, abortp, wc)) { ok = false; break; }
+        tc::fence_after_sync();
+        for (int a = 0; a < P.katoms; ++a) {
+          if (!tc::mbar_wait(&afull[slot], sphase, abortp, wc) || !tc::mbar_wait(&full[stage], phase, abortp, wc)) {
+            ok = false;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t sb = tc::smem_u32(smem + (size_t)stage * P.stage_bytes);
+          const uint32_t ahi = tbase + kApplySlotCol + (uint32_t)slot * 64u;
+          const uint32_t alo = ahi + 32u;
+#pragma unroll
+          for (int ks = 0; ks < kAtomK / 8; ++ks) {
+            const uint32_t acc0 = (a > 0 || ks > 0) ? 1u : 0u;
+#pragma unroll
+            for (int ch = 0; ch < NCH; ++ch) {
+              if (a >= na[ch]) continue;
+              const uint32_t d = tbase + (uint32_t)(ch * P.ch0);
+              const uint32_t id = ch ? id1 : id0;
+              const uint32_t boff = (uint32_t)(ch * P.ch0 * 128 + ks * 32);
+              const uint64_t bhi = tc::desc_sw128(sb + boff, 16, 1024);
+              const uint64_t blo = tc::desc_sw128(sb + P.b_bytes + boff, 16, 1024);
+              tc::mma_tf32_ts(d, ahi + (uint32_t)(ks * 8), bhi, id, acc0);
+              tc::mma_tf32_ts(d, ahi + (uint32_t)(ks * 8), blo, id, 1u);
+              tc::mma_tf32_ts(d, alo + (uint32_t)(ks * 8), bhi, id, 1u);
+            }
+          }
+          tc::mma_commit(&empty[stage]);
+          tc::mma_commit(&aempty[slot]);
+          if (++stage == kApplyStages) { stage = 0; phase ^= 1u; }
+          if (++slot == kApplySlots) { slot = 0; sphase ^= 1u; }
+        }
+        if (!ok) break;
+        tc::mma_commit(dfull);
+      }
+      tc::mma_commit(done);
+      const long long t0 = clock64();
+      while (!tc::mbar_try_wait(done, 0) && clock64() - t0 < tc::kWaitCycles) {}
+    }
+  } else if (warp < 6) {
+    // ------------------------------------------------------------ converter
+    // thread = row r of the tile = TMEM lane r: the row's 32 values of the
+    // staged atom (column c at c * 128 + r: a warp reads 32 consecutive
+    // floats per column) go to the slot as hi (the container) and lo
+    const int q = warp & 3;
+    const int r = q * 32 + lane;
+    const uint32_t tl = tbase + ((uint32_t)(q * 32) << 16) + kApplySlotCol;
+    int stage = 0, slot = 0;
+    uint32_t phase = 0, sphase = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
+      for (int a = 0; a < P.katoms; ++a) {
+        if (!__all_sync(0xffffffffu, tc::mbar_wait(&aempty[slot], sphase ^ 1u, abortp, wc) &&
+                                         tc::mbar_wait(&full[stage], phase, abortp, wc))) {
+          ok = false;
+          break;
+        }
+        const float* xs = reinterpret_cast<const float*>(smem + (size_t)stage * P.stage_bytes + 2 * P.b_bytes);
+        float hi[2][16], lo[2][16];
+#pragma unroll
+        for (int c = 0; c < kAtomK; ++c) {
+          const float x = xs[c * 128 + r];
+          hi[c >> 4][c & 15] = x;
+          lo[c >> 4][c & 15] = tf32_rest(x);
+        }
+        tc::fence_after_sync();
+        const uint32_t ts = tl + (uint32_t)slot * 64u;
+        tc::tmem_st16(ts, hi[0]);
+        tc::tmem_st16(ts + 16u, hi[1]);
+        tc::tmem_st16(ts + 32u, lo[0]);
+        tc::tmem_st16(ts + 48u, lo[1]);
+        tc::tmem_st_wait();
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&afull[slot]);
+        if (++stage == kApplyStages) { stage = 0; phase ^= 1u; }
+        if (++slot == kApplySlots) { slot = 0; sphase ^= 1u; }
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3;
+    const int r = q * 32 + lane;
+    const uint32_t tl = tbase + ((uint32_t)(q * 32) << 16);
+    int tcount = 0;
+    for (int64_t t = blockIdx.x; t < P.ntiles; t += gridDim.x, ++tcount) {
+      if (!__all_sync(0xffffffffu, tc::mbar_wait(dfull, (uint32_t)tcount & 1u, abortp, wc))) break;
+      tc::fence_after_sync();
+      const int64_t grow = t * 128 + r;
+      const bool rok = grow < P.rows;
+      for (int c = 0; c < P.NP; c += 16) {
+        float v[16];
+        tc::tmem_ld16(tl + (uint32_t)c, v);
+        tc::tmem_ld_wait();
+        if (rok) {
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            const int j = c + u;
+            if (j < P.N) {
+              P.Y[grow + (int64_t)j * P.ldy] = v[u];
+              if (P.kind16 == 1)
+                reinterpret_cast<bf16*>(P.Y16)[grow + (int64_t)j * P.ld16] = __float2bfloat16_rn(v[u]);
+              else if (P.kind16 == 2)
+                reinterpret_cast<f16*>(P.Y16)[grow + (int64_t)j * P.ld16] = __float2half_rn(v[u]);
+            }
+          }
+        }
+      }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(dempty);
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (threadIdx.x == 0 && *abortp) raise_status(P.status, SORSVD_ERR_TIMEOUT);
+  if (warp == 1) tc::tmem_dealloc(tbase, kTmemCols);
+}
+
+int env_tsk() {
+  static const int v = [] {
+    const char* s = std::getenv("SORSVD_TSK");
+    return s ? std::atoi(s) : 1;
+  }();
+  return v;
+}
+
+int round16(int x) { return (x + 15) / 16 * 16; }
+
+// the TMEM blocks of the lower triangle of an l x l Gram (see the header)
+int gram_blocks(int l, GramBlock* blk, int* sym_split) {
+  const int L16 = round16(l);
+  int n = 0;
+  if (L16 <= 128) {
+    blk[n++] = {0, 0, L16, 0, 0};
+    *sym_split = L16;
+  } else if (L16 <= 256) {
+    blk[n++] = {0, 0, 128, 0, 0};
+    blk[n++] = {128, 0, L16, 128, 0};
+    *sym_split = L16;
+  } else {
+    const int w = L16 - 256;
+    blk[n++] = {0, 0, 128, 0, 0};
+    blk[n++] = {128, 0, 256, 128, 0};
+    blk[n++] = {0, 256, w, 384, 0};
+    blk[n++] = {128, 256, w, 384 + w, 0};
+    blk[n++] = {L16 - 128, 256, w, 384 + 2 * w, 256};
+    *sym_split = 256;
+  }
+  return n;
+}
+
+}  // namespace
+
+bool tsk_enabled() { return env_tsk() != 0; }
+
+bool tsk_gram_supported(const float* X, int64_t ldx, int l) {
+  if (!tsk_enabled() || l < 1 || l > kTskMaxL) return false;
+  if ((reinterpret_cast<uintptr_t>(X) & 15) || (ldx & 3)) return false;
+  return true;
+}
+
+int tsk_gram_parts(int64_t rows) {
+  const int64_t natoms = (rows + kAtomK - 1) / kAtomK;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(natoms, num_sms()));
+}
+
+cudaError_t launch_tsk_gram(const float* X, int64_t ldx, int64_t rows, int l, float* parts, int* nparts,
+                            int* sym_split, const int* skip, DeviceStatus* status, cudaStream_t st) {
+  if (rows < 1 || !tsk_gram_supported(X, ldx, l)) return cudaErrorInvalidValue;
+  GramParams P{};
+  P.rows = rows;
+  P.natoms = (rows + kAtomK - 1) / kAtomK;
+  P.l = l;
+  P.L16 = round16(l);
+  P.nblk = gram_blocks(l, P.blk, sym_split);
+  // staged columns: every MMA row block reads 128 columns of the tile
+  int TR = P.L16;
+  for (int b = 0; b < P.nblk; ++b) TR = std::max(TR, P.blk[b].a0 + 128);
+  P.nbox = TR > 256 ? 2 : 1;
+  P.boxc = TR / P.nbox;                            // a multiple of 8: boxes start on 1024-byte boundaries
+  P.tile_bytes = (uint32_t)TR * 128u;
+  const uint32_t bar_bytes = 256;
+  P.stages = (int)std::min<uint32_t>(4u, (kSmemBudget - bar_bytes) / (2u * P.tile_bytes));
+  if (P.stages < 2) return cudaErrorInvalidValue;
+  P.parts = parts;
+  P.pstride = (int64_t)l * l;
+  P.skip = skip;
+  P.status = status;
+  P.wait_cycles = tc_wait_cycles();
+  CUtensorMap m;
+  if (!tc_map_2d(&m, X, 2, rows, l, ldx, (uint32_t)kAtomK, (uint32_t)P.boxc, true)) return cudaErrorInvalidValue;
+  const int G = tsk_gram_parts(rows);
+  *nparts = G;
+  const size_t smem = (size_t)P.stages * 2 * P.tile_bytes + bar_bytes + 1024;
+  auto go = [&](auto kern) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<G, kGramThreads, smem, st>>>(m, P);
+    return cudaGetLastError();
+  };
+  switch (P.nblk) {
+    case 1: return go(tsk_gram_kernel<1>);
+    case 2: return go(tsk_gram_kernel<2>);
+    case 5: return go(tsk_gram_kernel<5>);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+bool tsk_apply_supported(const float* X, int64_t ldx, int K, int N) {
+  if (!tsk_enabled() || K < 1 || N < 1 || K > kTskMaxL || N > kTskMaxN) return false;
+  if ((reinterpret_cast<uintptr_t>(X) & 15) || (ldx & 3)) return false;
+  return true;
+}
+
+cudaError_t launch_tsk_apply(const float* X, int64_t ldx, int64_t rows, int K, const float* Bhi, const float* Blo,
+                             int64_t ldb, int N, bool tri, float* Y, int64_t ldy, void* Y16, int64_t ld16,
+                             int kind16, const int* skip, DeviceStatus* status, cudaStream_t st) {
+  if (rows < 1) return cudaSuccess;
+  if (!tsk_apply_supported(X, ldx, K, N)) return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(Bhi) & 15) || (reinterpret_cast<uintptr_t>(Blo) & 15) || (ldb & 3))
+    return cudaErrorInvalidValue;
+  ApplyParams P{};
+  P.rows = rows;
+  P.ntiles = (rows + 127) / 128;
+  P.K = K;
+  P.N = N;
+  P.NP = round16(N);
+  P.nch = P.NP > 256 ? 2 : 1;
+  P.ch0 = P.nch == 2 ? round16((P.NP + 1) / 2) : P.NP;
+  P.katoms = (K + kAtomK - 1) / kAtomK;
+  P.tri = tri ? 1 : 0;
+  P.b_bytes = (uint32_t)(P.nch * P.ch0) * 128u;
+  P.x_bytes = 128u * 128u;
+  P.stage_bytes = 2 * P.b_bytes + P.x_bytes;
+  P.Y = Y;
+  P.ldy = ldy;
+  P.Y16 = Y16;
+  P.ld16 = ld16;
+  P.kind16 = Y16 ? kind16 : 0;
+  P.skip = skip;
+  P.status = status;
+  P.wait_cycles = tc_wait_cycles();
+  const size_t bar_bytes = 256;
+  const size_t smem = (size_t)kApplyStages * P.stage_bytes + bar_bytes + 1024;
+  if (smem > 227u * 1024u) return cudaErrorInvalidValue;
+  CUtensorMap mx, mh, ml;
+  // T: 128 rows x 32 columns per box, unswizzled (column c of the box at c x 512 bytes)
+  if (!tc_map_2d(&mx, X, 2, rows, K, ldx, 128u, (uint32_t)kAtomK, false)) return cudaErrorInvalidValue;
+  // B: K-major, 32 K x ch0 columns per box, 128-byte swizzle
+  if (!tc_map_2d(&mh, Bhi, 2, K, N, ldb, (uint32_t)kAtomK, (uint32_t)P.ch0, true)) return cudaErrorInvalidValue;
+  if (!tc_map_2d(&ml, Blo, 2, K, N, ldb, (uint32_t)kAtomK, (uint32_t)P.ch0, true)) return cudaErrorInvalidValue;
+  const int G = (int)std::max<int64_t>(1, std::min<int64_t>(P.ntiles, num_sms()));
+  cudaError_t e;
+  if (P.nch == 2) {
+    e = cudaFuncSetAttribute(tsk_apply_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    tsk_apply_kernel<2><<<G, kApplyThreads, smem, st>>>(mx, mh, ml, P);
+  } else {
+    e = cudaFuncSetAttribute(tsk_apply_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    tsk_apply_kernel<1><<<G, kApplyThreads, smem, st>>>(mx, mh, ml, P);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace sorsvd

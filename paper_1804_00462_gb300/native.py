@@ -64,6 +64,12 @@ _lib.sorsvd_chol_inv.argtypes = [_vp, _int, C.c_double, _int, _vp, _vp, _vp]
 _lib.sorsvd_chol_inv.restype = _int
 _lib.sorsvd_polar_inv.argtypes = [_vp, _int, _vp, _vp, _vp, _sz, _vp]
 _lib.sorsvd_polar_inv.restype = _int
+_lib.sorsvd_products_workspace_size.argtypes = [_i64, _int]
+_lib.sorsvd_products_workspace_size.restype = _sz
+_lib.sorsvd_gram.argtypes = [_vp, _i64, _int, _i64, _vp, _i64, _vp, _sz, _vp]
+_lib.sorsvd_gram.restype = _int
+_lib.sorsvd_apply.argtypes = [_vp, _i64, _int, _i64, _vp, _i64, _int, _int, _vp, _i64, _vp, _sz, _vp]
+_lib.sorsvd_apply.restype = _int
 
 lib = _lib
 
@@ -302,6 +308,55 @@ def polar_inv(G: torch.Tensor, stream=None):
     _check(_lib.sorsvd_polar_inv(Gc.data_ptr(), l, X.data_ptr(), ok.data_ptr(), scratch.data_ptr(), nb,
                                  _stream(stream)), "sorsvd_polar_inv")
     return X, int(ok.item())
+
+
+def colmajor_f32(X: torch.Tensor, ld: int = 0) -> torch.Tensor:
+    """fp32 column-major copy of a 2-D CUDA tensor whose leading dimension is
+    a multiple of 4 (ld, when given, at least the rows), as the tall-skinny
+    products require."""
+    rows, cols = X.shape
+    ld = max(ld, (rows + 3) // 4 * 4)
+    buf = torch.zeros(cols, ld, dtype=torch.float32, device=X.device)
+    buf[:, :rows] = X.T.to(torch.float32)
+    return buf.T[:rows]
+
+
+def _products_ws(rows: int, l: int, device):
+    nb = int(_lib.sorsvd_products_workspace_size(rows, l))
+    if nb == 0:
+        raise SorsvdError(1, "sorsvd_products_workspace_size")
+    return torch.empty(nb, dtype=torch.uint8, device=device), nb
+
+
+def gram(X: torch.Tensor, stream=None):
+    """G = X^T X (l x l binary64) of a column-major fp32 CUDA tensor with
+    ld % 4 == 0 (colmajor_f32), through sorsvd_gram.  Returns (G, status)."""
+    ptr, rows, l, ld, tr = _colmajor(X)
+    if tr or X.dtype != torch.float32:
+        raise ValueError("X must be a column-major fp32 tensor")
+    ws, nb = _products_ws(rows, l, X.device)
+    G = colmajor_empty(l, l, torch.float64, X.device)
+    _check(_lib.sorsvd_gram(ptr, rows, l, ld, G.data_ptr(), l, ws.data_ptr(), nb, _stream(stream)), "sorsvd_gram")
+    s, _ = get_status(ws, stream)
+    return G, s
+
+
+def apply(X: torch.Tensor, B: torch.Tensor, upper_tri: bool = False, stream=None):
+    """Y = X B (fp32) for a column-major fp32 X (ld % 4 == 0, colmajor_f32)
+    and a small fp32 B, through sorsvd_apply.  Returns (Y, status)."""
+    ptr, rows, K, ld, tr = _colmajor(X)
+    if tr or X.dtype != torch.float32:
+        raise ValueError("X must be a column-major fp32 tensor")
+    if B.dim() != 2 or B.shape[0] != K:
+        raise ValueError("B must be K x N")
+    N = B.shape[1]
+    Bc = B.to(torch.float32).T.contiguous().T
+    ws, nb = _products_ws(rows, max(K, N), X.device)
+    Y = colmajor_empty(rows, N, torch.float32, X.device)
+    _check(_lib.sorsvd_apply(ptr, rows, K, ld, Bc.data_ptr(), K, N, 1 if upper_tri else 0, Y.data_ptr(), rows,
+                             ws.data_ptr(), nb, _stream(stream)), "sorsvd_apply")
+    s, _ = get_status(ws, stream)
+    return Y, s
 
 
 # ---- batched SOR-SVD ----------------------------------------------------------
