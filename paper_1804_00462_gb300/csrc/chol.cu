@@ -163,69 +163,71 @@ __device__ __forceinline__ void tri_index(int q, int* i, int* j) {
 
 constexpr int BT = 512;           // threads of the blocked kernel
 
-constexpr int SB = 8;             // sub-panel width inside a tile column
-
 // correctly rounded 1/sqrt (fp32 intrinsic; binary64 through sqrt and a
 // division, only used by the binary64 factor)
 __device__ __forceinline__ float rsqrt_rn(float x) { return __frsqrt_rn(x); }
 __device__ __forceinline__ double rsqrt_rn(double x) { return 1.0 / sqrt(x); }
 
-// L = chol of the SB x SB diagonal sub-block at (c0, c0) of tile D, lanes
-// 0..SB-1 own its rows; 1 / L_jj goes to rdiag[c0 + j].  Returns false when
-// a pivot is not safely positive (same answer in every lane).
+// Cholesky factor of the 32 x 32 diagonal tile DK in one warp's registers
+// (lane = row): right-looking, the pivot and the column entries broadcast by
+// shuffle.  Writes L_KK densely to Ld (row-major, stride 32, zeros above the
+// diagonal) and 1 / L_jj to rd.  Returns false (in every lane) when a pivot
+// is not safely positive.
 template <typename F>
-__device__ __forceinline__ bool chol_sub_warp(F* D, int c0, F thr, int lane, F* rdiag) {
-  F* row = D + (c0 + (lane & (SB - 1))) * TLD + c0;
-  for (int j = 0; j < SB; ++j) {
-    const F d = D[(c0 + j) * TLD + c0 + j];
-    if (!(d > thr)) return false;
-    const F rs = rsqrt_rn(d);
-    F lcol = 0;
-    if (lane < SB && lane > j) { lcol = row[j] * rs; row[j] = lcol; }
-    __syncwarp();
-    if (lane == j) { row[j] = d * rs; rdiag[c0 + j] = rs; }
+__device__ __noinline__ bool chol_tile_warp(const F* DK, F* Ld, F* rd, F thr, int lane) {
+  F a[TB];
 #pragma unroll
-    for (int c = j + 1; c < SB; ++c) {
-      const F lcj = __shfl_sync(0xffffffffu, lcol, c);
-      if (lane < SB && lane >= c) row[c] -= lcol * lcj;
+  for (int c = 0; c < TB; ++c) a[c] = DK[lane * TLD + c];
+  bool ok = true;
+  // straight-line code (no early exit, so a[] stays in registers); after a
+  // bad pivot the values are not used
+#pragma unroll
+  for (int j = 0; j < TB; ++j) {
+    const F d = __shfl_sync(0xffffffffu, a[j], j);
+    ok = ok && (d > thr);
+    const F rs = rsqrt_rn(d);
+    if (lane == j) a[j] = d * rs;
+    else if (lane > j) a[j] *= rs;
+    if (lane == 0) rd[j] = rs;
+#pragma unroll
+    for (int c = j + 1; c < TB; ++c) {
+      const F lcj = __shfl_sync(0xffffffffu, a[j], c);
+      if (lane >= c) a[c] -= a[j] * lcj;
     }
-    __syncwarp();
   }
-  return true;
+#pragma unroll
+  for (int c = 0; c < TB; ++c) Ld[lane * TB + c] = c <= lane ? a[c] : (F)0;
+  return ok;
 }
 
-// x <- x L^{-T} for the SB entries of one row at x (L the SB x SB lower
-// block at Lb, row stride TLD, reciprocal diagonal rd): forward substitution
-// in registers
+// v <- v L^{-T} for one row v of 32 values (forward substitution with the
+// dense L of stride 32 and its reciprocal diagonal rd; L read as broadcast
+// vectors)
 template <typename F>
-__device__ __forceinline__ void trsm_sub(F* x, const F* Lb, const F* rd) {
-  F v[SB];
+__device__ __forceinline__ void trsm_row(F (&v)[TB], const F* Ld, const F* rd) {
 #pragma unroll
-  for (int j = 0; j < SB; ++j) v[j] = x[j];
-#pragma unroll
-  for (int j = 0; j < SB; ++j) {
+  for (int j = 0; j < TB; ++j) {
     F s = v[j];
 #pragma unroll
-    for (int k = 0; k < j; ++k) s -= v[k] * Lb[j * TLD + k];
+    for (int k = 0; k < j; ++k) s -= v[k] * Ld[j * TB + k];
     v[j] = s * rd[j];
   }
-#pragma unroll
-  for (int j = 0; j < SB; ++j) x[j] = v[j];
 }
 
-// column c of X = L^{-1} for a lower-triangular tile, one warp, lane = row:
-// forward substitution with the solved entry broadcast by shuffle; the
-// column is written back after the whole warp has read the tile's column
-// entries it needed (the column below the diagonal is L's until then)
+// 4 x 4 block (rows r0.., columns c0..) of A B for 32 x 32 tiles, A read by
+// rows (A[r * TLD + k]) and B by rows (B[k * TLD + c])
 template <typename F>
-__device__ __forceinline__ F inv_col_warp(const F* D, int c, int lane, const F* rdiag) {
-  F b = (lane == c) ? (F)1 : (F)0;
-  for (int i = c; i < TB; ++i) {
-    const F xi = __shfl_sync(0xffffffffu, b, i) * rdiag[i];
-    if (lane == i) b = xi;
-    else if (lane > i) b -= D[lane * TLD + i] * xi;
+__device__ __forceinline__ void tile_mm44(const F* A, const F* B, int r0, int c0, F (&acc)[4][4]) {
+#pragma unroll 4
+  for (int k = 0; k < TB; ++k) {
+    F av[4], bv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) { av[u] = A[(r0 + u) * TLD + k]; bv[u] = B[k * TLD + c0 + u]; }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] += av[u] * bv[v];
   }
-  return lane >= c ? b : (F)0;
 }
 
 template <typename F>
@@ -239,8 +241,9 @@ __device__ __forceinline__ void chol_inv_blocked_body(const double* __restrict__
   const int nb = (l + TB - 1) / TB;
   const int ntile = nb * (nb + 1) / 2;
   F* T = reinterpret_cast<F*>(smem_raw);
-  const size_t dofs = (sizeof(F) * (size_t)ntile * TS + 7) & ~(size_t)7;
-  double* dscale = reinterpret_cast<double*>(smem_raw + dofs);     // D^{-1/2}, nb * 32
+  const size_t dofs = (sizeof(F) * (size_t)ntile * TS + 15) & ~(size_t)15;
+  F* Ld = reinterpret_cast<F*>(smem_raw + dofs);                     // dense L_KK, 32 x 32
+  double* dscale = reinterpret_cast<double*>(Ld + TB * TB);          // D^{-1/2}, nb * 32
   F* dsf = reinterpret_cast<F*>(dscale + nb * TB);                   // the same in F
   F* rdiag = dsf + nb * TB;                                          // 1 / L_jj
   __shared__ int s_fail, s_retry;
@@ -267,83 +270,95 @@ __device__ __forceinline__ void chol_inv_blocked_body(const double* __restrict__
   double shift = shift_rel;
   const int max_try = 12;
   int attempt = 0;
+  // 64 threads per 32 x 32 output tile, a 4 x 4 block each
+  const int sub = t & 63, r0 = 4 * (sub >> 3), c0 = 4 * (sub & 7), slot = t >> 6;
+  constexpr int NSLOT = BT / 64;
   for (; attempt < max_try; ++attempt) {
     // equilibrated, shifted Gram in the lower tiles (factor precision);
     // padding and zero columns of T become identity rows / columns; the
-    // largest off-diagonal entry (a column cosine) is recorded for conv_out
+    // largest off-diagonal entry (a column cosine) is recorded for conv_out.
+    // Eight independent loads in flight per thread.
     const F fshift = (F)shift;
     float offmax = 0.f;
-    for (int I = 0; I < nb; ++I)
-      for (int J = 0; J <= I; ++J) {
-        F* D = tile(I, J);
-        for (int e = t; e < TB * TB; e += BT) {
-          const int r = e >> 5, c = e & 31;
-          const int gi = I * TB + r, gc = J * TB + c;
-          const F si = dsf[gi], sc = dsf[gc];
-          F v;
-          if (si == (F)0 || sc == (F)0) v = (gi == gc) ? (F)1 : (F)0;
-          else {
-            v = (F)G[gc + (int64_t)gi * l] * si * sc;   // G symmetric: coalesced
-            if (gi > gc) offmax = fmaxf(offmax, fabsf((float)v));
-            if (gi == gc) v += fshift;
-          }
-          D[r * TLD + c] = v;
+    const int total = ntile * TB * TB;
+    for (int e0 = t; e0 < total; e0 += 8 * BT) {
+      double gv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * BT;
+        gv[u] = 0.0;
+        if (e < total) {
+          const int q = e >> 10, w = e & 1023;
+          int I, J;
+          tri_index(q, &I, &J);
+          const int gi = I * TB + (w >> 5), gc = J * TB + (w & 31);
+          if (gi < l && gc < l) gv[u] = G[gc + (int64_t)gi * l];     // G symmetric: coalesced
         }
       }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * BT;
+        if (e >= total) continue;
+        const int q = e >> 10, w = e & 1023;
+        int I, J;
+        tri_index(q, &I, &J);
+        const int r = w >> 5, c = w & 31;
+        const int gi = I * TB + r, gc = J * TB + c;
+        const F si = dsf[gi], sc = dsf[gc];
+        F v;
+        if (si == (F)0 || sc == (F)0) v = (gi == gc) ? (F)1 : (F)0;
+        else {
+          v = (F)gv[u] * si * sc;
+          if (gi > gc) offmax = fmaxf(offmax, fabsf((float)v));
+          if (gi == gc) v += fshift;
+        }
+        T[(size_t)q * TS + r * TLD + c] = v;
+      }
+    }
     if (conv_out && attempt == 0) atomicMax(&s_offmax, __float_as_uint(offmax));
     if (t == 0) s_fail = 0;
     __syncthreads();
-    for (int K = 0; K < nb && !s_fail; ++K) {
+    for (int K = 0; K < nb; ++K) {
       F* DK = tile(K, K);
-      // tile column K in SB-wide sub-panels: factor the SB x SB diagonal
-      // block, solve the rows below it (rest of tile K and tiles I > K),
-      // rank-SB update of the sub-panel's remaining columns
-      for (int c0 = 0; c0 < TB; c0 += SB) {
-        if (warp == 0) {
-          const bool ok = chol_sub_warp(DK, c0, thr, lane, rdiag + K * TB);
-          if (!ok && lane == 0) s_fail = 1;
-        }
-        __syncthreads();
-        if (s_fail) break;
-        const int below = TB - c0 - SB;                 // rows of tile K under the block
-        const int rows = below + TB * (nb - K - 1);
-        for (int rr = t; rr < rows; rr += BT) {
-          F* x = rr < below ? DK + (c0 + SB + rr) * TLD + c0
-                            : tile(K + 1 + (rr - below) / TB, K) + ((rr - below) % TB) * TLD + c0;
-          trsm_sub(x, DK + c0 * TLD + c0, rdiag + K * TB + c0);
-        }
-        __syncthreads();
-        if (below > 0) {
-          // columns c in [c0+SB, TB) of every panel row r (tile K: r >= c)
-          const int ncol = below;
-          const int total = rows * ncol;
-          for (int e = t; e < total; e += BT) {
-            const int rr = e / ncol, cc = e - rr * ncol;
-            const int c = c0 + SB + cc;
-            F* xr;
-            if (rr < below) {
-              const int r = c0 + SB + rr;
-              if (c > r) continue;
-              xr = DK + r * TLD;
-            } else {
-              xr = tile(K + 1 + (rr - below) / TB, K) + ((rr - below) % TB) * TLD;
-            }
-            const F* lc = DK + c * TLD + c0;
-            F s = 0;
+      F* rd = rdiag + K * TB;
+      // (a) L_KK in one warp's registers
+      if (warp == 0) {
+        const bool ok = chol_tile_warp(DK, Ld, rd, thr, lane);
+        if (!ok && lane == 0) s_fail = 1;
+      }
+      __syncthreads();
+      if (s_fail) break;
+      // (b) the panel rows below: L_IK = A_IK L_KK^{-T} (one row per thread,
+      // warps 1..); warp 0 meanwhile inverts L_KK into the diagonal tile
+      // (lane = column: X_ic = (delta_ic - sum_k L_ik X_kc) / L_ii)
+      if (warp == 0) {
+        F x[TB];
 #pragma unroll
-            for (int k = 0; k < SB; ++k) s += xr[c0 + k] * lc[k];
-            xr[c] -= s;
-          }
-          __syncthreads();
+        for (int i = 0; i < TB; ++i) {
+          F s = (i == lane) ? (F)1 : (F)0;
+#pragma unroll
+          for (int k = 0; k < i; ++k) s -= Ld[i * TB + k] * x[k];
+          x[i] = s * rd[i];
+        }
+#pragma unroll
+        for (int i = 0; i < TB; ++i) DK[i * TLD + lane] = x[i];
+      } else {
+        const int rows = TB * (nb - K - 1);
+        for (int rr = t - 32; rr < rows; rr += BT - 32) {
+          F* xr = tile(K + 1 + rr / TB, K) + (rr % TB) * TLD;
+          F v[TB];
+#pragma unroll
+          for (int c = 0; c < TB; ++c) v[c] = xr[c];
+          trsm_row(v, Ld, rd);
+#pragma unroll
+          for (int c = 0; c < TB; ++c) xr[c] = v[c];
         }
       }
-      if (s_fail) break;
-      // A_IJ -= L_IK L_JK^T for K < J <= I: 64 threads per tile, a 4 x 4
-      // block of it each (8 row and column values per k for 16 FMAs)
+      __syncthreads();
+      // (c) A_IJ -= L_IK L_JK^T for K < J <= I
       {
         const int nrem = nb - K - 1, ntr = nrem * (nrem + 1) / 2;
-        const int sub = t & 63, r0 = 4 * (sub >> 3), c0 = 4 * (sub & 7);
-        for (int q = t >> 6; q < ntr; q += BT / 64) {
+        for (int q = slot; q < ntr; q += NSLOT) {
           int bi, bj;
           tri_index(q, &bi, &bj);
           const F* a = tile(K + 1 + bi, K) + r0 * TLD;
@@ -385,135 +400,68 @@ __device__ __forceinline__ void chol_inv_blocked_body(const double* __restrict__
   if (t == 0 && s_retry) atomicOr(&status->info, 1);
   if (conv_out && t == 0) *conv_out = (__uint_as_float(s_offmax) <= conv_tol && !s_retry) ? 1 : 0;
 
-  // X_II = L_II^{-1}: warp w solves L x = e_c for the columns c = w, w + NW,
-  // ... of every diagonal tile, all its columns' chains interleaved (lane =
-  // row, the solved entry broadcast by shuffle); a column c starts from e_c,
-  // so the steps i < c leave it zero.  Every column is read before any is
-  // written back.
-  {
-    constexpr int NW = BT / 32;
-    constexpr int CPW = (SORSVD_MAX_L + TB - 1) / TB * TB / NW;   // columns per warp, at most
-    F b[CPW];
-    const int ncol = nb * TB / NW;                  // this warp's columns (nb * TB is a multiple of NW)
+  // Z = L^{-1} in place, right-looking (L^{-1} = E_{nb-1}^{-1} ... E_0^{-1},
+  // E_K the identity with L's block column K): the diagonal tiles already
+  // hold X_KK = L_KK^{-1}.  Step K finalises block row K, Z_KJ = X_KK Z_KJ
+  // (J < K), then updates the rows below, Z_IJ -= L_IK Z_KJ (J < K) and
+  // Z_IK = -L_IK X_KK, which replaces L_IK.  A tile that is read in a phase
+  // is written only after the phase's barrier.  nb <= NSLOT + 1, so each
+  // phase's in-place tiles take one round of the slots.
+  for (int K = 0; K < nb; ++K) {
+    if (K > 0) {
+      F acc[4][4];
 #pragma unroll
-    for (int q = 0; q < CPW; ++q) {
-      const int col = warp + q * NW;
-      b[q] = (q < ncol && lane == col % TB) ? (F)1 : (F)0;
-    }
-    for (int i = 0; i < TB; ++i) {
+      for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int q = 0; q < CPW; ++q) {
-        if (q < ncol) {
-          const int col = warp + q * NW, I = col / TB;
-          const F xi = __shfl_sync(0xffffffffu, b[q], i) * rdiag[I * TB + i];
-          if (lane == i) b[q] = xi;
-          else if (lane > i) b[q] -= tile(I, I)[lane * TLD + i] * xi;
-        }
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < CPW; ++q) {
-      if (q < ncol) {
-        const int col = warp + q * NW, c = col % TB;
-        tile(col / TB, col / TB)[lane * TLD + c] = lane >= c ? b[q] : (F)0;
-      }
-    }
-  }
-  __syncthreads();
-  // Off-diagonal blocks one block row I at a time: X_IJ = -X_II S_IJ with
-  // S_IJ = sum_{K=J}^{I-1} L_IK X_KJ for every J < I at once (block rows
-  // above I are final); all S_IJ are formed before any X_IJ overwrites the
-  // L_IJ they read.  64 threads per tile, a 4 x 4 block each; the I tiles
-  // of a block row take ceil(I / 8) waves of the 512 threads.
-  {
-    constexpr int NWAVE = ((SORSVD_MAX_L + TB - 1) / TB + 7) / 8;
-    const int sub = t & 63, r0 = 4 * (sub >> 3), c0 = 4 * (sub & 7), slot = t >> 6;
-    for (int I = 1; I < nb; ++I) {
-      F acc[NWAVE][4][4];
-#pragma unroll
-      for (int w = 0; w < NWAVE; ++w) {
-        const int J = slot + 8 * w;
+        for (int v = 0; v < 4; ++v) acc[u][v] = (F)0;
+      const bool act = slot < K;
+      if (act) tile_mm44(tile(K, K), tile(K, slot), r0, c0, acc);
+      __syncthreads();
+      if (act) {
+        F* o = tile(K, slot) + r0 * TLD + c0;
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
-          for (int v = 0; v < 4; ++v) acc[w][u][v] = (F)0;
-        if (J < I) {
-          for (int K = J; K < I; ++K) {
-            const F* a = tile(I, K) + r0 * TLD;          // L_IK (rows r0..)
-            const F* bb = tile(K, J) + c0;               // X_KJ (X_JJ, lower, when K == J)
-#pragma unroll 4
-            for (int k = 0; k < TB; ++k) {
-              F av[4], bv[4];
-#pragma unroll
-              for (int u = 0; u < 4; ++u) { av[u] = a[u * TLD + k]; bv[u] = bb[k * TLD + u]; }
-#pragma unroll
-              for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int v = 0; v < 4; ++v) acc[w][u][v] += av[u] * bv[v];
-            }
-          }
-        }
+          for (int v = 0; v < 4; ++v) o[u * TLD + v] = acc[u][v];
       }
       __syncthreads();
+    }
+    const int nbelow = nb - K - 1;
+    if (nbelow > 0) {
+      // J < K: these tiles are read by no one in this phase
+      for (int q = slot; q < nbelow * K; q += NSLOT) {
+        const int I = K + 1 + q / K, J = q % K;
+        F acc[4][4];
 #pragma unroll
-      for (int w = 0; w < NWAVE; ++w) {
-        const int J = slot + 8 * w;
-        if (J < I) {
-          F* o = tile(I, J) + r0 * TLD + c0;
+        for (int u = 0; u < 4; ++u)
 #pragma unroll
-          for (int u = 0; u < 4; ++u)
+          for (int v = 0; v < 4; ++v) acc[u][v] = (F)0;
+        tile_mm44(tile(I, K), tile(K, J), r0, c0, acc);
+        F* o = tile(I, J) + r0 * TLD + c0;
 #pragma unroll
-            for (int v = 0; v < 4; ++v) o[u * TLD + v] = acc[w][u][v];
-        }
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) o[u * TLD + v] -= acc[u][v];
       }
+      F acc[4][4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = (F)0;
+      const bool act = slot < nbelow;
+      if (act) tile_mm44(tile(K + 1 + slot, K), tile(K, K), r0, c0, acc);
       __syncthreads();
-      // X_IJ = -X_II S_IJ, X_II lower triangular (k <= row)
-      const F* xi0 = tile(I, I);
+      if (act) {
+        F* o = tile(K + 1 + slot, K) + r0 * TLD + c0;
 #pragma unroll
-      for (int w = 0; w < NWAVE; ++w) {
-        const int J = slot + 8 * w;
-        if (J < I) {
-          const F* sm = tile(I, J) + c0;
-          F x[4][4];
+        for (int u = 0; u < 4; ++u)
 #pragma unroll
-          for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) x[u][v] = (F)0;
-          for (int k = 0; k < r0 + 4; ++k) {
-            F av[4], bv[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              av[u] = k <= r0 + u ? xi0[(r0 + u) * TLD + k] : (F)0;
-              bv[u] = sm[k * TLD + u];
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-              for (int v = 0; v < 4; ++v) x[u][v] += av[u] * bv[v];
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) acc[w][u][v] = -x[u][v];
-        }
-      }
-      __syncthreads();
-#pragma unroll
-      for (int w = 0; w < NWAVE; ++w) {
-        const int J = slot + 8 * w;
-        if (J < I) {
-          F* o = tile(I, J) + r0 * TLD + c0;
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) o[u * TLD + v] = acc[w][u][v];
-        }
+          for (int v = 0; v < 4; ++v) o[u * TLD + v] = -acc[u][v];
       }
       __syncthreads();
     }
   }
-  // R^{-1} = D^{-1/2} X^T: upper triangular, column-major
+  // R^{-1} = D^{-1/2} Z^T: upper triangular, column-major
   for (int c = warp; c < l; c += BT / 32)
     for (int r = lane; r < l; r += 32) {
       F v = 0;
@@ -540,11 +488,15 @@ __global__ void __launch_bounds__(BT) chol_batched_kernel(const CholJob* __restr
   chol_inv_blocked_body<F>(j.G, j.l, j.shift, (F*)j.Rinv, j.status, nullptr, nullptr, 0.f, nullptr);
 }
 
+// shared memory of the blocked kernel (the lower tiles, the dense diagonal
+// factor and the scale vectors); beyond 9 tile rows the in-place inverse
+// would need a second round of thread slots, and the packed kernel is used
 template <typename F>
 size_t chol_blocked_smem(int l) {
   const int nb = (l + TB - 1) / TB;
-  size_t b = (sizeof(F) * (size_t)(nb * (nb + 1) / 2) * TS + 7) & ~(size_t)7;
-  return b + sizeof(double) * nb * TB + 2 * sizeof(F) * nb * TB;
+  if (nb > BT / 64 + 1) return ~(size_t)0 >> 1;
+  size_t b = (sizeof(F) * (size_t)(nb * (nb + 1) / 2) * TS + 15) & ~(size_t)15;
+  return b + sizeof(F) * TB * TB + sizeof(double) * nb * TB + 2 * sizeof(F) * nb * TB;
 }
 
 constexpr size_t kCholSmemMax = 220 * 1024;
