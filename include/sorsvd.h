@@ -248,21 +248,23 @@ int sorsvd_polar_inv(const double* G, int l, float* X, int* ok, void* scratch, s
  * a TF32 hi and an fp32 lo part and each product formed as
  * hi*hi + hi*lo + lo*hi (fp32 accuracy; SORSVD_TSK=0 in the environment
  * selects the CUDA-core kernels instead), else on CUDA cores.
- *   sorsvd_gram:  G = X^T X, l x l binary64 (ldg >= l), for X rows x l; the
- *                 per-CTA fp32 partials are summed in binary64 in a fixed
- *                 order (bitwise repeatable).
+ *   sorsvd_gram:  G = X^T Y (Y = X when Y is NULL), l x l binary64
+ *                 (ldg >= l), for X, Y rows x l (the CholeskyQR Gram, and
+ *                 the core's Q1^T W); the per-CTA fp32 partials are summed
+ *                 in binary64 in a fixed order (bitwise repeatable).
  *   sorsvd_apply: Y = X B, rows x N fp32 (ldy >= rows), for X rows x K and
  *                 B K x N (ldb >= K); upper_tri != 0 declares B upper
  *                 triangular (its entries below the diagonal must be zero).
- * X: fp32, 16-byte aligned, ldx >= rows and a multiple of 4.  l, K, N in
+ * X (and Y): fp32, 16-byte aligned, leading dimension >= rows and a
+ * multiple of 4.  l, K, N in
  * [1, SORSVD_MAX_L].  workspace: at least
  * sorsvd_products_workspace_size(rows, l) bytes (l = max(K, N) for
  * sorsvd_apply), 256-byte aligned; it starts with the device status word
  * (sorsvd_get_status), where a bounded wait that gave up records
  * SORSVD_ERR_TIMEOUT. */
 size_t sorsvd_products_workspace_size(int64_t rows, int l);
-int sorsvd_gram(const float* X, int64_t rows, int l, int64_t ldx, double* G, int64_t ldg,
-                void* workspace, size_t ws_bytes, void* stream);
+int sorsvd_gram(const float* X, int64_t ldx, const float* Y, int64_t ldy, int64_t rows, int l,
+                double* G, int64_t ldg, void* workspace, size_t ws_bytes, void* stream);
 int sorsvd_apply(const float* X, int64_t rows, int K, int64_t ldx, const float* B, int64_t ldb, int N,
                  int upper_tri, float* Y, int64_t ldy, void* workspace, size_t ws_bytes, void* stream);
 

@@ -179,22 +179,27 @@ __device__ __noinline__ bool chol_tile_warp(const F* DK, F* Ld, F* rd, F thr, in
 #pragma unroll
   for (int c = 0; c < TB; ++c) a[c] = DK[lane * TLD + c];
   bool ok = true;
-  // straight-line code (no early exit, so a[] stays in registers); after a
-  // bad pivot the values are not used
+  F my_rs = (F)0;
+  // straight-line, branch-free code: per-lane choices are selects, so the
+  // warp never diverges between its shuffles (a divergent update made every
+  // shuffle wait for reconvergence, ~100 cycles each); after a bad pivot
+  // the values are not used
 #pragma unroll
   for (int j = 0; j < TB; ++j) {
     const F d = __shfl_sync(0xffffffffu, a[j], j);
     ok = ok && (d > thr);
     const F rs = rsqrt_rn(d);
-    if (lane == j) a[j] = d * rs;
-    else if (lane > j) a[j] *= rs;
-    if (lane == 0) rd[j] = rs;
+    const F lj = a[j] * rs;
+    a[j] = lane == j ? d * rs : (lane > j ? lj : a[j]);
+    my_rs = lane == j ? rs : my_rs;
 #pragma unroll
     for (int c = j + 1; c < TB; ++c) {
       const F lcj = __shfl_sync(0xffffffffu, a[j], c);
-      if (lane >= c) a[c] -= a[j] * lcj;
+      const F m = lane >= c ? a[j] : (F)0;
+      a[c] -= m * lcj;
     }
   }
+  rd[lane] = my_rs;
 #pragma unroll
   for (int c = 0; c < TB; ++c) Ld[lane * TB + c] = c <= lane ? a[c] : (F)0;
   return ok;
@@ -277,42 +282,50 @@ __device__ __forceinline__ void chol_inv_blocked_body(const double* __restrict__
     // equilibrated, shifted Gram in the lower tiles (factor precision);
     // padding and zero columns of T become identity rows / columns; the
     // largest off-diagonal entry (a column cosine) is recorded for conv_out.
-    // Eight independent loads in flight per thread.
+    // Tiles in groups of four, their loads issued before any is used.
     const F fshift = (F)shift;
     float offmax = 0.f;
-    const int total = ntile * TB * TB;
-    for (int e0 = t; e0 < total; e0 += 8 * BT) {
-      double gv[8];
+    {
+      int I0 = 0, J0 = 0;                          // (I, J) of tile q0
+      for (int q0 = 0; q0 < ntile; q0 += 4) {
+        double gv[4][2];
+        int Iq[4], Jq[4];
+        int I = I0, J = J0;
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int e = e0 + u * BT;
-        gv[u] = 0.0;
-        if (e < total) {
-          const int q = e >> 10, w = e & 1023;
-          int I, J;
-          tri_index(q, &I, &J);
-          const int gi = I * TB + (w >> 5), gc = J * TB + (w & 31);
-          if (gi < l && gc < l) gv[u] = G[gc + (int64_t)gi * l];     // G symmetric: coalesced
+        for (int u = 0; u < 4; ++u) {
+          Iq[u] = I;
+          Jq[u] = J;
+          if (++J > I) { ++I; J = 0; }
         }
-      }
+        I0 = I;
+        J0 = J;
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int e = e0 + u * BT;
-        if (e >= total) continue;
-        const int q = e >> 10, w = e & 1023;
-        int I, J;
-        tri_index(q, &I, &J);
-        const int r = w >> 5, c = w & 31;
-        const int gi = I * TB + r, gc = J * TB + c;
-        const F si = dsf[gi], sc = dsf[gc];
-        F v;
-        if (si == (F)0 || sc == (F)0) v = (gi == gc) ? (F)1 : (F)0;
-        else {
-          v = (F)gv[u] * si * sc;
-          if (gi > gc) offmax = fmaxf(offmax, fabsf((float)v));
-          if (gi == gc) v += fshift;
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int e = t + h * BT, r = e >> 5, c = e & 31;
+            const int gi = Iq[u] * TB + r, gc = Jq[u] * TB + c;
+            gv[u][h] = (q0 + u < ntile && gi < l && gc < l) ? G[gc + (int64_t)gi * l] : 0.0;   // symmetric: coalesced
+          }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (q0 + u >= ntile) break;
+          F* D = T + (size_t)(q0 + u) * TS;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int e = t + h * BT, r = e >> 5, c = e & 31;
+            const int gi = Iq[u] * TB + r, gc = Jq[u] * TB + c;
+            const F si = dsf[gi], sc = dsf[gc];
+            F v;
+            if (si == (F)0 || sc == (F)0) v = (gi == gc) ? (F)1 : (F)0;
+            else {
+              v = (F)gv[u][h] * si * sc;
+              if (gi > gc) offmax = fmaxf(offmax, fabsf((float)v));
+              if (gi == gc) v += fshift;
+            }
+            D[r * TLD + c] = v;
+          }
         }
-        T[(size_t)q * TS + r * TLD + c] = v;
       }
     }
     if (conv_out && attempt == 0) atomicMax(&s_offmax, __float_as_uint(offmax));

@@ -231,6 +231,12 @@ bool tsk_gram_supported(const float* X, int64_t ldx, int l);
 int tsk_gram_parts(int64_t rows);
 cudaError_t launch_tsk_gram(const float* X, int64_t ldx, int64_t rows, int l, float* parts, int* nparts,
                             int* sym_split, const int* skip, DeviceStatus* status, cudaStream_t st);
+// launch_tsk_xty: tsk_xty_parts() partials (l x l, ld l, stride l*l) of
+// X^T Y over the rows (plain reduction)
+bool tsk_xty_supported(const float* X, int64_t ldx, const float* Y, int64_t ldy, int l);
+int tsk_xty_parts(int64_t rows, int l);
+cudaError_t launch_tsk_xty(const float* X, int64_t ldx, const float* Y, int64_t ldy, int64_t rows, int l,
+                           float* parts, int* nparts, const int* skip, DeviceStatus* status, cudaStream_t st);
 bool tsk_apply_supported(const float* X, int64_t ldx, int K, int N);
 cudaError_t launch_tsk_apply(const float* X, int64_t ldx, int64_t rows, int K, const float* Bhi, const float* Blo,
                              int64_t ldb, int N, bool tri, float* Y, int64_t ldy, void* Y16, int64_t ld16,

@@ -154,6 +154,8 @@ Layout make_layout(int64_t m, int64_t n, int l, int dt, unsigned flags = 0) {
     if (l <= kTskMaxL) {                            // tensor-core Gram partials
       pb = std::max(pb, (size_t)tsk_gram_parts(m) * l * l * sizeof(float));
       pb = std::max(pb, (size_t)tsk_gram_parts(n) * l * l * sizeof(float));
+      pb = std::max(pb, (size_t)tsk_xty_parts(m, l) * l * l * sizeof(float));
+      pb = std::max(pb, (size_t)tsk_xty_parts(n, l) * l * l * sizeof(float));
     }
   }
   L.parts = take(pb);
@@ -451,6 +453,13 @@ int cross_gram(const Ctx& c, const void* X, int64_t ldx, const void* Y, int64_t 
     return gemm(c, K_SMALL_GEMM, true, l, l, rows, X, ldx, adt, Y, ldy, adt, M, ldm, true, kCapSmall);
   }
   float* parts = (float*)c.at(c.L.parts);
+  if (tsk_xty_supported((const float*)X, ldx, (const float*)Y, ldy, l)) {
+    int np = 0;
+    LAUNCH(K_SMALL_GEMM, launch_tsk_xty((const float*)X, ldx, (const float*)Y, ldy, rows, l, parts, &np, nullptr,
+                                        c.status(), c.st));
+    LAUNCH(K_REDUCE, launch_reduce_parts(parts, np, (int64_t)l * l, l, l, l, M, (int)ldm, c.st));
+    return SORSVD_OK;
+  }
   LAUNCH(K_SMALL_GEMM, launch_rb_gram((const float*)X, ldx, (const float*)Y, ldy, rows, l, l, false, parts, nullptr,
                                       c.st));
   LAUNCH(K_REDUCE, launch_reduce_parts(parts, (int)rb_gram_blocks(rows, l, l, false), (int64_t)l * l, l, l, l, M,
@@ -822,8 +831,10 @@ static Layout products_layout(int64_t rows, int l) {
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
   L.status = take(sizeof(DeviceStatus));
-  size_t pb = rb_gram_parts_bytes(rows, l, l, true);
-  if (l <= kTskMaxL) pb = std::max(pb, (size_t)tsk_gram_parts(rows) * l * l * sizeof(float));
+  size_t pb = std::max(rb_gram_parts_bytes(rows, l, l, true), rb_gram_parts_bytes(rows, l, l, false));
+  if (l <= kTskMaxL)
+    pb = std::max({pb, (size_t)tsk_gram_parts(rows) * l * l * sizeof(float),
+                   (size_t)tsk_xty_parts(rows, l) * l * l * sizeof(float)});
   L.parts = take(pb);
   L.ldk = (l + 31) / 32 * 32;
   L.bsplit = take((size_t)2 * L.ldk * L.ldk * sizeof(float));
@@ -836,15 +847,18 @@ size_t sorsvd_products_workspace_size(int64_t rows, int l) {
   return products_layout(rows, l).total;
 }
 
-int sorsvd_gram(const float* X, int64_t rows, int l, int64_t ldx, double* G, int64_t ldg, void* workspace,
-                size_t ws_bytes, void* stream) {
+int sorsvd_gram(const float* X, int64_t ldx, const float* Y, int64_t ldy, int64_t rows, int l, double* G,
+                int64_t ldg, void* workspace, size_t ws_bytes, void* stream) {
   if (!X || !G || rows < 1 || l < 1 || ldx < rows || ldg < l || ldg > INT32_MAX) return SORSVD_ERR_ARG;
+  if (Y && ldy < rows) return SORSVD_ERR_ARG;
   if (l > SORSVD_MAX_L) return SORSVD_ERR_UNSUPPORTED;
   if ((reinterpret_cast<uintptr_t>(X) & 15) || (ldx & 3)) return SORSVD_ERR_ARG;
+  if (Y && ((reinterpret_cast<uintptr_t>(Y) & 15) || (ldy & 3))) return SORSVD_ERR_ARG;
   const Layout L = products_layout(rows, l);
   if (int r = check_ws(workspace, ws_bytes, L)) return r;
   Ctx c{(char*)workspace, L, SORSVD_F32, false, (cudaStream_t)stream};
   CK(cudaMemsetAsync(c.status(), 0, sizeof(DeviceStatus), c.st));
+  if (Y) return cross_gram(c, X, ldx, Y, ldy, rows, l, G, ldg);
   return gram_sym(c, X, ldx, rows, l, nullptr, G, ldg);
 }
 

@@ -28,6 +28,14 @@
 // and summed in a fixed order by the reduction kernel, which mirrors the
 // lower triangle (deterministic).
 //
+// tsk_xty_kernel: partial sums of C = X^T Y (two rows x l operands, the
+// core product Q1^T W and the cross products of the two-pass core).  The
+// full l x l result does not fit in TMEM next to its operands, so CTAs come
+// in ceil(L16 / 128) types (blockIdx.y): type t holds MMA rows = columns
+// a0_t .. a0_t + 127 of X (a0_t = min(128 t, L16 - 128), keeping rows
+// >= 128 t) against all L16 columns of Y, and each row range is one
+// partial shared by the types.
+//
 // tsk_apply_kernel: Y = T B with B small (K x N, K = l).  Here T's
 // contiguous dimension (rows) is an M dimension of the product, and a TF32
 // operand must be K-major, so the 128-row tile of T goes to TMEM as the A
@@ -72,6 +80,17 @@ struct GramParams {
   int l, L16, nbox, boxc, nblk, stages;
   uint32_t tile_bytes;           // TR x 128 bytes: one K atom of the TR >= L16 columns the MMAs read
   GramBlock blk[kMaxGramBlocks];
+  float* parts;
+  int64_t pstride;
+  const int* skip;
+  DeviceStatus* status;
+  long long wait_cycles;
+};
+
+struct XtyParams {
+  int64_t rows, natoms;
+  int l, L16, ntypes, nch, ch0, nboxy, boxy, stages;
+  uint32_t x_bytes, y_bytes, stage_bytes;   // X: 128 columns, Y: nboxy boxes of boxy columns (x 128 bytes)
   float* parts;
   int64_t pstride;
   const int* skip;
@@ -254,6 +273,158 @@ tsk_gram_kernel(const __grid_constant__ CUtensorMap tmX, const GramParams P) {
               const int j = g.b0 + c + u;
               if (j < P.l) out[i + (size_t)j * P.l] = v[u];
             }
+          }
+        }
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (threadIdx.x == 0 && *abortp) raise_status(P.status, SORSVD_ERR_TIMEOUT);
+  if (warp == 1) tc::tmem_dealloc(tbase, kTmemCols);
+}
+
+
+template <int NCH>
+__global__ void __launch_bounds__(kGramThreads, 1)
+tsk_xty_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, const XtyParams P) {
+  if (P.skip && *P.skip) return;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = align1024(smem_raw);
+  // stage s: [X hi | Y hi | X lo | Y lo]; X and Y lo sit x_bytes + y_bytes after their hi
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)P.stages * P.stage_bytes);
+  uint64_t* lofull = full + P.stages;
+  uint64_t* empty = lofull + P.stages;
+  uint64_t* dfull = empty + P.stages;
+  uint64_t* done = dfull + 1;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abortp = reinterpret_cast<volatile int*>(tslot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int type = blockIdx.y;
+  const int a0 = min(128 * type, P.L16 - 128 > 0 ? P.L16 - 128 : 0);
+  const int row_lo = 128 * type;
+  const uint32_t hbytes = P.x_bytes + P.y_bytes;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < P.stages; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&lofull[s], 4);
+      tc::mbar_init(&empty[s], 1);
+    }
+    tc::mbar_init(dfull, 1);
+    tc::mbar_init(done, 1);
+    *abortp = 0;
+    tc::fence_barrier_init();
+  }
+  if (warp == 1) {
+    tc::tmem_alloc(tslot, kTmemCols);
+    tc::tmem_relinquish();
+  }
+  if (warp == 0 && lane == 0) {
+    tc::prefetch_tmap(&tmX);
+    tc::prefetch_tmap(&tmY);
+  }
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *tslot;
+  const int64_t at0 = (int64_t)blockIdx.x * P.natoms / gridDim.x;
+  const int64_t at1 = (int64_t)(blockIdx.x + 1) * P.natoms / gridDim.x;
+  const long long wc = P.wait_cycles;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      uint32_t armed = 0, armed_par = 0;
+      int stage = 0;
+      uint32_t phase = 0;
+      for (int64_t a = at0; a < at1; ++a) {
+        if (!tc::mbar_wait(&empty[stage], phase ^ 1u, abortp, wc)) break;
+        tc::mbar_arrive_expect_tx(&full[stage], hbytes);
+        armed |= 1u << stage;
+        armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
+        uint8_t* dst = smem + (size_t)stage * P.stage_bytes;
+        tc::tma_load_2d(dst, &tmX, &full[stage], (int)(a * kAtomK), a0);
+        for (int b = 0; b < P.nboxy; ++b)
+          tc::tma_load_2d(dst + P.x_bytes + (size_t)b * P.boxy * 128, &tmY, &full[stage], (int)(a * kAtomK),
+                          b * P.boxy);
+        if (++stage == P.stages) { stage = 0; phase ^= 1u; }
+      }
+      if (*abortp) drain_armed(full, P.stages, armed, armed_par);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t id0 = tc::idesc_make(2u, false, false, 128, P.ch0);
+      const uint32_t id1 = tc::idesc_make(2u, false, false, 128, NCH > 1 ? P.L16 - P.ch0 : 16);
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int64_t a = at0; a < at1 && ok; ++a) {
+        if (!tc::mbar_wait(&lofull[stage], phase, abortp, wc) || !tc::mbar_wait(&full[stage], phase, abortp, wc)) {
+          ok = false;
+          break;
+        }
+        tc::fence_after_sync();
+        const uint32_t sx = tc::smem_u32(smem + (size_t)stage * P.stage_bytes);
+        const uint32_t sy = sx + P.x_bytes;
+#pragma unroll
+        for (int ks = 0; ks < kAtomK / 8; ++ks) {
+          const uint32_t acc0 = (a > at0 || ks > 0) ? 1u : 0u;
+          const uint64_t ahi = tc::desc_sw128(sx + ks * 32, 16, 1024);
+          const uint64_t alo = tc::desc_sw128(sx + hbytes + ks * 32, 16, 1024);
+#pragma unroll
+          for (int ch = 0; ch < NCH; ++ch) {
+            const uint32_t boff = (uint32_t)(ch * P.ch0 * 128 + ks * 32);
+            const uint64_t bhi = tc::desc_sw128(sy + boff, 16, 1024);
+            const uint64_t blo = tc::desc_sw128(sy + hbytes + boff, 16, 1024);
+            const uint32_t d = tbase + (uint32_t)(ch * P.ch0);
+            const uint32_t id = ch ? id1 : id0;
+            tc::mma_tf32(d, ahi, bhi, id, acc0);
+            tc::mma_tf32(d, ahi, blo, id, 1u);
+            tc::mma_tf32(d, alo, bhi, id, 1u);
+          }
+        }
+        tc::mma_commit(&empty[stage]);
+        if (++stage == P.stages) { stage = 0; phase ^= 1u; }
+      }
+      if (ok) tc::mma_commit(dfull);
+      tc::mma_commit(done);
+      const long long t0 = clock64();
+      while (!tc::mbar_try_wait(done, 0) && clock64() - t0 < tc::kWaitCycles) {}
+    }
+  } else {
+    const int ct = threadIdx.x - 64;
+    int stage = 0;
+    uint32_t phase = 0;
+    bool ok = true;
+    const int n4 = (int)(hbytes / 16);
+    for (int64_t a = at0; a < at1; ++a) {
+      if (!__all_sync(0xffffffffu, tc::mbar_wait(&full[stage], phase, abortp, wc))) { ok = false; break; }
+      const float4* src = reinterpret_cast<const float4*>(smem + (size_t)stage * P.stage_bytes);
+      float4* dst = reinterpret_cast<float4*>(smem + (size_t)stage * P.stage_bytes + hbytes);
+      for (int e = ct; e < n4; e += 128) {
+        const float4 x = src[e];
+        dst[e] = make_float4(tf32_rest(x.x), tf32_rest(x.y), tf32_rest(x.z), tf32_rest(x.w));
+      }
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&lofull[stage]);
+      if (++stage == P.stages) { stage = 0; phase ^= 1u; }
+    }
+    if (ok && __all_sync(0xffffffffu, tc::mbar_wait(dfull, 0, abortp, wc))) {
+      tc::fence_after_sync();
+      const int q = warp & 3;
+      const int i = a0 + q * 32 + lane;
+      const bool keep = i >= row_lo && i < P.l;
+      float* out = P.parts + (size_t)blockIdx.x * P.pstride;
+      for (int c = 0; c < P.L16; c += 16) {
+        float v[16];
+        tc::tmem_ld16(tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+        tc::tmem_ld_wait();
+        if (keep) {
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            const int j = c + u;
+            if (j < P.l) out[i + (size_t)j * P.l] = v[u];
           }
         }
       }
@@ -564,6 +735,57 @@ cudaError_t launch_tsk_gram(const float* X, int64_t ldx, int64_t rows, int l, fl
     case 5: return go(tsk_gram_kernel<5>);
     default: return cudaErrorInvalidValue;
   }
+}
+
+bool tsk_xty_supported(const float* X, int64_t ldx, const float* Y, int64_t ldy, int l) {
+  return tsk_gram_supported(X, ldx, l) && tsk_gram_supported(Y, ldy, l);
+}
+
+int tsk_xty_parts(int64_t rows, int l) {
+  const int64_t natoms = (rows + kAtomK - 1) / kAtomK;
+  const int ntypes = std::max(1, (round16(l) + 127) / 128);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(natoms, std::max(1, num_sms() / ntypes)));
+}
+
+cudaError_t launch_tsk_xty(const float* X, int64_t ldx, const float* Y, int64_t ldy, int64_t rows, int l,
+                           float* parts, int* nparts, const int* skip, DeviceStatus* status, cudaStream_t st) {
+  if (rows < 1 || !tsk_xty_supported(X, ldx, Y, ldy, l)) return cudaErrorInvalidValue;
+  XtyParams P{};
+  P.rows = rows;
+  P.natoms = (rows + kAtomK - 1) / kAtomK;
+  P.l = l;
+  P.L16 = std::max(round16(l), 16);
+  P.ntypes = (P.L16 + 127) / 128;
+  P.nch = P.L16 > 256 ? 2 : 1;
+  P.ch0 = P.nch == 2 ? 256 : P.L16;
+  // Y: all L16 columns (two boxes past 256, each starting on a 1024-byte boundary)
+  P.nboxy = P.L16 > 256 ? 2 : 1;
+  P.boxy = P.L16 / P.nboxy;
+  P.x_bytes = 128u * 128u;
+  P.y_bytes = (uint32_t)P.L16 * 128u;
+  P.stage_bytes = 2u * (P.x_bytes + P.y_bytes);
+  const uint32_t bar_bytes = 256;
+  P.stages = (int)std::min<uint32_t>(4u, (kSmemBudget - bar_bytes) / P.stage_bytes);
+  if (P.stages < 2) return cudaErrorInvalidValue;
+  P.parts = parts;
+  P.pstride = (int64_t)l * l;
+  P.skip = skip;
+  P.status = status;
+  P.wait_cycles = tc_wait_cycles();
+  CUtensorMap mx, my;
+  if (!tc_map_2d(&mx, X, 2, rows, l, ldx, (uint32_t)kAtomK, 128u, true)) return cudaErrorInvalidValue;
+  if (!tc_map_2d(&my, Y, 2, rows, l, ldy, (uint32_t)kAtomK, (uint32_t)P.boxy, true)) return cudaErrorInvalidValue;
+  const int G = tsk_xty_parts(rows, l);
+  *nparts = G;
+  const size_t smem = (size_t)P.stages * P.stage_bytes + bar_bytes + 1024;
+  const dim3 grid((unsigned)G, (unsigned)P.ntypes);
+  auto go = [&](auto kern) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, kGramThreads, smem, st>>>(mx, my, P);
+    return cudaGetLastError();
+  };
+  return P.nch == 2 ? go(tsk_xty_kernel<2>) : go(tsk_xty_kernel<1>);
 }
 
 bool tsk_apply_supported(const float* X, int64_t ldx, int K, int N) {

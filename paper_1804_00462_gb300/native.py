@@ -66,7 +66,7 @@ _lib.sorsvd_polar_inv.argtypes = [_vp, _int, _vp, _vp, _vp, _sz, _vp]
 _lib.sorsvd_polar_inv.restype = _int
 _lib.sorsvd_products_workspace_size.argtypes = [_i64, _int]
 _lib.sorsvd_products_workspace_size.restype = _sz
-_lib.sorsvd_gram.argtypes = [_vp, _i64, _int, _i64, _vp, _i64, _vp, _sz, _vp]
+_lib.sorsvd_gram.argtypes = [_vp, _i64, _vp, _i64, _i64, _int, _vp, _i64, _vp, _sz, _vp]
 _lib.sorsvd_gram.restype = _int
 _lib.sorsvd_apply.argtypes = [_vp, _i64, _int, _i64, _vp, _i64, _int, _int, _vp, _i64, _vp, _sz, _vp]
 _lib.sorsvd_apply.restype = _int
@@ -315,7 +315,7 @@ def colmajor_f32(X: torch.Tensor, ld: int = 0) -> torch.Tensor:
     a multiple of 4 (ld, when given, at least the rows), as the tall-skinny
     products require."""
     rows, cols = X.shape
-    ld = max(ld, (rows + 3) // 4 * 4)
+    ld = (max(ld, rows) + 3) // 4 * 4
     buf = torch.zeros(cols, ld, dtype=torch.float32, device=X.device)
     buf[:, :rows] = X.T.to(torch.float32)
     return buf.T[:rows]
@@ -328,15 +328,22 @@ def _products_ws(rows: int, l: int, device):
     return torch.empty(nb, dtype=torch.uint8, device=device), nb
 
 
-def gram(X: torch.Tensor, stream=None):
-    """G = X^T X (l x l binary64) of a column-major fp32 CUDA tensor with
-    ld % 4 == 0 (colmajor_f32), through sorsvd_gram.  Returns (G, status)."""
+def gram(X: torch.Tensor, Y: torch.Tensor = None, stream=None):
+    """G = X^T Y (Y = X when omitted; l x l binary64) of column-major fp32
+    CUDA tensors with ld % 4 == 0 (colmajor_f32), through sorsvd_gram.
+    Returns (G, status)."""
     ptr, rows, l, ld, tr = _colmajor(X)
     if tr or X.dtype != torch.float32:
         raise ValueError("X must be a column-major fp32 tensor")
+    yptr, ldy = None, 0
+    if Y is not None:
+        yptr, yrows, yl, ldy, ytr = _colmajor(Y)
+        if ytr or Y.dtype != torch.float32 or (yrows, yl) != (rows, l):
+            raise ValueError("Y must be a column-major fp32 tensor shaped like X")
     ws, nb = _products_ws(rows, l, X.device)
     G = colmajor_empty(l, l, torch.float64, X.device)
-    _check(_lib.sorsvd_gram(ptr, rows, l, ld, G.data_ptr(), l, ws.data_ptr(), nb, _stream(stream)), "sorsvd_gram")
+    _check(_lib.sorsvd_gram(ptr, ld, yptr, ldy, rows, l, G.data_ptr(), l, ws.data_ptr(), nb, _stream(stream)),
+           "sorsvd_gram")
     s, _ = get_status(ws, stream)
     return G, s
 

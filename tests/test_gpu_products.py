@@ -75,6 +75,32 @@ def test_gram_elementwise(nat, rows, l):
     assert torch.equal(G, G2)                          # fixed summation order
 
 
+def _xty_bound(X32, Y32, rows, l):
+    S = np.abs(X32.astype(np.float64)).T @ np.abs(Y32.astype(np.float64))
+    ntypes = max(1, (-(-l // 16) * 16 + 127) // 128)
+    natoms = math.ceil(rows / 32)
+    n_acc = 3 * 4 * math.ceil(natoms / min(natoms, max(1, 148 // ntypes)))
+    return (3 * 2.0 ** -20 + n_acc * 2.0 ** -23 + rows * 2.0 ** -24) * 1.01 * S
+
+
+@pytest.mark.parametrize("rows,l", [(1, 1), (33, 16), (1000, 110), (4133, 128), (2049, 129), (5000, 200),
+                                    (3001, 256), (65537, 266), (9000, 288), (3000, 300)])
+def test_cross_gram_elementwise(nat, rows, l):
+    X = _rand(rows, l, seed=3 * rows + l)
+    Y = _rand(rows, l, seed=5 * rows + l, scale_cols=False)
+    Xd = nat.colmajor_f32(torch.from_numpy(X).cuda())
+    Yd = nat.colmajor_f32(torch.from_numpy(Y).cuda(), ld=rows + 8)
+    G, st = nat.gram(Xd, Yd)
+    torch.cuda.synchronize()
+    assert st == 0
+    ref = X.astype(np.float64).T @ Y.astype(np.float64)
+    ratio = (np.abs(G.cpu().numpy() - ref) / np.maximum(_xty_bound(X, Y, rows, l), 1e-300)).max()
+    assert ratio <= 1.0, (rows, l, ratio)
+    G2, _ = nat.gram(Xd, Yd)
+    torch.cuda.synchronize()
+    assert torch.equal(G, G2)
+
+
 @pytest.mark.parametrize("rows,K,N,tri", [(50, 7, 7, True), (1000, 110, 110, True), (1000, 110, 100, False),
                                           (5000, 128, 128, False), (4099, 266, 266, True),
                                           (70001, 266, 266, False), (70001, 266, 256, False),
@@ -116,8 +142,10 @@ def test_products_reject_bad_arguments(nat):
     ws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
     G = torch.empty(8, 8, dtype=torch.float64, device="cuda")
     # ldx not a multiple of 4, l = 0, a workspace that is too small
-    assert _lib.sorsvd_gram(X.data_ptr(), 64, 8, 66, G.data_ptr(), 8, ws.data_ptr(), ws.numel(), None) == 1
-    assert _lib.sorsvd_gram(X.data_ptr(), 64, 0, 64, G.data_ptr(), 8, ws.data_ptr(), ws.numel(), None) == 1
-    assert _lib.sorsvd_gram(X.data_ptr(), 64, 8, 64, G.data_ptr(), 8, ws.data_ptr(), 16, None) == 7
+    assert _lib.sorsvd_gram(X.data_ptr(), 66, None, 0, 64, 8, G.data_ptr(), 8, ws.data_ptr(), ws.numel(), None) == 1
+    assert _lib.sorsvd_gram(X.data_ptr(), 64, None, 0, 64, 0, G.data_ptr(), 8, ws.data_ptr(), ws.numel(), None) == 1
+    assert _lib.sorsvd_gram(X.data_ptr(), 64, X.data_ptr(), 62, 64, 8, G.data_ptr(), 8, ws.data_ptr(), ws.numel(),
+                            None) == 1
+    assert _lib.sorsvd_gram(X.data_ptr(), 64, None, 0, 64, 8, G.data_ptr(), 8, ws.data_ptr(), 16, None) == 7
     assert int(_lib.sorsvd_products_workspace_size(64, 0)) == 0
     assert C.sizeof(C.c_void_p) == 8
