@@ -61,14 +61,24 @@ __device__ __forceinline__ void rotation(float al, float be, float ga, float* c,
   *c = cs;
   *s = cs * t;
 }
+// Binary64 rotation: the tangent t to binary32 accuracy (enough for the
+// angle: a relative error e in t leaves e times the original off-diagonal
+// term, and the sweeps repeat until every term is below tolerance), the
+// rotation itself orthogonal to binary64 accuracy: c = (1 + t^2)^{-1/2} by
+// two Newton steps x <- x (3 - w x^2) / 2 from the binary32 estimate (each
+// step squares the relative error), s = c t.  One binary64 division instead
+// of three divisions and three square roots, all slow at the FP64 rate.
 __device__ __forceinline__ void rotation(double al, double be, double ga, double* c, double* s) {
   const double z = (be - al) / (2.0 * ga);
-  const double az = fabs(z);
-  const double root = az > 1.0 ? az * sqrt(1.0 + (1.0 / az) * (1.0 / az)) : sqrt(1.0 + az * az);
-  const double t = (z >= 0.0 ? 1.0 : -1.0) / (az + root);
-  const double cs = 1.0 / sqrt(1.0 + t * t);
-  *c = cs;
-  *s = cs * t;
+  const float az = (float)fabs(z);                 // inf when out of range: t = 0
+  const float tf = copysignf(1.f / (az + sqrtf(fmaf(az, az, 1.f))), (float)z);
+  const double t = (double)tf;
+  const double w = fma(t, t, 1.0);
+  double x = (double)rsqrtf((float)w);
+  x = x * fma(-0.5 * w, x * x, 1.5);
+  x = x * fma(-0.5 * w, x * x, 1.5);
+  *c = x;
+  *s = x * t;
 }
 
 template <typename J>
