@@ -219,20 +219,32 @@ __device__ __forceinline__ void trsm_row(F (&v)[TB], const F* Ld, const F* rd) {
   }
 }
 
-// 4 x 4 block (rows r0.., columns c0..) of A B for 32 x 32 tiles, A read by
-// rows (A[r * TLD + k]) and B by rows (B[k * TLD + c])
-template <typename F>
-__device__ __forceinline__ void tile_mm44(const F* A, const F* B, int r0, int c0, F (&acc)[4][4]) {
+// 8 x 4 block (rows r0.., columns c0..) of A B (BT: A B^T) for 32 x 32
+// tiles: one warp per output tile, lane -> (r0, c0) = (8 (lane / 8),
+// 4 (lane % 8)); per k the warp reads 4 distinct rows of A and 8 distinct
+// columns of B, each load one conflict-free wavefront, for 32 FMAs
+template <typename F, bool BT>
+__device__ __forceinline__ void tile_mm84(const F* A, const F* B, int r0, int c0, F (&acc)[8][4]) {
 #pragma unroll 4
   for (int k = 0; k < TB; ++k) {
-    F av[4], bv[4];
+    F av[8], bv[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) { av[u] = A[(r0 + u) * TLD + k]; bv[u] = B[k * TLD + c0 + u]; }
+    for (int u = 0; u < 8; ++u) av[u] = A[(r0 + u) * TLD + k];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int v = 0; v < 4; ++v) bv[v] = BT ? B[(c0 + v) * TLD + k] : B[k * TLD + c0 + v];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
 #pragma unroll
       for (int v = 0; v < 4; ++v) acc[u][v] += av[u] * bv[v];
   }
+}
+
+template <typename F>
+__device__ __forceinline__ void zero84(F (&acc)[8][4]) {
+#pragma unroll
+  for (int u = 0; u < 8; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = (F)0;
 }
 
 template <typename F>
@@ -275,9 +287,9 @@ __device__ __forceinline__ void chol_inv_blocked_body(const double* __restrict__
   double shift = shift_rel;
   const int max_try = 12;
   int attempt = 0;
-  // 64 threads per 32 x 32 output tile, a 4 x 4 block each
-  const int sub = t & 63, r0 = 4 * (sub >> 3), c0 = 4 * (sub & 7), slot = t >> 6;
-  constexpr int NSLOT = BT / 64;
+  // one warp per 32 x 32 output tile, an 8 x 4 block per lane
+  const int r0 = 8 * (lane >> 3), c0 = 4 * (lane & 7);
+  constexpr int NW = BT / 32;
   for (; attempt < max_try; ++attempt) {
     // equilibrated, shifted Gram in the lower tiles (factor precision);
     // padding and zero columns of T become identity rows / columns; the
@@ -331,16 +343,13 @@ __device__ __forceinline__ void chol_inv_blocked_body(const double* __restrict__
     if (conv_out && attempt == 0) atomicMax(&s_offmax, __float_as_uint(offmax));
     if (t == 0) s_fail = 0;
     __syncthreads();
-    for (int K = 0; K < nb; ++K) {
+    // (a) for tile column 0: L_00 in one warp's registers (later diagonal
+    // tiles are factored ahead, inside the previous column's update)
+    if (warp == 0 && !chol_tile_warp(tile(0, 0), Ld, rdiag, thr, lane) && lane == 0) s_fail = 1;
+    __syncthreads();
+    for (int K = 0; K < nb && !s_fail; ++K) {
       F* DK = tile(K, K);
       F* rd = rdiag + K * TB;
-      // (a) L_KK in one warp's registers
-      if (warp == 0) {
-        const bool ok = chol_tile_warp(DK, Ld, rd, thr, lane);
-        if (!ok && lane == 0) s_fail = 1;
-      }
-      __syncthreads();
-      if (s_fail) break;
       // (b) the panel rows below: L_IK = A_IK L_KK^{-T} (one row per thread,
       // warps 1..); warp 0 meanwhile inverts L_KK into the diagonal tile
       // (lane = column: X_ic = (delta_ic - sum_k L_ik X_kc) / L_ii)
@@ -368,34 +377,39 @@ __device__ __forceinline__ void chol_inv_blocked_body(const double* __restrict__
         }
       }
       __syncthreads();
-      // (c) A_IJ -= L_IK L_JK^T for K < J <= I
+      // (c) A_IJ -= L_IK L_JK^T for K < J <= I, one warp per tile.  Warp 0
+      // takes the next diagonal tile (K+1, K+1) alone and then factors it
+      // (look-ahead: the factorisation overlaps the rest of the update);
+      // warps 1.. take the other tiles.
       {
         const int nrem = nb - K - 1, ntr = nrem * (nrem + 1) / 2;
-        for (int q = slot; q < ntr; q += NSLOT) {
-          int bi, bj;
-          tri_index(q, &bi, &bj);
-          const F* a = tile(K + 1 + bi, K) + r0 * TLD;
-          const F* b = tile(K + 1 + bj, K) + c0 * TLD;
-          F acc[4][4];
+        if (warp == 0) {
+          if (nrem > 0) {
+            F acc[8][4];
+            zero84(acc);
+            const F* lk = tile(K + 1, K);
+            tile_mm84<F, true>(lk, lk, r0, c0, acc);
+            F* out = tile(K + 1, K + 1) + r0 * TLD + c0;
 #pragma unroll
-          for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 8; ++u)
 #pragma unroll
-            for (int v = 0; v < 4; ++v) acc[u][v] = (F)0;
-#pragma unroll 4
-          for (int k = 0; k < TB; ++k) {
-            F av[4], bv[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) { av[u] = a[u * TLD + k]; bv[u] = b[u * TLD + k]; }
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-              for (int v = 0; v < 4; ++v) acc[u][v] += av[u] * bv[v];
+              for (int v = 0; v < 4; ++v) out[u * TLD + v] -= acc[u][v];
+            __syncwarp();
+            if (!chol_tile_warp(tile(K + 1, K + 1), Ld, rdiag + (K + 1) * TB, thr, lane) && lane == 0) s_fail = 1;
           }
-          F* out = tile(K + 1 + bi, K + 1 + bj) + r0 * TLD + c0;
+        } else {
+          for (int q = warp; q < ntr; q += NW - 1) {
+            int bi, bj;
+            tri_index(q, &bi, &bj);
+            F acc[8][4];
+            zero84(acc);
+            tile_mm84<F, true>(tile(K + 1 + bi, K), tile(K + 1 + bj, K), r0, c0, acc);
+            F* out = tile(K + 1 + bi, K + 1 + bj) + r0 * TLD + c0;
 #pragma unroll
-          for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 8; ++u)
 #pragma unroll
-            for (int v = 0; v < 4; ++v) out[u * TLD + v] -= acc[u][v];
+              for (int v = 0; v < 4; ++v) out[u * TLD + v] -= acc[u][v];
+          }
         }
       }
       __syncthreads();
@@ -418,22 +432,19 @@ __device__ __forceinline__ void chol_inv_blocked_body(const double* __restrict__
   // hold X_KK = L_KK^{-1}.  Step K finalises block row K, Z_KJ = X_KK Z_KJ
   // (J < K), then updates the rows below, Z_IJ -= L_IK Z_KJ (J < K) and
   // Z_IK = -L_IK X_KK, which replaces L_IK.  A tile that is read in a phase
-  // is written only after the phase's barrier.  nb <= NSLOT + 1, so each
-  // phase's in-place tiles take one round of the slots.
+  // is written only after the phase's barrier.  nb <= 9 <= NW, so each
+  // phase's in-place tiles take one round of the warps.
   for (int K = 0; K < nb; ++K) {
     if (K > 0) {
-      F acc[4][4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = (F)0;
-      const bool act = slot < K;
-      if (act) tile_mm44(tile(K, K), tile(K, slot), r0, c0, acc);
+      F acc[8][4];
+      zero84(acc);
+      const bool act = warp < K;
+      if (act) tile_mm84<F, false>(tile(K, K), tile(K, warp), r0, c0, acc);
       __syncthreads();
       if (act) {
-        F* o = tile(K, slot) + r0 * TLD + c0;
+        F* o = tile(K, warp) + r0 * TLD + c0;
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < 8; ++u)
 #pragma unroll
           for (int v = 0; v < 4; ++v) o[u * TLD + v] = acc[u][v];
       }
@@ -442,32 +453,28 @@ __device__ __forceinline__ void chol_inv_blocked_body(const double* __restrict__
     const int nbelow = nb - K - 1;
     if (nbelow > 0) {
       // J < K: these tiles are read by no one in this phase
-      for (int q = slot; q < nbelow * K; q += NSLOT) {
+      for (int q = warp; q < nbelow * K; q += NW) {
         const int I = K + 1 + q / K, J = q % K;
-        F acc[4][4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int v = 0; v < 4; ++v) acc[u][v] = (F)0;
-        tile_mm44(tile(I, K), tile(K, J), r0, c0, acc);
+        F acc[8][4];
+        zero84(acc);
+        tile_mm84<F, false>(tile(I, K), tile(K, J), r0, c0, acc);
         F* o = tile(I, J) + r0 * TLD + c0;
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < 8; ++u)
 #pragma unroll
           for (int v = 0; v < 4; ++v) o[u * TLD + v] -= acc[u][v];
       }
-      F acc[4][4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = (F)0;
-      const bool act = slot < nbelow;
-      if (act) tile_mm44(tile(K + 1 + slot, K), tile(K, K), r0, c0, acc);
+      F acc[8][4];
+      zero84(acc);
+      // J = K: the last warps, so that the J < K tiles start on the first
+      const int w2 = NW - 1 - warp;
+      const bool act = w2 < nbelow;
+      if (act) tile_mm84<F, false>(tile(K + 1 + w2, K), tile(K, K), r0, c0, acc);
       __syncthreads();
       if (act) {
-        F* o = tile(K + 1 + slot, K) + r0 * TLD + c0;
+        F* o = tile(K + 1 + w2, K) + r0 * TLD + c0;
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < 8; ++u)
 #pragma unroll
           for (int v = 0; v < 4; ++v) o[u * TLD + v] = -acc[u][v];
       }

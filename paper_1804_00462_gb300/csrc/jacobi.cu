@@ -68,11 +68,18 @@ __device__ __forceinline__ void rotation(float al, float be, float ga, float* c,
 // two Newton steps x <- x (3 - w x^2) / 2 from the binary32 estimate (each
 // step squares the relative error), s = c t.  One binary64 division instead
 // of three divisions and three square roots, all slow at the FP64 rate.
+// For |z| > 1e8, t = 1 / (2 z) in binary64 (relative error below 1e-16
+// there): a binary32 t would underflow for the columns of a null space,
+// whose rotations against columns 1e30 larger still matter to them.
 __device__ __forceinline__ void rotation(double al, double be, double ga, double* c, double* s) {
   const double z = (be - al) / (2.0 * ga);
-  const float az = (float)fabs(z);                 // inf when out of range: t = 0
-  const float tf = copysignf(1.f / (az + sqrtf(fmaf(az, az, 1.f))), (float)z);
-  const double t = (double)tf;
+  double t;
+  if (fabs(z) > 1e8) {
+    t = 0.5 / z;
+  } else {
+    const float az = (float)fabs(z);
+    t = (double)copysignf(1.f / (az + sqrtf(fmaf(az, az, 1.f))), (float)z);
+  }
   const double w = fma(t, t, 1.0);
   double x = (double)rsqrtf((float)w);
   x = x * fma(-0.5 * w, x * x, 1.5);
