@@ -163,10 +163,19 @@ __device__ __forceinline__ void tri_index(int q, int* i, int* j) {
 
 constexpr int BT = 512;           // threads of the blocked kernel
 
-// correctly rounded 1/sqrt (fp32 intrinsic; binary64 through sqrt and a
-// division, only used by the binary64 factor)
+// 1/sqrt of a pivot: fp32, the correctly rounded intrinsic; binary64, the
+// fp32 estimate refined by two Newton steps y <- y (3 - x y^2) / 2 (each
+// squares the relative error: 2^-23 -> ~2^-46 -> below binary64 rounding),
+// a few FMAs where a binary64 square root and division cost tens of FP64
+// operations each on this GPU's FP64 rate
 __device__ __forceinline__ float rsqrt_rn(float x) { return __frsqrt_rn(x); }
-__device__ __forceinline__ double rsqrt_rn(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ double rsqrt_rn(double x) {
+  if (!(x > 1e-36 && x < 1e36)) return 1.0 / sqrt(x);     // outside fp32's range (and NaN, <= 0)
+  double y = (double)rsqrtf((float)x);
+  y = y * fma(-0.5 * x, y * y, 1.5);
+  y = y * fma(-0.5 * x, y * y, 1.5);
+  return y;
+}
 
 // Cholesky factor of the 32 x 32 diagonal tile DK in one warp's registers
 // (lane = row): right-looking, the pivot and the column entries broadcast by
