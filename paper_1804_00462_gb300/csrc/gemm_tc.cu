@@ -340,7 +340,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       const uint32_t idesc0 = tc::idesc_make(FMT, A_MN, false, 128, P.ch0);
-      const uint32_t idesc1 = tc::idesc_make(FMT, A_MN, false, 128, P.Npad - P.ch0);
+      // the last N-chunk takes what the equal chunks before it leave
+      const uint32_t idesc1 = tc::idesc_make(FMT, A_MN, false, 128, NCH > 1 ? P.Npad - (NCH - 1) * P.ch0 : 16);
       // split mode: hi x [B_hi | B_lo], N = 2 Npad
       const uint32_t idescW = tc::idesc_make(FMT, false, false, 128, SPLIT ? 2 * P.Npad : 16);
       uint32_t stage = 0, phase = 0, bstage = 0, bphase = 0;
@@ -409,9 +410,9 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                   const uint32_t dm = dcol + (uint32_t)(mt * P.Npad);
 #pragma unroll
                   for (int ch = 0; ch < NCH; ++ch) {
-                    const uint32_t id = ch ? idesc1 : idesc0;
-                    const uint32_t dch = dm + (ch ? (uint32_t)P.ch0 : 0u);
-                    const uint32_t bat = sb + (uint32_t)j * P.b_atom + (ch ? (uint32_t)(P.ch0 * 128) : 0u);
+                    const uint32_t id = (ch == NCH - 1 && NCH > 1) ? idesc1 : idesc0;
+                    const uint32_t dch = dm + (uint32_t)(ch * P.ch0);
+                    const uint32_t bat = sb + (uint32_t)j * P.b_atom + (uint32_t)(ch * P.ch0 * 128);
                     const uint64_t bd = tc::desc_sw128(bat + ks * 32, 16, 1024);
                     if (ELT == 2) tc::mma_tf32(dch, ad, bd, id, acc);
                     else tc::mma_f16(dch, ad, bd, id, acc);
@@ -769,6 +770,10 @@ cudaError_t launch_typed(const CUtensorMap& ma, const CUtensorMap& mb, const CUt
     if (P.MT != 1 || P.nch != 1 || P.KA != 1) return cudaErrorInvalidValue;
     return launch_shape<ELT, A_MN, 1, 1, 1>(ma, mb, mblo, P, smem, st);
   } else {
+  // more N-chunks (independent accumulators in flight) for one row block
+  if (P.nch == 3 && P.MT == 1 && P.KA == 1) return launch_shape<ELT, A_MN, 1, 3, 1>(ma, mb, mblo, P, smem, st);
+  if (P.nch == 4 && P.MT == 1 && P.KA == 1) return launch_shape<ELT, A_MN, 1, 4, 1>(ma, mb, mblo, P, smem, st);
+  if (P.nch > 2) return cudaErrorInvalidValue;
   const int code = (P.MT - 1) * 4 + (P.nch - 1) * 2 + (P.KA - 1);
   switch (code) {
     case 0: return launch_shape<ELT, A_MN, 1, 1, 1>(ma, mb, mblo, P, smem, st);
@@ -799,8 +804,14 @@ TcParams shape(int elt, int64_t M, int64_t N, int64_t K, int KA, int MT) {
   TcParams P{};
   P.M = M; P.K = K; P.N = (int)N;
   P.Npad = (int)((N + 15) / 16 * 16);
-  if (P.Npad <= 256) { P.nch = 1; P.ch0 = P.Npad; }
-  else { P.nch = 2; P.ch0 = (P.Npad / 2 + 15) / 16 * 16; }
+  // N-chunks: independent accumulators whose MMAs overlap in the tensor
+  // pipe (SORSVD_TC_NCH 1..4 overrides; 3 and 4 only with one row block
+  // and one K atom per stage)
+  const int envN = env_int("SORSVD_TC_NCH", 0);
+  P.nch = (envN >= 1 && envN <= 4 && (envN <= 2 || (MT == 1 && KA == 1)) && elt != 3) ? envN
+          : (P.Npad <= 256 ? 1 : 2);
+  P.ch0 = (int)((P.Npad + P.nch - 1) / P.nch + 15) / 16 * 16;
+  if (P.nch > 1 && P.Npad - (P.nch - 1) * P.ch0 < 16) { P.nch = P.Npad <= 256 ? 1 : 2; P.ch0 = (P.Npad / P.nch + 15) / 16 * 16; }
   P.KA = KA; P.MT = MT;
   const int AK = elt >= 2 ? 32 : 64;
   const int64_t urows = 128 * MT;
