@@ -167,7 +167,15 @@ __device__ __forceinline__ void jacobi_sweep_body(const double* __restrict__ Min
         if (!(ga * ga > tol2 * al * be)) continue;
         if (ga * ga > big2 * al * be) big_local = 1;
         J cs, sn;
-        rotation(al, be, ga, &cs, &sn);
+        if (sizeof(J) == 8) {
+          // binary64: one lane forms the rotation (tens of FP64 operations at
+          // this GPU's FP64 rate), the group takes it by shuffle
+          if (gl == 0) rotation(al, be, ga, &cs, &sn);
+          cs = __shfl_sync(gmask, cs, grp * 8);
+          sn = __shfl_sync(gmask, sn, grp * 8);
+        } else {
+          rotation(al, be, ga, &cs, &sn);
+        }
         J* vp = V + oa;
         J* vq = V + ob;
 #pragma unroll
@@ -647,7 +655,7 @@ __device__ __forceinline__ int rotate_pair16(float* cx, float* cy, int gl, unsig
   return flags;
 }
 
-template <int EP>
+template <int EP, int C>
 __global__ void __launch_bounds__(352)
 jacobi_block_cluster_kernel(const double* __restrict__ Min, int l, int b, float* __restrict__ Vout,
                             DeviceStatus* status) {
@@ -655,7 +663,7 @@ jacobi_block_cluster_kernel(const double* __restrict__ Min, int l, int b, float*
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   constexpr int LDW = 32 * EP;                       // floats per column (W or V)
-  constexpr int NB = kBlockNb, C = kClusterCtas;
+  constexpr int NB = 2 * C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* S = reinterpret_cast<float*>(smem_raw);     // [buffer 2][slot 2][column b][W, V][LDW]
   __shared__ int s_flag[2], s_big[2];                // used in CTA 0, by sweep parity
@@ -1073,33 +1081,42 @@ inline int sweep_cluster_ep(int l) {
   return need <= 10 ? need : 0;
 }
 
-// block-cyclic cluster sweep: b = ceil(l / 32) columns per block, 16 lanes
-// per pair, (b rounded up to even) pairs per CTA at once
-inline int block_cluster_b(int l) { return (l + kBlockNb - 1) / kBlockNb; }
-inline size_t block_cluster_smem(int l) {
-  return (size_t)2 * 2 * block_cluster_b(l) * 2 * 32 * std::max(1, sweep_cluster_ep(l)) * sizeof(float);
+// block-cyclic cluster sweep on C CTAs: b = ceil(l / 2C) columns per block,
+// 16 lanes per pair, (b rounded up to even) pairs per CTA at once.  The
+// cluster has 16 CTAs, or 8 (SORSVD_JACOBI_CLUSTER=8: half the block
+// rounds and exchanges per sweep, twice the columns per local round) when
+// its blocks fit in shared memory.
+inline int block_cluster_b(int l, int C = kClusterCtas) { return (l + 2 * C - 1) / (2 * C); }
+inline size_t block_cluster_smem(int l, int C = kClusterCtas) {
+  return (size_t)2 * 2 * block_cluster_b(l, C) * 2 * 32 * std::max(1, sweep_cluster_ep(l)) * sizeof(float);
+}
+inline int block_cluster_ctas(int l) {
+  static const int env = [] { const char* v = std::getenv("SORSVD_JACOBI_CLUSTER"); return v ? std::atoi(v) : 16; }();
+  if (env == 8 && block_cluster_smem(l, 8) <= kSweepSmemMax && 16 * (block_cluster_b(l, 8) + 1) <= 352) return 8;
+  return 16;
 }
 
 cudaError_t launch_block_cluster(const double* M, int l, float* vout, DeviceStatus* status, cudaStream_t st) {
-  const int ep = sweep_cluster_ep(l), b = block_cluster_b(l);
-  const size_t smem = block_cluster_smem(l);
+  const int C = block_cluster_ctas(l);
+  const int ep = sweep_cluster_ep(l), b = block_cluster_b(l, C);
+  const size_t smem = block_cluster_smem(l, C);
   const int nt = 16 * (b + (b & 1));
   if (!ep || nt > 352 || smem > kSweepSmemMax) return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(kClusterCtas, 1, 1);
+  cfg.gridDim = dim3(C, 1, 1);
   cfg.blockDim = dim3(nt, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = kClusterCtas;
+  attr[0].val.clusterDim.x = C;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
 #define BLSWEEP(E)                                                                                  \
   {                                                                                                 \
-    auto kern = jacobi_block_cluster_kernel<E>;                                                     \
+    auto kern = C == 8 ? jacobi_block_cluster_kernel<E, 8> : jacobi_block_cluster_kernel<E, 16>;    \
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);  \
     if (e == cudaSuccess)                                                                           \
       e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);       \
