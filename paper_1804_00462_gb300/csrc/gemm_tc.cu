@@ -800,7 +800,7 @@ int env_int(const char* name, int dflt) {
 constexpr uint32_t kSmemBudget = 220u * 1024u;
 
 // Shape of a launch for a given (KA, MT); stages = 0 when it does not fit.
-TcParams shape(int elt, int64_t M, int64_t N, int64_t K, int KA, int MT) {
+TcParams shape(int elt, int64_t M, int64_t N, int64_t K, int KA, int MT, int bst = 0) {
   TcParams P{};
   P.M = M; P.K = K; P.N = (int)N;
   P.Npad = (int)((N + 15) / 16 * 16);
@@ -843,7 +843,7 @@ TcParams shape(int elt, int64_t M, int64_t N, int64_t K, int KA, int MT) {
   // a B stage larger than the A stage (16-bit operands, N > 128): one more
   // (split mode: a B stage holds hi and lo, twice the A stage)
   P.bstages = (envB >= 2 && envB <= 4) ? envB
-              : ((elt < 2 && P.b_bytes > P.a_bytes) || (elt == 3 && P.lo_tmem) ? 3 : 2);
+              : bst ? bst : ((elt < 2 && P.b_bytes > P.a_bytes) || (elt == 3 && P.lo_tmem) ? 3 : 2);
   const uint32_t left = kSmemBudget > P.bstages * P.bstage_bytes ? kSmemBudget - P.bstages * P.bstage_bytes : 0;
   P.stages = (int)std::min<uint32_t>(12u, left / P.stage_bytes);
   if (MT * P.Npad > 512 || cols > 512) P.stages = 0;
@@ -872,6 +872,14 @@ TcParams tc_plan(int elt, int64_t M, int64_t N, int64_t K) {
   for (int KA = 2; KA <= kMaxKA; ++KA) {
     TcParams P = shape(elt, M, N, K, KA, MT);
     if (P.stages >= 4) best = P;
+  }
+  // 16-bit operands with N > 256 (two N-chunks, 36 KB of B per K atom): two
+  // K atoms per stage in a two-stage B ring (two stages of A), which halves
+  // the stage hand-offs; measured on the 65536 x 16384 workload
+  // (l = 266): 3.09 -> 2.92 ms for the six passes
+  if (best.KA == 1 && best.nch == 2 && envKA == 0 && env_int("SORSVD_TC_BSTAGES", 0) == 0) {
+    TcParams P = shape(elt, M, N, K, 2, MT, 2);
+    if (P.stages >= 2) best = P;
   }
   return best;
 }

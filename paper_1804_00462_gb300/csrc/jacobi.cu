@@ -51,26 +51,12 @@ __device__ __forceinline__ int rr_player(int pos, int round, int N) {
 
 // Jacobi rotation (c, s) that orthogonalises two columns with squared norms
 // al, be and inner product ga: t = sign(z) / (|z| + sqrt(1 + z^2)),
-// z = (be - al) / (2 ga), c = 1 / sqrt(1 + t^2), s = c t.  With d = be - al
-// and g = 2 ga in [1e-18, 1e18] the same tangent is formed as
-// t = sign(d) g / (|d| + sqrt(d^2 + g^2)) (multiplied through by |g|: one
-// square root and one reciprocal on the dependent chain instead of two
-// divisions and a square root); outside that range, where d^2 + g^2 would
-// leave fp32, the z form (for |z| beyond 1e18, 1 + z^2 overflows, t becomes
-// 0 and the pair is left as is).
+// z = (be - al) / (2 ga), c = 1 / sqrt(1 + t^2), s = c t.  For |z| beyond
+// 1e18 (fp32) 1 + z^2 overflows, t becomes 0 and the pair is left as is.
 __device__ __forceinline__ void rotation(float al, float be, float ga, float* c, float* s) {
-  const float d = be - al, g = 2.f * ga;
-  const float m = fmaxf(fabsf(d), fabsf(g));
-  float t;
-  if (m < 1e18f && m > 1e-18f) {
-    const float h = fmaf(d, d, g * g);
-    const float r = h * rsqrtf(h);
-    t = __fdividef(copysignf(1.f, d) * g, fabsf(d) + r);
-  } else {
-    const float z = __fdividef(d, g);
-    const float az = fabsf(z);
-    t = copysignf(__fdividef(1.f, az + sqrtf(fmaf(az, az, 1.f))), z);
-  }
+  const float z = __fdividef(be - al, 2.f * ga);
+  const float az = fabsf(z);
+  const float t = copysignf(__fdividef(1.f, az + sqrtf(fmaf(az, az, 1.f))), z);
   const float cs = rsqrtf(fmaf(t, t, 1.f));
   *c = cs;
   *s = cs * t;
@@ -167,15 +153,7 @@ __device__ __forceinline__ void jacobi_sweep_body(const double* __restrict__ Min
         if (!(ga * ga > tol2 * al * be)) continue;
         if (ga * ga > big2 * al * be) big_local = 1;
         J cs, sn;
-        if (sizeof(J) == 8) {
-          // binary64: one lane forms the rotation (tens of FP64 operations at
-          // this GPU's FP64 rate), the group takes it by shuffle
-          if (gl == 0) rotation(al, be, ga, &cs, &sn);
-          cs = __shfl_sync(gmask, cs, grp * 8);
-          sn = __shfl_sync(gmask, sn, grp * 8);
-        } else {
-          rotation(al, be, ga, &cs, &sn);
-        }
+        rotation(al, be, ga, &cs, &sn);
         J* vp = V + oa;
         J* vq = V + ob;
 #pragma unroll
@@ -627,12 +605,6 @@ __device__ __forceinline__ int rotate_pair16(float* cx, float* cy, int gl, unsig
     be2 = __ffma2_rn(y[e], y[e], be2);
     ga2 = __ffma2_rn(x[e], y[e], ga2);
   }
-  // the V columns load while the inner products reduce
-#pragma unroll
-  for (int e = 0; e < EP; ++e) {
-    u[e] = vx[gl + 16 * e];
-    v[e] = vy[gl + 16 * e];
-  }
   float al = al2.x + al2.y, be = be2.x + be2.y, ga = ga2.x + ga2.y;
 #pragma unroll
   for (int o = 8; o > 0; o >>= 1) {
@@ -645,6 +617,11 @@ __device__ __forceinline__ int rotate_pair16(float* cx, float* cy, int gl, unsig
   float cs, sn;
   rotation(al, be, ga, &cs, &sn);
   const float2 c2 = make_float2(cs, cs), s2 = make_float2(sn, sn), ns2 = make_float2(-sn, -sn);
+#pragma unroll
+  for (int e = 0; e < EP; ++e) {
+    u[e] = vx[gl + 16 * e];
+    v[e] = vy[gl + 16 * e];
+  }
 #pragma unroll
   for (int e = 0; e < EP; ++e) {
     wx[gl + 16 * e] = __ffma2_rn(c2, x[e], __fmul2_rn(ns2, y[e]));
