@@ -24,6 +24,10 @@ columns of T2 from collapsing onto the leading singular direction.
 Q1^T T1 (Q2^T T2_prev)^+ (the second core option of Algorithm 3), where T2_prev
 is the T2 that entered the last pass (the "non-updated" T2, Sec. III).
 
+``rsvd`` and ``tsrsvd`` are the paper's comparison methods on the same
+steps: the randomized SVD (Algorithm 1) and the two-sided randomized SVD
+(Algorithm 2).
+
 The GEMMs are numpy matmul calls (a library primitive); QR and SVD are the
 oracle's own Householder and one-sided Jacobi routines.
 """
@@ -84,6 +88,60 @@ def sorsvd(A: np.ndarray, k: int, p: int, q: int, seed: int, *,
                     sigma_core=st, sweeps=sweeps)
         return U, S, V, info
     return U, S, V
+
+
+def rsvd(A: np.ndarray, k: int, p: int, q: int, seed: int, *, omega_dtype: str = "f64",
+         mode: str = "stabilised"):
+    """Randomized SVD, R-SVD (Algorithm 1, Sec. II), cut to rank k.
+
+    Omega (n x l) is the same Gaussian test matrix as SOR-SVD's;
+    Y = (A A^T)^q A Omega; Y = Q R; B = Q^T A (l x n); B = U~ S W^T (SVD);
+    A ~ (Q U~_k) S_k W_k^T.  ``mode="stabilised"`` replaces the running
+    product by the Q factor of its QR decomposition before each multiplication
+    by A^T (Lemma 1: range(Q) is unchanged in exact arithmetic).
+    The SVD of the wide B is taken from the one-sided Jacobi SVD of B^T
+    (n x l): B^T = W S Z^T gives B = Z S W^T.
+    Returns (U m x k, S k, V n x k)."""
+    A = np.asanyarray(A, dtype=np.float64)
+    m, n = A.shape
+    l = k + p
+    if not (1 <= k <= l <= min(m, n)) or q < 0:
+        raise ValueError(f"need 1 <= k <= l=k+p <= min(m,n), q >= 0; got k={k}, p={p}, q={q}, shape={A.shape}")
+    omega = gaussian_matrix(n, l, seed, 0, omega_dtype)
+    Y = A @ omega
+    for _ in range(q):
+        if mode == "stabilised":
+            Y, _ = householder_qr(Y)
+        elif mode != "literal":
+            raise ValueError(f"unknown mode {mode!r}")
+        Y = A @ (A.T @ Y)
+    Q, _ = householder_qr(Y)
+    B = Q.T @ A
+    W, s, Z, _ = jacobi_svd(B.T)
+    return Q @ Z[:, :k], s[:k].copy(), W[:, :k]
+
+
+def tsrsvd(A: np.ndarray, k: int, p: int, seed: int, *, omega_dtype: str = "f64"):
+    """Two-sided randomized SVD, TSR-SVD (Algorithm 2, Sec. II), cut to rank k.
+
+    Psi1 (n x l) is SOR-SVD's Gaussian test matrix (Philox stream 0) and Psi2
+    (m x l) the same generator's stream 1; Y1 = A Psi1 and Y2 = A^T Psi2;
+    Y1 = Q1 R1, Y2 = Q2 R2; B_approx = Q1^T Y1 (Q2^T Psi1)^+; its SVD
+    U~ S V~^T gives A ~ (Q1 U~_k) S_k (Q2 V~_k)^T.  Returns (U, S, V)."""
+    A = np.asanyarray(A, dtype=np.float64)
+    m, n = A.shape
+    l = k + p
+    if not (1 <= k <= l <= min(m, n)):
+        raise ValueError(f"need 1 <= k <= l=k+p <= min(m,n); got k={k}, p={p}, shape={A.shape}")
+    psi1 = gaussian_matrix(n, l, seed, 0, omega_dtype)
+    psi2 = gaussian_matrix(m, l, seed, 1, omega_dtype)
+    Y1 = A @ psi1
+    Y2 = A.T @ psi2
+    Q1, _ = householder_qr(Y1)
+    Q2, _ = householder_qr(Y2)
+    Bm = (Q1.T @ Y1) @ np.linalg.pinv(Q2.T @ psi1)
+    Ut, st, Vt, _ = jacobi_svd(Bm)
+    return Q1 @ Ut[:, :k], st[:k].copy(), Q2 @ Vt[:, :k]
 
 
 def flop_count(m: int, n: int, k: int, p: int, q: int) -> float:
