@@ -81,6 +81,28 @@ typedef enum {
 #define SORSVD_FLAG_FIXED_TILES   0x10u /* batched plans: no autotuning, every
                                           grouped product on the 128 x 64
                                           tile shape */
+#define SORSVD_FLAG_RSVD          0x20u /* sorsvd_run / sorsvd_run_host: the
+                                          randomized SVD (R-SVD, Algorithm 1,
+                                          Sec. II) on the same kernels:
+                                          Y = (A A^T)^q A Omega, Y = Q R,
+                                          B = Q^T A (the last A^T pass),
+                                          rank-k truncation of B's SVD; B's SVD
+                                          is that of M = (A^T Q)^T Q2 with Q2
+                                          the QR factor of A^T Q (no core pass:
+                                          2q + 2 passes over A).  Not with
+                                          LITERAL_POWER, TWO_PASS or TSR. */
+#define SORSVD_FLAG_TSR           0x40u /* sorsvd_run / sorsvd_run_host: the
+                                          two-sided randomized SVD (TSR-SVD,
+                                          Algorithm 2, Sec. II): Psi1 = Omega,
+                                          Psi2 (m x l) the same Philox
+                                          generator's stream 1, Y1 = A Psi1,
+                                          Y2 = A^T Psi2, QR of both,
+                                          B_approx = Q1^T Y1 (Q2^T Psi1)^+,
+                                          rank-k truncation of its SVD.  Needs
+                                          q = 0; not with LITERAL_POWER,
+                                          TWO_PASS or RSVD.  Needs the same
+                                          flag in sorsvd_workspace_size (as
+                                          RSVD and TWO_PASS). */
 
 /* Largest sketch width l = k + p supported (the small l x l factorisations
  * run in one thread block with the factor in shared memory). */

@@ -169,7 +169,7 @@ Layout make_layout(int64_t m, int64_t n, int l, int dt, unsigned flags = 0) {
   L.jwork = take(std::max(jacobi_work_bytes(l), polar_scratch_bytes(l)));
   L.ldk = (l + 31) / 32 * 32;
   L.bsplit = dt != SORSVD_F64 ? take((size_t)2 * L.ldk * L.ldk * sizeof(float)) : 0;
-  if (flags & SORSVD_FLAG_TWO_PASS) {
+  if (flags & (SORSVD_FLAG_TWO_PASS | SORSVD_FLAG_RSVD | SORSVD_FLAG_TSR)) {
     L.t1s = take((size_t)L.ldm * l * acc);
     L.t2s = take((size_t)L.ldn * l * acc);
     L.tp = take((size_t)5 * l * l * 8);
@@ -532,6 +532,17 @@ int core_impl(const Ctx& c, const void* A, int64_t m, int64_t n, int64_t lda, un
 
 int check_dtype(int dt) { return (dt >= SORSVD_F64 && dt <= SORSVD_F16) ? SORSVD_OK : SORSVD_ERR_DTYPE; }
 
+// the method flags of sorsvd_run / sorsvd_run_host: at most one of
+// TWO_PASS, RSVD and TSR; RSVD and TSR need the stabilised loop; TSR is a
+// single round (q = 0)
+bool method_flags_ok(unsigned flags, int q) {
+  const int methods = !!(flags & SORSVD_FLAG_TWO_PASS) + !!(flags & SORSVD_FLAG_RSVD) + !!(flags & SORSVD_FLAG_TSR);
+  if (methods > 1) return false;
+  if ((flags & (SORSVD_FLAG_RSVD | SORSVD_FLAG_TSR)) && (flags & SORSVD_FLAG_LITERAL_POWER)) return false;
+  if ((flags & SORSVD_FLAG_TSR) && q != 0) return false;
+  return true;
+}
+
 int check_ws(void* ws, size_t ws_bytes, const Layout& L) {
   if (!ws) return SORSVD_ERR_WORKSPACE;
   if (((uintptr_t)ws) % kAlign) return SORSVD_ERR_WORKSPACE;
@@ -657,12 +668,14 @@ int core_two_pass(const Ctx& c, int64_t m, int64_t n, int l, double* M) {
 // transposed copy of A are in place: the power loop, the QR step, the core,
 // its truncated SVD and the output assembly, all queued on c.st.
 int solve(const Ctx& c, const void* A, int64_t m, int64_t n, int64_t lda, int k, int l, int q, unsigned flags,
-          void* U, int64_t ldu, void* S, void* V, int64_t ldv) {
+          uint64_t seed, void* U, int64_t ldu, void* S, void* V, int64_t ldv) {
   const Layout& L = c.L;
   const int dtype = c.dt;
   const int adt = c.f64 ? SORSVD_F64 : SORSVD_F32;
   const bool h16 = dtype_is_16(dtype);
   const bool two = (flags & SORSVD_FLAG_TWO_PASS) != 0;
+  const bool rsvd = (flags & SORSVD_FLAG_RSVD) != 0;
+  const bool tsr = (flags & SORSVD_FLAG_TSR) != 0;
   auto orth1 = [&](int np, void* o16, void** res) {
     return orth(c, c.at(L.t1), m, L.ldm, l, np, first_shift(dtype), o16, L.ldm, res);
   };
@@ -670,7 +683,27 @@ int solve(const Ctx& c, const void* A, int64_t m, int64_t n, int64_t lda, int k,
     return orth(c, c.at(L.t2), n, L.ldn, l, np, first_shift(dtype), o16, L.ldn, res);
   };
   int r;
-  if (flags & SORSVD_FLAG_LITERAL_POWER) {
+  if (tsr) {
+    // Algorithm 2 (TSR-SVD): Y1 = A Psi1 with Psi1 = Omega (in t2op) and
+    // Y2 = A^T Psi2 with Psi2 (m x l) from Philox stream 1, one round; QR of
+    // both; B_approx = Q1^T Y1 (Q2^T Psi1)^+ by the two-pass core, with Y1
+    // and Psi1 kept before the QR
+    const int kc = dtype == SORSVD_F32 ? K_PASS_SPLIT : K_PASS;
+    void* psi2 = h16 ? c.at(L.t1op) : c.at(L.t1);
+    LAUNCH(K_GAUSSIAN, launch_gaussian(psi2, m, l, L.ldm, seed, 1, dtype, c.st));
+    r = save_t2prev(c, c.at(L.t2op), L.ldn, n, l);
+    if (r) return r;
+    r = pass(c, kc, true, n, l, m, A, lda, psi2, L.ldm, h16 ? dtype : adt, c.at(L.t2), L.ldn, nullptr, 0, true);
+    if (r) return r;
+    r = pass(c, kc, false, m, l, n, A, lda, c.at(L.t2op), L.ldn, h16 ? dtype : adt, c.at(L.t1), L.ldm, nullptr, 0,
+             true);
+    if (r) return r;
+    LAUNCH(K_MISC, launch_copy2d(c.at(L.t1), L.ldm, c.at(L.t1s), L.ldm, m, l, acc_size(dtype), c.st));
+    r = orth1(3, nullptr, nullptr);
+    if (r) return r;
+    r = orth2(3, nullptr, nullptr);
+    if (r) return r;
+  } else if (flags & SORSVD_FLAG_LITERAL_POWER) {
     // Algorithm 3 as printed: the sketches are orthonormalised only at the end
     for (int i = 1; i <= q + 1; ++i) {
       if (i > 1 && h16)
@@ -723,14 +756,26 @@ int solve(const Ctx& c, const void* A, int64_t m, int64_t n, int64_t lda, int k,
       r = pass(c, last ? kc : K_PASS, true, n, l, m, A, lda, y1, L.ldm, h16 ? dtype : adt, c.at(L.t2), L.ldn,
                nullptr, 0, last);
       if (r) return r;
+      // R-SVD keeps B^T = A^T Q1 (the last T2) before its QR
+      if (last && rsvd)
+        LAUNCH(K_MISC, launch_copy2d(c.at(L.t2), L.ldn, c.at(L.t2s), L.ldn, n, l, acc_size(dtype), c.st));
       void* q2 = nullptr;
       r = orth2(np, (!last && h16) ? c.at(L.t2op) : nullptr, last ? nullptr : &q2);
       if (r) return r;
       x2 = h16 ? c.at(L.t2op) : (q2 ? q2 : c.at(L.t2));
     }
   }
-  r = two ? core_two_pass(c, m, n, l, (double*)c.at(L.M))
-          : core_impl(c, A, m, n, lda, flags, c.at(L.t1), L.ldm, c.at(L.t2), L.ldn, l, (double*)c.at(L.M), l);
+  if (two || tsr) {
+    r = core_two_pass(c, m, n, l, (double*)c.at(L.M));
+  } else if (rsvd) {
+    // Algorithm 1 (R-SVD): B = Q1^T A = (A^T Q1)^T, whose rows lie in
+    // range(Q2) = range(A^T Q1): B = M Q2^T with M = (A^T Q1)^T Q2 (l x l),
+    // so the SVD of B is that of M with its right factor multiplied by Q2 -
+    // no pass over A beyond the sketch's (2q + 2 in all)
+    r = cross_gram(c, c.at(L.t2s), L.ldn, c.at(L.t2), L.ldn, n, l, (double*)c.at(L.M), l);
+  } else {
+    r = core_impl(c, A, m, n, lda, flags, c.at(L.t1), L.ldm, c.at(L.t2), L.ldn, l, (double*)c.at(L.M), l);
+  }
   if (r) return r;
   LAUNCH(K_JACOBI, launch_jacobi((const double*)c.at(L.M), l, k, c.f64, c.at(L.Ut), c.at(L.Vt), S, c.f64,
                                   c.at(L.jwork), c.status(), c.st));
@@ -919,7 +964,10 @@ int sorsvd_run(const void* A, int64_t m, int64_t n, int64_t lda, int k, int p, i
   if (!A || !U || !S || !V) return SORSVD_ERR_ARG;
   if (m < 1 || n < 1 || k < 1 || p < 0 || q < 0 || q > 1000 || lda < m || ldu < m || ldv < n)
     return SORSVD_ERR_ARG;
-  if (flags & ~(SORSVD_FLAG_LITERAL_POWER | SORSVD_FLAG_REFINE | SORSVD_FLAG_TWO_PASS)) return SORSVD_ERR_ARG;
+  if (flags & ~(SORSVD_FLAG_LITERAL_POWER | SORSVD_FLAG_REFINE | SORSVD_FLAG_TWO_PASS | SORSVD_FLAG_RSVD |
+                SORSVD_FLAG_TSR))
+    return SORSVD_ERR_ARG;
+  if (!method_flags_ok(flags, q)) return SORSVD_ERR_ARG;
   const int l = k + p;
   if (l > std::min(m, n)) return SORSVD_ERR_ARG;
   if (l > max_l(dtype)) return SORSVD_ERR_UNSUPPORTED;
@@ -939,7 +987,7 @@ int sorsvd_run(const void* A, int64_t m, int64_t n, int64_t lda, int k, int p, i
     if (r) return r;
     LAUNCH(K_GAUSSIAN, launch_gaussian(c.at(L.t2op), n, l, L.ldn, seed, 0, dtype, c.st));
   }
-  return solve(c, A, m, n, lda, k, l, q, flags, U, ldu, S, V, ldv);
+  return solve(c, A, m, n, lda, k, l, q, flags, seed, U, ldu, S, V, ldv);
 }
 
 int sorsvd_run_host(const void* A, int64_t m, int64_t n, int64_t lda, int k, int p, int q, uint64_t seed, int dtype,
@@ -949,8 +997,10 @@ int sorsvd_run_host(const void* A, int64_t m, int64_t n, int64_t lda, int k, int
   if (!A || !U || !S || !V) return SORSVD_ERR_ARG;
   if (m < 1 || n < 1 || k < 1 || p < 0 || q < 0 || q > 1000 || lda < m || ldu < m || ldv < n)
     return SORSVD_ERR_ARG;
-  if (flags & ~(SORSVD_FLAG_LITERAL_POWER | SORSVD_FLAG_REFINE | SORSVD_FLAG_HOST_IO | SORSVD_FLAG_TWO_PASS))
+  if (flags & ~(SORSVD_FLAG_LITERAL_POWER | SORSVD_FLAG_REFINE | SORSVD_FLAG_HOST_IO | SORSVD_FLAG_TWO_PASS |
+                SORSVD_FLAG_RSVD | SORSVD_FLAG_TSR))
     return SORSVD_ERR_ARG;
+  if (!method_flags_ok(flags, q)) return SORSVD_ERR_ARG;
   const int l = k + p;
   if (l > std::min(m, n)) return SORSVD_ERR_ARG;
   if (l > max_l(dtype)) return SORSVD_ERR_UNSUPPORTED;
@@ -969,7 +1019,7 @@ int sorsvd_run_host(const void* A, int64_t m, int64_t n, int64_t lda, int k, int
   r = gaussian_beside(c, c.at(L.t2op), n, l, L.ldn, seed, dtype,
                       [&] { return upload_a(c, A, lda, m, n, Ad, H.lda); });
   if (r) return r;
-  r = solve(c, Ad, m, n, H.lda, k, l, q, flags & ~SORSVD_FLAG_HOST_IO, Ud, H.ldu, Sd, Vd, H.ldv);
+  r = solve(c, Ad, m, n, H.lda, k, l, q, flags & ~SORSVD_FLAG_HOST_IO, seed, Ud, H.ldu, Sd, Vd, H.ldv);
   if (r) return r;
   const size_t acc = acc_size(dtype);
   CK(cudaMemcpy2DAsync(U, (size_t)ldu * acc, Ud, (size_t)H.ldu * acc, (size_t)m * acc, (size_t)k,

@@ -25,6 +25,8 @@ FLAG_LITERAL_POWER = 0x1
 FLAG_REFINE = 0x2
 FLAG_TWO_PASS = 0x8
 FLAG_FIXED_TILES = 0x10
+FLAG_RSVD = 0x20
+FLAG_TSR = 0x40
 MAX_L, MAX_L_F64 = 320, 224
 
 _TORCH_OF = {F64: torch.float64, F32: torch.float32, TF32: torch.float32, BF16: torch.bfloat16,
