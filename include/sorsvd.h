@@ -290,6 +290,40 @@ int sorsvd_gram(const float* X, int64_t ldx, const float* Y, int64_t ldy, int64_
 int sorsvd_apply(const float* X, int64_t rows, int K, int64_t ldx, const float* B, int64_t ldb, int N,
                  int upper_tri, float* Y, int64_t ldy, void* workspace, size_t ws_bytes, void* stream);
 
+/* Bounds of Sec. IV on the rank-k SOR-SVD approximation A_hat (l = k + p,
+ * q power iterations) for a matrix with singular values sigma[0..r-1]
+ * (descending, r >= k + 1; the tail beyond r is taken as zero), as an
+ * a-posteriori quality check.  Host function: no GPU, no stream.
+ *   ey_2, ey_fro:        the optimum (Theorem 1): sigma_{k+1} and
+ *                        sqrt(sum_{j>k} sigma_j^2).
+ *   thm7_upper_2 / _fro: Theorem 7, upper bound on E ||A - A_hat|| (2- and
+ *                        F-norm) over the Gaussian test matrix.
+ *   thm6_lower[j]:       Theorem 6, lower bound on E sigma_j(A_hat),
+ *                        j = 1..k (k doubles; may be NULL).
+ *   thm5_upper_2 / _fro: Theorem 5, deterministic upper bound on
+ *                        ||A - A_hat|| for a given test matrix Omega, from
+ *                        omega2_norm = ||V2^T Omega||_2 and
+ *                        omega1_pinv_norm = ||(V1^T Omega)^+||_2 (V1 the
+ *                        first k right singular vectors of A, V2 the rest);
+ *                        NaN when either is negative (unknown).
+ *   thm4_lower[j]:       Theorem 4, the deterministic lower bound for the
+ *                        same Omega (k doubles; may be NULL; NaN when the
+ *                        norms are unknown).  Its proof bounds
+ *                        sigma_j(A Q2 Q2^T); Theorem 5's tau for q > 0 is
+ *                        read as (sigma_k / sigma_{k+1}) beta.
+ * The singular values an SOR-SVD returns are lower bounds on A's (Sec. IV),
+ * so bounds evaluated on them are estimates, not guarantees.
+ * SORSVD_ERR_ARG for a null pointer, k < 1, p < 0, q < 0, r < k + 1,
+ * n < k + p, a negative or increasing sigma, or sigma_k = 0. */
+typedef struct {
+  double ey_2, ey_fro;
+  double thm5_upper_2, thm5_upper_fro;
+  double thm7_upper_2, thm7_upper_fro;
+} sorsvd_bounds_out;
+int sorsvd_bounds(const double* sigma, int r, int64_t n, int k, int p, int q,
+                  double omega2_norm, double omega1_pinv_norm, sorsvd_bounds_out* out,
+                  double* thm4_lower, double* thm6_lower);
+
 /* ---- batched SOR-SVD -------------------------------------------------------
  * Many independent problems of uneven shape (m, n, k, p, q may all differ)
  * in one sequence of grouped launches: each launch runs one stage of

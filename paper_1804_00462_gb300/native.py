@@ -368,6 +368,36 @@ def apply(X: torch.Tensor, B: torch.Tensor, upper_tri: bool = False, stream=None
     return Y, s
 
 
+class BoundsOut(C.Structure):
+    """sorsvd_bounds_out of the C header."""
+    _fields_ = [("ey_2", C.c_double), ("ey_fro", C.c_double), ("thm5_upper_2", C.c_double),
+                ("thm5_upper_fro", C.c_double), ("thm7_upper_2", C.c_double), ("thm7_upper_fro", C.c_double)]
+
+
+_lib.sorsvd_bounds.argtypes = [C.POINTER(C.c_double), _int, _i64, _int, _int, _int, C.c_double, C.c_double,
+                               C.POINTER(BoundsOut), C.POINTER(C.c_double), C.POINTER(C.c_double)]
+_lib.sorsvd_bounds.restype = _int
+
+
+def bounds(sigma, n: int, k: int, p: int, q: int, omega2_norm: float = -1.0, omega1_pinv_norm: float = -1.0):
+    """Theorems 4-7 of Sec. IV for the spectrum ``sigma`` (descending, at
+    least k + 1 values) through sorsvd_bounds (host code, no GPU).  Returns a
+    dict with ey_2, ey_fro, thm5_upper_2 / _fro, thm7_upper_2 / _fro (floats)
+    and thm4_lower, thm6_lower (lists of k floats; Theorems 4 and 5 are NaN
+    unless both Omega norms are given)."""
+    s = [float(v) for v in sigma]
+    arr = (C.c_double * len(s))(*s)
+    out = BoundsOut()
+    t4 = (C.c_double * k)()
+    t6 = (C.c_double * k)()
+    _check(_lib.sorsvd_bounds(arr, len(s), n, k, p, q, omega2_norm, omega1_pinv_norm, C.byref(out), t4, t6),
+           "sorsvd_bounds")
+    d = {f: getattr(out, f) for f, _ in BoundsOut._fields_}
+    d["thm4_lower"] = list(t4)
+    d["thm6_lower"] = list(t6)
+    return d
+
+
 # ---- batched SOR-SVD ----------------------------------------------------------
 class Problem(C.Structure):
     """sorsvd_problem of the C header."""
