@@ -688,15 +688,17 @@ int solve(const Ctx& c, const void* A, int64_t m, int64_t n, int64_t lda, int k,
     // Y2 = A^T Psi2 with Psi2 (m x l) from Philox stream 1, one round; QR of
     // both; B_approx = Q1^T Y1 (Q2^T Psi1)^+ by the two-pass core, with Y1
     // and Psi1 kept before the QR
+    // (for the fp32 and binary64 containers Omega shares its buffer with T2,
+    // so Psi1 is read from its saved copy and Psi2 waits in the T1 copy)
     const int kc = dtype == SORSVD_F32 ? K_PASS_SPLIT : K_PASS;
-    void* psi2 = h16 ? c.at(L.t1op) : c.at(L.t1);
-    LAUNCH(K_GAUSSIAN, launch_gaussian(psi2, m, l, L.ldm, seed, 1, dtype, c.st));
     r = save_t2prev(c, c.at(L.t2op), L.ldn, n, l);
     if (r) return r;
+    void* psi2 = h16 ? c.at(L.t1op) : c.at(L.t1s);
+    const void* psi1 = h16 ? c.at(L.t2op) : c.at(L.t2s);
+    LAUNCH(K_GAUSSIAN, launch_gaussian(psi2, m, l, L.ldm, seed, 1, dtype, c.st));
     r = pass(c, kc, true, n, l, m, A, lda, psi2, L.ldm, h16 ? dtype : adt, c.at(L.t2), L.ldn, nullptr, 0, true);
     if (r) return r;
-    r = pass(c, kc, false, m, l, n, A, lda, c.at(L.t2op), L.ldn, h16 ? dtype : adt, c.at(L.t1), L.ldm, nullptr, 0,
-             true);
+    r = pass(c, kc, false, m, l, n, A, lda, psi1, L.ldn, h16 ? dtype : adt, c.at(L.t1), L.ldm, nullptr, 0, true);
     if (r) return r;
     LAUNCH(K_MISC, launch_copy2d(c.at(L.t1), L.ldm, c.at(L.t1s), L.ldm, m, l, acc_size(dtype), c.st));
     r = orth1(3, nullptr, nullptr);
