@@ -262,6 +262,26 @@ int sorsvd_chol_inv(const double* G, int l, double shift_rel, int dtype, void* R
 int sorsvd_polar_inv(const double* G, int l, float* X, int* ok, void* scratch, size_t scratch_bytes,
                      void* stream);
 
+/* Out-of-core SOR-SVD (Algorithm 3 with the stabilised power loop, as
+ * sorsvd_run without flags) for an A that stays in HOST memory, e.g. one
+ * larger than the device's memory: the paper counts the method's cost in
+ * passes over A (Sec. III, 2q + 3 passes), and every pass here streams A
+ * to the device in blocks of block_rows rows, copying block b + 1 while the
+ * tensor cores work on block b (two device block buffers).  T1 = A X and
+ * W = A Q2 are formed block by block; T2 = A^T Q1 as the sum of the blocks'
+ * products (so its rounding differs from sorsvd_run's).  A: column-major
+ * m x n host array (lda >= m) of the dtype's element type; page-locked
+ * memory (cudaHostAlloc / cudaHostRegister) lets the copies run
+ * asynchronously, pageable memory works at lower speed.  U, S, V are device
+ * outputs as in sorsvd_run; the workspace (device) holds the sketches, the
+ * two blocks and the solve's scratch: sorsvd_streamed_workspace_size bytes,
+ * 256-byte aligned.  A must stay valid and unchanged until the stream has
+ * finished the call. */
+size_t sorsvd_streamed_workspace_size(int64_t m, int64_t n, int k, int p, int dtype, int64_t block_rows);
+int sorsvd_run_streamed(const void* A, int64_t m, int64_t n, int64_t lda, int k, int p, int q, uint64_t seed,
+                        int dtype, int64_t block_rows, void* U, int64_t ldu, void* S, void* V, int64_t ldv,
+                        void* workspace, size_t ws_bytes, void* stream);
+
 /* Tall-skinny fp32 products of the QR step (CholeskyQR of a sketch T:
  * G = T^T T, then Q = T R^{-1}; Sec. III) and of the output assembly
  * (U = Q1 U~_k, V = Q2 V~_k; Algorithm 3), computed as sorsvd_run computes

@@ -459,7 +459,23 @@ __global__ void add_f64_kernel(const double* __restrict__ x, int64_t ldx, double
     y[i + j * ldy] += x[i + j * ldx];
   }
 }
+__global__ void add_f32_kernel(const float* __restrict__ x, int64_t ldx, float* __restrict__ y, int64_t ldy,
+                               int64_t rows, int64_t cols) {
+  const int64_t total = rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / rows, i = e - j * rows;
+    y[i + j * ldy] += x[i + j * ldx];
+  }
+}
 }  // namespace
+
+cudaError_t launch_add_f32(const float* x, int64_t ldx, float* y, int64_t ldy, int64_t rows, int64_t cols,
+                           cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  add_f32_kernel<<<grid_for(rows * cols), 256, 0, st>>>(x, ldx, y, ldy, rows, cols);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_add_f64(const double* x, int64_t ldx, double* y, int64_t ldy, int64_t rows, int64_t cols,
                            cudaStream_t st) {

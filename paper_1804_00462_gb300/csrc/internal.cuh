@@ -99,8 +99,10 @@ cudaError_t launch_convert_f32(const float* x, int64_t ldx, int64_t rows, int64_
 // At (cols x rows, ldt) = A^T of a column-major fp32 matrix
 cudaError_t launch_transpose_f32(const float* A, int64_t lda, int64_t rows, int64_t cols, float* At, int64_t ldt,
                                  cudaStream_t st);
-// y += x (binary64, rows x cols, leading dimensions)
+// y += x (binary64 / fp32, rows x cols, leading dimensions)
 cudaError_t launch_add_f64(const double* x, int64_t ldx, double* y, int64_t ldy, int64_t rows, int64_t cols,
+                           cudaStream_t st);
+cudaError_t launch_add_f32(const float* x, int64_t ldx, float* y, int64_t ldy, int64_t rows, int64_t cols,
                            cudaStream_t st);
 // copy with leading dimensions (same element size)
 cudaError_t launch_copy2d(const void* x, int64_t ldx, void* y, int64_t ldy,

@@ -89,7 +89,9 @@ struct Layout {
   bool has_at;           // fp32 containers: A^T kept for the products A X
 };
 
-Layout make_layout(int64_t m, int64_t n, int l, int dt, unsigned flags = 0) {
+// at_rows: the rows of A the transposed copy holds (m; a block of rows for
+// the streamed entry point)
+Layout make_layout(int64_t m, int64_t n, int l, int dt, unsigned flags = 0, int64_t at_rows = -1) {
   Layout L{};
   const size_t acc = acc_size(dt), op = dtype_size(dt);
   const bool h16 = dtype_is_16(dt);
@@ -105,7 +107,7 @@ Layout make_layout(int64_t m, int64_t n, int l, int dt, unsigned flags = 0) {
   // all-zero products on GB300), so the fp32-container dtypes keep a
   // transposed copy A^T (n x m, ld ldn) for T1 = A T2 and W = A Q2.
   L.has_at = (dt == SORSVD_F32 || dt == SORSVD_TF32);
-  L.at = L.has_at ? take((size_t)L.ldn * m * 4) : 0;
+  L.at = L.has_at ? take((size_t)L.ldn * (at_rows >= 0 ? at_rows : m) * 4) : 0;
   L.t2op = h16 ? take((size_t)L.ldn * l * op) : 0;
   L.t2 = take((size_t)L.ldn * l * acc);
   if (!h16) L.t2op = L.t2;
@@ -788,6 +790,143 @@ int solve(const Ctx& c, const void* A, int64_t m, int64_t n, int64_t lda, int k,
   return SORSVD_OK;
 }
 
+// ---- out-of-core A: host memory, streamed to the device once per pass -----
+// The passes over A (Sec. III counts them: 2q + 3 for Algorithm 3) read A
+// from host memory in blocks of rows, two device block buffers in
+// alternation: the copy of block b + 1 (copy stream) overlaps the products of
+// block b (caller's stream).  T1 = A X and W = A Q2 are row-blockwise;
+// T2 = A^T Q1 is the sum of the blocks' A_b^T Q1_b.  The sketches, the QR
+// step, the core and the small SVD stay on the device as in sorsvd_run.
+struct StreamLayout {
+  Layout L;              // the solve's regions; the transposed copy holds one block
+  size_t blk[2], t2p, total;
+  int64_t rows, ldb;     // rows per block, leading dimension of the device blocks
+};
+
+StreamLayout stream_layout(int64_t m, int64_t n, int l, int dt, int64_t block_rows) {
+  StreamLayout S{};
+  S.rows = std::max<int64_t>(1, std::min(block_rows, m));
+  S.L = make_layout(m, n, l, dt, 0, S.rows);
+  S.ldb = pad16(S.rows);
+  size_t off = S.L.total;
+  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
+  const size_t blk_bytes = (size_t)S.ldb * n * dtype_size(dt);
+  S.blk[0] = take(blk_bytes);
+  S.blk[1] = take(blk_bytes);
+  S.t2p = take((size_t)S.L.ldn * l * acc_size(dt));
+  S.total = off;
+  return S;
+}
+
+// One pass over A: `work(r0, rows, block, ldb)` queues the products of block
+// [r0, r0 + rows) on c.st once its copy has landed.
+template <typename Work>
+int stream_blocks(const Ctx& c, const StreamLayout& SL, const void* Ah, int64_t lda, int64_t m, int64_t n, Work work) {
+  const size_t esz = dtype_size(c.dt);
+  cudaStream_t cs = side_stream(1);
+  if (!cs) cs = c.st;
+  cudaEvent_t ev[5] = {};                        // ready[2], freed[2], start
+  for (cudaEvent_t& e : ev)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      for (cudaEvent_t& f : ev)
+        if (f) cudaEventDestroy(f);
+      return SORSVD_ERR_CUDA;
+    }
+  int r = SORSVD_OK;
+  // the copies start after what is already queued on c.st (earlier readers of the buffers)
+  if (cudaEventRecord(ev[4], c.st) != cudaSuccess || cudaStreamWaitEvent(cs, ev[4], 0) != cudaSuccess)
+    r = SORSVD_ERR_CUDA;
+  const int64_t nb = (m + SL.rows - 1) / SL.rows;
+  for (int64_t b = 0; b < nb && !r; ++b) {
+    const int i = (int)(b & 1);
+    const int64_t r0 = b * SL.rows, rows = std::min<int64_t>(SL.rows, m - r0);
+    void* blk = c.at(SL.blk[i]);
+    if (b >= 2 && cudaStreamWaitEvent(cs, ev[2 + i], 0) != cudaSuccess) { r = SORSVD_ERR_CUDA; break; }
+    if (cudaMemcpy2DAsync(blk, (size_t)SL.ldb * esz, (const char*)Ah + (size_t)r0 * esz, (size_t)lda * esz,
+                          (size_t)rows * esz, (size_t)n, cudaMemcpyHostToDevice, cs) != cudaSuccess ||
+        cudaEventRecord(ev[i], cs) != cudaSuccess || cudaStreamWaitEvent(c.st, ev[i], 0) != cudaSuccess) {
+      r = SORSVD_ERR_CUDA;
+      break;
+    }
+    r = work(r0, rows, blk, SL.ldb);
+    if (!r && cudaEventRecord(ev[2 + i], c.st) != cudaSuccess) r = SORSVD_ERR_CUDA;
+  }
+  for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  return r;
+}
+
+// Algorithm 3 with the stabilised power loop (as solve() without method
+// flags), every pass over A streamed from host memory.
+int solve_streamed(const Ctx& c, const StreamLayout& SL, const void* Ah, int64_t m, int64_t n, int64_t lda, int k,
+                   int l, int q, void* U, int64_t ldu, void* S, void* V, int64_t ldv) {
+  const Layout& L = c.L;
+  const int dtype = c.dt;
+  const int adt = c.f64 ? SORSVD_F64 : SORSVD_F32;
+  const bool h16 = dtype_is_16(dtype);
+  const size_t acc = acc_size(dtype);
+  const int kc = dtype == SORSVD_F32 ? K_PASS_SPLIT : K_PASS;
+  void* t1op = h16 ? c.at(L.t1op) : c.at(L.t1);
+  const void* x2 = c.at(L.t2op);
+  int r;
+  for (int i = 1; i <= q + 1; ++i) {
+    const bool last = (i == q + 1);
+    const int np = last ? 3 : 1;
+    const int kind = last ? kc : K_PASS;
+    // T1 = A X, a block of rows of T1 per block of A
+    r = stream_blocks(c, SL, Ah, lda, m, n, [&](int64_t r0, int64_t rows, void* blk, int64_t ldb) -> int {
+      int e = prepare_at(c, blk, rows, n, ldb);
+      if (e) return e;
+      return pass(c, kind, false, rows, l, n, blk, ldb, x2, L.ldn, h16 ? dtype : adt,
+                  (char*)c.at(L.t1) + (size_t)r0 * acc, L.ldm, nullptr, 0, last);
+    });
+    if (r) return r;
+    void* q1 = nullptr;
+    r = orth(c, c.at(L.t1), m, L.ldm, l, np, first_shift(dtype), h16 ? t1op : nullptr, L.ldm, last ? nullptr : &q1);
+    if (r) return r;
+    const char* y1 = (const char*)(h16 ? t1op : (q1 ? q1 : c.at(L.t1)));
+    const size_t ysz = h16 ? dtype_size(dtype) : acc;
+    // T2 = A^T Q1 = sum over the blocks of A_b^T Q1_b
+    r = stream_blocks(c, SL, Ah, lda, m, n, [&](int64_t r0, int64_t rows, void* blk, int64_t ldb) -> int {
+      void* out = r0 == 0 ? c.at(L.t2) : c.at(SL.t2p);
+      int e = pass(c, kind, true, n, l, rows, blk, ldb, y1 + (size_t)r0 * ysz, L.ldm, h16 ? dtype : adt, out, L.ldn,
+                   nullptr, 0, last);
+      if (e || r0 == 0) return e;
+      if (c.f64) LAUNCH(K_MISC, launch_add_f64((const double*)out, L.ldn, (double*)c.at(L.t2), L.ldn, n, l, c.st));
+      else LAUNCH(K_MISC, launch_add_f32((const float*)out, L.ldn, (float*)c.at(L.t2), L.ldn, n, l, c.st));
+      return SORSVD_OK;
+    });
+    if (r) return r;
+    void* q2 = nullptr;
+    r = orth(c, c.at(L.t2), n, L.ldn, l, np, first_shift(dtype), (!last && h16) ? c.at(L.t2op) : nullptr, L.ldn,
+             last ? nullptr : &q2);
+    if (r) return r;
+    x2 = h16 ? c.at(L.t2op) : (q2 ? q2 : c.at(L.t2));
+  }
+  // core: W = A Q2 a block of rows at a time (in tmp), then M = Q1^T W
+  const void* q2op = c.at(L.t2);
+  int q2dt = adt;
+  if (h16) {
+    LAUNCH(K_MISC, launch_convert_f32((const float*)c.at(L.t2), L.ldn, n, l, c.at(L.q2op), L.ldn, dtype, nullptr,
+                                      c.st));
+    q2op = c.at(L.q2op);
+    q2dt = dtype;
+  }
+  r = stream_blocks(c, SL, Ah, lda, m, n, [&](int64_t r0, int64_t rows, void* blk, int64_t ldb) -> int {
+    int e = prepare_at(c, blk, rows, n, ldb);
+    if (e) return e;
+    return pass(c, K_CORE, false, rows, l, n, blk, ldb, q2op, L.ldn, q2dt, (char*)c.at(L.tmp) + (size_t)r0 * acc,
+                L.ldm, nullptr, 0, !h16);
+  });
+  if (r) return r;
+  r = cross_gram(c, c.at(L.t1), L.ldm, c.at(L.tmp), L.ldm, m, l, (double*)c.at(L.M), l);
+  if (r) return r;
+  LAUNCH(K_JACOBI, launch_jacobi((const double*)c.at(L.M), l, k, c.f64, c.at(L.Ut), c.at(L.Vt), S, c.f64,
+                                  c.at(L.jwork), c.status(), c.st));
+  r = assemble(c, c.at(L.t1), L.ldm, m, l, c.at(L.Ut), k, U, ldu);
+  if (r) return r;
+  return assemble(c, c.at(L.t2), L.ldn, n, l, c.at(L.Vt), k, V, ldv);
+}
+
 }  // namespace
 
 // the status word is the first region of every workspace layout
@@ -887,6 +1026,31 @@ static Layout products_layout(int64_t rows, int l) {
   L.bsplit = take((size_t)2 * L.ldk * L.ldk * sizeof(float));
   L.total = off;
   return L;
+}
+
+size_t sorsvd_streamed_workspace_size(int64_t m, int64_t n, int k, int p, int dtype, int64_t block_rows) {
+  if (check_dtype(dtype) || m < 1 || n < 1 || k < 1 || p < 0 || block_rows < 1) return 0;
+  const int l = k + p;
+  if (l > std::min(m, n) || l > max_l(dtype)) return 0;
+  return stream_layout(m, n, l, dtype, block_rows).total;
+}
+
+int sorsvd_run_streamed(const void* A, int64_t m, int64_t n, int64_t lda, int k, int p, int q, uint64_t seed,
+                        int dtype, int64_t block_rows, void* U, int64_t ldu, void* S, void* V, int64_t ldv,
+                        void* workspace, size_t ws_bytes, void* stream) {
+  if (check_dtype(dtype)) return SORSVD_ERR_DTYPE;
+  if (!A || !U || !S || !V) return SORSVD_ERR_ARG;
+  if (m < 1 || n < 1 || k < 1 || p < 0 || q < 0 || q > 1000 || lda < m || ldu < m || ldv < n || block_rows < 1)
+    return SORSVD_ERR_ARG;
+  const int l = k + p;
+  if (l > std::min(m, n)) return SORSVD_ERR_ARG;
+  if (l > max_l(dtype)) return SORSVD_ERR_UNSUPPORTED;
+  const StreamLayout SL = stream_layout(m, n, l, dtype, block_rows);
+  if (!workspace || ((uintptr_t)workspace) % kAlign || ws_bytes < SL.total) return SORSVD_ERR_WORKSPACE;
+  Ctx c{(char*)workspace, SL.L, dtype, dtype == SORSVD_F64, (cudaStream_t)stream};
+  CK(begin_call(c));
+  LAUNCH(K_GAUSSIAN, launch_gaussian(c.at(SL.L.t2op), n, l, SL.L.ldn, seed, 0, dtype, c.st));
+  return solve_streamed(c, SL, A, m, n, lda, k, l, q, U, ldu, S, V, ldv);
 }
 
 size_t sorsvd_products_workspace_size(int64_t rows, int l) {

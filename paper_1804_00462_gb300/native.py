@@ -47,6 +47,11 @@ _lib.sorsvd_run.restype = _int
 _lib.sorsvd_run_host.argtypes = [_vp, _i64, _i64, _i64, _int, _int, _int, _u64, _int, _uint,
                                  _vp, _i64, _vp, _vp, _i64, _vp, _sz, _vp]
 _lib.sorsvd_run_host.restype = _int
+_lib.sorsvd_streamed_workspace_size.argtypes = [_i64, _i64, _int, _int, _int, _i64]
+_lib.sorsvd_streamed_workspace_size.restype = _sz
+_lib.sorsvd_run_streamed.argtypes = [_vp, _i64, _i64, _i64, _int, _int, _int, _u64, _int, _i64,
+                                     _vp, _i64, _vp, _vp, _i64, _vp, _sz, _vp]
+_lib.sorsvd_run_streamed.restype = _int
 _lib.sorsvd_get_status.argtypes = [_vp, C.POINTER(_int), C.POINTER(_int), _vp]
 _lib.sorsvd_get_status.restype = _int
 _lib.sorsvd_set_limits.argtypes = [C.c_longlong, _int]
@@ -215,6 +220,34 @@ def run_host(A: torch.Tensor, k: int, p: int, q: int, seed: int = 0, dtype=None,
                                 workspace.data_ptr(), workspace.numel(), _stream(stream)), "sorsvd_run_host")
     if trans:
         U, V = V, U
+    return U, S, V
+
+
+def run_streamed(A: torch.Tensor, k: int, p: int, q: int, seed: int = 0, dtype=None, block_rows: int = 65536,
+                 workspace: torch.Tensor | None = None, stream=None, device=None):
+    """sorsvd_run_streamed: A stays in host memory (pin it with
+    ``pin_memory()`` for asynchronous copies) and every pass streams it to
+    the device in blocks of ``block_rows`` rows.  Returns device (U, S, V)
+    as ``run`` does."""
+    ptr, m, n, lda, trans = _colmajor_host(A)
+    if trans:
+        raise ValueError("A must be column-major (a transposed view of a row-major tensor)")
+    code = dtype_code(dtype if dtype is not None else A.dtype)
+    if _TORCH_OF[code] != A.dtype:
+        raise ValueError(f"dtype code {code} does not match tensor dtype {A.dtype}")
+    dev = torch.device(device or "cuda")
+    od = out_dtype(code)
+    U = colmajor_empty(m, k, od, dev)
+    S = torch.empty(k, dtype=od, device=dev)
+    V = colmajor_empty(n, k, od, dev)
+    if workspace is None:
+        nb = int(_lib.sorsvd_streamed_workspace_size(m, n, k, p, code, block_rows))
+        if nb == 0:
+            raise SorsvdError(1, "sorsvd_streamed_workspace_size")
+        workspace = torch.empty(nb, dtype=torch.uint8, device=dev)
+    _check(_lib.sorsvd_run_streamed(ptr, m, n, lda, k, p, q, seed & 0xFFFFFFFFFFFFFFFF, code, block_rows,
+                                    U.data_ptr(), U.stride(1), S.data_ptr(), V.data_ptr(), V.stride(1),
+                                    workspace.data_ptr(), workspace.numel(), _stream(stream)), "sorsvd_run_streamed")
     return U, S, V
 
 
