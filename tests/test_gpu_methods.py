@@ -73,7 +73,7 @@ def test_rsvd_equals_sorsvd_on_the_gpu(nat):
 
 
 @pytest.mark.parametrize("dt,m,n,k,p", [("f64", 400, 300, 20, 5), ("f64", 200, 450, 10, 6),
-                                        ("f32", 1500, 1000, 30, 10)])
+                                        ("f32", 1500, 1000, 30, 10), ("bf16", 2048, 1024, 32, 8)])
 def test_tsr_matches_oracle(nat, dt, m, n, k, p):
     A64, s, _, _ = inputs.spectral(m, n, inputs.sigma_exp(min(m, n), 10.0), seed=m + 2 * n)
     store, exact = inputs.to_storage(A64, dt)
@@ -83,7 +83,7 @@ def test_tsr_matches_oracle(nat, dt, m, n, k, p):
     r_gpu, r_orc, ds = gates(exact, got, ref)
     # B_approx multiplies by (Q2^T Psi1)^+: rounding is amplified by its
     # condition number (a Gaussian l x l matrix: a few tens here)
-    tol = {"f64": 1e-9, "f32": 1e-4}[dt]
+    tol = {"f64": 1e-9, "f32": 1e-4, "bf16": 1e-2}[dt]
     assert abs(r_gpu - r_orc) <= tol and ds <= tol, (r_gpu, r_orc, ds)
 
 
@@ -104,6 +104,16 @@ def test_methods_recover_low_rank(nat, dt, method):
         # B_approx = Q1^T Y1 (Q2^T Psi1)^+ amplifies the fp32 rounding of its
         # factors by cond(Q2^T Psi1), that of a Gaussian l x l matrix
         bound = 1e-4
+    if method == "tsr" and dt == "bf16":
+        # the bf16 copy of a rank-r matrix is rank r plus its rounding (about
+        # 2e-3 of |A|), and Algorithm 2 recovers only inputs of rank <= l:
+        # (Q2^T Psi1)^+ amplifies that tail (the oracle's own error on the
+        # same stored input is near 8e-2), so the GPU result is held to the
+        # oracle's error on that input instead of to zero
+        Uo, So, Vo = oracle.tsrsvd(exact, k, p, 3, omega_dtype=dt)
+        rel_o = np.linalg.norm(exact - (Uo * So[None, :]) @ Vo.T) / np.linalg.norm(exact)
+        assert abs(rel - rel_o) <= TOL[dt], (rel, rel_o)
+        return
     assert rel <= bound, (method, dt, rel)
 
 
