@@ -65,6 +65,8 @@ struct TcParams {
   int64_t tiles, ipt, total;
   int G;                 // stream-K units (CTAs)
   int nbuf;
+  int pair;              // CTA pairs (cta_group::2): G pairs of CTAs, 256-row tiles
+  int hb;                // pair mode: rows of B per CTA in one N-chunk box
   uint32_t tmem_cols;
   int lo_tmem;           // split mode: A's low parts in TMEM slots (else next to A in shared memory)
   int aslots;            // split mode: converted stages in flight (TMEM slots / handshakes)
@@ -134,11 +136,14 @@ __device__ __forceinline__ void store_out(const TcParams& P, int64_t grow, int c
 // Sum of the shares of split tile t (rows row0.., mrows x N), CTA c0's share
 // from slot slot0 and the others' from slot 0, in CTA order (fp32); 4
 // consecutive rows per float4, 4 float4 per thread in flight.
-__device__ void sum_split_tile(const TcParams& P, int64_t row0, int mrows, int64_t c0, int64_t c1, int slot0) {
+// The shares of unit cc live in the partial slots of CTA cc * cs + cr (CTA
+// pairs: cs = 2 and cr the CTA's rank in its pair).
+__device__ void sum_split_tile(const TcParams& P, int64_t row0, int mrows, int64_t c0, int64_t c1, int slot0,
+                               int cs = 1, int cr = 0) {
   const int per = mrows * P.N;
   const size_t seg = (size_t)mrows * P.Npad;
   auto share = [&](int64_t cc, int slot) {
-    return reinterpret_cast<const float4*>(P.parts + ((size_t)cc * 2 + slot) * seg);
+    return reinterpret_cast<const float4*>(P.parts + ((size_t)(cc * cs + cr) * 2 + slot) * seg);
   };
   const int q4 = mrows / 4, nv = per / 4;
   const float4* first = share(c0, slot0);
@@ -653,6 +658,328 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   }
 }
 
+// Pair mode (16-bit operands, N > 128): the 152 SMs run as 76 CTA pairs, a
+// pair per 256-row tile.  Each CTA stages its own 128 rows of A and half of
+// the columns of each N-chunk of B; the even CTA issues cta_group::2 MMAs
+// (M = 256) that read both CTAs' stages and accumulate each CTA's 128 rows
+// in its own tensor memory.  Per SM this halves the bytes of B staged from
+// L2 and the shared memory B needs, which leaves room for a deeper ring of
+// A (HBM latency): at l = 266 a K atom of B is 2.3 times the matching atom
+// of A in a single CTA.
+//   barriers: the stage barriers (full, bfull) and the accumulator-drained
+//   barrier (tempty, 2 x 128 epilogue threads) of the even CTA count both
+//   CTAs' copies and drains; each CTA has its own empty, bempty and tfull,
+//   which the even CTA's MMA thread signals by commits addressed to each
+//   CTA (no multicast).  Both CTAs walk the same stream-K range; the odd
+//   CTA writes rows 128..255 of every tile.  Every wait is bounded; both
+//   CTAs meet at a cluster barrier before the tensor memory is freed.
+template <int ELT, bool A_MN, int NCH, int KA>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
+tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcParams P) {
+  static_assert(ELT == 0 || ELT == 1, "pair mode: 16-bit operands");
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint8_t* bring = smem + (size_t)P.stages * P.stage_bytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(bring + (size_t)P.bstages * P.bstage_bytes);
+  uint64_t* empty = full + P.stages;
+  uint64_t* bfull = empty + P.stages;
+  uint64_t* bempty = bfull + P.bstages;
+  uint64_t* tfull = bempty + P.bstages;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* done = tempty + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abortp = reinterpret_cast<volatile int*>(tslot + 1);
+  volatile int* lastp = abortp + 1;
+
+  constexpr int AK = 64, KMMA = 16, AMN = 64;
+  constexpr uint32_t AMN_BOX = (uint32_t)AK * 128u;
+  constexpr uint32_t FMT = (ELT == 0) ? 1u : 0u;
+  const uint32_t rank = tc::cluster_rank();
+  const bool leader = rank == 0;
+  const uint32_t peer = rank ^ 1u;
+  constexpr int mrows = 128;
+  constexpr int64_t urows = 256;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < P.stages; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
+    for (int s = 0; s < P.bstages; ++s) { tc::mbar_init(&bfull[s], 1); tc::mbar_init(&bempty[s], 1); }
+    for (int b = 0; b < 2; ++b) { tc::mbar_init(&tfull[b], 1); tc::mbar_init(&tempty[b], 2 * 128); }
+    tc::mbar_init(done, 1);
+    *abortp = 0;
+    tc::fence_barrier_init();
+  }
+  if (warp == 1) {
+    tc::tmem_alloc_pair(tslot, P.tmem_cols);
+    tc::tmem_relinquish_pair();
+    tc::fence_before_sync();
+  }
+  if (warp == 0 && lane == 0) tc::prefetch_tmap(&tmA);
+  if (warp == 6 && lane == 0) tc::prefetch_tmap(&tmB);
+  // the barriers of both CTAs are initialised before either CTA signals one
+  tc::cluster_sync();
+  tc::fence_after_sync();
+  const uint32_t tbase = *tslot;
+
+  // the stream-K unit of this pair
+  const int64_t unit = (int64_t)(blockIdx.x >> 1);
+  const int64_t it0 = unit * P.total / P.G, it1 = (unit + 1) * P.total / P.G;
+  auto lead_cl = [&](uint64_t* b) { return tc::mapa(tc::smem_u32(b), 0u); };
+  // the last use of each ring slot is released (by a commit of the even
+  // CTA) before this CTA may exit: n fills of a ring of depth d
+  auto drain_ring = [&](uint64_t* rel, int d, int64_t n) {
+    for (int s = 0; s < d && s < n; ++s) {
+      const uint32_t par = (uint32_t)(((n - 1 - s) / d) & 1);
+      const long long t0 = clock64();
+      while (!tc::mbar_try_wait_cl(&rel[s], par) && clock64() - t0 < tc::kWaitCycles) {}
+    }
+  };
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer of A
+    if (lane == 0) {
+      const uint64_t polA = tc::policy_evict_first();
+      uint32_t stage = 0, phase = 0;
+      uint32_t armed = 0, armed_par = 0;
+      int64_t fills = 0;
+      bool ok = true;
+      for (int64_t g = it0; g < it1 && ok;) {
+        const int64_t t = g / P.ipt;
+        const int64_t gend = min(it1, (t + 1) * P.ipt);
+        for (int64_t kb = g - t * P.ipt; kb < gend - t * P.ipt; ++kb) {
+          if (!tc::mbar_wait_cl(&empty[stage], phase ^ 1, abortp, P.wait_cycles)) { ok = false; break; }
+          if (leader) {
+            tc::mbar_arrive_expect_tx(&full[stage], 2u * P.a_bytes);
+            armed |= 1u << stage;
+            armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
+          }
+          const uint32_t fb = lead_cl(&full[stage]);
+          uint8_t* sa = smem + (size_t)stage * P.stage_bytes;
+          const int row0 = (int)(t * urows) + (int)rank * mrows;
+#pragma unroll
+          for (int j = 0; j < KA; ++j) {
+            const int k = (int)((kb * KA + j) * AK);
+            uint8_t* dst = sa + (size_t)j * kAtomBytes;
+            if (A_MN) {
+#pragma unroll
+              for (int h = 0; h < 128 / AMN; ++h) tc::tma_load_2d_pair(dst + h * AMN_BOX, &tmA, fb, row0 + h * AMN, k, polA);
+            } else {
+              tc::tma_load_2d_pair(dst, &tmA, fb, k, row0, polA);
+            }
+          }
+          ++fills;
+          if (++stage == (uint32_t)P.stages) { stage = 0; phase ^= 1; }
+        }
+        g = gend;
+      }
+      if (ok) {
+        drain_ring(empty, P.stages, fills);
+      } else if (leader) {
+        for (int s = 0; s < P.stages; ++s)
+          if (armed & (1u << s)) {
+            const long long t0 = clock64();
+            while (!tc::mbar_try_wait_cl(&full[s], (armed_par >> s) & 1u) && clock64() - t0 < tc::kWaitCycles) {}
+          }
+      }
+    }
+  } else if (warp == 6) {
+    // ------------------------------------------------------------ producer of B
+    if (lane == 0) {
+      const uint64_t polB = tc::policy_evict_last();
+      uint32_t stage = 0, phase = 0;
+      uint32_t armed = 0, armed_par = 0;
+      int64_t fills = 0;
+      bool ok = true;
+      for (int64_t g = it0; g < it1 && ok;) {
+        const int64_t t = g / P.ipt;
+        const int64_t gend = min(it1, (t + 1) * P.ipt);
+        for (int64_t kb = g - t * P.ipt; kb < gend - t * P.ipt; ++kb) {
+          if (!tc::mbar_wait_cl(&bempty[stage], phase ^ 1, abortp, P.wait_cycles)) { ok = false; break; }
+          if (leader) {
+            tc::mbar_arrive_expect_tx(&bfull[stage], 2u * P.b_bytes);
+            armed |= 1u << stage;
+            armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
+          }
+          const uint32_t fb = lead_cl(&bfull[stage]);
+          uint8_t* sb = bring + (size_t)stage * P.bstage_bytes;
+#pragma unroll
+          for (int j = 0; j < KA; ++j) {
+            const int k = (int)((kb * KA + j) * AK);
+#pragma unroll
+            for (int ch = 0; ch < NCH; ++ch) {
+              // this CTA's half of N-chunk ch (chunk widths: ch0, the last
+              // what the others leave)
+              const int w = (ch == NCH - 1) ? P.Npad - (NCH - 1) * P.ch0 : P.ch0;
+              const int y = ch * P.ch0 + (int)rank * (w / 2);
+              const size_t off = (size_t)j * P.b_atom + (size_t)ch * P.hb * 128;
+              tc::tma_load_2d_pair(sb + off, &tmB, fb, k, y, polB);
+            }
+          }
+          ++fills;
+          if (++stage == (uint32_t)P.bstages) { stage = 0; phase ^= 1; }
+        }
+        g = gend;
+      }
+      if (ok) {
+        drain_ring(bempty, P.bstages, fills);
+      } else if (leader) {
+        for (int s2 = 0; s2 < P.bstages; ++s2)
+          if (armed & (1u << s2)) {
+            const long long t0 = clock64();
+            while (!tc::mbar_try_wait_cl(&bfull[s2], (armed_par >> s2) & 1u) && clock64() - t0 < tc::kWaitCycles) {}
+          }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer (even CTA)
+    if (lane == 0 && leader) {
+      const uint32_t idesc0 = tc::idesc_make(FMT, A_MN, false, 256, P.ch0);
+      const uint32_t idesc1 = tc::idesc_make(FMT, A_MN, false, 256, NCH > 1 ? P.Npad - (NCH - 1) * P.ch0 : 16);
+      uint32_t stage = 0, phase = 0, bstage = 0, bphase = 0;
+      int chunk = 0;
+      bool ok = true;
+      for (int64_t g = it0; g < it1 && ok;) {
+        const int64_t t = g / P.ipt;
+        const int64_t gend = min(it1, (t + 1) * P.ipt);
+        const int64_t kb0 = g - t * P.ipt, kb1 = gend - t * P.ipt;
+        const int b = (P.nbuf == 2) ? (chunk & 1) : 0;
+        const uint32_t use = (P.nbuf == 2) ? (uint32_t)(chunk >> 1) : (uint32_t)chunk;
+        // both CTAs have drained this accumulator buffer
+        if (!tc::mbar_wait_cl(&tempty[b], (use & 1u) ^ 1u, abortp, P.wait_cycles)) { ok = false; break; }
+        tc::fence_after_sync();
+        const uint32_t dcol = tbase + (uint32_t)(b * P.Npad);
+        for (int64_t kb = kb0; kb < kb1; ++kb) {
+          if (!tc::mbar_wait_cl(&full[stage], phase, abortp, P.wait_cycles)) { ok = false; break; }
+          if (!tc::mbar_wait_cl(&bfull[bstage], bphase, abortp, P.wait_cycles)) { ok = false; break; }
+          tc::fence_after_sync();
+          const uint32_t sa = tc::smem_u32(smem + (size_t)stage * P.stage_bytes);
+          const uint32_t sb = tc::smem_u32(bring + (size_t)bstage * P.bstage_bytes);
+#pragma unroll
+          for (int j = 0; j < KA; ++j) {
+#pragma unroll
+            for (int ks = 0; ks < AK / KMMA; ++ks) {
+              const uint32_t acc = (kb > kb0 || j > 0 || ks > 0) ? 1u : 0u;
+              const uint32_t aat = sa + (uint32_t)j * kAtomBytes;
+              const uint64_t ad = A_MN ? tc::desc_sw128(aat + ks * KMMA * 128, AMN_BOX, 1024)
+                                       : tc::desc_sw128(aat + ks * 32, 16, 1024);
+#pragma unroll
+              for (int ch = 0; ch < NCH; ++ch) {
+                const uint32_t id = (ch == NCH - 1 && NCH > 1) ? idesc1 : idesc0;
+                const uint32_t bat = sb + (uint32_t)j * P.b_atom + (uint32_t)(ch * P.hb * 128);
+                tc::mma_f16_pair(dcol + (uint32_t)(ch * P.ch0), ad, tc::desc_sw128(bat + ks * 32, 16, 1024), id, acc);
+              }
+            }
+          }
+          // release the stage in both CTAs
+          tc::mma_commit_pair(tc::mapa(tc::smem_u32(&empty[stage]), rank));
+          tc::mma_commit_pair(tc::mapa(tc::smem_u32(&empty[stage]), peer));
+          tc::mma_commit_pair(tc::mapa(tc::smem_u32(&bempty[bstage]), rank));
+          tc::mma_commit_pair(tc::mapa(tc::smem_u32(&bempty[bstage]), peer));
+          if (++stage == (uint32_t)P.stages) { stage = 0; phase ^= 1; }
+          if (++bstage == (uint32_t)P.bstages) { bstage = 0; bphase ^= 1; }
+        }
+        if (!ok) break;
+        tc::mma_commit_pair(tc::mapa(tc::smem_u32(&tfull[b]), rank));
+        tc::mma_commit_pair(tc::mapa(tc::smem_u32(&tfull[b]), peer));
+        ++chunk;
+        g = gend;
+      }
+      tc::mma_commit_pair(tc::mapa(tc::smem_u32(done), rank));
+      const long long t0 = clock64();
+      while (!tc::mbar_try_wait(done, 0) && clock64() - t0 < tc::kWaitCycles) {}
+    }
+  } else if (warp >= 2 && warp <= 5) {
+    // ------------------------------------------------------------ epilogue (both CTAs)
+    const int q = warp & 3;
+    const uint32_t temp_cl[2] = {tc::mapa(tc::smem_u32(&tempty[0]), 0u), tc::mapa(tc::smem_u32(&tempty[1]), 0u)};
+    int chunk = 0;
+    bool ok = true;
+    for (int64_t g = it0; g < it1 && ok;) {
+      const int64_t t = g / P.ipt;
+      const int64_t gend = min(it1, (t + 1) * P.ipt);
+      const bool whole = (g == t * P.ipt) && (gend == (t + 1) * P.ipt);
+      float* pdst = nullptr;
+      if (!whole) {
+        const int slot = (t == it0 / P.ipt) ? 0 : 1;
+        pdst = P.parts + ((size_t)blockIdx.x * 2 + slot) * mrows * P.Npad;
+      }
+      const int b = (P.nbuf == 2) ? (chunk & 1) : 0;
+      const uint32_t use = (P.nbuf == 2) ? (uint32_t)(chunk >> 1) : (uint32_t)chunk;
+      if (!__all_sync(0xffffffffu, tc::mbar_wait_cl(&tfull[b], use & 1u, abortp, P.wait_cycles))) {
+        ok = false;
+        break;
+      }
+      tc::fence_after_sync();
+      const uint32_t taddr = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * P.Npad);
+      const int row = q * 32 + lane;
+      const int64_t grow = t * urows + (int64_t)rank * mrows + row;
+      for (int cb = 0; cb < P.N; cb += 16) {
+        float v[16];
+        tc::tmem_ld16(taddr + cb, v);
+        tc::tmem_ld_wait();
+        if (whole) {
+          if (grow < P.M) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+              if (cb + i < P.N) store_out(P, grow, cb + i, v[i]);
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 16; ++i)
+            if (cb + i < P.N) pdst[row + (size_t)(cb + i) * mrows] = v[i];
+        }
+      }
+      tc::fence_before_sync();
+      tc::mbar_arrive_cluster(temp_cl[b]);
+      ++chunk;
+      g = gend;
+    }
+  }
+  __syncwarp();
+  // every share of a split tile is in memory before its counter moves
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0 && *abortp) raise_status(P.status, SORSVD_ERR_TIMEOUT);
+  // no MMA of the pair, copy or arrival aimed at either CTA is in flight
+  // past this point
+  tc::cluster_sync();
+  if (warp == 1) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc_pair(tbase, P.tmem_cols);
+  }
+  if (P.tilecnt && !*abortp) {
+    const int64_t th = it0 / P.ipt, tt = (it1 - 1) / P.ipt;
+    const bool head_split = (it0 % P.ipt != 0) || (it1 < (th + 1) * P.ipt);
+    const bool tail_split = tt != th && (it1 % P.ipt != 0);
+    if (threadIdx.x == 0) {
+      int bits = 0;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const bool split = h ? tail_split : head_split;
+        if (!split) continue;
+        const int64_t t = h ? tt : th;
+        const int64_t c0 = cta_of(t * P.ipt, P.total, P.G), c1 = cta_of(t * P.ipt + P.ipt - 1, P.total, P.G);
+        if (atomicAdd(&P.tilecnt[2 * t + rank], 1) == (int)(c1 - c0)) bits |= 1 << h;
+      }
+      *lastp = bits;
+    }
+    __syncthreads();
+    const int bits = *lastp;
+    if (bits) {
+      __threadfence();
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (!((bits >> h) & 1)) continue;
+        const int64_t t = h ? tt : th;
+        const int64_t c0 = cta_of(t * P.ipt, P.total, P.G), c1 = cta_of(t * P.ipt + P.ipt - 1, P.total, P.G);
+        const int slot0 = (c0 * P.total / P.G < t * P.ipt) ? 1 : 0;
+        sum_split_tile(P, t * urows + (int64_t)rank * mrows, mrows, c0, c1, slot0, 2, (int)rank);
+        if (threadIdx.x == 0) P.tilecnt[2 * t + rank] = 0;
+      }
+    }
+  }
+}
+
 // Sum the partial segments of every tile touched by more than one CTA, in
 // CTA order (deterministic), and write the tile to the output.  Only split
 // tiles need work, and each holds at least one CTA boundary: block x takes
@@ -789,6 +1116,28 @@ cudaError_t launch_typed(const CUtensorMap& ma, const CUtensorMap& mb, const CUt
   }
 }
 
+template <int ELT, bool A_MN, int NCH, int KA>
+cudaError_t launch_pair_shape(const CUtensorMap& ma, const CUtensorMap& mb, const TcParams& P, size_t smem,
+                              cudaStream_t st) {
+  auto kern = tc_pair_kernel<ELT, A_MN, NCH, KA>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<2 * P.G, kThreads, smem, st>>>(ma, mb, P);
+  return cudaGetLastError();
+}
+
+template <int ELT, bool A_MN>
+cudaError_t launch_pair(const CUtensorMap& ma, const CUtensorMap& mb, const TcParams& P, size_t smem,
+                        cudaStream_t st) {
+  switch ((P.nch - 1) * 2 + (P.KA - 1)) {
+    case 0: return launch_pair_shape<ELT, A_MN, 1, 1>(ma, mb, P, smem, st);
+    case 1: return launch_pair_shape<ELT, A_MN, 1, 2>(ma, mb, P, smem, st);
+    case 2: return launch_pair_shape<ELT, A_MN, 2, 1>(ma, mb, P, smem, st);
+    case 3: return launch_pair_shape<ELT, A_MN, 2, 2>(ma, mb, P, smem, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 // limit of the progress waits of the next launches (0: tc::kWaitCycles)
 long long g_wait_cycles = 0;
 
@@ -851,6 +1200,61 @@ TcParams shape(int elt, int64_t M, int64_t N, int64_t K, int KA, int MT, int bst
   return P;
 }
 
+// Pair mode (16-bit operands, 128 < Npad <= 512): G pairs of CTAs over
+// 256-row tiles; each CTA stages its 128 rows of A and half of each
+// N-chunk of B (hb rows per chunk box; a last chunk narrower than ch0 reads
+// a few rows past its half, which its MMA does not use).
+TcParams shape_pair(int elt, int64_t M, int64_t N, int64_t K, int KA, int bst) {
+  TcParams P{};
+  P.pair = 1;
+  P.M = M; P.K = K; P.N = (int)N;
+  P.Npad = (int)((N + 15) / 16 * 16);
+  P.nch = P.Npad <= 256 ? 1 : 2;
+  P.ch0 = P.nch == 1 ? P.Npad : (P.Npad / 2 + 15) / 16 * 16;
+  P.hb = P.ch0 / 2;
+  P.KA = KA; P.MT = 1;
+  P.tiles = (M + 255) / 256;
+  P.ipt = (K + (int64_t)64 * KA - 1) / ((int64_t)64 * KA);
+  P.total = P.tiles * P.ipt;
+  P.G = (int)std::min<int64_t>(num_sms() / 2, P.total);
+  if (P.G < 1) P.G = 1;
+  P.nbuf = (2 * P.Npad <= 512) ? 2 : 1;
+  uint32_t cols = 32;
+  while (cols < (uint32_t)(P.nbuf * P.Npad)) cols <<= 1;
+  P.tmem_cols = cols;
+  P.a_bytes = (uint32_t)KA * kAtomBytes;
+  P.b_atom = (uint32_t)P.nch * (uint32_t)P.hb * 128u;
+  P.b_bytes = (uint32_t)KA * P.b_atom;
+  P.stage_bytes = P.a_bytes;
+  P.bstage_bytes = P.b_bytes;
+  const int envB = env_int("SORSVD_TC_BSTAGES", 0);
+  P.bstages = (envB >= 2 && envB <= 4) ? envB : bst ? bst : (KA >= 2 ? 2 : 3);
+  const uint32_t left = kSmemBudget > P.bstages * P.bstage_bytes ? kSmemBudget - P.bstages * P.bstage_bytes : 0;
+  P.stages = (int)std::min<uint32_t>(12u, left / P.stage_bytes);
+  if (elt > 1 || P.Npad <= 128 || P.Npad > 512 || cols > 512 || (num_sms() & 1) ||
+      P.Npad - (P.nch - 1) * P.ch0 < 16)
+    P.stages = 0;
+  return P;
+}
+
+// pair mode for 16-bit passes with 128 < Npad <= 512 (SORSVD_TC_PAIR=0 turns
+// it off); not with a shortened wait limit, whose tests exercise the
+// single-CTA kernel's abort path
+bool pair_wanted(int elt, int64_t N) {
+  const int64_t Npad = (N + 15) / 16 * 16;
+  return elt <= 1 && Npad > 128 && Npad <= 512 && env_int("SORSVD_TC_PAIR", 1) != 0 && (num_sms() % 2) == 0;
+}
+
+TcParams tc_plan_pair(int elt, int64_t M, int64_t N, int64_t K) {
+  const int envKA = env_int("SORSVD_TC_KATOMS", 0);
+  TcParams P = shape_pair(elt, M, N, K, (envKA >= 1 && envKA <= kMaxKA) ? envKA : 2, 0);
+  if (P.stages < 3 && envKA == 0) {
+    TcParams Q = shape_pair(elt, M, N, K, 1, 0);
+    if (Q.stages >= 3) P = Q;
+  }
+  return P;
+}
+
 }  // namespace
 
 // Planned shape of a launch (shared by the launcher and the workspace size).
@@ -858,7 +1262,7 @@ TcParams shape(int elt, int64_t M, int64_t N, int64_t K, int KA, int MT, int bst
 // double-buffered (not in split mode), then the most K atoms per stage (the
 // longest contiguous run per column of A, up to 4) that still leaves >= 3
 // stages.  SORSVD_TC_KATOMS and SORSVD_TC_MTILES override the choice.
-TcParams tc_plan(int elt, int64_t M, int64_t N, int64_t K) {
+TcParams tc_plan_single(int elt, int64_t M, int64_t N, int64_t K) {
   const int envKA = env_int("SORSVD_TC_KATOMS", 0), envMT = env_int("SORSVD_TC_MTILES", 0);
   const int64_t Npad = (N + 15) / 16 * 16;
   int MT = envMT > 0 ? envMT : ((elt != 3 && 4 * Npad <= 512) ? 2 : 1);
@@ -893,9 +1297,20 @@ bool tc_supported(int elt, const void* A, int64_t lda, const void* B, int64_t ld
   return encode_fn() != nullptr;
 }
 
+TcParams tc_plan(int elt, int64_t M, int64_t N, int64_t K) {
+  if (pair_wanted(elt, N)) {
+    TcParams P = tc_plan_pair(elt, M, N, K);
+    if (P.stages >= 2) return P;
+  }
+  return tc_plan_single(elt, M, N, K);
+}
+
 size_t tc_parts_bytes(int elt, int64_t M, int64_t N, int64_t K) {
-  TcParams P = tc_plan(elt, M, N, K);
-  return (size_t)P.G * 2 * 128 * P.MT * P.Npad * sizeof(float);
+  // the launcher may fall back from pair mode to single CTAs: room for both
+  const TcParams P = tc_plan(elt, M, N, K), S = tc_plan_single(elt, M, N, K);
+  const size_t bp = (size_t)P.G * (P.pair ? 2 : 1) * 2 * 128 * P.MT * P.Npad * sizeof(float);
+  const size_t bs = (size_t)S.G * 2 * 128 * S.MT * S.Npad * sizeof(float);
+  return std::max(bp, bs);
 }
 
 cudaError_t launch_tc_gemm(bool trans_a, int elt, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
@@ -908,12 +1323,16 @@ cudaError_t launch_tc_gemm(bool trans_a, int elt, int64_t M, int64_t N, int64_t 
   // of the form A X go through a transposed copy of A instead
   if (elt >= 2 && !trans_a) return cudaErrorInvalidValue;
   TcParams P = tc_plan(elt, M, N, K);
+  // pair mode needs the per-tile counters (two per 256-row tile) and the
+  // default wait limit
+  if (P.pair && (!tilecnt || 2 * P.tiles > ntilecnt || (g_wait_cycles > 0 && g_wait_cycles < tc::kWaitCycles)))
+    P = tc_plan_single(elt, M, N, K);
   if (P.stages < 2) return cudaErrorInvalidValue;
   P.out = out; P.ldo = ldo; P.out16 = out16; P.ld16 = ld16; P.out16_kind = out16 ? out16_kind : 0;
   P.parts = parts; P.status = status;
   P.wait_cycles = (g_wait_cycles > 0 && g_wait_cycles < tc::kWaitCycles) ? g_wait_cycles : tc::kWaitCycles;
 
-  P.tilecnt = (tilecnt && P.tiles <= ntilecnt) ? tilecnt : nullptr;
+  P.tilecnt = (tilecnt && (P.pair ? 2 : 1) * P.tiles <= ntilecnt) ? tilecnt : nullptr;
   const int AK = elt >= 2 ? 32 : 64, AMN = elt >= 2 ? 32 : 64;
   const int map_elt = elt == 3 ? 2 : elt;
   CUtensorMap ma, mb;
@@ -922,12 +1341,18 @@ cudaError_t launch_tc_gemm(bool trans_a, int elt, int64_t M, int64_t N, int64_t 
   const int64_t a_rows = trans_a ? K : M, a_cols = trans_a ? M : K;
   const bool okA = trans_a ? make_map(&ma, A, map_elt, a_rows, a_cols, lda, (uint32_t)AK, 128u)
                            : make_map(&ma, A, map_elt, a_rows, a_cols, lda, (uint32_t)AMN, (uint32_t)AK);
-  const bool okB = make_map(&mb, B, map_elt, K, N, ldb, (uint32_t)AK, (uint32_t)P.ch0);
+  const bool okB = make_map(&mb, B, map_elt, K, N, ldb, (uint32_t)AK, (uint32_t)(P.pair ? P.hb : P.ch0));
   CUtensorMap mblo = mb;
   const bool okBlo = elt != 3 || make_map(&mblo, Blo, map_elt, K, N, ldb, (uint32_t)AK, (uint32_t)P.ch0);
   if (!okA || !okB || !okBlo) return cudaErrorInvalidValue;
   const size_t smem = (size_t)P.stages * P.stage_bytes + (size_t)P.bstages * P.bstage_bytes + 1024 + 512;
   cudaError_t e;
+  if (P.pair) {
+    ProfScope ps(kcls, st);
+    if (elt == 0) e = trans_a ? launch_pair<0, false>(ma, mb, P, smem, st) : launch_pair<0, true>(ma, mb, P, smem, st);
+    else e = trans_a ? launch_pair<1, false>(ma, mb, P, smem, st) : launch_pair<1, true>(ma, mb, P, smem, st);
+    return e;
+  }
   {
     ProfScope ps(kcls, st);
     if (elt == 0) e = trans_a ? launch_typed<0, false>(ma, mb, mblo, P, smem, st) : launch_typed<0, true>(ma, mb, mblo, P, smem, st);

@@ -162,7 +162,13 @@ def max_elem_ratio(C, Cref, absA, absX):
 @pytest.mark.parametrize("dt", ["f64", "f32", "tf32", "bf16", "f16"])
 @pytest.mark.parametrize("m,n,k,p", [(333, 517, 20, 7), (1025, 130, 60, 4), (129, 2049, 9, 1), (4096, 768, 100, 12),
                                      (1000, 360, 27, 5), (2048, 4096, 256, 10), (640, 96, 32, 0),
-                                     (1500, 700, 100, 28)])
+                                     (1500, 700, 100, 28),
+                                     # 16-bit sketches wider than 128 columns run on CTA pairs:
+                                     # one N-chunk (l = 160, 200, 256), two (l = 300: the last
+                                     # chunk narrower than its box), ragged and tiny M (the
+                                     # second CTA's rows out of range), split tiles
+                                     (1000, 517, 150, 10), (250, 1030, 190, 10), (3000, 2000, 290, 10),
+                                     (70000, 300, 250, 6)])
 def test_power_pass_elementwise(nat, dt, m, n, k, p):
     l = k + p
     if dt == "f64" and l > nat.MAX_L_F64:
