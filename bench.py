@@ -311,7 +311,11 @@ def run_ours(args, w, rank, world, local_rank):
         roofline["frac"] = roofline["achieved"] / roofline["peak"]
     else:
         mma = 3.0 if dom == "pass_split" or (dom == "core_pass" and dt == "f32") else 1.0
-        roofline = {"bound": "hbm", "kernel": f"tc_gemm_kernel ({dom})", "achieved": achieved_gbs,
+        # 16-bit sketches wider than 128 columns run on CTA pairs (SORSVD_TC_PAIR=0: single CTAs)
+        npad = (l + 15) // 16 * 16
+        pair = dt in ("bf16", "f16") and 128 < npad <= 512 and os.environ.get("SORSVD_TC_PAIR", "1") != "0"
+        kname = "tc_pair_kernel" if pair else "tc_gemm_kernel"
+        roofline = {"bound": "hbm", "kernel": f"{kname} ({dom})", "achieved": achieved_gbs,
                     "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved_gbs / pk["hbm_gbs"],
                     "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({pk_src})",
                     "algorithmic_bytes_per_launch": algo_bytes,
