@@ -16,18 +16,15 @@
 // chol_inv_blocked_kernel (when its tiles fit in shared memory): the matrix
 // is padded to nb x 32 with an identity block and kept as the nb(nb+1)/2
 // lower 32 x 32 tiles (row stride 33: conflict-free row and column access).
-//   factorisation, right-looking by tile column K, the column itself in
-//   8-wide sub-panels (short dependency chains, every warp busy):
-//     chol of the 8 x 8 diagonal block        (one warp, shuffles)
-//     the panel rows below it times its L^{-T} (one thread per row, registers)
-//     rank-8 update of the sub-panel's remaining columns (one thread per element)
-//   then A_IJ -= L_IK L_JK^T, K < J <= I      (one thread per element)
-//   inverse X = L^{-1}, in place:
-//     X_II = L_II^{-1} for every I at once     (every warp, columns
-//                                              interleaved, shuffles)
-//     for I = 1..: X_IJ = -X_II sum_{K=J}^{I-1} L_IK X_KJ for all J < I
-//   (the sums for block row I are all formed before any X_IJ replaces the
-//   L_IJ they read.)
+//   factorisation, right-looking by tile column K:
+//     L_KK: factored in one warp's registers (ahead of time, see below)
+//     L_IK = A_IK L_KK^{-T} for I > K         (one thread per row, registers),
+//       while warp 0 inverts L_KK into the diagonal tile
+//     A_IJ -= L_IK L_JK^T, K < J <= I          (one warp per tile); warp 0
+//       updates A_{K+1,K+1} first and factors it (look-ahead)
+//   inverse Z = L^{-1}, in place, right-looking by K:
+//     Z_KJ = X_KK Z_KJ (J < K), then Z_IJ -= L_IK Z_KJ and
+//     Z_IK = -L_IK X_KK for I > K              (one warp per tile)
 //
 // chol_inv_kernel (largest l), the factor packed (row-major lower triangle);
 // l <= SORSVD_MAX_L_F64 / SORSVD_MAX_L.  Both phases need one block-wide
@@ -177,37 +174,57 @@ __device__ __forceinline__ double rsqrt_rn(double x) {
   return y;
 }
 
+// 16-byte vector of shared memory (4 fp32 or 2 binary64 values)
+__device__ __forceinline__ void load_vec16(const float* p, float (&x)[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  x[0] = t.x; x[1] = t.y; x[2] = t.z; x[3] = t.w;
+}
+__device__ __forceinline__ void load_vec16(const double* p, double (&x)[2]) {
+  const double2 t = *reinterpret_cast<const double2*>(p);
+  x[0] = t.x; x[1] = t.y;
+}
+
 // Cholesky factor of the 32 x 32 diagonal tile DK in one warp's registers
-// (lane = row): right-looking, the pivot and the column entries broadcast by
-// shuffle.  Writes L_KK densely to Ld (row-major, stride 32, zeros above the
-// diagonal) and 1 / L_jj to rd.  Returns false (in every lane) when a pivot
-// is not safely positive.
+// (lane = row), right-looking.  Column j goes through shared memory: every
+// lane stores its a_ij, and each lane then reads the pivot a_jj and the
+// column below it as 16-byte broadcast vectors (a few loads per column
+// where shuffles took one per entry), and updates its row by
+//   a_ic -= (a_ij / a_jj) a_cj   (c > j),   then l_ij = a_ij / sqrt(a_jj).
+// The scratch is the first two columns' worth of Ld (alternating, so one
+// __syncwarp per column orders the stores and loads); Ld then receives L_KK
+// densely (row-major, stride 32, zeros above the diagonal) and rd 1 / L_jj.
+// Entries above the diagonal are updated too (selects, no divergence) and
+// never read.  Returns false (in every lane) when a pivot is not safely
+// positive; Ld must be 16-byte aligned.
 template <typename F>
 __device__ __noinline__ bool chol_tile_warp(const F* DK, F* Ld, F* rd, F thr, int lane) {
+  constexpr int V = 16 / (int)sizeof(F);
   F a[TB];
 #pragma unroll
   for (int c = 0; c < TB; ++c) a[c] = DK[lane * TLD + c];
   bool ok = true;
   F my_rs = (F)0;
-  // straight-line, branch-free code: per-lane choices are selects, so the
-  // warp never diverges between its shuffles (a divergent update made every
-  // shuffle wait for reconvergence, ~100 cycles each); after a bad pivot
-  // the values are not used
 #pragma unroll
   for (int j = 0; j < TB; ++j) {
-    const F d = __shfl_sync(0xffffffffu, a[j], j);
+    F* cb = Ld + (j & 1) * TB;
+    cb[lane] = a[j];
+    __syncwarp();
+    const F d = cb[j];
     ok = ok && (d > thr);
     const F rs = rsqrt_rn(d);
-    const F lj = a[j] * rs;
-    a[j] = lane == j ? d * rs : (lane > j ? lj : a[j]);
-    my_rs = lane == j ? rs : my_rs;
+    const F f = a[j] * (rs * rs);
 #pragma unroll
-    for (int c = j + 1; c < TB; ++c) {
-      const F lcj = __shfl_sync(0xffffffffu, a[j], c);
-      const F m = lane >= c ? a[j] : (F)0;
-      a[c] -= m * lcj;
+    for (int v0 = (j + 1) / V * V; v0 < TB; v0 += V) {
+      F x[V];
+      load_vec16(cb + v0, x);
+#pragma unroll
+      for (int u = 0; u < V; ++u)
+        if (v0 + u > j) a[v0 + u] -= f * x[u];
     }
+    a[j] = lane == j ? d * rs : a[j] * rs;
+    my_rs = lane == j ? rs : my_rs;
   }
+  __syncwarp();                      // every read of the scratch is done
   rd[lane] = my_rs;
 #pragma unroll
   for (int c = 0; c < TB; ++c) Ld[lane * TB + c] = c <= lane ? a[c] : (F)0;
