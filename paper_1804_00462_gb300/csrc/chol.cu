@@ -320,17 +320,19 @@ __device__ __forceinline__ void chol_inv_blocked_body(const double* __restrict__
     // equilibrated, shifted Gram in the lower tiles (factor precision);
     // padding and zero columns of T become identity rows / columns; the
     // largest off-diagonal entry (a column cosine) is recorded for conv_out.
-    // Tiles in groups of four, their loads issued before any is used.
+    // Tiles in groups of GQ, their loads (2 GQ per thread) issued before any
+    // is used: the Gram comes from L2, and the load is latency-bound.
+    constexpr int GQ = 8;
     const F fshift = (F)shift;
     float offmax = 0.f;
     {
       int I0 = 0, J0 = 0;                          // (I, J) of tile q0
-      for (int q0 = 0; q0 < ntile; q0 += 4) {
-        double gv[4][2];
-        int Iq[4], Jq[4];
+      for (int q0 = 0; q0 < ntile; q0 += GQ) {
+        double gv[GQ][2];
+        int Iq[GQ], Jq[GQ];
         int I = I0, J = J0;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < GQ; ++u) {
           Iq[u] = I;
           Jq[u] = J;
           if (++J > I) { ++I; J = 0; }
@@ -338,7 +340,7 @@ __device__ __forceinline__ void chol_inv_blocked_body(const double* __restrict__
         I0 = I;
         J0 = J;
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < GQ; ++u)
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const int e = t + h * BT, r = e >> 5, c = e & 31;
@@ -346,7 +348,7 @@ __device__ __forceinline__ void chol_inv_blocked_body(const double* __restrict__
             gv[u][h] = (q0 + u < ntile && gi < l && gc < l) ? G[gc + (int64_t)gi * l] : 0.0;   // symmetric: coalesced
           }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < GQ; ++u) {
           if (q0 + u >= ntile) break;
           F* D = T + (size_t)(q0 + u) * TS;
 #pragma unroll
@@ -373,27 +375,70 @@ __device__ __forceinline__ void chol_inv_blocked_body(const double* __restrict__
     // tiles are factored ahead, inside the previous column's update)
     if (warp == 0 && !chol_tile_warp(tile(0, 0), Ld, rdiag, thr, lane) && lane == 0) s_fail = 1;
     __syncthreads();
-    for (int K = 0; K < nb && !s_fail; ++K) {
-      F* DK = tile(K, K);
-      F* rd = rdiag + K * TB;
-      // (b) the panel rows below: L_IK = A_IK L_KK^{-T} (one row per thread,
-      // warps 1..); warp 0 meanwhile inverts L_KK into the diagonal tile
-      // (lane = column: X_ic = (delta_ic - sum_k L_ik X_kc) / L_ii)
+    // The factorisation and the in-place inverse Z = L^{-1} run together,
+    // the inverse one tile column behind: its step K - 1 shares the two
+    // phases of factorisation step K (see the inverse's description below).
+    // Z_{I,K-1} = -L_{I,K-1} X_{K-1,K-1} replaces L_{I,K-1}, which the phase
+    // that forms it still reads, so its warp holds it in registers (pend)
+    // and writes it at the start of the next phase.  Pass K = nb is the
+    // inverse's last step alone.
+    // binary64 factors form the inverse afterwards (the held tile would not
+    // fit in the registers)
+    constexpr bool IL = sizeof(F) == 4;
+    F pend[8][4];
+    bool has_pend = false;
+    int pend_i = 0, pend_j = 0;
+    for (int K = 0; K <= nb && !s_fail; ++K) {
+      // ---- phase (b): warp 0 inverts L_KK into the diagonal tile (lane =
+      // column: X_ic = (delta_ic - sum_k L_ik X_kc) / L_ii); the last warps
+      // solve the panel rows L_IK = A_IK L_KK^{-T} (a warp per tile, a row
+      // per lane); the first warps write the held tiles Z_{I,K-2} and form
+      // row K - 1 of Z: Z_{K-1,J} = X_{K-1,K-1} Z_{K-1,J}, J < K - 1
       if (warp == 0) {
-        F x[TB];
+        if (K < nb) {
+          F* DK = tile(K, K);
+          const F* rd = rdiag + K * TB;
+          F x[TB];
 #pragma unroll
-        for (int i = 0; i < TB; ++i) {
-          F s = (i == lane) ? (F)1 : (F)0;
+          for (int i = 0; i < TB; ++i) {
+            F s = (i == lane) ? (F)1 : (F)0;
 #pragma unroll
-          for (int k = 0; k < i; ++k) s -= Ld[i * TB + k] * x[k];
-          x[i] = s * rd[i];
+            for (int k = 0; k < i; ++k) s -= Ld[i * TB + k] * x[k];
+            x[i] = s * rd[i];
+          }
+#pragma unroll
+          for (int i = 0; i < TB; ++i) DK[i * TLD + lane] = x[i];
         }
-#pragma unroll
-        for (int i = 0; i < TB; ++i) DK[i * TLD + lane] = x[i];
       } else {
-        const int rows = TB * (nb - K - 1);
-        for (int rr = t - 32; rr < rows; rr += BT - 32) {
-          F* xr = tile(K + 1 + rr / TB, K) + (rr % TB) * TLD;
+        if (IL && has_pend) {
+          F* o = tile(pend_i, pend_j) + r0 * TLD + c0;
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) o[u * TLD + v] = -pend[u][v];
+          has_pend = false;
+          __syncwarp();
+        }
+        // row K - 1: J = K - 2 on warp 1 (which held that tile), J < K - 2
+        // on warps nb - K + 2 + J (after the holders, before the panel)
+        int jj = -1;
+        if (IL && K >= 2 && warp == 1) jj = K - 2;
+        if (IL && K >= 3 && warp >= nb - K + 2 && warp - (nb - K + 2) < K - 2) jj = warp - (nb - K + 2);
+        if (jj >= 0) {
+          F acc[8][4];
+          zero84(acc);
+          tile_mm84<F, false>(tile(K - 1, K - 1), tile(K - 1, jj), r0, c0, acc);
+          __syncwarp();                        // the warp has read the whole tile
+          F* o = tile(K - 1, jj) + r0 * TLD + c0;
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) o[u * TLD + v] = acc[u][v];
+        }
+        const int pi = K + 1 + (NW - 1 - warp);   // panel tile of this warp
+        if (K < nb && pi < nb) {
+          const F* rd = rdiag + K * TB;
+          F* xr = tile(pi, K) + lane * TLD;
           F v[TB];
 #pragma unroll
           for (int c = 0; c < TB; ++c) v[c] = xr[c];
@@ -403,10 +448,13 @@ __device__ __forceinline__ void chol_inv_blocked_body(const double* __restrict__
         }
       }
       __syncthreads();
-      // (c) A_IJ -= L_IK L_JK^T for K < J <= I, one warp per tile.  Warp 0
-      // takes the next diagonal tile (K+1, K+1) alone and then factors it
-      // (look-ahead: the factorisation overlaps the rest of the update);
-      // warps 1.. take the other tiles.
+      if (K == nb) break;
+      // ---- phase (c): A_IJ -= L_IK L_JK^T for K < J <= I, a warp per tile.
+      // Warp 0 takes the next diagonal tile (K+1, K+1) alone and then factors
+      // it (look-ahead).  Inverse step K - 1 (K >= 1): warps 1..nb-K form
+      // Z_{I,K-1} = -L_{I,K-1} X_{K-1,K-1} (I >= K, held), and the remaining
+      // warps share the trailing tiles with Z_IJ -= L_{I,K-1} Z_{K-1,J}
+      // (I >= K, J < K - 1).
       {
         const int nrem = nb - K - 1, ntr = nrem * (nrem + 1) / 2;
         if (warp == 0) {
@@ -423,14 +471,32 @@ __device__ __forceinline__ void chol_inv_blocked_body(const double* __restrict__
             __syncwarp();
             if (!chol_tile_warp(tile(K + 1, K + 1), Ld, rdiag + (K + 1) * TB, thr, lane) && lane == 0) s_fail = 1;
           }
+        } else if (IL && K >= 1 && warp <= nb - K) {
+          const int I = K + warp - 1;
+          zero84(pend);
+          tile_mm84<F, false>(tile(I, K - 1), tile(K - 1, K - 1), r0, c0, pend);
+          has_pend = true;
+          pend_i = I;
+          pend_j = K - 1;
         } else {
-          for (int q = warp; q < ntr; q += NW - 1) {
-            int bi, bj;
-            tri_index(q, &bi, &bj);
+          const int w0 = (IL && K >= 1) ? nb - K + 1 : 1;   // first free warp
+          const int nfw = NW - w0;
+          const int ntrail = ntr > 0 ? ntr - 1 : 0;
+          const int nupd = (IL && K >= 2) ? (nb - K) * (K - 1) : 0;
+          for (int f = warp - w0; f < ntrail + nupd; f += nfw) {
             F acc[8][4];
             zero84(acc);
-            tile_mm84<F, true>(tile(K + 1 + bi, K), tile(K + 1 + bj, K), r0, c0, acc);
-            F* out = tile(K + 1 + bi, K + 1 + bj) + r0 * TLD + c0;
+            F* out;
+            if (f < ntrail) {
+              int bi, bj;
+              tri_index(f + 1, &bi, &bj);
+              tile_mm84<F, true>(tile(K + 1 + bi, K), tile(K + 1 + bj, K), r0, c0, acc);
+              out = tile(K + 1 + bi, K + 1 + bj) + r0 * TLD + c0;
+            } else {
+              const int g = f - ntrail, I = K + g / (K - 1), J = g % (K - 1);
+              tile_mm84<F, false>(tile(I, K - 1), tile(K - 1, J), r0, c0, acc);
+              out = tile(I, J) + r0 * TLD + c0;
+            }
 #pragma unroll
             for (int u = 0; u < 8; ++u)
 #pragma unroll
@@ -453,58 +519,61 @@ __device__ __forceinline__ void chol_inv_blocked_body(const double* __restrict__
   if (t == 0 && s_retry) atomicOr(&status->info, 1);
   if (conv_out && t == 0) *conv_out = (__uint_as_float(s_offmax) <= conv_tol && !s_retry) ? 1 : 0;
 
-  // Z = L^{-1} in place, right-looking (L^{-1} = E_{nb-1}^{-1} ... E_0^{-1},
-  // E_K the identity with L's block column K): the diagonal tiles already
-  // hold X_KK = L_KK^{-1}.  Step K finalises block row K, Z_KJ = X_KK Z_KJ
-  // (J < K), then updates the rows below, Z_IJ -= L_IK Z_KJ (J < K) and
-  // Z_IK = -L_IK X_KK, which replaces L_IK.  A tile that is read in a phase
-  // is written only after the phase's barrier.  nb <= 9 <= NW, so each
-  // phase's in-place tiles take one round of the warps.
-  for (int K = 0; K < nb; ++K) {
-    if (K > 0) {
-      F acc[8][4];
-      zero84(acc);
-      const bool act = warp < K;
-      if (act) tile_mm84<F, false>(tile(K, K), tile(K, warp), r0, c0, acc);
-      __syncthreads();
-      if (act) {
-        F* o = tile(K, warp) + r0 * TLD + c0;
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-#pragma unroll
-          for (int v = 0; v < 4; ++v) o[u * TLD + v] = acc[u][v];
-      }
-      __syncthreads();
-    }
-    const int nbelow = nb - K - 1;
-    if (nbelow > 0) {
-      // J < K: these tiles are read by no one in this phase
-      for (int q = warp; q < nbelow * K; q += NW) {
-        const int I = K + 1 + q / K, J = q % K;
+  // Z = L^{-1} (formed in place above, right-looking: L^{-1} =
+  // E_{nb-1}^{-1} ... E_0^{-1}, E_K the identity with L's block column K).
+  // The diagonal tiles hold X_KK = L_KK^{-1}; step K finalises block row K,
+  // Z_KJ = X_KK Z_KJ (J < K), then updates the rows below, Z_IJ -= L_IK Z_KJ
+  // (J < K) and Z_IK = -L_IK X_KK, which replaces L_IK.  Step K's first part
+  // runs in phase (b) of factorisation step K + 1, its second part in phase
+  // (c) of step K + 1, when column K of L has served its trailing update;
+  // the tiles each phase writes are read by no other warp in that phase.
+  if constexpr (sizeof(F) == 8) {
+    for (int K = 0; K < nb; ++K) {
+      if (K > 0) {
         F acc[8][4];
         zero84(acc);
-        tile_mm84<F, false>(tile(I, K), tile(K, J), r0, c0, acc);
-        F* o = tile(I, J) + r0 * TLD + c0;
+        const bool act = warp < K;
+        if (act) tile_mm84<F, false>(tile(K, K), tile(K, warp), r0, c0, acc);
+        __syncthreads();
+        if (act) {
+          F* o = tile(K, warp) + r0 * TLD + c0;
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
+          for (int u = 0; u < 8; ++u)
 #pragma unroll
-          for (int v = 0; v < 4; ++v) o[u * TLD + v] -= acc[u][v];
+            for (int v = 0; v < 4; ++v) o[u * TLD + v] = acc[u][v];
+        }
+        __syncthreads();
       }
-      F acc[8][4];
-      zero84(acc);
-      // J = K: the last warps, so that the J < K tiles start on the first
-      const int w2 = NW - 1 - warp;
-      const bool act = w2 < nbelow;
-      if (act) tile_mm84<F, false>(tile(K + 1 + w2, K), tile(K, K), r0, c0, acc);
-      __syncthreads();
-      if (act) {
-        F* o = tile(K + 1 + w2, K) + r0 * TLD + c0;
+      const int nbelow = nb - K - 1;
+      if (nbelow > 0) {
+        // J < K: these tiles are read by no one in this phase
+        for (int q = warp; q < nbelow * K; q += NW) {
+          const int I = K + 1 + q / K, J = q % K;
+          F acc[8][4];
+          zero84(acc);
+          tile_mm84<F, false>(tile(I, K), tile(K, J), r0, c0, acc);
+          F* o = tile(I, J) + r0 * TLD + c0;
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
+          for (int u = 0; u < 8; ++u)
 #pragma unroll
-          for (int v = 0; v < 4; ++v) o[u * TLD + v] = -acc[u][v];
+            for (int v = 0; v < 4; ++v) o[u * TLD + v] -= acc[u][v];
+        }
+        F acc[8][4];
+        zero84(acc);
+        // J = K: the last warps, so that the J < K tiles start on the first
+        const int w2 = NW - 1 - warp;
+        const bool act = w2 < nbelow;
+        if (act) tile_mm84<F, false>(tile(K + 1 + w2, K), tile(K, K), r0, c0, acc);
+        __syncthreads();
+        if (act) {
+          F* o = tile(K + 1 + w2, K) + r0 * TLD + c0;
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) o[u * TLD + v] = -acc[u][v];
+        }
+        __syncthreads();
       }
-      __syncthreads();
     }
   }
   // R^{-1} = D^{-1/2} Z^T: upper triangular, column-major

@@ -422,8 +422,9 @@ def _rinv_ref(G, shift):
     return d[:, None] * np.linalg.inv(L).T
 
 
-@pytest.mark.parametrize("dt,l", [("f32", 1), ("f32", 7), ("f32", 32), ("f32", 33), ("f32", 110), ("f32", 266),
-                                  ("f32", 300), ("f64", 25), ("f64", 150), ("f64", 224)])
+@pytest.mark.parametrize("dt,l", [("f32", 1), ("f32", 7), ("f32", 32), ("f32", 33), ("f32", 64), ("f32", 65),
+                                  ("f32", 110), ("f32", 150), ("f32", 200), ("f32", 250), ("f32", 266),
+                                  ("f32", 288), ("f32", 300), ("f64", 25), ("f64", 64), ("f64", 150), ("f64", 224)])
 def test_chol_inv_matches_numpy(nat, dt, l):
     g = np.random.default_rng(l)
     T = g.standard_normal((2 * l + 3, l)) * np.exp(np.linspace(0, -3, l))[None, :]
@@ -454,6 +455,28 @@ def test_chol_inv_retry_and_breakdown(nat):
     torch.cuda.synchronize()
     assert st == 5                                  # SORSVD_ERR_BREAKDOWN
     assert np.array_equal(R.cpu().numpy(), np.eye(20, dtype=np.float32))
+
+
+@pytest.mark.parametrize("l", [100, 250])
+def test_chol_inv_retry_many_tiles(nat, l):
+    # a failed pivot deep in the factorisation restarts it with a larger
+    # shift: every tile, including the inverse's tiles formed alongside the
+    # factorisation, is rebuilt from the Gram
+    g = np.random.default_rng(l)
+    T = g.standard_normal((3 * l, l))
+    T[:, l - 3] = T[:, l - 40]
+    G = T.T @ T
+    R, st, info = nat.chol_inv(torch.from_numpy(G).cuda(), 0.0, dtype="f32")
+    torch.cuda.synchronize()
+    assert st == 0 and (info & 1) == 1
+    Rg = R.double().cpu().numpy()
+    assert np.all(np.isfinite(Rg)) and np.array_equal(np.tril(Rg, -1), np.zeros_like(Rg))
+    # Q = T R: Q^T Q = I - s (G')^{-1} (G' the equilibrated, shifted Gram),
+    # so the columns away from the duplicated pair stay orthonormal
+    Q = T @ Rg
+    keep = [j for j in range(l) if j not in (l - 3, l - 40)]
+    E = Q[:, keep].T @ Q[:, keep] - np.eye(l - 2)
+    assert np.abs(E).max() <= 0.1
 
 
 @pytest.mark.parametrize("l,scale", [(1, 0.0), (17, 1e-3), (64, 1e-6), (110, 1e-4), (266, 2e-5), (320, 1e-5)])
