@@ -43,10 +43,14 @@
 // values of a staged K atom (stored column by column, conflict-free) and
 // writes hi and lo to a TMEM slot.  B comes split into hi (rounded to TF32)
 // and lo by the caller, K-major (B is column-major: a column is a run of K),
-// streamed from L2 per K atom.  One accumulator of N <= 320 columns per row
-// tile (two MMA column chunks when N > 256); an epilogue warpgroup drains it
-// while the converter prepares the next tile.  For an upper-triangular B
-// the K atoms below a chunk's last column are skipped.
+// streamed from L2 per K atom.  T and B come in separate rings: the atoms
+// of T (16 KB each, from HBM) in a deep ring that the converter releases as
+// soon as it has read an atom, those of B (hi and lo, up to 74 KB per atom,
+// from L2) in a two-stage ring that the MMAs release; each ring has its own
+// TMA warp.  One accumulator of N <= 320 columns per row tile (two MMA
+// column chunks when N > 256); an epilogue warpgroup drains it while the
+// converter prepares the next tile.  For an upper-triangular B the K atoms
+// below a chunk's last column are skipped.
 //
 // Every mbarrier wait is bounded (the library's tensor-core wait limit); a
 // timeout records SORSVD_ERR_TIMEOUT, stops every role, waits for the
@@ -64,11 +68,13 @@ namespace {
 constexpr int kAtomK = 32;                 // fp32 elements per 128-byte swizzle row
 constexpr int kMaxGramBlocks = 5;
 constexpr int kGramThreads = 192;          // warp 0 TMA, warp 1 MMA, warps 2-5 low parts + epilogue
-constexpr int kApplyThreads = 320;         // warp 0 TMA, warp 1 MMA, warps 2-5 convert, warps 6-9 epilogue
+// warp 0 TMA of T, warp 1 MMA, warps 2-5 convert, warps 6-9 epilogue, warp 10 TMA of B
+constexpr int kApplyThreads = 352;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kApplySlotCol = 320;    // first TMEM column of the apply's A slots (hi 32 + lo 32 each)
-constexpr int kApplySlots = 2;
-constexpr int kApplyStages = 2;
+constexpr int kApplySlots = 3;
+constexpr int kApplyBStages = 2;           // B (hi and lo) from L2
+constexpr int kApplyMaxTStages = 8;        // K atoms of T from HBM
 constexpr uint32_t kSmemBudget = 220u * 1024u;
 
 struct GramBlock {
@@ -102,6 +108,7 @@ struct ApplyParams {
   int64_t rows, ntiles;
   int K, N, NP, nch, ch0, katoms, tri;
   uint32_t x_bytes, b_bytes, stage_bytes;   // b_bytes: one of B_hi / B_lo (2 ch0 rows x 128 bytes)
+  int tstages;                               // depth of the ring of T atoms
   float* Y;
   int64_t ldy;
   void* Y16;
@@ -444,10 +451,14 @@ tsk_apply_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
   if (P.skip && *P.skip) return;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = align1024(smem_raw);
-  // stage s: B_hi (2 ch0 rows x 128 B), B_lo (same), then the K atom of T (32 columns x 128 rows)
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)kApplyStages * P.stage_bytes);
-  uint64_t* empty = full + kApplyStages;
-  uint64_t* afull = empty + kApplyStages;      // a TMEM slot written (4 converter warps)
+  // B stage s: B_hi (2 ch0 rows x 128 B), B_lo (same); then the T ring (a K
+  // atom of T, 32 columns x 128 rows, per stage)
+  uint8_t* tring = smem + (size_t)kApplyBStages * 2 * P.b_bytes;
+  uint64_t* bfull = reinterpret_cast<uint64_t*>(tring + (size_t)P.tstages * P.x_bytes);
+  uint64_t* bempty = bfull + kApplyBStages;
+  uint64_t* tfull = bempty + kApplyBStages;    // a T atom landed
+  uint64_t* tempty = tfull + kApplyMaxTStages; // a T atom read by the converter (4 warps)
+  uint64_t* afull = tempty + kApplyMaxTStages; // a TMEM slot written (4 converter warps)
   uint64_t* aempty = afull + kApplySlots;      // a slot read by its MMAs
   uint64_t* dfull = aempty + kApplySlots;      // the tile's accumulator complete
   uint64_t* dempty = dfull + 1;                // the accumulator drained (4 epilogue warps)
@@ -457,7 +468,8 @@ tsk_apply_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kApplyStages; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
+    for (int s = 0; s < kApplyBStages; ++s) { tc::mbar_init(&bfull[s], 1); tc::mbar_init(&bempty[s], 1); }
+    for (int s = 0; s < P.tstages; ++s) { tc::mbar_init(&tfull[s], 1); tc::mbar_init(&tempty[s], 4); }
     for (int s = 0; s < kApplySlots; ++s) { tc::mbar_init(&afull[s], 4); tc::mbar_init(&aempty[s], 1); }
     tc::mbar_init(dfull, 1);
     tc::mbar_init(dempty, 4);
@@ -469,8 +481,8 @@ tsk_apply_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
     tc::tmem_alloc(tslot, kTmemCols);
     tc::tmem_relinquish();
   }
-  if (warp == 0 && lane == 0) {
-    tc::prefetch_tmap(&tmX);
+  if (warp == 0 && lane == 0) tc::prefetch_tmap(&tmX);
+  if (warp == 10 && lane == 0) {
     tc::prefetch_tmap(&tmBhi);
     tc::prefetch_tmap(&tmBlo);
   }
@@ -488,7 +500,7 @@ tsk_apply_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
   };
 
   if (warp == 0) {
-    // ------------------------------------------------------------ TMA producer
+    // ------------------------------------------------------------ TMA producer of T
     if (lane == 0) {
       uint32_t armed = 0, armed_par = 0;
       int stage = 0;
@@ -496,22 +508,40 @@ tsk_apply_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
       bool ok = true;
       for (int64_t t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
         for (int a = 0; a < P.katoms; ++a) {
-          if (!tc::mbar_wait(&empty[stage], phase ^ 1u, abortp, wc)) { ok = false; break; }
-          tc::mbar_arrive_expect_tx(&full[stage], P.stage_bytes);
+          if (!tc::mbar_wait(&tempty[stage], phase ^ 1u, abortp, wc)) { ok = false; break; }
+          tc::mbar_arrive_expect_tx(&tfull[stage], P.x_bytes);
           armed |= 1u << stage;
           armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
-          uint8_t* sb = smem + (size_t)stage * P.stage_bytes;
-#pragma unroll
-          for (int ch = 0; ch < NCH; ++ch) {
-            tc::tma_load_2d(sb + (size_t)ch * P.ch0 * 128, &tmBhi, &full[stage], a * kAtomK, ch * P.ch0);
-            tc::tma_load_2d(sb + P.b_bytes + (size_t)ch * P.ch0 * 128, &tmBlo, &full[stage], a * kAtomK,
-                            ch * P.ch0);
-          }
-          tc::tma_load_2d(sb + 2 * P.b_bytes, &tmX, &full[stage], (int)(t * 128), a * kAtomK);
-          if (++stage == kApplyStages) { stage = 0; phase ^= 1u; }
+          tc::tma_load_2d(tring + (size_t)stage * P.x_bytes, &tmX, &tfull[stage], (int)(t * 128), a * kAtomK);
+          if (++stage == P.tstages) { stage = 0; phase ^= 1u; }
         }
       }
-      if (*abortp) drain_armed(full, kApplyStages, armed, armed_par);
+      if (*abortp) drain_armed(tfull, P.tstages, armed, armed_par);
+    }
+  } else if (warp == 10) {
+    // ------------------------------------------------------------ TMA producer of B
+    if (lane == 0) {
+      uint32_t armed = 0, armed_par = 0;
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
+        for (int a = 0; a < P.katoms; ++a) {
+          if (!tc::mbar_wait(&bempty[stage], phase ^ 1u, abortp, wc)) { ok = false; break; }
+          tc::mbar_arrive_expect_tx(&bfull[stage], 2 * P.b_bytes);
+          armed |= 1u << stage;
+          armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
+          uint8_t* sb = smem + (size_t)stage * 2 * P.b_bytes;
+#pragma unroll
+          for (int ch = 0; ch < NCH; ++ch) {
+            tc::tma_load_2d(sb + (size_t)ch * P.ch0 * 128, &tmBhi, &bfull[stage], a * kAtomK, ch * P.ch0);
+            tc::tma_load_2d(sb + P.b_bytes + (size_t)ch * P.ch0 * 128, &tmBlo, &bfull[stage], a * kAtomK,
+                            ch * P.ch0);
+          }
+          if (++stage == kApplyBStages) { stage = 0; phase ^= 1u; }
+        }
+      }
+      if (*abortp) drain_armed(bfull, kApplyBStages, armed, armed_par);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
@@ -530,12 +560,12 @@ tsk_apply_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
         if (tcount > 0 && !tc::mbar_wait(dempty, (uint32_t)(tcount - 1) & 1u, abortp, wc)) { ok = false; break; }
         tc::fence_after_sync();
         for (int a = 0; a < P.katoms; ++a) {
-          if (!tc::mbar_wait(&afull[slot], sphase, abortp, wc) || !tc::mbar_wait(&full[stage], phase, abortp, wc)) {
+          if (!tc::mbar_wait(&afull[slot], sphase, abortp, wc) || !tc::mbar_wait(&bfull[stage], phase, abortp, wc)) {
             ok = false;
             break;
           }
           tc::fence_after_sync();
-          const uint32_t sb = tc::smem_u32(smem + (size_t)stage * P.stage_bytes);
+          const uint32_t sb = tc::smem_u32(smem + (size_t)stage * 2 * P.b_bytes);
           const uint32_t ahi = tbase + kApplySlotCol + (uint32_t)slot * 64u;
           const uint32_t alo = ahi + 32u;
 #pragma unroll
@@ -554,9 +584,9 @@ tsk_apply_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
               tc::mma_tf32_ts(d, alo + (uint32_t)(ks * 8), bhi, id, 1u);
             }
           }
-          tc::mma_commit(&empty[stage]);
+          tc::mma_commit(&bempty[stage]);
           tc::mma_commit(&aempty[slot]);
-          if (++stage == kApplyStages) { stage = 0; phase ^= 1u; }
+          if (++stage == kApplyBStages) { stage = 0; phase ^= 1u; }
           if (++slot == kApplySlots) { slot = 0; sphase ^= 1u; }
         }
         if (!ok) break;
@@ -570,7 +600,8 @@ tsk_apply_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
     // ------------------------------------------------------------ converter
     // thread = row r of the tile = TMEM lane r: the row's 32 values of the
     // staged atom (column c at c * 128 + r: a warp reads 32 consecutive
-    // floats per column) go to the slot as hi (the container) and lo
+    // floats per column) go to the slot as hi (the container) and lo; the
+    // T stage is released once read
     const int q = warp & 3;
     const int r = q * 32 + lane;
     const uint32_t tl = tbase + ((uint32_t)(q * 32) << 16) + kApplySlotCol;
@@ -579,12 +610,8 @@ tsk_apply_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
     bool ok = true;
     for (int64_t t = blockIdx.x; t < P.ntiles && ok; t += gridDim.x) {
       for (int a = 0; a < P.katoms; ++a) {
-        if (!__all_sync(0xffffffffu, tc::mbar_wait(&aempty[slot], sphase ^ 1u, abortp, wc) &&
-                                         tc::mbar_wait(&full[stage], phase, abortp, wc))) {
-          ok = false;
-          break;
-        }
-        const float* xs = reinterpret_cast<const float*>(smem + (size_t)stage * P.stage_bytes + 2 * P.b_bytes);
+        if (!__all_sync(0xffffffffu, tc::mbar_wait(&tfull[stage], phase, abortp, wc))) { ok = false; break; }
+        const float* xs = reinterpret_cast<const float*>(tring + (size_t)stage * P.x_bytes);
         float hi[2][16], lo[2][16];
 #pragma unroll
         for (int c = 0; c < kAtomK; ++c) {
@@ -592,6 +619,9 @@ tsk_apply_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
           hi[c >> 4][c & 15] = x;
           lo[c >> 4][c & 15] = tf32_rest(x);
         }
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&tempty[stage]);
+        if (!__all_sync(0xffffffffu, tc::mbar_wait(&aempty[slot], sphase ^ 1u, abortp, wc))) { ok = false; break; }
         tc::fence_after_sync();
         const uint32_t ts = tl + (uint32_t)slot * 64u;
         tc::tmem_st16(ts, hi[0]);
@@ -602,7 +632,7 @@ tsk_apply_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
         tc::fence_before_sync();
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&afull[slot]);
-        if (++stage == kApplyStages) { stage = 0; phase ^= 1u; }
+        if (++stage == P.tstages) { stage = 0; phase ^= 1u; }
         if (++slot == kApplySlots) { slot = 0; sphase ^= 1u; }
       }
     }
@@ -813,7 +843,7 @@ cudaError_t launch_tsk_apply(const float* X, int64_t ldx, int64_t rows, int K, c
   P.tri = tri ? 1 : 0;
   P.b_bytes = (uint32_t)(P.nch * P.ch0) * 128u;
   P.x_bytes = 128u * 128u;
-  P.stage_bytes = 2 * P.b_bytes + P.x_bytes;
+  P.stage_bytes = 2 * P.b_bytes;
   P.Y = Y;
   P.ldy = ldy;
   P.Y16 = Y16;
@@ -822,8 +852,11 @@ cudaError_t launch_tsk_apply(const float* X, int64_t ldx, int64_t rows, int K, c
   P.skip = skip;
   P.status = status;
   P.wait_cycles = tc_wait_cycles();
-  const size_t bar_bytes = 256;
-  const size_t smem = (size_t)kApplyStages * P.stage_bytes + bar_bytes + 1024;
+  const size_t bar_bytes = 512;
+  const size_t bring = (size_t)kApplyBStages * P.stage_bytes;
+  if (bring + 2 * (size_t)P.x_bytes > kSmemBudget) return cudaErrorInvalidValue;
+  P.tstages = (int)std::min<size_t>(kApplyMaxTStages, (kSmemBudget - bring) / P.x_bytes);
+  const size_t smem = bring + (size_t)P.tstages * P.x_bytes + bar_bytes + 1024;
   if (smem > 227u * 1024u) return cudaErrorInvalidValue;
   CUtensorMap mx, mh, ml;
   // T: 128 rows x 32 columns per box, unswizzled (column c of the box at c x 512 bytes)
