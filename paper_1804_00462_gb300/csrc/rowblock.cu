@@ -267,7 +267,9 @@ rb_apply_kernel(const float* __restrict__ X, int64_t ldx, int64_t rows, int K, c
   for (int v = 0; v < 8; ++v) {
     const int j = kT * jt + b_off + v;
     if (j >= N) continue;
-    if (vec) {
+    if (!Yo) {
+      // only the 16-bit copy is wanted
+    } else if (vec) {
       *reinterpret_cast<float4*>(Yo + rb + (int64_t)j * ldy) = make_float4(acc[0][v], acc[1][v], acc[2][v], acc[3][v]);
     } else {
 #pragma unroll

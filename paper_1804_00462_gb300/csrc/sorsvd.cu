@@ -389,7 +389,10 @@ int orth(const Ctx& c, void* T, int64_t rows, int64_t ld, int l, int passes, dou
   const int kind16 = out16 ? (c.dt == SORSVD_BF16 ? 1 : 2) : 0;
   if (result) *result = T;
   if (!c.f64 && result && passes == 1) {
-    float* Y = (float*)c.at(c.L.tmp);
+    // with a 16-bit copy requested, that copy is the only result the
+    // caller reads (the next product's operand): the fp32 Q is not written
+    // and *result is null
+    float* Y = out16 ? nullptr : (float*)c.at(c.L.tmp);
     int r = gram_sym(c, (const float*)T, ld, rows, l, nullptr);
     if (r) return r;
     LAUNCH(K_CHOL, launch_chol_inv((const double*)c.at(c.L.G), l, shift0, c.at(c.L.Rinv), false, c.status(), c.st));

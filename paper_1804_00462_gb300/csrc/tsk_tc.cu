@@ -647,19 +647,43 @@ tsk_apply_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
       tc::fence_after_sync();
       const int64_t grow = t * 128 + r;
       const bool rok = grow < P.rows;
+      // the 16-bit copy as pairs of rows (one 4-byte store per lane and
+      // column pair) when the tile's rows are all in range and aligned
+      const bool pack = P.kind16 && t * 128 + 128 <= P.rows && (P.ld16 & 1) == 0 &&
+                        (reinterpret_cast<uintptr_t>(P.Y16) & 3) == 0;
       for (int c = 0; c < P.NP; c += 16) {
         float v[16];
         tc::tmem_ld16(tl + (uint32_t)c, v);
         tc::tmem_ld_wait();
-        if (rok) {
+        if (rok && P.Y) {
+#pragma unroll
+          for (int u = 0; u < 16; ++u)
+            if (c + u < P.N) P.Y[grow + (int64_t)(c + u) * P.ldy] = v[u];
+        }
+        if (pack) {
+          // even lanes: rows (r, r + 1) of column j; odd lanes: rows
+          // (r - 1, r) of column j + 1
+          const int odd = lane & 1;
+#pragma unroll
+          for (int u = 0; u < 16; u += 2) {
+            const int j = c + u;
+            const float got = __shfl_xor_sync(0xffffffffu, odd ? v[u] : v[u + 1], 1);
+            const float a = odd ? got : v[u], b = odd ? v[u + 1] : got;
+            const int64_t off = (grow - odd) + (int64_t)(j + odd) * P.ld16;
+            if (j + odd < P.N) {
+              if (P.kind16 == 1) reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<bf16*>(P.Y16) + off)[0] =
+                  __floats2bfloat162_rn(a, b);
+              else reinterpret_cast<__half2*>(reinterpret_cast<f16*>(P.Y16) + off)[0] = __floats2half2_rn(a, b);
+            }
+          }
+        } else if (rok && P.kind16) {
 #pragma unroll
           for (int u = 0; u < 16; ++u) {
             const int j = c + u;
             if (j < P.N) {
-              P.Y[grow + (int64_t)j * P.ldy] = v[u];
               if (P.kind16 == 1)
                 reinterpret_cast<bf16*>(P.Y16)[grow + (int64_t)j * P.ld16] = __float2bfloat16_rn(v[u]);
-              else if (P.kind16 == 2)
+              else
                 reinterpret_cast<f16*>(P.Y16)[grow + (int64_t)j * P.ld16] = __float2half_rn(v[u]);
             }
           }
