@@ -632,6 +632,50 @@ __device__ __forceinline__ int rotate_pair16(float* cx, float* cy, int gl, unsig
   return flags;
 }
 
+// The same rotation with column x (W) and its V column u held in the
+// lanes' registers (the group keeps them through every cross round of a
+// block round); column y and its V column come from shared memory.
+template <int EP>
+__device__ __forceinline__ int rotate_xreg16(float2 (&x)[EP], float2 (&u)[EP], float* cy, int gl, unsigned gmask,
+                                             float tol2, float big2) {
+  constexpr int LDW = 32 * EP;
+  float2* wy = reinterpret_cast<float2*>(cy);
+  float2* vy = reinterpret_cast<float2*>(cy + LDW);
+  float2 y[EP], v[EP];
+  float2 al2 = make_float2(0.f, 0.f), be2 = al2, ga2 = al2;
+#pragma unroll
+  for (int e = 0; e < EP; ++e) {
+    y[e] = wy[gl + 16 * e];
+    al2 = __ffma2_rn(x[e], x[e], al2);
+    be2 = __ffma2_rn(y[e], y[e], be2);
+    ga2 = __ffma2_rn(x[e], y[e], ga2);
+  }
+  float al = al2.x + al2.y, be = be2.x + be2.y, ga = ga2.x + ga2.y;
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) {
+    al += __shfl_xor_sync(gmask, al, o);
+    be += __shfl_xor_sync(gmask, be, o);
+    ga += __shfl_xor_sync(gmask, ga, o);
+  }
+  if (!(ga * ga > tol2 * al * be)) return 0;
+  const int flags = (ga * ga > big2 * al * be) ? 3 : 1;
+  float cs, sn;
+  rotation(al, be, ga, &cs, &sn);
+  const float2 c2 = make_float2(cs, cs), s2 = make_float2(sn, sn), ns2 = make_float2(-sn, -sn);
+#pragma unroll
+  for (int e = 0; e < EP; ++e) v[e] = vy[gl + 16 * e];
+#pragma unroll
+  for (int e = 0; e < EP; ++e) {
+    const float2 xn = __ffma2_rn(c2, x[e], __fmul2_rn(ns2, y[e]));
+    wy[gl + 16 * e] = __ffma2_rn(s2, x[e], __fmul2_rn(c2, y[e]));
+    x[e] = xn;
+    const float2 un = __ffma2_rn(c2, u[e], __fmul2_rn(ns2, v[e]));
+    vy[gl + 16 * e] = __ffma2_rn(s2, u[e], __fmul2_rn(c2, v[e]));
+    u[e] = un;
+  }
+  return flags;
+}
+
 template <int EP, int C>
 __global__ void __launch_bounds__(352)
 jacobi_block_cluster_kernel(const double* __restrict__ Min, int l, int b, float* __restrict__ Vout,
@@ -705,12 +749,33 @@ jacobi_block_cluster_kernel(const double* __restrict__ Min, int l, int b, float*
           __syncthreads();
         }
       }
-      // the pairs across the two blocks
-      for (int s = 0; s < b; ++s) {
+      // the pairs across the two blocks: group grp keeps column grp of
+      // slot 0 (W and V) in registers through the b cross rounds
+      {
+        float2 xr[EP], ur[EP];
         if (grp < b) {
-          int j = grp + s;
-          if (j >= b) j -= b;
-          fl |= rotate_pair16<EP>(col(buf, 0, grp), col(buf, 1, j), gl, gmask, tol2, big2);
+          const float2* wx = reinterpret_cast<const float2*>(col(buf, 0, grp));
+#pragma unroll
+          for (int e = 0; e < EP; ++e) {
+            xr[e] = wx[gl + 16 * e];
+            ur[e] = wx[LDW / 2 + gl + 16 * e];
+          }
+        }
+        for (int s = 0; s < b; ++s) {
+          if (grp < b) {
+            int j = grp + s;
+            if (j >= b) j -= b;
+            fl |= rotate_xreg16<EP>(xr, ur, col(buf, 1, j), gl, gmask, tol2, big2);
+          }
+          __syncthreads();
+        }
+        if (grp < b) {
+          float2* wx = reinterpret_cast<float2*>(col(buf, 0, grp));
+#pragma unroll
+          for (int e = 0; e < EP; ++e) {
+            wx[gl + 16 * e] = xr[e];
+            wx[LDW / 2 + gl + 16 * e] = ur[e];
+          }
         }
         __syncthreads();
       }

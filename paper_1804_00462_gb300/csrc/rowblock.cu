@@ -312,22 +312,22 @@ __global__ void rb_copy_kernel(const float* __restrict__ src, float* __restrict_
 }
 
 // out[i + j ldo] = sum_s parts[s * stride + i + j ldp] (binary64) for an
-// rows x cols result.  kRedLanes threads per element: thread u sums the
-// partials u, u + kRedLanes, ... in index order with Neumaier's
-// compensation in fp32 (error ~ 2 eps |sum| plus second-order terms), then
-// the (sum + compensation) values are added in binary64 in a fixed xor
-// order: deterministic.  More lanes per element mean more independent
-// chains and loads in flight (the sum is latency-bound: a few MB from L2).
-// Neighbouring elements sit in neighbouring thread groups, so every partial
-// is read in runs of neighbouring addresses.
-constexpr int kRedLanes = 8;
-__global__ void reduce_parts_kernel(const float* __restrict__ parts, int nparts, int64_t stride, int rows,
-                                    int cols, int ldp, double* __restrict__ out, int ldo, int sym_split) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t e = g / kRedLanes;
-  const int u = (int)(g % kRedLanes);
+// rows x cols result.  A block takes 32 consecutive elements (column-major
+// index); warp w of its kRedWarps sums the partials w, w + kRedWarps, ... in
+// index order with Neumaier's compensation in fp32 (error ~ 2 eps |sum| plus
+// second-order terms), a lane per element, so every load of a warp is one
+// run of 32 neighbouring floats.  The warps' (sum + compensation) values are
+// then added in binary64 in warp order: deterministic.  The sum is
+// latency-bound (a few MB from L2); kRedWarps independent chains per
+// element keep the loads in flight.
+constexpr int kRedWarps = 8;
+__global__ void __launch_bounds__(32 * kRedWarps)
+reduce_parts_kernel(const float* __restrict__ parts, int nparts, int64_t stride, int rows, int cols, int ldp,
+                    double* __restrict__ out, int ldo, int sym_split) {
+  __shared__ double part[kRedWarps][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t e = (int64_t)blockIdx.x * 32 + lane;
   bool ok = e < (int64_t)rows * cols;
-  float s = 0.f, c = 0.f;
   int oi = 0, oj = 0;
   if (ok) {
     oj = (int)(e / rows);
@@ -335,22 +335,25 @@ __global__ void reduce_parts_kernel(const float* __restrict__ parts, int nparts,
     // symmetric: the lower-triangle element writes both halves
     if (sym_split >= 0 && oi < oj) ok = false;
   }
+  float s = 0.f, c = 0.f;
   if (ok) {
     int i = oi, j = oj;
     if (sym_split >= 0 && i >= sym_split && j < sym_split) { i = oj; j = oi; }
     const float* p = parts + i + (int64_t)j * ldp;
 #pragma unroll 4
-    for (int q = u; q < nparts; q += kRedLanes) {
+    for (int q = w; q < nparts; q += kRedWarps) {
       const float x = p[(int64_t)q * stride];
       const float t = __fadd_rn(s, x);
       c = __fadd_rn(c, fabsf(s) >= fabsf(x) ? __fadd_rn(__fsub_rn(s, t), x) : __fadd_rn(__fsub_rn(x, t), s));
       s = t;
     }
   }
-  double v = (double)s + (double)c;
+  part[w][lane] = (double)s + (double)c;
+  __syncthreads();
+  if (w == 0 && ok) {
+    double v = part[0][lane];
 #pragma unroll
-  for (int o = 1; o < kRedLanes; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if (ok && u == 0) {
+    for (int u = 1; u < kRedWarps; ++u) v += part[u][lane];
     out[oi + (int64_t)oj * ldo] = v;
     if (sym_split >= 0 && oi != oj) out[oj + (int64_t)oi * ldo] = v;
   }
@@ -435,11 +438,11 @@ cudaError_t launch_rb_copy(const float* src, float* dst, int64_t ld, int64_t row
 
 cudaError_t launch_reduce_parts(const float* parts, int nparts, int64_t stride, int rows, int cols, int ldp,
                                 double* out, int ldo, cudaStream_t st, int sym_split) {
-  const int64_t threads = (int64_t)rows * cols * kRedLanes;
-  if (threads <= 0) return cudaSuccess;
+  const int64_t elems = (int64_t)rows * cols;
+  if (elems <= 0) return cudaSuccess;
   if (sym_split >= 0 && rows != cols) return cudaErrorInvalidValue;
-  reduce_parts_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(parts, nparts, stride, rows, cols, ldp, out,
-                                                                     ldo, sym_split);
+  reduce_parts_kernel<<<(unsigned)((elems + 31) / 32), 32 * kRedWarps, 0, st>>>(parts, nparts, stride, rows, cols,
+                                                                             ldp, out, ldo, sym_split);
   return cudaGetLastError();
 }
 
