@@ -669,10 +669,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 //   barriers: the stage barriers (full, bfull) and the accumulator-drained
 //   barrier (tempty, 2 x 128 epilogue threads) of the even CTA count both
 //   CTAs' copies and drains; each CTA has its own empty, bempty and tfull,
-//   which the even CTA's MMA thread signals by commits addressed to each
-//   CTA (no multicast).  Both CTAs walk the same stream-K range; the odd
-//   CTA writes rows 128..255 of every tile.  Every wait is bounded; both
-//   CTAs meet at a cluster barrier before the tensor memory is freed.
+//   which the even CTA's MMA thread signals by one commit per barrier,
+//   addressed to that CTA.  Both CTAs walk the same stream-K range; the
+//   odd CTA writes rows 128..255 of every tile.  Every wait is bounded;
+//   both CTAs meet at a cluster barrier before the tensor memory is freed.
 template <int ELT, bool A_MN, int NCH, int KA>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
 tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcParams P) {
