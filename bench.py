@@ -592,6 +592,11 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.gpus != world and rank == 0:
+        # one rank per GPU: --gpus N is launched by torchrun with N ranks;
+        # the line reports the ranks that actually ran
+        print(f"bench.py: --gpus {args.gpus} but {world} rank(s) running; n_gpus reports {world}",
+              file=sys.stderr, flush=True)
     w = dict(WORKLOADS[args.workload])
     if args.shrink > 1 and "m" in w and args.workload not in ("cfg4", "cfg5"):
         w["m"] //= args.shrink
