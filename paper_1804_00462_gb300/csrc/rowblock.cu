@@ -300,6 +300,7 @@ size_t apply_smem(int K, int N, bool tri, int jt_max) {
 __global__ void rb_copy_kernel(const float* __restrict__ src, float* __restrict__ dst, int64_t ld, int64_t rows,
                                int l, void* __restrict__ Y16, int64_t ld16, int kind16, const int* __restrict__ skip) {
   const bool skipped = skip && *skip;
+  if (skipped && !kind16) return;
   const float* from = skipped ? dst : src;
   const int64_t total = rows * l;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {

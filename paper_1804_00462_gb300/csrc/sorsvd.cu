@@ -421,13 +421,17 @@ int orth(const Ctx& c, void* T, int64_t rows, int64_t ld, int l, int passes, dou
       LAUNCH(K_CHOL, launch_chol_inv((const double*)c.at(c.L.G), l, p == 0 ? shift0 : 0.0, c.at(c.L.Rinv), false,
                                      c.status(), c.st, skip, p == 1 ? conv : nullptr, kOrthTol,
                                      polar ? pol_ok : nullptr));
-      r = apply(c, X, ld, rows, l, (const float*)c.at(c.L.Rinv), l, l, !polar, Y, ld, nullptr, 0, 0, skip);
+      // the 16-bit copy comes from the last pass that runs: the last pass,
+      // and the second of three (the third may be skipped on the device)
+      void* o16 = (p == passes - 1 || (passes == 3 && p == 1)) ? out16 : nullptr;
+      r = apply(c, X, ld, rows, l, (const float*)c.at(c.L.Rinv), l, l, !polar, Y, ld, o16, ld16, o16 ? kind16 : 0,
+                skip);
       if (r) return r;
       std::swap(X, Y);
     }
-    if (X != (float*)T || kind16)
-      LAUNCH(K_MISC, launch_rb_copy(X, (float*)T, ld, rows, l, out16, ld16, kind16,
-                                    (passes == 3 && X != (float*)T) ? conv : nullptr, c.st));
+    // the fp32 result back into T (not when a skipped third pass left it there)
+    if (X != (float*)T)
+      LAUNCH(K_MISC, launch_rb_copy(X, (float*)T, ld, rows, l, nullptr, 0, 0, passes == 3 ? conv : nullptr, c.st));
     return SORSVD_OK;
   }
   // binary64: the same device-side skip of the third pass as above (the
