@@ -1313,10 +1313,12 @@ size_t tc_parts_bytes(int elt, int64_t M, int64_t N, int64_t K) {
   return std::max(bp, bs);
 }
 
-cudaError_t launch_tc_gemm(bool trans_a, int elt, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
-                           const void* B, int64_t ldb, const void* Blo, float* out, int64_t ldo, void* out16,
-                           int64_t ld16, int out16_kind, float* parts, int* tilecnt, int64_t ntilecnt,
-                           DeviceStatus* status, int kcls, cudaStream_t st) {
+namespace {
+
+cudaError_t launch_tc_gemm_impl(bool trans_a, int elt, int64_t M, int64_t N, int64_t K, const void* A,
+                                int64_t lda, const void* B, int64_t ldb, const void* Blo, float* out, int64_t ldo,
+                                void* out16, int64_t ld16, int out16_kind, float* parts, int* tilecnt,
+                                int64_t ntilecnt, DeviceStatus* status, int kcls, cudaStream_t st, bool allow_pair) {
   if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
   if (elt == 3 && (!Blo || (reinterpret_cast<uintptr_t>(Blo) & 15))) return cudaErrorInvalidValue;
   // an MN-major TF32 operand gave all-zero products on GB300: fp32 products
@@ -1325,7 +1327,8 @@ cudaError_t launch_tc_gemm(bool trans_a, int elt, int64_t M, int64_t N, int64_t 
   TcParams P = tc_plan(elt, M, N, K);
   // pair mode needs the per-tile counters (two per 256-row tile) and the
   // default wait limit
-  if (P.pair && (!tilecnt || 2 * P.tiles > ntilecnt || (g_wait_cycles > 0 && g_wait_cycles < tc::kWaitCycles)))
+  if (P.pair && (!allow_pair || !tilecnt || 2 * P.tiles > ntilecnt ||
+                 (g_wait_cycles > 0 && g_wait_cycles < tc::kWaitCycles)))
     P = tc_plan_single(elt, M, N, K);
   if (P.stages < 2) return cudaErrorInvalidValue;
   P.out = out; P.ldo = ldo; P.out16 = out16; P.ld16 = ld16; P.out16_kind = out16 ? out16_kind : 0;
@@ -1369,6 +1372,22 @@ cudaError_t launch_tc_gemm(bool trans_a, int elt, int64_t M, int64_t N, int64_t 
   ProfScope ps2(K_REDUCE, st);
   tc_fixup_kernel<<<dim3((unsigned)(P.G - 1), (unsigned)gy), 256, 0, st>>>(P);
   return cudaGetLastError();
+}
+
+}  // namespace
+
+// A pass on CTA pairs whose launch is refused (no room for a two-CTA
+// cluster, for instance) runs on single CTAs instead.
+cudaError_t launch_tc_gemm(bool trans_a, int elt, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
+                           const void* B, int64_t ldb, const void* Blo, float* out, int64_t ldo, void* out16,
+                           int64_t ld16, int out16_kind, float* parts, int* tilecnt, int64_t ntilecnt,
+                           DeviceStatus* status, int kcls, cudaStream_t st) {
+  const cudaError_t e = launch_tc_gemm_impl(trans_a, elt, M, N, K, A, lda, B, ldb, Blo, out, ldo, out16, ld16,
+                                            out16_kind, parts, tilecnt, ntilecnt, status, kcls, st, true);
+  if (e == cudaSuccess || !pair_wanted(elt, N)) return e;
+  cudaGetLastError();                        // clear the launch error (not a sticky one)
+  return launch_tc_gemm_impl(trans_a, elt, M, N, K, A, lda, B, ldb, Blo, out, ldo, out16, ld16, out16_kind, parts,
+                             tilecnt, ntilecnt, status, kcls, st, false);
 }
 
 void set_tc_wait_cycles(long long cycles) { g_wait_cycles = cycles > 0 ? cycles : 0; }
