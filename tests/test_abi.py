@@ -204,3 +204,83 @@ def test_batched_rejects_bad_arguments_before_any_device_work():
     assert create(good, 2, ws=256, wsb=need - 1) == 7
     assert lib.sorsvd_batched_plan_launch(None, None) == 1
     lib.sorsvd_batched_plan_destroy(None)
+
+
+def test_streamed_sizes_and_rejects_bad_arguments_before_any_device_work():
+    lib = _lib()
+    sz = lib.sorsvd_streamed_workspace_size
+    sz.argtypes = [C.c_int64, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_int64]
+    sz.restype = C.c_size_t
+    ws = lib.sorsvd_workspace_size
+    ws.argtypes = [C.c_int64, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_uint]
+    ws.restype = C.c_size_t
+    m, n, k, p = 200000, 4096, 100, 10
+    for dt, esz in ((1, 4), (3, 2), (0, 8)):
+        small, big = sz(m, n, k, p, dt, 8192), sz(m, n, k, p, dt, 65536)
+        # two device blocks of rows of A (ld rounded to 16) on top of the sketches
+        assert small > 0 and big > small and big - small >= 2 * (65536 - 8192) * n * esz
+        assert small % 256 == 0 and big % 256 == 0
+    # a block as large as A: no smaller than the in-core workspace without its copy of A^T
+    assert sz(20000, 10000, 100, 10, 3, 20000) >= ws(20000, 10000, 100, 10, 3, 0)
+    assert sz(m, n, 0, p, 1, 8192) == 0                # k < 1
+    assert sz(m, n, k, p, 1, 0) == 0                   # no rows per block
+    assert sz(100, 50, 45, 10, 1, 16) == 0             # l > min(m, n)
+    assert sz(m, n, k, p, 9, 8192) == 0                # unknown dtype
+    f = lib.sorsvd_run_streamed
+    f.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_int,
+                  C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_size_t,
+                  C.c_void_p]
+    fake = 0x1000
+    ok = dict(A=fake, m=1000, n=800, lda=1000, k=20, p=5, q=1, seed=0, dt=1, br=256, U=fake, ldu=1000, S=fake,
+              V=fake, ldv=800, ws=None, wsb=0, st=None)
+
+    def call(**kw):
+        a = dict(ok, **kw)
+        return f(a["A"], a["m"], a["n"], a["lda"], a["k"], a["p"], a["q"], a["seed"], a["dt"], a["br"], a["U"],
+                 a["ldu"], a["S"], a["V"], a["ldv"], a["ws"], a["wsb"], a["st"])
+    assert call(A=None) == 1
+    assert call(V=None) == 1
+    assert call(lda=999) == 1
+    assert call(ldv=799) == 1
+    assert call(br=0) == 1
+    assert call(k=800, p=1) == 1                       # l > min(m, n)
+    assert call(k=400, p=0) == 8                       # l beyond the fp32 limit
+    assert call(dt=7) == 2
+    assert call() == 7                                 # no workspace
+    need = sz(1000, 800, 20, 5, 1, 256)
+    assert call(ws=0x100000, wsb=need - 256) == 7      # too small
+    assert call(ws=0x100010, wsb=need) == 7            # misaligned
+
+
+def test_products_size_and_reject_bad_arguments_before_any_device_work():
+    lib = _lib()
+    sz = lib.sorsvd_products_workspace_size
+    sz.argtypes = [C.c_int64, C.c_int]
+    sz.restype = C.c_size_t
+    # the operands are the caller's: the workspace holds per-CTA partials and
+    # l x l matrices, so it grows with l, not with the rows past one wave
+    assert sz(65536, 266) >= sz(64, 266) > 0
+    assert sz(4096, 266) > sz(4096, 32) > 0
+    assert sz(4096, 266) % 256 == 0
+    assert sz(0, 10) == 0 and sz(100, 0) == 0 and sz(1000, 321) == 0
+    g = lib.sorsvd_gram
+    g.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int64, C.c_int, C.c_void_p, C.c_int64,
+                  C.c_void_p, C.c_size_t, C.c_void_p]
+    x = 0x1000
+    assert g(None, 64, None, 0, 64, 8, x, 8, x, 1 << 20, None) == 1
+    assert g(x, 63, None, 0, 64, 8, x, 8, x, 1 << 20, None) == 1      # ldx < rows
+    assert g(x, 66, None, 0, 64, 8, x, 8, x, 1 << 20, None) == 1      # ldx not a multiple of 4
+    assert g(x + 4, 64, None, 0, 64, 8, x, 8, x, 1 << 20, None) == 1  # X not 16-byte aligned
+    assert g(x, 64, x + 8, 64, 64, 8, x, 8, x, 1 << 20, None) == 1    # Y not 16-byte aligned
+    assert g(x, 64, None, 0, 64, 8, x, 7, x, 1 << 20, None) == 1      # ldg < l
+    assert g(x, 400, None, 0, 400, 321, x, 321, x, 1 << 30, None) == 8  # beyond SORSVD_MAX_L
+    assert g(x, 64, None, 0, 64, 8, x, 8, x, 16, None) == 7           # workspace too small
+    a = lib.sorsvd_apply
+    a.argtypes = [C.c_void_p, C.c_int64, C.c_int, C.c_int64, C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_void_p,
+                  C.c_int64, C.c_void_p, C.c_size_t, C.c_void_p]
+    assert a(x, 64, 8, 64, None, 8, 8, 0, x, 64, x, 1 << 20, None) == 1    # no B
+    assert a(x, 64, 8, 64, x, 7, 8, 0, x, 64, x, 1 << 20, None) == 1       # ldb < K
+    assert a(x, 64, 8, 64, x, 8, 8, 0, x, 63, x, 1 << 20, None) == 1       # ldy < rows
+    assert a(x, 64, 8, 66, x, 8, 8, 0, x, 64, x, 1 << 20, None) == 1       # ldx not a multiple of 4
+    assert a(x, 64, 8, 64, x, 8, 321, 0, x, 64, x, 1 << 30, None) == 8     # N beyond SORSVD_MAX_L
+    assert a(x, 64, 8, 64, x, 8, 8, 0, x, 64, x + 8, 1 << 20, None) == 7   # workspace misaligned
