@@ -284,3 +284,38 @@ def test_products_size_and_reject_bad_arguments_before_any_device_work():
     assert a(x, 64, 8, 66, x, 8, 8, 0, x, 64, x, 1 << 20, None) == 1       # ldx not a multiple of 4
     assert a(x, 64, 8, 64, x, 8, 321, 0, x, 64, x, 1 << 30, None) == 8     # N beyond SORSVD_MAX_L
     assert a(x, 64, 8, 64, x, 8, 8, 0, x, 64, x + 8, 1 << 20, None) == 7   # workspace misaligned
+
+
+def test_stage_entry_points_reject_bad_arguments_before_any_device_work():
+    lib = _lib()
+    x = 0x1000
+    gs = lib.sorsvd_gaussian
+    gs.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_uint64, C.c_uint64, C.c_int, C.c_void_p]
+    assert gs(None, 10, 3, 10, 0, 0, 1, None) == 1
+    assert gs(x, 10, 3, 9, 0, 0, 1, None) == 1                    # ld < rows
+    assert gs(x, -1, 3, 10, 0, 0, 1, None) == 1
+    assert gs(x, 10, 3, 10, 0, 0, 9, None) == 2                   # unknown dtype
+    ch = lib.sorsvd_chol_inv
+    ch.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+    assert ch(None, 10, 0.0, 1, x, x, None) == 1
+    assert ch(x, 0, 0.0, 1, x, x, None) == 1
+    assert ch(x, 10, -1.0, 1, x, x, None) == 1                    # negative shift
+    assert ch(x, 10, float("nan"), 1, x, x, None) == 1
+    assert ch(x, 225, 0.0, 0, x, x, None) == 8                    # beyond SORSVD_MAX_L_F64
+    assert ch(x, 10, 0.0, 9, x, x, None) == 2
+    pp = lib.sorsvd_power_pass
+    pp.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int, C.c_void_p, C.c_int64, C.c_int,
+                   C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_size_t, C.c_void_p]
+    assert pp(None, 100, 80, 100, 1, x, 80, 10, x, 100, x, 80, x, 1 << 20, None) == 1
+    assert pp(x, 100, 80, 99, 1, x, 80, 10, x, 100, x, 80, x, 1 << 20, None) == 1    # lda < m
+    assert pp(x, 100, 80, 100, 1, x, 79, 10, x, 100, x, 80, x, 1 << 20, None) == 1   # ldx < n
+    assert pp(x, 100, 80, 100, 1, x, 80, 81, x, 100, x, 80, x, 1 << 20, None) == 8   # l > min(m, n)
+    assert pp(x, 100, 80, 100, 1, x, 80, 10, x, 100, x, 80, None, 0, None) == 7      # no workspace
+    assert pp(x, 100, 80, 100, 9, x, 80, 10, x, 100, x, 80, x, 1 << 20, None) == 2
+    co = lib.sorsvd_core
+    co.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int, C.c_uint, C.c_void_p, C.c_int64,
+                   C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_size_t, C.c_void_p]
+    assert co(x, 100, 80, 100, 1, 0, None, 100, x, 80, 10, x, 10, x, 1 << 20, None) == 1
+    assert co(x, 100, 80, 100, 1, 0, x, 100, x, 80, 10, x, 9, x, 1 << 20, None) == 1    # ldm < l
+    assert co(x, 100, 80, 100, 1, 0x40, x, 100, x, 80, 10, x, 10, x, 1 << 20, None) == 1  # flag not of the core
+    assert co(x, 100, 80, 100, 1, 0, x, 100, x, 80, 10, x, 10, None, 0, None) == 7      # no workspace
